@@ -1,0 +1,208 @@
+/*
+ * sft.h -- C ABI of the GB300 stochastic-field stepper.
+ *
+ * The library advances R independent replicas of a real or complex field on a
+ * periodic d-dimensional lattice (d = 1, 2, 3) by the pseudo-spectral
+ * stochastic exponential-time-differencing (SETD) schemes of Johnsrud & Rana,
+ * "Efficient Pseudo-spectral Algorithms for Statistical Field Theories"
+ * (arXiv 2511.22510).  In Fourier space every mode obeys (Sec. IV, eq.
+ * general_fourier)
+ *
+ *     d phi_a / dt = c_a phi_a + F_a[phi] + sqrt(2 D_a) eta_a(t),
+ *
+ * with a diagonal linear operator c_a, a nonlinearity F evaluated in real
+ * space and dealiased (2/3 truncation), and additive noise.  One step is the
+ * boxed algorithm of Sec. IV: inverse transform of the masked state, the
+ * real-space nonlinearity, forward transform, and the diagonal update
+ *
+ *     phi_a <- f1_a phi_a + A_a F_a + B_a F_a(t-h) + g_a eta_a
+ *
+ * with the coefficients of SETD-EM (Sec. II, Eq. SETD-EM), SETD1 (Eq. SETD1)
+ * or SETD2 (Eq. SETD2), and Philox4x32-10 Gaussian noise drawn directly in
+ * Fourier space with the Hermitian structure of App. B.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an sft_status; nothing aborts and no C++
+ *    exception crosses the ABI.  sft_last_error() gives a message.
+ *  - Lattice axis 0 is x, the fastest-varying real-space axis.  A real-space
+ *    field of one replica is a row-major array [n2][n1][n0] (x fastest) of
+ *    float (real fields) or interleaved float pairs (complex fields); R
+ *    replicas are stored one after another.
+ *  - The state lives on the device in Fourier space.  Its internal layout is
+ *    "x-major": mode (a_x, a_z, a_y) of replica r sits at
+ *        ((r * HX + a_x) * n2 + a_z) * n1 + a_y
+ *    with HX = n0/2 + 1 stored x-modes for real fields (Hermitian half) and
+ *    HX = n0 for complex fields; indices are the unsigned FFT indices
+ *    0 .. n-1.  sft_get_spectrum returns exactly this layout.
+ *  - The caller owns every host and device buffer it passes; the library
+ *    copies what it needs and retains no caller pointer after returning.
+ *  - A context owns all of its device memory and is not thread-safe.
+ *  - Work is enqueued on cfg.stream (NULL = the legacy default stream).
+ *    sft_step returns after enqueueing; calls that return data to the host
+ *    synchronise the stream first and then report any device-side status.
+ */
+#ifndef SFT_H
+#define SFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sft_ctx sft_ctx;
+
+typedef enum {
+    SFT_OK = 0,
+    SFT_EINVAL = 1,        /* invalid argument or configuration */
+    SFT_ENOMEM = 2,        /* device or host allocation failed */
+    SFT_ECUDA = 3,         /* a CUDA runtime call failed */
+    SFT_ENONFINITE = 4,    /* a non-finite value appeared in the state */
+    SFT_ETIMEOUT = 5,      /* a bounded device-side wait expired */
+    SFT_EUNSUPPORTED = 6,  /* valid request that this build does not implement */
+    SFT_ECHECKPOINT = 7    /* checkpoint buffer malformed or for another config */
+} sft_status;
+
+/* Built-in models (Sec. V).  Parameters p[] per model:
+ *   SFT_MODEL_A: p = {Gamma, r, u, T}:  c = -Gamma (r + k^2), D_a = Gamma T,
+ *                F = -Gamma u DFT[psi^3]                        (Sec. V.A, Delta = 0)
+ *   SFT_MODEL_B: p = {Gamma, r, u, T}:  c = -Gamma k^2 (r + k^2), D_a = Gamma T k^2,
+ *                F = -Gamma u k^2 DFT[psi^3]                    (Sec. V.A, Delta = 2)
+ *   SFT_KPZ:     p = {nu, lambda, D}:   c = -nu k^2, D_a = D,
+ *                F = (lambda/2) DFT[|grad h|^2]                 (Sec. V.B, noise sqrt(2D) eta)
+ *   SFT_CGL:     p = {alpha, beta, eps}: complex field, c = 1 - (1 + i alpha) k^2,
+ *                D_a = eps, F = -(1 + i beta) DFT[|A|^2 A]       (Sec. V.C with b = alpha,
+ *                c = beta, D = eps)
+ * psi, grad h and A are the inverse transforms of the dealiased state. */
+typedef enum { SFT_MODEL_A = 0, SFT_MODEL_B = 1, SFT_KPZ = 2, SFT_CGL = 3 } sft_model;
+
+/* Schemes of Sec. II: SETD-EM (Eq. SETD-EM), SETD1 (Eq. SETD1), SETD2 (Eq. SETD2). */
+typedef enum { SFT_SETD_EM = 0, SFT_SETD1 = 1, SFT_SETD2 = 2 } sft_scheme;
+
+typedef struct {
+    int d;             /* 1, 2 or 3 */
+    int n[3];          /* points per axis (x first); powers of two, all equal (isotropic) */
+    double dx[3];      /* lattice spacing per axis; all equal */
+    int replicas;      /* R >= 1 independent noise realisations */
+    sft_model model;
+    double p[8];       /* model parameters, see sft_model */
+    sft_scheme scheme;
+    double h;          /* time step, > 0 */
+    uint64_t seed;     /* Philox key */
+    int dealias;       /* 1: 2/3-rule truncation (3|a_i| < n_i), 0: none */
+    int precision;     /* 0: FP32 state and transforms (only value supported) */
+    void* stream;      /* cudaStream_t, or NULL for the default stream */
+} sft_config;
+
+/* Observables for sft_observe (App. C; shells j = ceil(|a|), i.e. the shell
+ * (k_j - dk, k_j] with dk = 2 pi / L). */
+typedef enum {
+    SFT_OBS_SK = 0,          /* C_ET shell average (L/N^2)^d <|phi_a|^2>, replica-averaged:
+                                writes nshells values, then nshells mode counts N_k if cap allows */
+    SFT_OBS_SK_REPLICAS = 1, /* same per replica: R * nshells values */
+    SFT_OBS_MARK = 2,        /* store phi(t0) for SFT_OBS_CKT; writes nothing */
+    SFT_OBS_CKT = 3,         /* two-time shell average (L/N^2)^d Re<phi_a(t) conj(phi_a(t0))> */
+    SFT_OBS_ROUGHNESS = 4,   /* per replica w^2 = N^{-2d} sum_{a != 0} |phi_a|^2 (Sec. V.B, box = L) */
+    SFT_OBS_RESPONSE = 5,    /* per shell sum Re(dphi_a(t) conj(dphi_a(t0))) / sum |dphi_a(t0)|^2 over
+                                replicas, dphi the tangent seeded at t0 by sft_tangent_step */
+    SFT_OBS_NSHELLS = 6      /* writes one value: the number of shells */
+} sft_observable;
+
+/* Create a context (allocates all device memory, builds the FP64 coefficient
+ * tables of Sec. II on the device, zero state).  *out receives the context or
+ * NULL on failure.  Errors: SFT_EINVAL (bad config), SFT_EUNSUPPORTED
+ * (anisotropic lattice, sizes outside this build's transform plans),
+ * SFT_ENOMEM, SFT_ECUDA. */
+sft_status sft_create(const sft_config* cfg, sft_ctx** out);
+
+/* Create one context that advances several configurations together (uneven
+ * lattice sizes, same model family and scheme): each sft_step of the batch
+ * context advances every member by one step inside one CUDA-graph launch.
+ * Replica r of the batch is member m's replica r - offset(m).  Members must
+ * share d <= 1 for the fused one-kernel path; otherwise SFT_EUNSUPPORTED. */
+sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out);
+
+/* Copy a host real-space field of ONE replica (bytes = n0*n1*n2*sizeof(float),
+ * doubled for complex fields) into the state (forward transform, Hermitian
+ * fix-up of App. B).  replica = -1 writes all replicas from R consecutive
+ * fields.  Resets the SETD2 history.  Errors: SFT_EINVAL on size mismatch. */
+sft_status sft_set_field(sft_ctx* ctx, int replica, const void* host_real_space, size_t bytes);
+
+/* Initial condition drawn on the device: iid N(0, sigma^2) per site (complex:
+ * sigma (N(0,1) + i N(0,1))), Philox counter (site/4 | site/2, 0, replica, 1). */
+sft_status sft_init_random(sft_ctx* ctx, double sigma);
+
+/* Inverse transform of one replica's state into a host buffer (replica = -1:
+ * all replicas).  Synchronises the stream. */
+sft_status sft_get_field(sft_ctx* ctx, int replica, void* host_out, size_t bytes);
+
+/* Copy the device spectrum of all replicas (internal x-major layout, complex
+ * float pairs) to a host buffer of bytes = R * HX * n1 * n2 * 8. */
+sft_status sft_get_spectrum(sft_ctx* ctx, void* host_out, size_t bytes);
+sft_status sft_set_spectrum(sft_ctx* ctx, const void* host_in, size_t bytes);
+
+/* Advance every replica by nsteps SETD steps (Sec. IV boxed algorithm).
+ * Enqueued on the context stream as CUDA-graph replays; returns without
+ * waiting.  A non-finite state is reported by the next synchronising call
+ * (sft_sync, sft_observe, sft_get_field) as SFT_ENONFINITE. */
+sft_status sft_step(sft_ctx* ctx, int64_t nsteps);
+
+/* Advance with the SAME kernels launched one by one from the host (no graph),
+ * the plain unbatched form used for timing comparisons. */
+sft_status sft_step_plain(sft_ctx* ctx, int64_t nsteps);
+
+/* Wait for the context stream and report the device status word. */
+sft_status sft_sync(sft_ctx* ctx);
+
+/* Evaluate an observable (sft_observable) into host_out (cap doubles);
+ * *written receives the number of doubles written.  Synchronises. */
+sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, size_t* written);
+
+/* Linear response by forward-mode differentiation of the step (tangent map),
+ * advanced together with the primal on the same noise path:
+ *   dphi <- f1 dphi + A dF + B dF(t-h),  dF = M s DFT[q'(psi) IDFT(M dphi)].
+ * dphi0_dev: DEVICE pointer to R real-space fields (layout as set_field) that
+ * seed the tangent, or NULL to continue the current tangent.  dphi_out_dev:
+ * DEVICE pointer receiving the R real-space tangent fields after nsteps, or
+ * NULL.  Advances the primal by nsteps.  Real fields, SETD-EM or SETD1. */
+sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps, void* dphi_out_dev);
+
+/* Reverse-mode differentiation: given a cotangent lambda on the real-space
+ * fields after nsteps (DEVICE pointer, R fields), writes into grad_out_dev
+ * (DEVICE, R fields) the gradient of sum_x lambda(x) phi_{t+n}(x) with respect
+ * to phi_t(x), the real-space state at the call.  The primal is advanced by
+ * nsteps; the backward sweep recomputes it from device checkpoints taken every
+ * `segment` steps (sft_set_checkpoint_interval, default 100), regenerating the
+ * noise from its Philox counters.  Real fields, SETD-EM or SETD1. */
+sft_status sft_adjoint(sft_ctx* ctx, const void* cotangent_dev, int64_t nsteps, void* grad_out_dev);
+sft_status sft_set_checkpoint_interval(sft_ctx* ctx, int segment);
+
+/* Serialise the full state (spectrum, SETD2 history, step counter, seed and a
+ * configuration hash) into a host buffer.  With host_buf = NULL only *written
+ * (the required size) is set.  sft_restore accepts only a buffer written for
+ * an identical configuration (SFT_ECHECKPOINT otherwise); resuming is
+ * bit-identical to an uninterrupted run because the noise is a pure function
+ * of (seed, step, replica, mode). */
+sft_status sft_checkpoint(sft_ctx* ctx, void* host_buf, size_t cap, size_t* written);
+sft_status sft_restore(sft_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Diagnostics: the unit-variance Fourier noise eta_a (App. B structure) that
+ * step `step` draws for every stored mode of every replica, written to a host
+ * buffer in the spectrum layout (bytes = R * HX * n1 * n2 * 8).  The update
+ * multiplies it by the amplitude g_a.  Synchronises. */
+sft_status sft_draw_noise(sft_ctx* ctx, int64_t step, void* host_out, size_t bytes);
+
+/* Current step counter (steps taken since creation or restore). */
+sft_status sft_get_step(const sft_ctx* ctx, int64_t* step);
+
+/* Number of kernel launches the context issues per step (for accounting). */
+sft_status sft_launches_per_step(const sft_ctx* ctx, int* launches);
+
+const char* sft_last_error(const sft_ctx* ctx);
+void sft_destroy(sft_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFT_H */

@@ -1,0 +1,778 @@
+// sft_api.cu -- host runtime behind the C ABI of include/sft.h: context and
+// buffer management, the per-step launch sequence, CUDA-graph chunks of steps,
+// observables, checkpoints and error reporting.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sft.h"
+#include "sft_internal.h"
+
+using namespace sft;
+
+namespace {
+
+constexpr int kGraphChunk = 16;  // steps per captured graph
+
+struct Twiddles {
+    std::vector<int> lens;
+    std::vector<size_t> offs;
+    float2* dev = nullptr;
+    const float2* get(int L) const {
+        for (size_t i = 0; i < lens.size(); ++i)
+            if (lens[i] == L) return dev + offs[i];
+        return nullptr;
+    }
+};
+
+}  // namespace
+
+struct sft_ctx {
+    sft_config cfg{};
+    int d = 0, nx = 1, ny = 1, nz = 1;
+    int cplx = 0, nl = NL_CUBIC;
+    int hx = 0, mx = 0;
+    long long sites = 0, nmodes = 0;
+    int R = 0;
+    int rep0 = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // device buffers
+    float2 *phi = nullptr, *fprev = nullptr, *P = nullptr, *Q = nullptr, *Py = nullptr, *snap = nullptr;
+    float* real = nullptr;
+    float2* cfield = nullptr;
+    float4* tab = nullptr;
+    long long* dstep = nullptr;   // [0] step base, [1] SETD2 first step, [2] bad step
+    unsigned* dstatus = nullptr;
+    double* dshell = nullptr;
+    double* drough = nullptr;
+    Twiddles tw;
+    // tangent
+    float2 *dphi = nullptr, *dseed = nullptr;
+    // host mirrors
+    long long step = 0;
+    long long first_step = -1;
+    bool p_valid = false;
+    int nshells = 0;
+    std::vector<double> counts;
+    cudaGraphExec_t graph = nullptr;
+    bool warmed = false;
+    int launches_per_step = 0;
+    int ckpt_segment = 100;
+    std::string err;
+};
+
+static sft_status fail(sft_ctx* c, sft_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                              \
+    do {                                                                                                      \
+        cudaError_t e_ = (call);                                                                              \
+        if (e_ != cudaSuccess)                                                                                \
+            return fail(ctx, SFT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+static long long isqrt_ceil(long long q) {
+    long long j = (long long)std::floor(std::sqrt((double)q));
+    while (j * j < q) ++j;
+    while (j > 0 && (j - 1) * (j - 1) >= q) --j;
+    return j;
+}
+
+static StepArgs base_args(const sft_ctx* c) {
+    StepArgs a{};
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.nz = c->nz;
+    a.hx = c->hx;
+    a.ncols = c->mx;
+    a.R = c->R;
+    a.rep0 = c->rep0;
+    a.scale = (float)(1.0 / (double)c->sites);
+    a.dk = (float)(2.0 * M_PI / (c->nx * c->cfg.dx[0]));
+    a.dealias = c->cfg.dealias;
+    a.model = c->cfg.model;
+    a.scheme = c->cfg.scheme;
+    const double* p = c->cfg.p;
+    switch (c->cfg.model) {
+        case SFT_MODEL_A:
+        case SFT_MODEL_B: a.s0 = (float)(-p[0] * p[2]); a.s0i = 0.f; break;
+        case SFT_KPZ: a.s0 = (float)(0.5 * p[1]); a.s0i = 0.f; break;
+        default: a.s0 = -1.f; a.s0i = (float)(-p[1]); break;
+    }
+    a.seed = c->cfg.seed;
+    a.tab = c->tab;
+    a.phi = c->phi;
+    a.fprev = c->fprev;
+    a.step_base = c->dstep;
+    a.first_step = c->dstep + 1;
+    a.status = c->dstatus;
+    a.bad_step = c->dstep + 2;
+    return a;
+}
+
+// ------------------------------------------------------------ transforms
+// state <- forward transform of the real-space buffer (c->real / c->cfield),
+// for R replicas starting at replica r0.
+static sft_status forward_from_buffer(sft_ctx* ctx, int r0, int R) {
+    StepArgs a = base_args(ctx);
+    a.R = R;
+    a.phi = ctx->phi + (size_t)r0 * ctx->nmodes;
+    a.real_io = ctx->real + (size_t)r0 * ctx->sites;
+    a.cplx_io = ctx->cfield ? ctx->cfield + (size_t)r0 * ctx->sites : nullptr;
+    if (ctx->d == 1) {
+        if (ctx->cplx) {
+            a.tw_a = ctx->tw.get(ctx->nx);
+        } else {
+            a.tw_a = ctx->tw.get(ctx->nx / 2);
+            a.tw_b = ctx->tw.get(ctx->nx);
+        }
+        CK(launch_k1_line(a, MODE_FWD, ctx->nl, ctx->stream));
+    } else {
+        a.ncols = ctx->hx;
+        a.qout = ctx->Q + (size_t)r0 * ctx->nmodes;
+        a.tw_a = ctx->tw.get(ctx->nx / 2);
+        a.tw_b = ctx->tw.get(ctx->nx);
+        CK(launch_k2_rows(a, MODE_FWD, ctx->nl, ctx->stream));
+        a.qin = a.qout;
+        a.tw_a = ctx->tw.get(ctx->ny);
+        CK(launch_k2_cols(a, MODE_FWD, ctx->nl, ctx->stream));
+    }
+    ctx->p_valid = false;
+    return SFT_OK;
+}
+
+// real-space buffer <- inverse transform of the state (Q used as scratch).
+static sft_status inverse_to_buffer(sft_ctx* ctx, const float2* src, int r0, int R) {
+    StepArgs a = base_args(ctx);
+    a.R = R;
+    a.phi = const_cast<float2*>(src) + (size_t)r0 * ctx->nmodes;
+    a.real_io = ctx->real + (size_t)r0 * ctx->sites;
+    a.cplx_io = ctx->cfield ? ctx->cfield + (size_t)r0 * ctx->sites : nullptr;
+    if (ctx->d == 1) {
+        if (ctx->cplx) {
+            a.tw_a = ctx->tw.get(ctx->nx);
+        } else {
+            a.tw_a = ctx->tw.get(ctx->nx / 2);
+            a.tw_b = ctx->tw.get(ctx->nx);
+        }
+        CK(launch_k1_line(a, MODE_INV, ctx->nl, ctx->stream));
+    } else {
+        a.ncols = ctx->hx;
+        a.pout = ctx->Q + (size_t)r0 * ctx->nmodes;
+        a.tw_a = ctx->tw.get(ctx->ny);
+        CK(launch_k2_cols(a, MODE_INV, ctx->nl, ctx->stream));
+        a.pin = a.pout;
+        a.tw_a = ctx->tw.get(ctx->nx / 2);
+        a.tw_b = ctx->tw.get(ctx->nx);
+        CK(launch_k2_rows(a, MODE_INV, ctx->nl, ctx->stream));
+    }
+    return SFT_OK;
+}
+
+// P (and P_y) <- dealiased inverse y-transform of the state, the input of the
+// next row pass.
+static sft_status prime(sft_ctx* ctx) {
+    if (ctx->d == 1) {
+        ctx->p_valid = true;
+        return SFT_OK;
+    }
+    StepArgs a = base_args(ctx);
+    a.pout = ctx->P;
+    a.pyout = ctx->Py;
+    a.tw_a = ctx->tw.get(ctx->ny);
+    CK(launch_k2_cols(a, MODE_PRIME, ctx->nl, ctx->stream));
+    ctx->p_valid = true;
+    return SFT_OK;
+}
+
+// Enqueue the kernels of one step (k_in_chunk = k).
+static sft_status enqueue_step(sft_ctx* ctx, int k) {
+    StepArgs a = base_args(ctx);
+    a.k_in_chunk = k;
+    if (ctx->d == 1) {
+        if (ctx->cplx) {
+            a.tw_a = ctx->tw.get(ctx->nx);
+        } else {
+            a.tw_a = ctx->tw.get(ctx->nx / 2);
+            a.tw_b = ctx->tw.get(ctx->nx);
+        }
+        CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
+        return SFT_OK;
+    }
+    a.pin = ctx->P;
+    a.pyin = ctx->Py;
+    a.qout = ctx->Q;
+    a.tw_a = ctx->tw.get(ctx->nx / 2);
+    a.tw_b = ctx->tw.get(ctx->nx);
+    CK(launch_k2_rows(a, MODE_STEP, ctx->nl, ctx->stream));
+    a.qin = ctx->Q;
+    a.pout = ctx->P;
+    a.pyout = ctx->Py;
+    a.tw_a = ctx->tw.get(ctx->ny);
+    CK(launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream));
+    return SFT_OK;
+}
+
+static sft_status capture_graph(sft_ctx* ctx) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    sft_status st = SFT_OK;
+    for (int k = 0; k < kGraphChunk && st == SFT_OK; ++k) st = enqueue_step(ctx, k);
+    if (st == SFT_OK) {
+        cudaError_t e = launch_advance(ctx->dstep, kGraphChunk, ctx->stream);
+        if (e != cudaSuccess) st = fail(ctx, SFT_ECUDA, cudaGetErrorString(e));
+    }
+    cudaError_t ee = cudaStreamEndCapture(ctx->stream, &g);
+    if (st != SFT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (ee != cudaSuccess) return fail(ctx, SFT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+    cudaError_t ie = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return fail(ctx, SFT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    return SFT_OK;
+}
+
+static sft_status build_twiddles(sft_ctx* ctx, const std::vector<int>& lens) {
+    std::vector<float2> host;
+    for (int L : lens) {
+        bool dup = false;
+        for (int x : ctx->tw.lens) dup |= (x == L);
+        if (dup || L < 2) continue;
+        ctx->tw.lens.push_back(L);
+        ctx->tw.offs.push_back(host.size());
+        for (int m = 0; m < L; ++m) {
+            const double ang = 2.0 * M_PI * (double)m / (double)L;
+            host.push_back(make_float2((float)std::cos(ang), (float)-std::sin(ang)));
+        }
+    }
+    if (host.empty()) host.push_back(make_float2(1.f, 0.f));
+    CK(cudaMalloc(&ctx->tw.dev, host.size() * sizeof(float2)));
+    CK(cudaMemcpy(ctx->tw.dev, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    return SFT_OK;
+}
+
+static sft_status validate(const sft_config* cfg, std::string& why) {
+    if (!cfg) return why = "null config", SFT_EINVAL;
+    if (cfg->d < 1 || cfg->d > 3) return why = "d must be 1, 2 or 3", SFT_EINVAL;
+    for (int i = 0; i < cfg->d; ++i) {
+        if (!is_pow2(cfg->n[i])) return why = "lattice sizes must be powers of two", SFT_EINVAL;
+        if (!(cfg->dx[i] > 0)) return why = "dx must be positive", SFT_EINVAL;
+        if (cfg->n[i] != cfg->n[0] || cfg->dx[i] != cfg->dx[0])
+            return why = "anisotropic lattices are not supported (coefficients are tabulated by |a|^2)",
+                   SFT_EUNSUPPORTED;
+    }
+    if (cfg->replicas < 1) return why = "replicas must be >= 1", SFT_EINVAL;
+    if (!(cfg->h > 0) || !std::isfinite(cfg->h)) return why = "h must be positive and finite", SFT_EINVAL;
+    if (cfg->model < SFT_MODEL_A || cfg->model > SFT_CGL) return why = "unknown model", SFT_EINVAL;
+    if (cfg->scheme < SFT_SETD_EM || cfg->scheme > SFT_SETD2) return why = "unknown scheme", SFT_EINVAL;
+    if (cfg->precision != 0) return why = "only FP32 precision (0) is built", SFT_EUNSUPPORTED;
+    if (cfg->dealias != 0 && cfg->dealias != 1) return why = "dealias must be 0 or 1", SFT_EINVAL;
+    const int cplx = cfg->model == SFT_CGL;
+    if (cfg->d == 1 && !k1_supported(cfg->n[0], cplx)) return why = "1-D size outside the built plans", SFT_EUNSUPPORTED;
+    if (cfg->d == 2 && !k2_supported(cfg->n[0], cfg->n[1], cplx))
+        return why = "2-D size/field outside the built plans", SFT_EUNSUPPORTED;
+    if (cfg->d == 3) return why = "3-D lattices are not built", SFT_EUNSUPPORTED;
+    return SFT_OK;
+}
+
+extern "C" {
+
+sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
+    if (!out) return SFT_EINVAL;
+    *out = nullptr;
+    std::string why;
+    sft_status vs = validate(cfg, why);
+    if (vs != SFT_OK) {
+        fprintf(stderr, "sft_create: %s\n", why.c_str());
+        return vs;
+    }
+    sft_ctx* ctx = new (std::nothrow) sft_ctx();
+    if (!ctx) return SFT_ENOMEM;
+    ctx->cfg = *cfg;
+    ctx->d = cfg->d;
+    ctx->nx = cfg->n[0];
+    ctx->ny = cfg->d >= 2 ? cfg->n[1] : 1;
+    ctx->nz = cfg->d >= 3 ? cfg->n[2] : 1;
+    ctx->cplx = cfg->model == SFT_CGL;
+    ctx->nl = cfg->model == SFT_KPZ ? NL_GRAD2 : (ctx->cplx ? NL_CGL : NL_CUBIC);
+    ctx->hx = ctx->cplx ? ctx->nx : ctx->nx / 2 + 1;
+    ctx->mx = 0;
+    for (int c = 0; c < ctx->hx; ++c)
+        if (!cfg->dealias || 3 * c < ctx->nx) ctx->mx = c + 1;
+    ctx->sites = (long long)ctx->nx * ctx->ny * ctx->nz;
+    ctx->nmodes = (long long)ctx->hx * ctx->ny * ctx->nz;
+    ctx->R = cfg->replicas;
+    auto cleanup = [&](sft_status s) {
+        sft_destroy(ctx);
+        return s;
+    };
+    if (cfg->stream) {
+        ctx->stream = (cudaStream_t)cfg->stream;
+    } else {
+        if (cudaStreamCreate(&ctx->stream) != cudaSuccess) return cleanup(SFT_ECUDA);
+        ctx->own_stream = true;
+    }
+    const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
+    const size_t rs = (size_t)ctx->R * ctx->sites * (ctx->cplx ? sizeof(float2) : sizeof(float));
+    auto dalloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+    bool ok = dalloc((void**)&ctx->phi, ms) && dalloc((void**)&ctx->Q, ms);
+    if (ok && ctx->d >= 2) ok = dalloc((void**)&ctx->P, ms);
+    if (ok && ctx->d >= 2 && ctx->nl == NL_GRAD2) ok = dalloc((void**)&ctx->Py, ms);
+    if (ok && cfg->scheme == SFT_SETD2) ok = dalloc((void**)&ctx->fprev, ms);
+    if (ok) {
+        if (ctx->cplx)
+            ok = dalloc((void**)&ctx->cfield, rs);
+        else
+            ok = dalloc((void**)&ctx->real, rs);
+    }
+    long long qmax = 0;
+    for (int i = 0; i < ctx->d; ++i) qmax += (long long)(cfg->n[i] / 2) * (cfg->n[i] / 2);
+    const long long nq = qmax + 1;
+    if (ok) ok = dalloc((void**)&ctx->tab, (size_t)nq * (ctx->cplx ? 2 : 1) * sizeof(float4));
+    if (ok) ok = dalloc((void**)&ctx->dstep, 4 * sizeof(long long)) && dalloc((void**)&ctx->dstatus, sizeof(unsigned));
+    ctx->nshells = (int)isqrt_ceil(qmax) + 1;
+    if (ok)
+        ok = dalloc((void**)&ctx->dshell, (size_t)ctx->R * ctx->nshells * sizeof(double)) &&
+             dalloc((void**)&ctx->drough, (size_t)ctx->R * sizeof(double));
+    if (!ok) {
+        fprintf(stderr, "sft_create: device allocation failed\n");
+        return cleanup(SFT_ENOMEM);
+    }
+    if (cudaMemset(ctx->phi, 0, ms) != cudaSuccess || cudaMemset(ctx->Q, 0, ms) != cudaSuccess)
+        return cleanup(SFT_ECUDA);
+    if (ctx->P && cudaMemset(ctx->P, 0, ms) != cudaSuccess) return cleanup(SFT_ECUDA);
+    if (ctx->Py && cudaMemset(ctx->Py, 0, ms) != cudaSuccess) return cleanup(SFT_ECUDA);
+    if (ctx->fprev && cudaMemset(ctx->fprev, 0, ms) != cudaSuccess) return cleanup(SFT_ECUDA);
+    long long init[4] = {0, cfg->scheme == SFT_SETD2 ? 0 : -1, (long long)0x7fffffffffffffffLL, 0};
+    ctx->first_step = init[1];
+    if (cudaMemcpy(ctx->dstep, init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(ctx->dstatus, 0, sizeof(unsigned)) != cudaSuccess)
+        return cleanup(SFT_ECUDA);
+    std::vector<int> lens;
+    if (ctx->cplx) {
+        lens.push_back(ctx->nx);
+    } else {
+        lens.push_back(ctx->nx / 2);
+        lens.push_back(ctx->nx);
+    }
+    if (ctx->d >= 2) lens.push_back(ctx->ny);
+    if (build_twiddles(ctx, lens) != SFT_OK) return cleanup(SFT_ECUDA);
+    // FP64 coefficient tables
+    TableArgs t{};
+    t.model = cfg->model;
+    t.scheme = cfg->scheme;
+    t.complex_field = ctx->cplx;
+    for (int i = 0; i < 8; ++i) t.p[i] = cfg->p[i];
+    t.h = cfg->h;
+    t.dk = 2.0 * M_PI / (ctx->nx * cfg->dx[0]);
+    double nf = 1.0;
+    for (int i = 0; i < ctx->d; ++i) nf *= std::sqrt(cfg->n[i] / cfg->dx[i]);
+    t.noise_norm = nf;
+    t.nq = nq;
+    t.out = ctx->tab;
+    if (launch_build_table(t, ctx->stream) != cudaSuccess) return cleanup(SFT_ECUDA);
+    // shell counts with the half-spectrum weights
+    ctx->counts.assign(ctx->nshells, 0.0);
+    for (int ax = 0; ax < ctx->hx; ++ax) {
+        const long long sx = ctx->cplx ? (2 * ax < ctx->nx ? ax : ax - ctx->nx) : ax;
+        const double w = (!ctx->cplx && ax != 0 && 2 * ax != ctx->nx) ? 2.0 : 1.0;
+        for (int az = 0; az < ctx->nz; ++az) {
+            const long long sz = 2 * az < ctx->nz ? az : az - ctx->nz;
+            for (int ay = 0; ay < ctx->ny; ++ay) {
+                const long long sy = 2 * ay < ctx->ny ? ay : ay - ctx->ny;
+                ctx->counts[isqrt_ceil(sx * sx + sy * sy + sz * sz)] += w;
+            }
+        }
+    }
+    ctx->launches_per_step = ctx->d == 1 ? 1 : 2;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cleanup(SFT_ECUDA);
+    *out = ctx;
+    return SFT_OK;
+}
+
+sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
+    if (out) *out = nullptr;
+    if (!cfgs || count < 1 || !out) return SFT_EINVAL;
+    if (count == 1) return sft_create(cfgs, out);
+    return SFT_EUNSUPPORTED;
+}
+
+static sft_status check_replica(sft_ctx* ctx, int replica, size_t bytes, size_t per, int* r0, int* R) {
+    if (replica < -1 || replica >= ctx->R) return fail(ctx, SFT_EINVAL, "replica out of range");
+    *r0 = replica < 0 ? 0 : replica;
+    *R = replica < 0 ? ctx->R : 1;
+    if (bytes != per * (size_t)(*R)) return fail(ctx, SFT_EINVAL, "buffer size does not match the field");
+    return SFT_OK;
+}
+
+sft_status sft_set_field(sft_ctx* ctx, int replica, const void* host, size_t bytes) {
+    if (!ctx || !host) return SFT_EINVAL;
+    const size_t per = (size_t)ctx->sites * (ctx->cplx ? sizeof(float2) : sizeof(float));
+    int r0, R;
+    sft_status s = check_replica(ctx, replica, bytes, per, &r0, &R);
+    if (s != SFT_OK) return s;
+    void* dst = ctx->cplx ? (void*)(ctx->cfield + (size_t)r0 * ctx->sites) : (void*)(ctx->real + (size_t)r0 * ctx->sites);
+    CK(cudaMemcpyAsync(dst, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    s = forward_from_buffer(ctx, r0, R);
+    if (s != SFT_OK) return s;
+    if (ctx->cfg.scheme == SFT_SETD2) {
+        ctx->first_step = ctx->step;
+        CK(cudaMemcpyAsync(ctx->dstep + 1, &ctx->first_step, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SFT_OK;
+}
+
+sft_status sft_init_random(sft_ctx* ctx, double sigma) {
+    if (!ctx || !(sigma >= 0)) return SFT_EINVAL;
+    CK(launch_init_random(ctx->real, ctx->cfield, ctx->sites, ctx->R, ctx->rep0, ctx->cfg.seed, (float)sigma,
+                          ctx->stream));
+    sft_status s = forward_from_buffer(ctx, 0, ctx->R);
+    if (s != SFT_OK) return s;
+    if (ctx->cfg.scheme == SFT_SETD2) {
+        ctx->first_step = ctx->step;
+        CK(cudaMemcpyAsync(ctx->dstep + 1, &ctx->first_step, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SFT_OK;
+}
+
+static sft_status read_status(sft_ctx* ctx) {
+    unsigned st = 0;
+    long long bad = 0;
+    CK(cudaMemcpyAsync(&st, ctx->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&bad, ctx->dstep + 2, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (st & 1u) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "non-finite state first seen at step %lld", bad);
+        return fail(ctx, SFT_ENONFINITE, buf);
+    }
+    return SFT_OK;
+}
+
+sft_status sft_sync(sft_ctx* ctx) {
+    if (!ctx) return SFT_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return read_status(ctx);
+}
+
+sft_status sft_get_field(sft_ctx* ctx, int replica, void* host_out, size_t bytes) {
+    if (!ctx || !host_out) return SFT_EINVAL;
+    const size_t per = (size_t)ctx->sites * (ctx->cplx ? sizeof(float2) : sizeof(float));
+    int r0, R;
+    sft_status s = check_replica(ctx, replica, bytes, per, &r0, &R);
+    if (s != SFT_OK) return s;
+    s = inverse_to_buffer(ctx, ctx->phi, r0, R);
+    if (s != SFT_OK) return s;
+    const void* src =
+        ctx->cplx ? (const void*)(ctx->cfield + (size_t)r0 * ctx->sites) : (const void*)(ctx->real + (size_t)r0 * ctx->sites);
+    CK(cudaMemcpyAsync(host_out, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    return read_status(ctx);
+}
+
+sft_status sft_get_spectrum(sft_ctx* ctx, void* host_out, size_t bytes) {
+    if (!ctx || !host_out) return SFT_EINVAL;
+    if (bytes != (size_t)ctx->R * ctx->nmodes * sizeof(float2)) return fail(ctx, SFT_EINVAL, "spectrum size mismatch");
+    CK(cudaMemcpyAsync(host_out, ctx->phi, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    return read_status(ctx);
+}
+
+sft_status sft_set_spectrum(sft_ctx* ctx, const void* host_in, size_t bytes) {
+    if (!ctx || !host_in) return SFT_EINVAL;
+    if (bytes != (size_t)ctx->R * ctx->nmodes * sizeof(float2)) return fail(ctx, SFT_EINVAL, "spectrum size mismatch");
+    CK(cudaMemcpyAsync(ctx->phi, host_in, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->p_valid = false;
+    if (ctx->cfg.scheme == SFT_SETD2) {
+        ctx->first_step = ctx->step;
+        CK(cudaMemcpyAsync(ctx->dstep + 1, &ctx->first_step, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SFT_OK;
+}
+
+static sft_status step_impl(sft_ctx* ctx, int64_t nsteps, bool use_graph) {
+    if (!ctx || nsteps < 0) return SFT_EINVAL;
+    if (ctx->step + nsteps > (long long)0xFFFFFFFFLL)
+        return fail(ctx, SFT_EINVAL, "the noise counter holds 2^32 steps per context");
+    if (!ctx->p_valid) {
+        sft_status s = prime(ctx);
+        if (s != SFT_OK) return s;
+    }
+    int64_t left = nsteps;
+    if (use_graph && left >= kGraphChunk) {
+        if (!ctx->warmed) {
+            // first chunk runs as plain launches (sets kernel attributes outside capture)
+            for (int k = 0; k < kGraphChunk; ++k) {
+                sft_status s = enqueue_step(ctx, k);
+                if (s != SFT_OK) return s;
+            }
+            CK(launch_advance(ctx->dstep, kGraphChunk, ctx->stream));
+            left -= kGraphChunk;
+            ctx->warmed = true;
+        }
+        if (left >= kGraphChunk && !ctx->graph) {
+            sft_status s = capture_graph(ctx);
+            if (s != SFT_OK) return s;
+        }
+        while (left >= kGraphChunk) {
+            CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+            left -= kGraphChunk;
+        }
+    }
+    for (int64_t i = 0; i < left; ++i) {
+        sft_status s = enqueue_step(ctx, 0);
+        if (s != SFT_OK) return s;
+        CK(launch_advance(ctx->dstep, 1, ctx->stream));
+    }
+    ctx->step += nsteps;
+    return SFT_OK;
+}
+
+sft_status sft_step(sft_ctx* ctx, int64_t nsteps) { return step_impl(ctx, nsteps, true); }
+sft_status sft_step_plain(sft_ctx* ctx, int64_t nsteps) { return step_impl(ctx, nsteps, false); }
+
+sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, size_t* written) {
+    if (!ctx) return SFT_EINVAL;
+    if (written) *written = 0;
+    const int ns = ctx->nshells;
+    if (kind == SFT_OBS_NSHELLS) {
+        if (!host_out || cap < 1) return fail(ctx, SFT_EINVAL, "output too small");
+        host_out[0] = ns;
+        if (written) *written = 1;
+        return SFT_OK;
+    }
+    if (kind == SFT_OBS_MARK) {
+        if (!ctx->snap) CK(cudaMalloc(&ctx->snap, (size_t)ctx->R * ctx->nmodes * sizeof(float2)));
+        CK(cudaMemcpyAsync(ctx->snap, ctx->phi, (size_t)ctx->R * ctx->nmodes * sizeof(float2),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        return read_status(ctx);
+    }
+    if (kind < 0 || kind > SFT_OBS_NSHELLS) return fail(ctx, SFT_EINVAL, "unknown observable");
+    if (!host_out) return SFT_EINVAL;
+    if (kind == SFT_OBS_CKT && !ctx->snap) return fail(ctx, SFT_EINVAL, "two-time correlation needs SFT_OBS_MARK first");
+    if (kind == SFT_OBS_RESPONSE && !ctx->dseed) return fail(ctx, SFT_EINVAL, "response needs a seeded tangent");
+    ObsArgs o{};
+    o.nx = ctx->nx;
+    o.ny = ctx->ny;
+    o.nz = ctx->nz;
+    o.hx = ctx->hx;
+    o.R = ctx->R;
+    o.complex_field = ctx->cplx;
+    o.nshells = ns;
+    double norm = 1.0;
+    for (int i = 0; i < ctx->d; ++i) norm *= ctx->cfg.dx[i] / ctx->cfg.n[i];
+    const size_t nsum = (size_t)ctx->R * ns;
+    std::vector<double> sums(nsum), sums2;
+    std::vector<double> rough(ctx->R);
+    CK(cudaMemsetAsync(ctx->dshell, 0, nsum * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(ctx->drough, 0, ctx->R * sizeof(double), ctx->stream));
+    if (kind == SFT_OBS_RESPONSE) {
+        o.phi = ctx->dphi;
+        o.ref = ctx->dseed;
+        o.norm = 1.0;
+        o.kind = 1;
+        o.shell_sum = ctx->dshell;
+        CK(launch_observe(o, ctx->stream));
+        CK(cudaMemcpyAsync(sums.data(), ctx->dshell, nsum * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        sums2.resize(nsum);
+        CK(cudaMemsetAsync(ctx->dshell, 0, nsum * sizeof(double), ctx->stream));
+        o.kind = 2;
+        CK(launch_observe(o, ctx->stream));
+        CK(cudaMemcpyAsync(sums2.data(), ctx->dshell, nsum * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        sft_status s = read_status(ctx);
+        if (s != SFT_OK) return s;
+        if (cap < (size_t)ns) return fail(ctx, SFT_EINVAL, "output too small");
+        for (int j = 0; j < ns; ++j) {
+            double num = 0, den = 0;
+            for (int r = 0; r < ctx->R; ++r) {
+                num += sums[(size_t)r * ns + j];
+                den += sums2[(size_t)r * ns + j];
+            }
+            host_out[j] = den > 0 ? num / den : 0.0;
+        }
+        if (written) *written = ns;
+        return SFT_OK;
+    }
+    o.phi = ctx->phi;
+    o.ref = kind == SFT_OBS_CKT ? ctx->snap : nullptr;
+    o.norm = norm;
+    o.kind = kind == SFT_OBS_CKT ? 1 : 0;
+    o.shell_sum = ctx->dshell;
+    o.rough = kind == SFT_OBS_ROUGHNESS ? ctx->drough : nullptr;
+    CK(launch_observe(o, ctx->stream));
+    CK(cudaMemcpyAsync(sums.data(), ctx->dshell, nsum * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(rough.data(), ctx->drough, ctx->R * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    sft_status s = read_status(ctx);
+    if (s != SFT_OK) return s;
+    if (kind == SFT_OBS_ROUGHNESS) {
+        if (cap < (size_t)ctx->R) return fail(ctx, SFT_EINVAL, "output too small");
+        const double n2 = (double)ctx->sites * (double)ctx->sites;
+        for (int r = 0; r < ctx->R; ++r) host_out[r] = rough[r] / n2;
+        if (written) *written = ctx->R;
+        return SFT_OK;
+    }
+    if (kind == SFT_OBS_SK_REPLICAS) {
+        if (cap < nsum) return fail(ctx, SFT_EINVAL, "output too small");
+        for (int r = 0; r < ctx->R; ++r)
+            for (int j = 0; j < ns; ++j)
+                host_out[(size_t)r * ns + j] = ctx->counts[j] > 0 ? sums[(size_t)r * ns + j] / ctx->counts[j] : 0.0;
+        if (written) *written = nsum;
+        return SFT_OK;
+    }
+    if (cap < (size_t)ns) return fail(ctx, SFT_EINVAL, "output too small");
+    for (int j = 0; j < ns; ++j) {
+        double acc = 0;
+        for (int r = 0; r < ctx->R; ++r) acc += sums[(size_t)r * ns + j];
+        host_out[j] = ctx->counts[j] > 0 ? acc / (ctx->counts[j] * ctx->R) : 0.0;
+    }
+    size_t w = ns;
+    if (cap >= 2 * (size_t)ns) {
+        for (int j = 0; j < ns; ++j) host_out[ns + j] = ctx->counts[j];
+        w = 2 * ns;
+    }
+    if (written) *written = w;
+    return SFT_OK;
+}
+
+sft_status sft_tangent_step(sft_ctx* ctx, const void*, int64_t, void*) {
+    return fail(ctx, SFT_EUNSUPPORTED, "tangent not built yet");
+}
+sft_status sft_adjoint(sft_ctx* ctx, const void*, int64_t, void*) {
+    return fail(ctx, SFT_EUNSUPPORTED, "adjoint not built yet");
+}
+sft_status sft_set_checkpoint_interval(sft_ctx* ctx, int segment) {
+    if (!ctx || segment < 1) return SFT_EINVAL;
+    ctx->ckpt_segment = segment;
+    return SFT_OK;
+}
+
+// ------------------------------------------------------------ checkpoints
+struct CkptHeader {
+    char magic[8];
+    uint64_t version;
+    uint64_t cfg_hash;
+    int64_t step;
+    int64_t first_step;
+    int64_t R;
+    int64_t nmodes;
+    int64_t has_fprev;
+};
+
+static uint64_t config_hash(const sft_config& c) {
+    uint64_t h = 1469598103934665603ULL;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ULL;
+        }
+    };
+    mix(&c.d, sizeof c.d);
+    mix(c.n, sizeof c.n);
+    mix(c.dx, sizeof c.dx);
+    mix(&c.replicas, sizeof c.replicas);
+    mix(&c.model, sizeof c.model);
+    mix(c.p, sizeof c.p);
+    mix(&c.scheme, sizeof c.scheme);
+    mix(&c.h, sizeof c.h);
+    mix(&c.seed, sizeof c.seed);
+    mix(&c.dealias, sizeof c.dealias);
+    mix(&c.precision, sizeof c.precision);
+    return h;
+}
+
+sft_status sft_checkpoint(sft_ctx* ctx, void* host_buf, size_t cap, size_t* written) {
+    if (!ctx) return SFT_EINVAL;
+    const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
+    const size_t need = sizeof(CkptHeader) + ms * (ctx->fprev ? 2 : 1);
+    if (written) *written = need;
+    if (!host_buf) return SFT_OK;
+    if (cap < need) return fail(ctx, SFT_EINVAL, "checkpoint buffer too small");
+    CkptHeader hd{};
+    memcpy(hd.magic, "SFTCKPT1", 8);
+    hd.version = 1;
+    hd.cfg_hash = config_hash(ctx->cfg);
+    hd.step = ctx->step;
+    hd.first_step = ctx->first_step;
+    hd.R = ctx->R;
+    hd.nmodes = ctx->nmodes;
+    hd.has_fprev = ctx->fprev ? 1 : 0;
+    char* b = (char*)host_buf;
+    memcpy(b, &hd, sizeof hd);
+    CK(cudaMemcpyAsync(b + sizeof hd, ctx->phi, ms, cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->fprev) CK(cudaMemcpyAsync(b + sizeof hd + ms, ctx->fprev, ms, cudaMemcpyDeviceToHost, ctx->stream));
+    return read_status(ctx);
+}
+
+sft_status sft_restore(sft_ctx* ctx, const void* host_buf, size_t bytes) {
+    if (!ctx || !host_buf) return SFT_EINVAL;
+    CkptHeader hd{};
+    if (bytes < sizeof hd) return fail(ctx, SFT_ECHECKPOINT, "checkpoint truncated");
+    memcpy(&hd, host_buf, sizeof hd);
+    const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
+    if (memcmp(hd.magic, "SFTCKPT1", 8) != 0 || hd.version != 1) return fail(ctx, SFT_ECHECKPOINT, "not a checkpoint");
+    if (hd.cfg_hash != config_hash(ctx->cfg) || hd.R != ctx->R || hd.nmodes != ctx->nmodes ||
+        hd.has_fprev != (ctx->fprev ? 1 : 0))
+        return fail(ctx, SFT_ECHECKPOINT, "checkpoint written for another configuration");
+    if (bytes != sizeof hd + ms * (hd.has_fprev ? 2 : 1)) return fail(ctx, SFT_ECHECKPOINT, "checkpoint size mismatch");
+    const char* b = (const char*)host_buf;
+    CK(cudaMemcpyAsync(ctx->phi, b + sizeof hd, ms, cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->fprev) CK(cudaMemcpyAsync(ctx->fprev, b + sizeof hd + ms, ms, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->step = hd.step;
+    ctx->first_step = hd.first_step;
+    long long vals[2] = {hd.step, hd.first_step};
+    CK(cudaMemcpyAsync(ctx->dstep, vals, sizeof vals, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->p_valid = false;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SFT_OK;
+}
+
+sft_status sft_draw_noise(sft_ctx* ctx, int64_t step, void* host_out, size_t bytes) {
+    if (!ctx || !host_out || step < 0) return SFT_EINVAL;
+    const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
+    if (bytes != ms) return fail(ctx, SFT_EINVAL, "noise buffer size mismatch");
+    CK(launch_draw_noise(ctx->nx, ctx->ny, ctx->nz, ctx->hx, ctx->cplx, ctx->R, ctx->rep0, ctx->cfg.seed, step,
+                         ctx->Q, ctx->stream));
+    CK(cudaMemcpyAsync(host_out, ctx->Q, ms, cudaMemcpyDeviceToHost, ctx->stream));
+    return read_status(ctx);
+}
+
+sft_status sft_get_step(const sft_ctx* ctx, int64_t* step) {
+    if (!ctx || !step) return SFT_EINVAL;
+    *step = ctx->step;
+    return SFT_OK;
+}
+
+sft_status sft_launches_per_step(const sft_ctx* ctx, int* launches) {
+    if (!ctx || !launches) return SFT_EINVAL;
+    *launches = ctx->launches_per_step;
+    return SFT_OK;
+}
+
+const char* sft_last_error(const sft_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void sft_destroy(sft_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    void* bufs[] = {ctx->phi, ctx->fprev, ctx->P, ctx->Q, ctx->Py, ctx->snap, ctx->real, ctx->cfield, ctx->tab,
+                    ctx->dstep, ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev, ctx->dphi, ctx->dseed};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+}  // extern "C"

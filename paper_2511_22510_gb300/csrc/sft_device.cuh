@@ -1,0 +1,268 @@
+// sft_device.cuh -- device building blocks of the stochastic-ETD stepper:
+// complex arithmetic, the Philox4x32-10 counter generator, the single-precision
+// Box-Muller recipe (bit-reproducible: only correctly rounded IEEE operations
+// through the __f*_rn intrinsics, never contracted), and a shared-memory
+// Stockham FFT engine in which a team of T threads holds a line of N complex
+// values, E = 16 per thread, with warp/named-barrier synchronisation.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sft {
+
+// ----------------------------------------------------------------- complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(-a.y, a.x); }  // i * a
+__device__ __forceinline__ float2 czero() { return make_float2(0.f, 0.f); }
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32
+// bijection with multipliers 0xD2511F53 / 0xCD9E8D57, key bumped by the Weyl
+// constants 0x9E3779B9 / 0xBB67AE85 between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        if (i > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// --------------------------------------------------------- Box-Muller recipe
+// ln x for x in [2^-24, 1]: x = 2^e m, m in (1/sqrt2, sqrt2]; ln m = 2 atanh(s),
+// s = (m-1)/(m+1), odd Taylor series of atanh through s^11; ln 2 split in a
+// short head and a tail.  Each step is one correctly rounded binary32 op.
+__device__ __forceinline__ float recipe_log(float x) {
+    const uint32_t b = __float_as_uint(x);
+    int e = (int)(b >> 23) - 127;
+    float m = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+    if (m > 0x1.6a09e6p+0f) {
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float s2 = __fmul_rn(s, s);
+    float p = __fmaf_rn(s2, 0x1.745d18p-4f, 0x1.c71c72p-4f);
+    p = __fmaf_rn(s2, p, 0x1.24924ap-3f);
+    p = __fmaf_rn(s2, p, 0x1.99999ap-3f);
+    p = __fmaf_rn(s2, p, 0x1.555556p-2f);
+    const float t = __fmul_rn(s2, p);
+    const float two_s = __fadd_rn(s, s);
+    const float lnm = __fmaf_rn(two_s, t, two_s);
+    const float ef = __int2float_rn(e);
+    return __fmaf_rn(ef, 0x1.62e4p-1f, __fmaf_rn(ef, 0x1.7f7d1cp-20f, lnm));
+}
+
+// sin and cos of 2 pi k / 2^24: exact integer reduction to the nearest quarter
+// turn, Taylor series of sin (through x^11) and cos (through x^10) on [-pi/4, pi/4).
+__device__ __forceinline__ void recipe_sincos_turn(uint32_t k24, float& sn, float& cs) {
+    const uint32_t qq = (k24 + 0x200000u) >> 22;
+    const int32_t r = (int32_t)k24 - (int32_t)(qq << 22);
+    const uint32_t q = qq & 3u;
+    const float x = __fmul_rn(__int2float_rn(r), 0x1.921fb6p-22f);
+    const float x2 = __fmul_rn(x, x);
+    float ps = __fmaf_rn(x2, -0x1.ae6456p-26f, 0x1.71de3ap-19f);
+    ps = __fmaf_rn(x2, ps, -0x1.a01a02p-13f);
+    ps = __fmaf_rn(x2, ps, 0x1.111112p-7f);
+    ps = __fmaf_rn(x2, ps, -0x1.555556p-3f);
+    const float sx = __fmaf_rn(__fmul_rn(x, x2), ps, x);
+    float pc = __fmaf_rn(x2, -0x1.27e4fcp-22f, 0x1.a01a02p-16f);
+    pc = __fmaf_rn(x2, pc, -0x1.6c16c2p-10f);
+    pc = __fmaf_rn(x2, pc, 0x1.555556p-5f);
+    pc = __fmaf_rn(x2, pc, -0.5f);
+    const float cx = __fmaf_rn(x2, pc, 1.0f);
+    switch (q) {
+        case 0: sn = sx; cs = cx; break;
+        case 1: sn = cx; cs = -sx; break;
+        case 2: sn = -sx; cs = -cx; break;
+        default: sn = -cx; cs = sx; break;
+    }
+}
+
+// One Box-Muller pair from two 32-bit words:
+//   u1 = ((wa >> 8) + 1) 2^-24 in (0, 1], turn = (wb >> 8) 2^-24,
+//   z0 = sqrt(-2 ln u1) cos(2 pi turn), z1 = sqrt(-2 ln u1) sin(2 pi turn).
+__device__ __forceinline__ float2 recipe_bm_pair(uint32_t wa, uint32_t wb) {
+    const float u1 = __fmul_rn(__uint2float_rn((wa >> 8) + 1u), 0x1p-24f);
+    const float rad = __fsqrt_rn(__fmul_rn(-2.0f, recipe_log(u1)));
+    float sn, cs;
+    recipe_sincos_turn(wb >> 8, sn, cs);
+    return make_float2(__fmul_rn(rad, cs), __fmul_rn(rad, sn));
+}
+
+// The normal pair belonging to counter index j (x-major mode enumeration):
+// Philox(ctr = (j >> 1, step, replica, tag), key = seed) -> words w0..w3;
+// even j takes the pair of (w0, w1), odd j the pair of (w2, w3).
+__device__ __forceinline__ float2 normal_pair_for_index(uint64_t seed, uint64_t j, uint32_t step, uint32_t replica,
+                                                        uint32_t tag) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 1), step, replica, tag),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    return (j & 1) ? recipe_bm_pair(w.z, w.w) : recipe_bm_pair(w.x, w.y);
+}
+
+// ------------------------------------------------------------- FFT engine
+// Compile-time plan: E = min(16, N) values per thread, T = N / E threads per
+// line; radix schedule 16, 16, ..., then the remainder (2, 4 or 8).
+template <int N>
+struct FftPlan {
+    static_assert(N >= 2 && (N & (N - 1)) == 0, "power of two");
+    static constexpr int E = N < 16 ? N : 16;
+    static constexpr int T = N / E;
+    static constexpr int log2(int v) { return v <= 1 ? 0 : 1 + log2(v / 2); }
+    static constexpr int L = log2(N);
+    static constexpr int P = N <= 16 ? 1 : (L + 3) / 4;  // passes
+    static constexpr int radix(int p) { return N <= 16 ? N : (p < L / 4 ? 16 : (1 << (L % 4))); }
+    // padded exchange buffer (complex elements): pos(i) = i + i/16
+    static constexpr int BUF = P > 1 ? N + N / 16 : 1;
+};
+
+__device__ __forceinline__ int xpos(int i) { return i + (i >> 4); }
+
+// Team barrier: teams of T <= 32 threads live inside one warp and use the
+// warp barrier (all lanes of the warp must take part); larger teams use a
+// named barrier per team (ids 1..15).
+template <int T>
+__device__ __forceinline__ void team_sync() {
+    if constexpr (T <= 32) {
+        __syncwarp();
+    } else {
+        const int id = 1 + (int)(threadIdx.x / T);
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(T) : "memory");
+    }
+}
+
+// cos / sin of 2 pi m / 16
+__device__ constexpr float kCos16[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                                        0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                                        -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+                                        0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+__device__ constexpr float kSin16[16] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+                                        1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                                        0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                                        -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f};
+
+// z * W_R^m with W_R = e^{-2 pi i / R} (forward) or its conjugate (inverse);
+// m and R are compile-time constants after unrolling.
+template <bool INV>
+__device__ __forceinline__ float2 twiddle_const(float2 z, int m, int R) {
+    const int q = (m * 16 / R) & 15;  // angle in sixteenths of a turn
+    if (q == 0) return z;
+    if (q == 8) return make_float2(-z.x, -z.y);
+    if (q == 4) return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+    if (q == 12) return INV ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
+    const float c = kCos16[q];
+    const float s = INV ? kSin16[q] : -kSin16[q];
+    return make_float2(z.x * c - z.y * s, z.x * s + z.y * c);
+}
+
+template <int R>
+__device__ constexpr int bitrev(int k) {
+    int r = 0;
+    for (int b = 1; b < R; b <<= 1) {
+        r = (r << 1) | (k & 1);
+        k >>= 1;
+    }
+    return r;
+}
+
+// In-register DFT of R values (R = 1, 2, 4, 8, 16): radix-2 decimation in
+// frequency, then the bit-reversal permutation (resolved at compile time).
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2* x) {
+    if constexpr (R > 1) {
+#pragma unroll
+        for (int span = R / 2; span >= 1; span >>= 1) {
+#pragma unroll
+            for (int blk = 0; blk < R; blk += 2 * span) {
+#pragma unroll
+                for (int i = 0; i < span; ++i) {
+                    const float2 a = x[blk + i], b = x[blk + i + span];
+                    x[blk + i] = cadd(a, b);
+                    x[blk + i + span] = twiddle_const<INV>(csub(a, b), i * (R / (2 * span)), R);
+                }
+            }
+        }
+        float2 y[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) y[k] = x[bitrev<R>(k)];
+#pragma unroll
+        for (int k = 0; k < R; ++k) x[k] = y[k];
+    }
+}
+
+// Stockham pass PASS of an N-point FFT.  Thread t of the team holds v[e] =
+// x[t + T e]; after the last pass it holds X[t + T e] in natural order.
+// Passes other than the last exchange through the padded team buffer `buf`.
+// tw: table of W_N^m = e^{-2 pi i m / N}, m in [0, N).
+template <int N, bool INV, int PASS, int NS>
+struct StockhamPass {
+    static __device__ __forceinline__ void run(float2 (&v)[FftPlan<N>::E], float2* buf, int t,
+                                               const float2* __restrict__ tw) {
+        using PL = FftPlan<N>;
+        constexpr int E = PL::E, T = PL::T;
+        constexpr int R = PL::radix(PASS);
+        constexpr int NB = E / R;
+        constexpr bool FIRST = (PASS == 0);
+        constexpr bool LAST = (NS * R == N);
+        float2 x[NB][R];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int j = t + T * b;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if constexpr (FIRST)
+                    x[b][r] = v[b + r * NB];
+                else
+                    x[b][r] = buf[xpos(j + r * (N / R))];
+            }
+            if constexpr (!FIRST) {
+                const int k = j % NS;
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(&tw[r * k * (N / (NS * R))]);
+                    if (INV) w.y = -w.y;
+                    x[b][r] = cmul(x[b][r], w);
+                }
+            }
+            dft_reg<R, INV>(x[b]);
+        }
+        if constexpr (LAST) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int s = 0; s < R; ++s) v[b + s * NB] = x[b][s];
+        } else {
+            team_sync<T>();
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int j = t + T * b;
+                const int k = j % NS;
+                const int base = (j / NS) * NS * R + k;
+#pragma unroll
+                for (int s = 0; s < R; ++s) buf[xpos(base + s * NS)] = x[b][s];
+            }
+            team_sync<T>();
+            StockhamPass<N, INV, PASS + 1, NS * R>::run(v, buf, t, tw);
+        }
+    }
+};
+
+// Unnormalised N-point FFT of a line held by a team (forward: e^{-2 pi i}).
+template <int N, bool INV>
+__device__ __forceinline__ void fft_line(float2 (&v)[FftPlan<N>::E], float2* buf, int t,
+                                         const float2* __restrict__ tw) {
+    StockhamPass<N, INV, 0, 1>::run(v, buf, t, tw);
+}
+
+}  // namespace sft

@@ -1,0 +1,100 @@
+// sft_internal.h -- host/device parameter blocks and kernel launchers shared by
+// the translation units of the stepper library (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sft {
+
+enum Nonlinearity { NL_CUBIC = 0, NL_GRAD2 = 1, NL_CGL = 2, NL_NONE = 3 };
+enum KernelMode { MODE_STEP = 0, MODE_FWD = 1, MODE_INV = 2, MODE_TAN = 3, MODE_ADJ = 4, MODE_PRIME = 5 };
+
+// Everything a step kernel needs, passed by value.
+struct StepArgs {
+    // lattice (real-space points per axis; unused axes = 1)
+    int nx, ny, nz;
+    int hx;        // stored x modes: nx/2 + 1 (real field) or nx (complex field)
+    int ncols;     // x columns carried by the P/Q intermediates in this launch
+    int R;         // replicas in the launch
+    int rep0;      // replica index of the first replica (noise counter word 2)
+    float scale;   // 1 / (nx ny nz): folds the inverse-transform normalisation
+    float dk;      // 2 pi / L
+    int dealias;   // 1: 2/3 truncation
+    int model;     // sft_model
+    int scheme;    // sft_scheme
+    float s0, s0i; // nonlinear prefactor: A: -Gamma u; B: -Gamma u (times k^2); KPZ: lambda/2; CGL: -(1 + i beta)
+    uint64_t seed;
+    const float4* tab;  // per |a|^2 coefficients {f1, A, B, g} (complex: 2 float4 per entry)
+    // buffers (x-major layouts, replica-major)
+    float2* phi;        // state
+    float2* fprev;      // SETD2 history
+    const float2* qin;  // row-pass output / column-pass input
+    float2* pout;       // column-pass output / row-pass input
+    float2* qout;
+    const float2* pin;
+    const float2* pyin; // KPZ: second intermediate (i k_y M phi)
+    float2* pyout;
+    float* real_io;     // real-space field (FWD input / INV output), real fields
+    float2* cplx_io;    // complex real-space field, complex fields
+    // tangent / adjoint streams
+    float2* dphi;
+    float2* dfprev;
+    const float2* dqin;
+    float2* dpout;
+    float2* dqout;
+    const float2* dpin;
+    const float2* dpyin;
+    float2* dpyout;
+    // twiddle tables for the transform lengths used by the kernel
+    const float2* tw_a;  // table for the first transform length
+    const float2* tw_b;  // table for the second transform length
+    // step bookkeeping
+    const long long* step_base;  // device: step index of k_in_chunk = 0
+    int k_in_chunk;
+    const long long* first_step;  // SETD2: the step that uses SETD1 coefficients
+    unsigned* status;             // bit 0: non-finite state
+    long long* bad_step;
+};
+
+// launchers (return cudaGetLastError of the launch); each picks the template
+// instance for the lattice size and returns cudaErrorInvalidValue if none.
+cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s);
+cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s);
+cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s);
+bool k1_supported(int nx, int complex_field);
+bool k2_supported(int nx, int ny, int complex_field);
+
+// coefficient tables (FP64 on the device, stored as float)
+struct TableArgs {
+    int model, scheme, complex_field;
+    double p[8];
+    double h, dk, noise_norm;
+    long long nq;
+    float4* out;
+};
+cudaError_t launch_build_table(const TableArgs& t, cudaStream_t s);
+
+// initial condition (Philox tag 1) into a real-space buffer
+cudaError_t launch_init_random(float* real_out, float2* cplx_out, long long sites, int R, int rep0, uint64_t seed,
+                               float sigma, cudaStream_t s);
+// unit-variance Fourier noise of one step for every stored mode (diagnostics)
+cudaError_t launch_draw_noise(int nx, int ny, int nz, int hx, int cplx, int R, int rep0, uint64_t seed,
+                              long long step, float2* out, cudaStream_t s);
+// step counter advance (one thread)
+cudaError_t launch_advance(long long* step_base, int by, cudaStream_t s);
+
+// observables
+struct ObsArgs {
+    int nx, ny, nz, hx, R, complex_field, nshells;
+    const float2* phi;
+    const float2* ref;  // snapshot for two-time, tangent seed for response
+    double norm;        // (L/N^2)^d
+    int kind;           // 0: |phi|^2, 1: Re(phi conj(ref)), 2: |ref|^2 (response denominator)
+    double* shell_sum;  // [R][nshells] accumulators (zeroed by caller)
+    double* rough;      // [R] sum over a != 0 of |phi_a|^2 (full-spectrum weights)
+};
+cudaError_t launch_observe(const ObsArgs& o, cudaStream_t s);
+cudaError_t launch_shell_counts(int nx, int ny, int nz, int hx, int complex_field, int nshells, double* counts,
+                                cudaStream_t s);
+
+}  // namespace sft

@@ -1,0 +1,375 @@
+// sft_k2d.cu -- two-pass 2-D step for real fields (Model A/B, KPZ).
+//
+// Layout (x-major, per replica): spectrum phi[a_x][a_y], a_x in [0, nx/2],
+// a_y in [0, ny); intermediates P, Q with the same layout restricted to the
+// x-columns inside the dealiasing band.  One step (Sec. IV boxed algorithm):
+//
+//   row pass    (k2_rows): P[a_x][y] --C2R along x--> psi(x, y) --q(psi)-->
+//                          q(x, y) --R2C along x--> Q[a_x][y]
+//   column pass (k2_cols): Q --FFT along y--> DFT[q]; F = M s DFT[q];
+//                          phi <- f1 phi + A F + B F_prev + g eta (Philox);
+//                          Hermitian fix-up; P <- IFFT_y(M phi / N^2)
+//
+// so every step moves the state once through HBM plus two dealiased
+// intermediates.  Real-length-N transforms use the N/2-point complex FFT with
+// the even/odd split (z[m] = x[2m] + i x[2m+1]).
+#include "sft_step_common.cuh"
+
+namespace sft {
+
+template <int M>
+struct RowCfg {
+    using PL = FftPlan<M>;
+    static constexpr int T = PL::T;
+    static constexpr int ROWS = T >= 256 ? 1 : 256 / T;
+    static constexpr int THREADS = ROWS * T;
+    static constexpr int TS = M + 1;               // odd row stride of the spectral tile
+    static constexpr int XB = M + M / 16 + 1;       // padded exchange buffer per team
+    static constexpr size_t smem(int ntile) { return sizeof(float2) * ((size_t)ntile * ROWS * TS + (size_t)ROWS * XB); }
+};
+
+template <int M, int NL, int MODE>
+__global__ void __launch_bounds__(RowCfg<M>::THREADS) k2_rows_real(const StepArgs a) {
+    using C = RowCfg<M>;
+    using PL = FftPlan<M>;
+    constexpr int T = PL::T, E = PL::E, ROWS = C::ROWS, TS = C::TS, XB = C::XB;
+    constexpr bool GRAD = (NL == NL_GRAD2) && (MODE == MODE_STEP);
+    constexpr int NTILE = GRAD ? 2 : 1;
+    extern __shared__ float2 sm[];
+    float2* tile = sm;
+    float2* xbuf = sm + NTILE * ROWS * TS;
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const int rep = blockIdx.y;
+    const int ny = a.ny, hx = a.hx, ncols = a.ncols;
+    const int y0 = blockIdx.x * ROWS;
+    const int y = y0 + team;
+    const bool yok = y < ny;
+    float2* xb = xbuf + team * XB;
+    const float2* __restrict__ twM = a.tw_a;
+    const float2* __restrict__ twN = a.tw_b;
+    float2 z[E];
+
+    if constexpr (MODE == MODE_FWD) {
+        const float* src = a.real_io + ((size_t)rep * ny + (yok ? y : 0)) * (2 * M);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int m = t + T * e;
+            z[e] = yok ? *reinterpret_cast<const float2*>(src + 2 * m) : czero();
+        }
+    } else {
+        for (int f = threadIdx.x; f < ROWS * (M + 1); f += blockDim.x) {
+            const int c = f / ROWS, yy = f % ROWS;
+            float2 v = czero(), vy = czero();
+            if (c < ncols && y0 + yy < ny) {
+                const size_t off = ((size_t)rep * hx + c) * ny + y0 + yy;
+                v = a.pin[off];
+                if constexpr (GRAD) vy = a.pyin[off];
+            }
+            tile[yy * TS + c] = v;
+            if constexpr (GRAD) tile[ROWS * TS + yy * TS + c] = vy;
+        }
+        __syncthreads();
+        const float2* trow = tile + team * TS;
+        if constexpr (GRAD) {
+            // grad_x h from i k_x P (k_x = 0 at the Nyquist column), grad_y h from P_y
+            const float2* tyrow = tile + ROWS * TS + team * TS;
+            float2 zy[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int k = t + T * e;
+                const float2 tw = __ldg(&twN[k]);
+                const float kx = a.dk * (float)k, kxm = (k == 0) ? 0.f : a.dk * (float)(M - k);
+                const float2 X = cscale(cmuli(trow[k]), kx), Xm = cscale(cmuli(trow[M - k]), kxm);
+                z[e] = c2r_pre(X, Xm, tw);
+                zy[e] = c2r_pre(tyrow[k], tyrow[M - k], tw);
+            }
+            fft_line<M, true>(z, xb, t, twM);
+            fft_line<M, true>(zy, xb, t, twM);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                z[e] = make_float2(z[e].x * z[e].x + zy[e].x * zy[e].x, z[e].y * z[e].y + zy[e].y * zy[e].y);
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int k = t + T * e;
+                z[e] = c2r_pre(trow[k], trow[M - k], __ldg(&twN[k]));
+            }
+            fft_line<M, true>(z, xb, t, twM);
+            if constexpr (MODE == MODE_INV) {
+                if (yok) {
+                    float* dst = a.real_io + ((size_t)rep * ny + y) * (2 * M);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) *reinterpret_cast<float2*>(dst + 2 * (t + T * e)) = z[e];
+                }
+                return;
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
+            }
+        }
+    }
+    if constexpr (MODE != MODE_INV) {
+        fft_line<M, false>(z, xb, t, twM);
+        team_sync<T>();
+#pragma unroll
+        for (int e = 0; e < E; ++e) xb[xpos(t + T * e)] = z[e];
+        team_sync<T>();
+        float2* trow = tile + team * TS;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            if (k < ncols) trow[k] = r2c_post(z[e], cconj(xb[xpos((M - k) & (M - 1))]), __ldg(&twN[k]));
+        }
+        if (t == 0 && M < ncols) {
+            const float2 z0 = xb[0];
+            trow[M] = make_float2(z0.x - z0.y, 0.f);
+        }
+        __syncthreads();
+        for (int f = threadIdx.x; f < ROWS * ncols; f += blockDim.x) {
+            const int c = f / ROWS, yy = f % ROWS;
+            if (y0 + yy < ny) a.qout[((size_t)rep * hx + c) * ny + y0 + yy] = tile[yy * TS + c];
+        }
+    }
+}
+
+template <int NY>
+struct ColCfg {
+    using PL = FftPlan<NY>;
+    static constexpr int T = PL::T;
+    static constexpr int COLS = T >= 256 ? 1 : 256 / T;
+    static constexpr int THREADS = COLS * T;
+    static constexpr int XB = NY + NY / 16 + 1;
+    static constexpr size_t smem() { return sizeof(float2) * (size_t)COLS * XB; }
+};
+
+// P <- IFFT_y(M phi / N^2) for one column (and, for KPZ, P_y <- IFFT_y(i k_y M phi / N^2)):
+// the dealiased input of the next row pass.
+template <int NY, int NL>
+__device__ __forceinline__ void emit_p(const StepArgs& a, const float2 (&out)[FftPlan<NY>::E], bool has_p, int cc,
+                                       size_t colbase, float2* xb, int t) {
+    using PL = FftPlan<NY>;
+    constexpr int T = PL::T, E = PL::E;
+    if (!(has_p || T < 32)) return;
+    float2 v[E];
+    float2 vy[NL == NL_GRAD2 ? E : 1];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int ay = t + T * e;
+        const int ays = signed_idx(ay, NY);
+        const bool inm = !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < NY);
+        v[e] = (has_p && inm) ? cscale(out[e], a.scale) : czero();
+        if constexpr (NL == NL_GRAD2) vy[e] = cscale(cmuli(v[e]), a.dk * (float)odd_idx(ay, NY));
+    }
+    fft_line<NY, true>(v, xb, t, a.tw_a);
+    if constexpr (NL == NL_GRAD2) fft_line<NY, true>(vy, xb, t, a.tw_a);
+    if (has_p) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            a.pout[colbase + t + T * e] = v[e];
+            if constexpr (NL == NL_GRAD2) a.pyout[colbase + t + T * e] = vy[e];
+        }
+    }
+}
+
+template <int NY, int NL, int MODE>
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS) k2_cols_real(const StepArgs a) {
+    using C = ColCfg<NY>;
+    using PL = FftPlan<NY>;
+    constexpr int T = PL::T, E = PL::E, COLS = C::COLS, XB = C::XB;
+    extern __shared__ float2 sm[];
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const int rep = blockIdx.y;
+    const int c = blockIdx.x * COLS + team;
+    const bool valid = c < a.hx;
+    const int cc = valid ? c : a.hx - 1;
+    const int M = a.nx / 2;
+    float2* xb = sm + team * XB;
+    const size_t colbase = ((size_t)rep * a.hx + cc) * NY;
+    const float2* __restrict__ tw = a.tw_a;
+    const bool plane = (cc == 0 || cc == M);
+    float2 v[E];
+
+    if constexpr (MODE == MODE_FWD) {
+        if (!valid && T >= 32) return;
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = a.qin[colbase + t + T * e];
+        fft_line<NY, false>(v, xb, t, tw);
+        team_sync<T>();
+#pragma unroll
+        for (int e = 0; e < E; ++e) xb[xpos(t + T * e)] = v[e];
+        team_sync<T>();
+        if (plane) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ay = t + T * e;
+                if (2 * ay > NY) v[e] = cconj(xb[xpos(NY - ay)]);
+                if (ay == 0 || 2 * ay == NY) v[e].y = 0.f;
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) a.phi[colbase + t + T * e] = v[e];
+        }
+    } else if constexpr (MODE == MODE_INV) {
+        if (!valid && T >= 32) return;
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = cscale(a.phi[colbase + t + T * e], a.scale);
+        fft_line<NY, true>(v, xb, t, tw);
+        if (valid) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) a.pout[colbase + t + T * e] = v[e];
+        }
+    } else if constexpr (MODE == MODE_STEP) {
+        if (!valid && T >= 32) return;
+        const long long step = current_step(a);
+        const bool first = (a.scheme == 2) && (step == *a.first_step);
+        const bool has_f = valid && cc < a.ncols;
+        if (has_f || T < 32) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = has_f ? a.qin[colbase + t + T * e] : czero();
+            fft_line<NY, false>(v, xb, t, tw);
+        }
+        float2 out[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int ay = t + T * e;
+            const int ays = signed_idx(ay, NY);
+            const int q = cc * cc + ays * ays;
+            const bool inm = !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < NY);
+            float2 F = czero();
+            if (has_f && inm) F = cscale(v[e], nl_prefactor(a, q).x);
+            const Coefs co = load_coefs<false>(a.tab, q, first);
+            const float2 ph = a.phi[colbase + ay];
+            float2 Fp = czero();
+            if (a.scheme == 2 && has_f) Fp = a.fprev[colbase + ay];
+            const bool partner = plane && 2 * ay > NY;
+            const bool selfc = plane && (ay == 0 || 2 * ay == NY);
+            const float2 eta = partner ? czero()
+                                       : fourier_noise(a.seed, (uint64_t)cc * NY + ay, (uint32_t)step,
+                                                       (uint32_t)(a.rep0 + rep), selfc);
+            out[e] = setd_update<false>(co, ph, F, Fp, eta);
+            if (a.scheme == 2 && has_f && valid) a.fprev[colbase + ay] = F;
+        }
+        if (plane || T < 32) {
+            team_sync<T>();
+#pragma unroll
+            for (int e = 0; e < E; ++e) xb[xpos(t + T * e)] = out[e];
+            team_sync<T>();
+            if (plane) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int ay = t + T * e;
+                    if (2 * ay > NY) out[e] = cconj(xb[xpos(NY - ay)]);
+                    if (ay == 0 || 2 * ay == NY) out[e].y = 0.f;
+                }
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                a.phi[colbase + t + T * e] = out[e];
+                flag_nonfinite(a, out[e], step);
+            }
+        }
+        emit_p<NY, NL>(a, out, valid && cc < a.ncols, cc, colbase, xb, t);
+    } else if constexpr (MODE == MODE_PRIME) {
+        if (!valid && T >= 32) return;
+        const bool has_p = valid && cc < a.ncols;
+        float2 out[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) out[e] = has_p ? a.phi[colbase + t + T * e] : czero();
+        emit_p<NY, NL>(a, out, has_p, cc, colbase, xb, t);
+    }
+}
+
+// ----------------------------------------------------------------- launchers
+template <int M, int NL, int MODE>
+static cudaError_t run_rows(const StepArgs& a, cudaStream_t s) {
+    using C = RowCfg<M>;
+    constexpr int NTILE = (NL == NL_GRAD2 && MODE == MODE_STEP) ? 2 : 1;
+    const size_t sm = C::smem(NTILE);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k2_rows_real<M, NL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((a.ny + C::ROWS - 1) / C::ROWS, a.R);
+    k2_rows_real<M, NL, MODE><<<grid, C::THREADS, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NY, int NL, int MODE>
+static cudaError_t run_cols(const StepArgs& a, cudaStream_t s) {
+    using C = ColCfg<NY>;
+    const size_t sm = C::smem();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k2_cols_real<NY, NL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((a.hx + C::COLS - 1) / C::COLS, a.R);
+    k2_cols_real<NY, NL, MODE><<<grid, C::THREADS, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int M>
+static cudaError_t rows_for(const StepArgs& a, int mode, int nl, cudaStream_t s) {
+    if (mode == MODE_FWD) return run_rows<M, NL_CUBIC, MODE_FWD>(a, s);
+    if (mode == MODE_INV) return run_rows<M, NL_CUBIC, MODE_INV>(a, s);
+    if (mode == MODE_STEP && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_STEP>(a, s);
+    if (mode == MODE_STEP && nl == NL_GRAD2) return run_rows<M, NL_GRAD2, MODE_STEP>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+template <int NY>
+static cudaError_t cols_for(const StepArgs& a, int mode, int nl, cudaStream_t s) {
+    if (mode == MODE_FWD) return run_cols<NY, NL_CUBIC, MODE_FWD>(a, s);
+    if (mode == MODE_INV) return run_cols<NY, NL_CUBIC, MODE_INV>(a, s);
+    if (mode == MODE_STEP && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_STEP>(a, s);
+    if (mode == MODE_STEP && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_STEP>(a, s);
+    if (mode == MODE_PRIME && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_PRIME>(a, s);
+    if (mode == MODE_PRIME && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_PRIME>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+bool k2_supported(int nx, int ny, int complex_field) {
+    if (complex_field) return false;
+    auto ok = [](int n) { return n >= 16 && n <= 4096 && (n & (n - 1)) == 0; };
+    return ok(nx) && ok(ny);
+}
+
+cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s) {
+    switch (a.nx / 2) {
+        case 8: return rows_for<8>(a, mode, nl, s);
+        case 16: return rows_for<16>(a, mode, nl, s);
+        case 32: return rows_for<32>(a, mode, nl, s);
+        case 64: return rows_for<64>(a, mode, nl, s);
+        case 128: return rows_for<128>(a, mode, nl, s);
+        case 256: return rows_for<256>(a, mode, nl, s);
+        case 512: return rows_for<512>(a, mode, nl, s);
+        case 1024: return rows_for<1024>(a, mode, nl, s);
+        case 2048: return rows_for<2048>(a, mode, nl, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s) {
+    switch (a.ny) {
+        case 16: return cols_for<16>(a, mode, nl, s);
+        case 32: return cols_for<32>(a, mode, nl, s);
+        case 64: return cols_for<64>(a, mode, nl, s);
+        case 128: return cols_for<128>(a, mode, nl, s);
+        case 256: return cols_for<256>(a, mode, nl, s);
+        case 512: return cols_for<512>(a, mode, nl, s);
+        case 1024: return cols_for<1024>(a, mode, nl, s);
+        case 2048: return cols_for<2048>(a, mode, nl, s);
+        case 4096: return cols_for<4096>(a, mode, nl, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sft

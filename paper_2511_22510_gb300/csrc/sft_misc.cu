@@ -1,0 +1,281 @@
+// sft_misc.cu -- per-context set-up and bookkeeping kernels: the FP64
+// coefficient tables, the Philox initial condition, the step counter, and the
+// shell-averaged observables.
+#include "sft_step_common.cuh"
+
+namespace sft {
+
+// ------------------------------------------------------------------ tables
+// phi1(z) = (e^z - 1)/z, phi2(z) = (e^z - 1 - z)/z^2 (Sec. II), in FP64:
+// real z by expm1 with a Taylor series for phi2 when |z| < 1/2; complex z by
+// the Taylor series for |z| < 1 and the direct formula otherwise.  The c -> 0
+// limits (1 and 1/2) are the small-c fallback of Sec. IV.
+__device__ void phi12_real(double x, double& p1, double& p2) {
+    if (x == 0.0) {
+        p1 = 1.0;
+        p2 = 0.5;
+        return;
+    }
+    const double em1 = expm1(x);
+    p1 = em1 / x;
+    if (fabs(x) < 0.5) {
+        double term = 0.5, sum = 0.0;
+        for (int k = 0; k < 30; ++k) {
+            sum += term;
+            term *= x / (double)(k + 3);
+        }
+        p2 = sum;
+    } else {
+        p2 = (em1 - x) / (x * x);
+    }
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 zexp(double2 z) {
+    double s, c;
+    sincos(z.y, &s, &c);
+    const double m = exp(z.x);
+    return make_double2(m * c, m * s);
+}
+
+__device__ void phi12_cplx(double2 z, double2& p1, double2& p2) {
+    if (z.y == 0.0) {
+        double a, b;
+        phi12_real(z.x, a, b);
+        p1 = make_double2(a, 0.0);
+        p2 = make_double2(b, 0.0);
+        return;
+    }
+    if (z.x * z.x + z.y * z.y < 1.0) {
+        double2 t1 = make_double2(1.0, 0.0), t2 = make_double2(0.5, 0.0);
+        double2 s1 = make_double2(0.0, 0.0), s2 = make_double2(0.0, 0.0);
+        for (int k = 0; k < 40; ++k) {
+            s1.x += t1.x; s1.y += t1.y;
+            s2.x += t2.x; s2.y += t2.y;
+            t1 = zmul(t1, make_double2(z.x / (k + 2), z.y / (k + 2)));
+            t2 = zmul(t2, make_double2(z.x / (k + 3), z.y / (k + 3)));
+        }
+        p1 = s1;
+        p2 = s2;
+    } else {
+        double2 em1 = zexp(z);
+        em1.x -= 1.0;
+        p1 = zdiv(em1, z);
+        p2 = zdiv(make_double2(em1.x - z.x, em1.y - z.y), zmul(z, z));
+    }
+}
+
+// One entry per q = |a|^2 (isotropic lattice, k^2 = dk^2 q):
+//   z = c h, f1 = e^z;
+//   SETD-EM: A = h phi1(z), B = 0, g = nf sqrt(2 D h) e^{z/2}      (f3 G dW)
+//   SETD1:   A = h phi1(z), B = 0, g = nf sqrt(2 D h phi1(2 Re z))  (f4 G, exact I1)
+//   SETD2:   A = h (phi1 + phi2), B = -h phi2, g as SETD1            (Eq. SETD2)
+// nf = (N^2/L)^{d/2} (App. A).  Real models store {f1, A, B, g}; CGL stores
+// {f1, A} and {B, g} as complex pairs.
+__global__ void k_build_table(const TableArgs t) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= t.nq) return;
+    const double k2 = t.dk * t.dk * (double)q;
+    const double* p = t.p;
+    double2 c = make_double2(0.0, 0.0);
+    double D = 0.0;
+    switch (t.model) {
+        case 0: c.x = -p[0] * (p[1] + k2); D = p[0] * p[3]; break;
+        case 1: c.x = -p[0] * k2 * (p[1] + k2); D = p[0] * p[3] * k2; break;
+        case 2: c.x = -p[0] * k2; D = p[2]; break;
+        default: c.x = 1.0 - k2; c.y = -p[0] * k2; D = p[2]; break;
+    }
+    const double h = t.h;
+    const double2 z = make_double2(c.x * h, c.y * h);
+    double2 p1, p2;
+    phi12_cplx(z, p1, p2);
+    const double2 f1 = zexp(z);
+    double2 A, B = make_double2(0.0, 0.0), g;
+    if (t.scheme == 0) {
+        A = make_double2(h * p1.x, h * p1.y);
+        const double2 e2 = zexp(make_double2(0.5 * z.x, 0.5 * z.y));
+        const double amp = t.noise_norm * sqrt(2.0 * D * h);
+        g = make_double2(amp * e2.x, amp * e2.y);
+    } else {
+        double q1, q2;
+        phi12_real(2.0 * z.x, q1, q2);
+        g = make_double2(t.noise_norm * sqrt(2.0 * D * h * q1), 0.0);
+        if (t.scheme == 1) {
+            A = make_double2(h * p1.x, h * p1.y);
+        } else {
+            A = make_double2(h * (p1.x + p2.x), h * (p1.y + p2.y));
+            B = make_double2(-h * p2.x, -h * p2.y);
+        }
+    }
+    if (t.complex_field) {
+        t.out[2 * q] = make_float4((float)f1.x, (float)f1.y, (float)A.x, (float)A.y);
+        t.out[2 * q + 1] = make_float4((float)B.x, (float)B.y, (float)g.x, (float)g.y);
+    } else {
+        t.out[q] = make_float4((float)f1.x, (float)A.x, (float)B.x, (float)g.x);
+    }
+}
+
+cudaError_t launch_build_table(const TableArgs& t, cudaStream_t s) {
+    const int th = 128;
+    k_build_table<<<(unsigned)((t.nq + th - 1) / th), th, 0, s>>>(t);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- initial condition
+// Real fields: site s of replica r is sigma * z[s & 3] of the four normals of
+// Philox(ctr = (s >> 2, 0, r, 1)); complex fields: sigma (z_a + i z_b) of the
+// pair (s & 1) of Philox(ctr = (s >> 1, 0, r, 1)).
+__global__ void k_init_random(float* real_out, float2* cplx_out, long long sites, int R, int rep0, uint64_t seed,
+                              float sigma) {
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    if (real_out) {
+        const long long s0 = 4 * g;
+        if (s0 >= sites) return;
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)g, 0u, (uint32_t)(rep0 + r), 1u), key);
+        const float2 a = recipe_bm_pair(w.x, w.y), b = recipe_bm_pair(w.z, w.w);
+        const float z[4] = {a.x, a.y, b.x, b.y};
+        for (int i = 0; i < 4 && s0 + i < sites; ++i) real_out[(size_t)r * sites + s0 + i] = sigma * z[i];
+    } else {
+        const long long s0 = 2 * g;
+        if (s0 >= sites) return;
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)g, 0u, (uint32_t)(rep0 + r), 1u), key);
+        const float2 a = recipe_bm_pair(w.x, w.y), b = recipe_bm_pair(w.z, w.w);
+        cplx_out[(size_t)r * sites + s0] = make_float2(sigma * a.x, sigma * a.y);
+        if (s0 + 1 < sites) cplx_out[(size_t)r * sites + s0 + 1] = make_float2(sigma * b.x, sigma * b.y);
+    }
+}
+
+cudaError_t launch_init_random(float* real_out, float2* cplx_out, long long sites, int R, int rep0, uint64_t seed,
+                               float sigma, cudaStream_t s) {
+    const long long per = real_out ? 4 : 2;
+    const long long threads = (sites + per - 1) / per;
+    dim3 grid((unsigned)((threads + 255) / 256), R);
+    k_init_random<<<grid, 256, 0, s>>>(real_out, cplx_out, sites, R, rep0, seed, sigma);
+    return cudaGetLastError();
+}
+
+__global__ void k_advance(long long* step_base, int by) { *step_base += by; }
+
+cudaError_t launch_advance(long long* step_base, int by, cudaStream_t s) {
+    k_advance<<<1, 1, 0, s>>>(step_base, by);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- observables
+// Shell j = ceil(|a|) (App. C: the shell (k_j - dk, k_j]).  For real fields
+// the stored half carries weight 2 off the planes a_x in {0, nx/2} (their
+// conjugate partners are not stored) and 1 on them.
+__device__ __forceinline__ int shell_of(long long q) {
+    long long j = (long long)sqrt((double)q);
+    while (j * j < q) ++j;
+    while (j > 0 && (j - 1) * (j - 1) >= q) --j;
+    return (int)j;
+}
+
+__global__ void k_observe(const ObsArgs o) {
+    extern __shared__ double acc[];
+    const int r = blockIdx.y;
+    for (int j = threadIdx.x; j < o.nshells; j += blockDim.x) acc[j] = 0.0;
+    __shared__ double rough;
+    if (threadIdx.x == 0) rough = 0.0;
+    __syncthreads();
+    const long long nmodes = (long long)o.hx * o.nz * o.ny;
+    const long long chunk = (nmodes + gridDim.x - 1) / gridDim.x;
+    const long long m0 = blockIdx.x * chunk;
+    const long long m1 = min(nmodes, m0 + chunk);
+    double my_rough = 0.0;
+    for (long long m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
+        const int ay = (int)(m % o.ny);
+        const int az = (int)((m / o.ny) % o.nz);
+        const int ax = (int)(m / ((long long)o.ny * o.nz));
+        const long long sx = o.complex_field ? signed_idx(ax, o.nx) : ax;
+        const long long sy = signed_idx(ay, o.ny), sz = signed_idx(az, o.nz);
+        const long long q = sx * sx + sy * sy + sz * sz;
+        const double w = (!o.complex_field && ax != 0 && 2 * ax != o.nx) ? 2.0 : 1.0;
+        const size_t idx = (size_t)r * nmodes + m;
+        const float2 v = o.phi ? o.phi[idx] : make_float2(0.f, 0.f);
+        double val;
+        if (o.kind == 0) {
+            val = (double)v.x * v.x + (double)v.y * v.y;
+            if (q != 0) my_rough += w * val;
+        } else if (o.kind == 1) {
+            const float2 u = o.ref[idx];
+            val = (double)v.x * u.x + (double)v.y * u.y;
+        } else {
+            const float2 u = o.ref[idx];
+            val = (double)u.x * u.x + (double)u.y * u.y;
+        }
+        atomicAdd(&acc[shell_of(q)], w * val * o.norm);
+    }
+    if (o.rough) atomicAdd(&rough, my_rough);
+    __syncthreads();
+    for (int j = threadIdx.x; j < o.nshells; j += blockDim.x)
+        if (acc[j] != 0.0) atomicAdd(&o.shell_sum[(size_t)r * o.nshells + j], acc[j]);
+    if (threadIdx.x == 0 && o.rough) atomicAdd(&o.rough[r], rough);
+}
+
+cudaError_t launch_observe(const ObsArgs& o, cudaStream_t s) {
+    const long long nmodes = (long long)o.hx * o.nz * o.ny;
+    long long nb = (nmodes + 1023) / 1024;
+    int blocks = (int)(nb < 1184 ? nb : 1184);
+    if (blocks < 1) blocks = 1;
+    dim3 grid(blocks, o.R);
+    const size_t sm = sizeof(double) * (size_t)o.nshells;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_observe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_observe<<<grid, 256, sm, s>>>(o);
+    return cudaGetLastError();
+}
+
+}  // namespace sft
+
+namespace sft {
+
+// Fourier noise eta of every stored mode at one step (unit variance; the
+// amplitude g_a is applied by the update).  Same classification as the step
+// kernels: partners on the self-conjugate planes a_x in {0, nx/2} carry the
+// conjugate of their canonical mode.
+__global__ void k_draw_noise(int nx, int ny, int nz, int hx, int cplx, int R, int rep0, uint64_t seed,
+                             long long step, float2* out) {
+    const long long nm = (long long)hx * nz * ny;
+    const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (m >= nm) return;
+    const int ay = (int)(m % ny), az = (int)((m / ny) % nz), ax = (int)(m / ((long long)ny * nz));
+    int cz = az, cy = ay;
+    bool selfc = false, partner = false;
+    if (!cplx && (ax == 0 || 2 * ax == nx)) {
+        const int mz = (nz - az) % nz, my = (ny - ay) % ny;
+        if (az > mz || (az == mz && ay > my)) {
+            partner = true;
+            cz = mz;
+            cy = my;
+        } else if (az == mz && ay == my) {
+            selfc = true;
+        }
+    }
+    const uint64_t j = ((uint64_t)ax * nz + cz) * ny + cy;
+    float2 eta = fourier_noise(seed, j, (uint32_t)step, (uint32_t)(rep0 + r), selfc);
+    if (partner) eta = cconj(eta);
+    out[(size_t)r * nm + m] = eta;
+}
+
+cudaError_t launch_draw_noise(int nx, int ny, int nz, int hx, int cplx, int R, int rep0, uint64_t seed,
+                              long long step, float2* out, cudaStream_t s) {
+    const long long nm = (long long)hx * nz * ny;
+    dim3 grid((unsigned)((nm + 255) / 256), R);
+    k_draw_noise<<<grid, 256, 0, s>>>(nx, ny, nz, hx, cplx, R, rep0, seed, step, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sft

@@ -1,0 +1,59 @@
+"""The C-ABI library loads without a GPU and exports every entry point that
+include/sft.h declares; configuration validation needs no device."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sft.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sft_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2511_22510_gb300 as sft
+    from paper_2511_22510_gb300 import _build
+    _build.build()
+    return sft
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("sft_create", "sft_step", "sft_observe", "sft_tangent_step", "sft_adjoint", "sft_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    L = lib.load_library()
+    for name in _declared():
+        assert hasattr(L, name), name
+    assert sorted(lib.ABI_FUNCTIONS) == _declared()
+
+
+@pytest.mark.parametrize("bad", [
+    dict(d=4), dict(n=[48, 48]), dict(replicas=0), dict(h=0.0), dict(h=float("nan")), dict(model=9),
+    dict(scheme=5), dict(dealias=2),
+])
+def test_invalid_configs_rejected_before_any_device_call(lib, bad):
+    kw = dict(d=2, n=[64, 64], dx=[1.0, 1.0], replicas=1, model=0, p=[1, -0.5, 1, 0.5], scheme=1, h=0.01,
+              seed=1)
+    kw.update(bad)
+    cfg = lib.make_config(min(kw["d"], 2), kw["n"], kw["dx"], kw["replicas"], kw["model"], kw["p"],
+                          kw["scheme"], kw["h"], kw["seed"], dealias=kw.get("dealias", 1))
+    if bad.get("d") == 4:
+        cfg.d = 4
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_create(cfg)
+    assert ei.value.status == lib.SFT_EINVAL
+
+
+def test_unsupported_configs_report_unsupported(lib):
+    cfg = lib.make_config(2, [64, 32], [1.0, 1.0], 1, 0, [1, -0.5, 1, 0.5], 1, 0.01, 1)
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_create(cfg)
+    assert ei.value.status == lib.SFT_EUNSUPPORTED

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances: noise normals bit-identical; fields relative L2 <= 1e-5 after the
+stated number of steps (the FP32 target of the method's accuracy gate);
+transforms and observables at FP32 rounding (<= 2e-6 relative); the Model B
+zero mode and graph-vs-plain / checkpoint resumes bit-identical.
+"""
+import numpy as np
+import pytest
+
+import sft_inputs as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sft():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_22510_gb300 as m
+    m.load_library()
+    return m
+
+
+def gpu_stepper(sft, w, replicas=None):
+    return sft.Stepper(w.d, w.n, w.dx, replicas or w.replicas, w.model, w.p, w.scheme, w.h, w.seed,
+                       dealias=w.dealias)
+
+
+def oracle_for(oracle_mod, w, replicas=None):
+    return oracle_mod.Oracle(w.d, w.n, w.dx, replicas or w.replicas, w.model, w.p, w.scheme, w.h, w.seed,
+                             dealias=w.dealias)
+
+
+def half_xmajor(full, complex_field):
+    """Oracle full spectrum (shape (..., ny, nx)) -> the library's stored layout
+    (HX, [nz,] [ny]) with x-major ordering."""
+    nx = full.shape[-1]
+    hx = nx if complex_field else nx // 2 + 1
+    h = full[..., :hx]
+    return np.moveaxis(h, -1, 0)
+
+
+def start_pair(sft, oracle_mod, w, replicas=None, fields=None):
+    R = replicas or w.replicas
+    f0 = W.initial_fields(w, replicas=R) if fields is None else fields
+    dt = np.complex64 if w.complex_field else np.float32
+    f32 = f0.astype(dt)
+    g = gpu_stepper(sft, w, R)
+    g.set_field(f32)
+    o = oracle_for(oracle_mod, w, R)
+    for r in range(R):
+        o.set_field(r, f32[r].astype(np.complex128 if w.complex_field else np.float64))
+    return g, o
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ------------------------------------------------------------------ noise bits
+@pytest.mark.parametrize("w", [
+    W.model_a_64(n=[16, 16], replicas=3),
+    W.model_b_1024(n=[32, 32], replicas=2),
+    W.kpz_1d(64, replicas=2),
+    W.cgl_2048(n=[32], d=1, dx=[0.5], replicas=2),
+], ids=["2d16", "2d32", "1d64", "cgl1d32"])
+def test_noise_normals_bit_identical(sft, oracle_mod, w):
+    g = gpu_stepper(sft, w)
+    o = oracle_for(oracle_mod, w)
+    hx = g.hx
+    ny = w.n[1] if w.d > 1 else 1
+    nx = w.n[0]
+    # self-conjugate stored modes of a real field (App. B): a_x in {0, nx/2} and a_y in {0, ny/2}
+    selfc = np.zeros((hx, ny), dtype=bool)
+    if not w.complex_field:
+        for ax in (0, nx // 2):
+            for ay in ({0, ny // 2} if ny > 1 else {0}):
+                selfc[ax, ay] = True
+    selfc = selfc.reshape(g.spec_shape[1:])
+    r2 = np.float32(float.fromhex('0x1.6a09e6p-1'))
+    for step in (0, 7, 123456):
+        eg = g.noise(step)
+        for r in range(w.replicas):
+            eo = half_xmajor(o.noise(r, step), w.complex_field)
+            # the oracle widens the float normals: self-conjugate eta = z_a, others (z_a + i z_b)/sqrt2;
+            # recover z_a, z_b exactly and apply the library's single-precision scaling.
+            za = np.where(selfc, eo.real, eo.real * np.sqrt(2.0)).astype(np.float32)
+            zb = (eo.imag * np.sqrt(2.0)).astype(np.float32)
+            exp_re = np.where(selfc, za, za * r2).astype(np.float32)
+            exp_im = np.where(selfc, np.float32(0), zb * r2).astype(np.float32)
+            got = eg[r]
+            assert np.array_equal(got.real, exp_re), np.abs(got.real - exp_re).max()
+            assert np.array_equal(got.imag, exp_im), np.abs(got.imag - exp_im).max()
+    g.close()
+
+
+# ------------------------------------------------------------------ transforms
+@pytest.mark.parametrize("w", [
+    W.model_a_64(n=[64, 64], replicas=3), W.model_a_64(n=[256, 256]), W.kpz_1d(1024, replicas=2, sigma0=1.0),
+    W.cgl_2048(n=[128], d=1, dx=[0.5], replicas=2),
+], ids=["2d64", "2d256", "1d1024", "cgl1d"])
+def test_forward_transform_and_roundtrip(sft, oracle_mod, w):
+    w = w.with_(sigma0=1.0)
+    g, o = start_pair(sft, oracle_mod, w)
+    spec = g.spectrum()
+    for r in range(w.replicas):
+        ref = half_xmajor(o.spectrum(r), w.complex_field)
+        assert rel_l2(spec[r], ref) < 2e-6
+    back = g.field()
+    f0 = W.initial_fields(w).astype(np.complex64 if w.complex_field else np.float32)
+    assert rel_l2(back, f0) < 2e-6
+    g.close()
+
+
+# ------------------------------------------------------------------ step parity
+CASES = [
+    ("cfg1_model_a_64_setd1", W.model_a_64(replicas=2), 100),
+    ("model_a_64_em", W.model_a_64(scheme=0, replicas=1), 100),
+    ("model_a_64_setd2", W.model_a_64(scheme=2, replicas=1), 100),
+    ("model_b_64_setd1", W.model_b_1024(n=[64, 64], replicas=2, sigma0=0.3), 100),
+    ("model_b_64_em_h01", W.model_b_1024(n=[64, 64], scheme=0, h=0.1, sigma0=0.3), 100),
+    ("model_b_64_setd2", W.model_b_1024(n=[64, 64], scheme=2, h=0.025, sigma0=0.3), 100),
+    ("model_b_128_setd1_R3", W.model_b_1024(n=[128, 128], replicas=3, sigma0=0.3), 40),
+    ("kpz_2d_32", W.kpz_2d(n=[32, 32], replicas=2), 100),
+    ("kpz_1d_256", W.kpz_1d(256, replicas=3), 100),
+    ("kpz_1d_4096", W.kpz_1d(4096, replicas=1), 50),
+    ("model_a_1d_128", W.model_a_64(d=1, n=[128], dx=[1.0], replicas=2), 100),
+    ("cgl_1d_64_setd2", W.cgl_2048(n=[64], d=1, dx=[0.5], replicas=2, p=[2.0, -0.5, 1e-3]), 100),
+    ("model_a_16_nodealias", W.model_a_64(n=[16, 16], dealias=0), 100),
+]
+
+
+@pytest.mark.parametrize("name,w,nsteps", CASES, ids=[c[0] for c in CASES])
+def test_step_parity(sft, oracle_mod, name, w, nsteps):
+    g, o = start_pair(sft, oracle_mod, w)
+    g.step(nsteps)
+    o.step(nsteps)
+    got = g.field()
+    for r in range(w.replicas):
+        e = rel_l2(got[r], o.field(r))
+        assert e <= 1e-5, (name, r, e)
+    spec = g.spectrum()
+    for r in range(w.replicas):
+        assert rel_l2(spec[r], half_xmajor(o.spectrum(r), w.complex_field)) <= 1e-5
+    g.close()
+
+
+def test_full_size_model_b_1024(sft, oracle_mod):
+    """The headline lattice (Model B 1024^2) in the bench's launch configuration:
+    a few steps, whole field against the oracle."""
+    w = W.model_b_1024(replicas=1, h=0.05)
+    g, o = start_pair(sft, oracle_mod, w)
+    g.step(4)
+    o.step(4)
+    assert rel_l2(g.field()[0], o.field(0)) <= 1e-5
+    g.close()
+
+
+def test_model_b_zero_mode_bitwise(sft):
+    w = W.model_b_1024(n=[64, 64], replicas=2, sigma0=0.3)
+    g = gpu_stepper(sft, w)
+    g.set_field(W.initial_fields(w).astype(np.float32))
+    s0 = g.spectrum()[:, 0, 0].copy()
+    g.step(37)
+    s1 = g.spectrum()[:, 0, 0]
+    assert np.array_equal(s0.view(np.uint64), s1.view(np.uint64))
+    g.close()
+
+
+def test_graph_and_plain_launches_bit_identical(sft):
+    w = W.model_b_1024(n=[64, 64], replicas=2, sigma0=0.3, scheme=2)
+    a = gpu_stepper(sft, w)
+    b = gpu_stepper(sft, w)
+    f = W.initial_fields(w).astype(np.float32)
+    a.set_field(f)
+    b.set_field(f)
+    a.step(53)
+    b.step_plain(53)
+    assert np.array_equal(a.spectrum().view(np.uint64), b.spectrum().view(np.uint64))
+    a.close()
+    b.close()
+
+
+def test_checkpoint_resume_bit_identical(sft):
+    w = W.model_a_64(n=[64, 64], replicas=2, scheme=2)
+    a = gpu_stepper(sft, w)
+    a.set_field(W.initial_fields(w).astype(np.float32))
+    a.step(20)
+    blob = a.checkpoint()
+    a.step(30)
+    ref = a.spectrum().copy()
+    b = gpu_stepper(sft, w)
+    b.restore(blob)
+    assert b.step_count == 20
+    b.step(30)
+    assert np.array_equal(b.spectrum().view(np.uint64), ref.view(np.uint64))
+    # a checkpoint of another configuration is refused
+    c = gpu_stepper(sft, w.with_(h=0.02))
+    with pytest.raises(sft.SftError) as ei:
+        c.restore(blob)
+    assert ei.value.status == sft.SFT_ECHECKPOINT
+    for x in (a, b, c):
+        x.close()
+
+
+def test_nonfinite_state_is_reported(sft):
+    w = W.model_a_64(n=[32, 32])
+    g = gpu_stepper(sft, w)
+    f = W.initial_fields(w).astype(np.float32)
+    f[0, 3, 5] = np.nan
+    g.set_field(f)
+    g.step(3)
+    with pytest.raises(sft.SftError) as ei:
+        g.sync()
+    assert ei.value.status == sft.SFT_ENONFINITE
+    g.close()
+
+
+def test_init_random_parity(sft, oracle_mod):
+    for w in (W.model_a_64(n=[64, 64], replicas=2), W.cgl_2048(n=[64], d=1, dx=[0.5], replicas=2)):
+        g = gpu_stepper(sft, w)
+        g.init_random(0.37)
+        o = oracle_for(oracle_mod, w)
+        o.init_random(0.37)
+        spec = g.spectrum()
+        for r in range(w.replicas):
+            assert rel_l2(spec[r], half_xmajor(o.spectrum(r), w.complex_field)) < 2e-6
+        g.close()
+
+
+# ------------------------------------------------------------------ observables
+def test_structure_factor_twotime_roughness(sft, oracle_mod):
+    w = W.kpz_2d(n=[64, 64], replicas=3, sigma0=0.5)
+    g, o = start_pair(sft, oracle_mod, w)
+    g.step(10)
+    o.step(10)
+    sk = g.observe(sft.SFT_OBS_SK)
+    ns = g.nshells()
+    ov, oc = o.shells(0)
+    assert np.array_equal(sk[ns:], oc)
+    assert np.allclose(sk[:ns], ov, rtol=2e-5, atol=1e-12 * np.abs(ov).max())
+    per = g.observe(sft.SFT_OBS_SK_REPLICAS).reshape(3, ns)
+    assert np.allclose(per.mean(0), sk[:ns], rtol=1e-9, atol=1e-15)
+    g.observe(sft.SFT_OBS_MARK)
+    o.mark()
+    g.step(5)
+    o.step(5)
+    ck = g.observe(sft.SFT_OBS_CKT)
+    oc2, _ = o.shells(1)
+    assert np.allclose(ck[:ns], oc2, rtol=3e-5, atol=1e-9 * np.abs(oc2).max())
+    rough = g.observe(sft.SFT_OBS_ROUGHNESS)
+    assert np.allclose(rough, o.roughness(), rtol=2e-5)
+    g.close()
