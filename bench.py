@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Throughput of the stochastic-ETD pseudo-spectral step on GB300.
+
+Workload (one bench step = one SETD step of every replica): Model B (conserved
+scalar field), d = 2, 1024 x 1024 periodic lattice, dx = 1, Gamma = 1, r = -1,
+u = 1, T = 0.1, SETD1, h = 0.05, 2/3 dealiasing, R replicas per GPU started
+from seeded iid N(0, 0.01^2) fields, with the shell-averaged structure factor
+S(k, t) taken every 100 steps inside the timed region.  Inputs are synthetic.
+
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun, one rank per GPU)
+shard replicas: every rank advances its own R replicas (disjoint Philox
+replica counters), no data-path collective; timing is the max over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sft_inputs as W  # noqa: E402
+
+METRIC = "Gsite-steps/s per GB300 + % HBM roofline, batched FP32 vs plain, at stated error"
+UNIT = "Gsite-steps/s"
+OBS_EVERY = 100
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=32)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--replicas", type=int, default=64)
+    ap.add_argument("--scheme", type=int, default=1)
+    ap.add_argument("--h", type=float, default=0.05)
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    return ap.parse_args()
+
+
+def workload(args):
+    return W.model_b_1024(n=[args.n, args.n], scheme=args.scheme, h=args.h, replicas=args.replicas)
+
+
+def scheme_name(s):
+    return {0: "SETD-EM", 1: "SETD1", 2: "SETD2"}[s]
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def algorithmic_bytes(w, scheme, ncols):
+    """Algorithmic HBM bytes per replica of each kernel of one step of the
+    two-pass design (x-major spectra, dealiased intermediates with ncols of the
+    nx/2+1 x-columns):
+      row pass:    read P, write Q                     (ncols * ny complex each)
+      column pass: read Q, read + write phi, write P   (phi: (nx/2+1) * ny complex)
+                   SETD2 adds read + write of F_prev on the ncols columns."""
+    nx, ny = w.n[0], w.n[1]
+    hx = nx // 2 + 1
+    c8 = 8
+    rows = 2 * ncols * ny * c8
+    cols = (2 * ncols + 2 * hx) * ny * c8
+    if scheme == 2:
+        cols += 2 * ncols * ny * c8
+    return rows, cols
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2511_22510_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel_tag):
+    """DRAM bytes per launch recorded by the ncu summary under profiles/, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    ent = rec.get(kernel_tag)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------- oracle
+def oracle_sample(w, nsteps, budget_s=25.0):
+    """FP64 oracle on one replica of the workload: returns (site-steps/s, steps
+    run, initial field, final field)."""
+    import oracle
+    oracle.build()
+    f0 = W.initial_fields(w, replicas=1)[0].astype(np.float32)
+    o = oracle.Oracle(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
+    o.set_field(0, f0.astype(np.float64))
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    done = 1
+    per = t1 - t0
+    more = max(0, min(nsteps - 1, int(budget_s / max(per, 1e-9)) - 1))
+    if more:
+        o.step(more)
+        done += more
+    el = time.perf_counter() - t0
+    return w.sites * done / el, done, f0, o.field(0)
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores: each timed step is one FP64
+    SETD step of one replica of the workload (a bounded sample), as many as fit
+    in about a minute."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = workload(args)
+    f0 = W.initial_fields(w, replicas=1)[0].astype(np.float32)
+    o = oracle.Oracle(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
+    o.set_field(0, f0.astype(np.float64))
+    if args.warmup > 0:
+        o.step(1)
+    times = []
+    t_start = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        o.step(1)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > 60.0:
+            break
+    el = sum(times)
+    value = w.sites * len(times) / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": len(times),
+        "warmup": 1 if args.warmup > 0 else 0, "ms_per_step": 1e3 * el / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "model_b_1024_%s_h%g" % (scheme_name(args.scheme), args.h),
+                   "lattice": "%dx%d" % (args.n, args.n), "replicas": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "FP64 serial oracle, %d single steps of one %dx%d replica (the GPU arm runs "
+                                   "%d replicas per step)" % (len(times), args.n, args.n, args.replicas)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import paper_2511_22510_gb300 as sft
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args)
+    R = args.replicas
+    stream = torch.cuda.Stream()
+    g = sft.Stepper(w.d, w.n, w.dx, R, w.model, w.p, w.scheme, w.h, w.seed, stream=stream.cuda_stream,
+                    replica0=rank * R)
+    f0 = W.initial_fields(w, replicas=R, seed_offset=rank).astype(np.float32)
+    g.set_field(f0)
+    ncols = sum(1 for c in range(w.n[0] // 2 + 1) if 3 * c < w.n[0])
+    rows_b, cols_b = algorithmic_bytes(w, w.scheme, ncols)
+    step_bytes_site = (rows_b + cols_b) / w.sites
+
+    # warm-up (also captures the step graph)
+    g.step(max(args.warmup, 3))
+    g.sync()
+    K = max(args.steps, 1)
+    n_obs = K // OBS_EVERY
+    l0 = sft.sft_kernel_launches(g.ctx)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        done = 0
+        while done < K:
+            n = min(OBS_EVERY, K - done)
+            g.step(n)
+            done += n
+            if n == OBS_EVERY:
+                g.observe(sft.SFT_OBS_SK)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = sft.sft_kernel_launches(g.ctx) - l0
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    units = w.sites * R * K * ws
+    value = units / (ms_max * 1e-3) / 1e9
+    clocks = clk.summary()
+
+    # per-kernel durations on the same stream (CUDA events around every launch)
+    prof = sft.sft_profile(g.ctx, 50)
+    kern = [("k2_rows_real", prof[0], rows_b * R), ("k2_cols_real", prof[1], cols_b * R)]
+    dom = max(kern, key=lambda k: k[1])
+    peak, peak_kind = measured_peak()
+    achieved = dom[2] / (dom[1] * 1e-3) / 1e9
+    tag = "%s_model_b_%d_R%d_%s" % (dom[0], w.n[0], R, scheme_name(w.scheme))
+    traffic = profile_traffic(tag)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom[0], "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "alg_bytes_per_launch": dom[2], "launch_ms": dom[1],
+                "kernels_ms": {k[0]: k[1] for k in kern}}
+    step_achieved = step_bytes_site * value  # GB/s over the whole step
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": max(args.warmup, 3),
+        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded iid N(0, 0.01^2) fields, Philox noise)",
+        "config": {"workload": "model_b_1024_%s_h%g" % (scheme_name(w.scheme), w.h), "model": "Model B",
+                   "lattice": "%dx%d" % (w.n[0], w.n[1]), "replicas_per_gpu": R, "global_batch": R * ws,
+                   "scheme": scheme_name(w.scheme), "h": w.h, "observe_every": OBS_EVERY,
+                   "parallelism": "replicas x%d" % ws,
+                   "l2": "working set %.0f MB > 129 MB L2, no flush" % (
+                       R * (w.n[0] // 2 + 1) * w.n[1] * 8 * 3 / 1e6)},
+        "roofline": roofline,
+        "step_roofline": {"bytes_per_site_step": step_bytes_site, "achieved_GBps": step_achieved,
+                          "frac": step_achieved / peak,
+                          "survey_24B_frac": 24.0 * value / peak},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.quick:
+        # plain unbatched form: one replica, host-launched kernels, no graph
+        p1 = sft.Stepper(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, stream=stream.cuda_stream)
+        p1.set_field(f0[:1])
+        p1.step_plain(10)
+        p1.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        p1.step_plain(200)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain = w.sites * 200 / (a.elapsed_time(b) * 1e-3) / 1e9
+        p1.close()
+        line["plain"] = {"value": plain, "unit": UNIT, "replicas": 1, "graph": False,
+                         "batched_speedup": value / plain}
+        # CPU oracle sample and the error of the GPU path against it on the same input
+        ov, od, of0, ofield = oracle_sample(w, 4, budget_s=20.0)
+        chk = sft.Stepper(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, stream=stream.cuda_stream)
+        chk.set_field(of0[None])
+        chk.step(od)
+        err = float(np.linalg.norm(chk.field()[0] - ofield) / np.linalg.norm(ofield))
+        chk.close()
+        line["cpu_baseline"] = {"value": ov / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "FP64 serial oracle, %d steps of one %dx%d replica" % (od, w.n[0], w.n[1])}
+        line["error_vs_fp64"] = {"rel_l2_field": err, "steps": od, "tolerance": 1e-5}
+    # end to end through the public API with host buffers (every rank)
+    pin = torch.from_numpy(f0).pin_memory()
+    host_in = pin.numpy()
+    chunks = 3
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    a.record(stream)
+    for _ in range(chunks):
+        sft.sft_set_field(g.ctx, -1, host_in)
+        g.step(OBS_EVERY)
+        sk = g.observe(sft.SFT_OBS_SK)
+    b.record(stream)
+    barrier()
+    te = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_val = w.sites * R * ws * OBS_EVERY * chunks / (float(te.item()) * 1e-3) / 1e9
+    line["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": f0.nbytes / OBS_EVERY,
+                   "d2h_bytes_per_step": sk.nbytes / OBS_EVERY,
+                   "note": "per chunk of 100 steps: set_field of all R fields from pinned host memory, "
+                           "the steps, S(k) back to the host"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -93,6 +93,8 @@ typedef struct {
     int dealias;       /* 1: 2/3-rule truncation (3|a_i| < n_i), 0: none */
     int precision;     /* 0: FP32 state and transforms (only value supported) */
     void* stream;      /* cudaStream_t, or NULL for the default stream */
+    int replica0;      /* global index of replica 0 (Philox counter word 2): ranks that shard one
+                          ensemble pass disjoint offsets; 0 for a stand-alone context */
 } sft_config;
 
 /* Observables for sft_observe (App. C; shells j = ceil(|a|), i.e. the shell
@@ -193,11 +195,23 @@ sft_status sft_restore(sft_ctx* ctx, const void* host_buf, size_t bytes);
  * multiplies it by the amplitude g_a.  Synchronises. */
 sft_status sft_draw_noise(sft_ctx* ctx, int64_t step, void* host_out, size_t bytes);
 
+/* Tracing: advance nsteps steps launching one kernel at a time, with CUDA
+ * events recorded on the context stream around every launch.  out_ms (cap >=
+ * kernels per step + 1) receives the mean duration in milliseconds of each
+ * kernel of the step in launch order (2-D: row pass, column pass; 1-D: the
+ * line kernel) followed by the mean step duration; *nkernels the kernel count.
+ * The state advances exactly as with sft_step_plain.  Synchronises. */
+sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, int* nkernels);
+
 /* Current step counter (steps taken since creation or restore). */
 sft_status sft_get_step(const sft_ctx* ctx, int64_t* step);
 
 /* Number of kernel launches the context issues per step (for accounting). */
 sft_status sft_launches_per_step(const sft_ctx* ctx, int* launches);
+
+/* Total kernels this context has launched since creation (kernel nodes of
+ * graph replays included). */
+sft_status sft_kernel_launches(const sft_ctx* ctx, int64_t* count);
 
 const char* sft_last_error(const sft_ctx* ctx);
 void sft_destroy(sft_ctx* ctx);

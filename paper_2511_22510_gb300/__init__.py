@@ -33,7 +33,7 @@ ABI_FUNCTIONS = [
     "sft_create", "sft_create_batch", "sft_set_field", "sft_init_random", "sft_get_field", "sft_get_spectrum",
     "sft_set_spectrum", "sft_step", "sft_step_plain", "sft_sync", "sft_observe", "sft_tangent_step",
     "sft_adjoint", "sft_set_checkpoint_interval", "sft_checkpoint", "sft_restore", "sft_get_step",
-    "sft_launches_per_step", "sft_draw_noise", "sft_last_error", "sft_destroy",
+    "sft_launches_per_step", "sft_kernel_launches", "sft_draw_noise", "sft_profile", "sft_last_error", "sft_destroy",
 ]
 
 
@@ -48,6 +48,7 @@ class sft_config(C.Structure):
         ("d", C.c_int), ("n", C.c_int * 3), ("dx", C.c_double * 3), ("replicas", C.c_int),
         ("model", C.c_int), ("p", C.c_double * 8), ("scheme", C.c_int), ("h", C.c_double),
         ("seed", C.c_uint64), ("dealias", C.c_int), ("precision", C.c_int), ("stream", C.c_void_p),
+        ("replica0", C.c_int),
     ]
 
 
@@ -83,6 +84,8 @@ def load_library(path: str = LIB_PATH):
     L.sft_get_step.argtypes = [vp, C.POINTER(i64)]
     L.sft_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.sft_draw_noise.argtypes = [vp, i64, vp, sz]
+    L.sft_kernel_launches.argtypes = [vp, C.POINTER(i64)]
+    L.sft_profile.argtypes = [vp, i64, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
     L.sft_last_error.argtypes = [vp]
     L.sft_last_error.restype = C.c_char_p
     L.sft_destroy.argtypes = [vp]
@@ -103,7 +106,8 @@ def _check(ctx, status: int):
 
 # ---------------------------------------------------------------- thin wrappers
 def make_config(d: int, n: Sequence[int], dx: Sequence[float], replicas: int, model: int, p: Sequence[float],
-                scheme: int, h: float, seed: int, dealias: int = 1, stream: Optional[int] = None) -> sft_config:
+                scheme: int, h: float, seed: int, dealias: int = 1, stream: Optional[int] = None,
+                replica0: int = 0) -> sft_config:
     cfg = sft_config()
     cfg.d = d
     for i in range(3):
@@ -119,6 +123,7 @@ def make_config(d: int, n: Sequence[int], dx: Sequence[float], replicas: int, mo
     cfg.dealias = dealias
     cfg.precision = 0
     cfg.stream = stream
+    cfg.replica0 = replica0
     return cfg
 
 
@@ -208,6 +213,12 @@ def sft_get_step(ctx) -> int:
     return v.value
 
 
+def sft_kernel_launches(ctx) -> int:
+    v = C.c_int64()
+    _check(ctx, load_library().sft_kernel_launches(ctx, C.byref(v)))
+    return v.value
+
+
 def sft_launches_per_step(ctx) -> int:
     v = C.c_int()
     _check(ctx, load_library().sft_launches_per_step(ctx, C.byref(v)))
@@ -217,6 +228,15 @@ def sft_launches_per_step(ctx) -> int:
 def sft_draw_noise(ctx, step: int, out: np.ndarray):
     _check(ctx, load_library().sft_draw_noise(ctx, int(step), out.ctypes.data, out.nbytes))
     return out
+
+
+def sft_profile(ctx, nsteps: int):
+    """Mean per-kernel and per-step durations (ms) over nsteps plain launches."""
+    out = np.zeros(8)
+    nk = C.c_int()
+    _check(ctx, load_library().sft_profile(ctx, int(nsteps), out.ctypes.data_as(C.POINTER(C.c_double)), 8,
+                                           C.byref(nk)))
+    return out[: nk.value + 1]
 
 
 # ---------------------------------------------------------------- convenience
@@ -229,8 +249,8 @@ class Stepper:
     arrays (see ``spectrum``).
     """
 
-    def __init__(self, d, n, dx, replicas, model, p, scheme, h, seed, dealias=1, stream=None):
-        self.cfg = make_config(d, n, dx, replicas, model, p, scheme, h, seed, dealias, stream)
+    def __init__(self, d, n, dx, replicas, model, p, scheme, h, seed, dealias=1, stream=None, replica0=0):
+        self.cfg = make_config(d, n, dx, replicas, model, p, scheme, h, seed, dealias, stream, replica0)
         self.ctx = sft_create(self.cfg)
         self.d, self.R = d, replicas
         self.n = [int(n[i]) for i in range(d)]

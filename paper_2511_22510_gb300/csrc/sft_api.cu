@@ -63,6 +63,7 @@ struct sft_ctx {
     bool warmed = false;
     int launches_per_step = 0;
     int ckpt_segment = 100;
+    long long launches = 0;
     std::string err;
 };
 
@@ -136,7 +137,9 @@ static sft_status forward_from_buffer(sft_ctx* ctx, int r0, int R) {
             a.tw_b = ctx->tw.get(ctx->nx);
         }
         CK(launch_k1_line(a, MODE_FWD, ctx->nl, ctx->stream));
+        ctx->launches += 1;
     } else {
+        ctx->launches += 2;
         a.ncols = ctx->hx;
         a.qout = ctx->Q + (size_t)r0 * ctx->nmodes;
         a.tw_a = ctx->tw.get(ctx->nx / 2);
@@ -165,7 +168,9 @@ static sft_status inverse_to_buffer(sft_ctx* ctx, const float2* src, int r0, int
             a.tw_b = ctx->tw.get(ctx->nx);
         }
         CK(launch_k1_line(a, MODE_INV, ctx->nl, ctx->stream));
+        ctx->launches += 1;
     } else {
+        ctx->launches += 2;
         a.ncols = ctx->hx;
         a.pout = ctx->Q + (size_t)r0 * ctx->nmodes;
         a.tw_a = ctx->tw.get(ctx->ny);
@@ -190,6 +195,7 @@ static sft_status prime(sft_ctx* ctx) {
     a.pyout = ctx->Py;
     a.tw_a = ctx->tw.get(ctx->ny);
     CK(launch_k2_cols(a, MODE_PRIME, ctx->nl, ctx->stream));
+    ctx->launches += 1;
     ctx->p_valid = true;
     return SFT_OK;
 }
@@ -273,6 +279,7 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
                    SFT_EUNSUPPORTED;
     }
     if (cfg->replicas < 1) return why = "replicas must be >= 1", SFT_EINVAL;
+    if (cfg->replica0 < 0) return why = "replica0 must be >= 0", SFT_EINVAL;
     if (!(cfg->h > 0) || !std::isfinite(cfg->h)) return why = "h must be positive and finite", SFT_EINVAL;
     if (cfg->model < SFT_MODEL_A || cfg->model > SFT_CGL) return why = "unknown model", SFT_EINVAL;
     if (cfg->scheme < SFT_SETD_EM || cfg->scheme > SFT_SETD2) return why = "unknown scheme", SFT_EINVAL;
@@ -313,6 +320,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     ctx->sites = (long long)ctx->nx * ctx->ny * ctx->nz;
     ctx->nmodes = (long long)ctx->hx * ctx->ny * ctx->nz;
     ctx->R = cfg->replicas;
+    ctx->rep0 = cfg->replica0;
     auto cleanup = [&](sft_status s) {
         sft_destroy(ctx);
         return s;
@@ -438,6 +446,7 @@ sft_status sft_init_random(sft_ctx* ctx, double sigma) {
     if (!ctx || !(sigma >= 0)) return SFT_EINVAL;
     CK(launch_init_random(ctx->real, ctx->cfield, ctx->sites, ctx->R, ctx->rep0, ctx->cfg.seed, (float)sigma,
                           ctx->stream));
+    ctx->launches += 1;
     sft_status s = forward_from_buffer(ctx, 0, ctx->R);
     if (s != SFT_OK) return s;
     if (ctx->cfg.scheme == SFT_SETD2) {
@@ -519,6 +528,7 @@ static sft_status step_impl(sft_ctx* ctx, int64_t nsteps, bool use_graph) {
                 if (s != SFT_OK) return s;
             }
             CK(launch_advance(ctx->dstep, kGraphChunk, ctx->stream));
+            ctx->launches += (long long)kGraphChunk * ctx->launches_per_step + 1;
             left -= kGraphChunk;
             ctx->warmed = true;
         }
@@ -528,6 +538,7 @@ static sft_status step_impl(sft_ctx* ctx, int64_t nsteps, bool use_graph) {
         }
         while (left >= kGraphChunk) {
             CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+            ctx->launches += (long long)kGraphChunk * ctx->launches_per_step + 1;
             left -= kGraphChunk;
         }
     }
@@ -535,6 +546,7 @@ static sft_status step_impl(sft_ctx* ctx, int64_t nsteps, bool use_graph) {
         sft_status s = enqueue_step(ctx, 0);
         if (s != SFT_OK) return s;
         CK(launch_advance(ctx->dstep, 1, ctx->stream));
+        ctx->launches += ctx->launches_per_step + 1;
     }
     ctx->step += nsteps;
     return SFT_OK;
@@ -585,12 +597,14 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
         o.kind = 1;
         o.shell_sum = ctx->dshell;
         CK(launch_observe(o, ctx->stream));
+        ctx->launches += 1;
         CK(cudaMemcpyAsync(sums.data(), ctx->dshell, nsum * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         sums2.resize(nsum);
         CK(cudaMemsetAsync(ctx->dshell, 0, nsum * sizeof(double), ctx->stream));
         o.kind = 2;
         CK(launch_observe(o, ctx->stream));
+        ctx->launches += 1;
         CK(cudaMemcpyAsync(sums2.data(), ctx->dshell, nsum * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         sft_status s = read_status(ctx);
         if (s != SFT_OK) return s;
@@ -613,6 +627,7 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
     o.shell_sum = ctx->dshell;
     o.rough = kind == SFT_OBS_ROUGHNESS ? ctx->drough : nullptr;
     CK(launch_observe(o, ctx->stream));
+    ctx->launches += 1;
     CK(cudaMemcpyAsync(sums.data(), ctx->dshell, nsum * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(rough.data(), ctx->drough, ctx->R * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     sft_status s = read_status(ctx);
@@ -740,6 +755,68 @@ sft_status sft_restore(sft_ctx* ctx, const void* host_buf, size_t bytes) {
     return SFT_OK;
 }
 
+// Per-kernel timing: nsteps steps launched one kernel at a time with CUDA
+// events around every launch on the context stream; out_ms receives the mean
+// duration of each kernel of the step in launch order (row pass, column pass;
+// or the line kernel in 1-D) followed by the mean whole-step duration.
+sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, int* nkernels) {
+    if (!ctx || !out_ms || nsteps < 1) return SFT_EINVAL;
+    const int nk = ctx->d == 1 ? 1 : 2;
+    if (cap < nk + 1) return fail(ctx, SFT_EINVAL, "output too small");
+    if (!ctx->p_valid) {
+        sft_status s = prime(ctx);
+        if (s != SFT_OK) return s;
+    }
+    std::vector<cudaEvent_t> ev((size_t)nsteps * (nk + 1));
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    for (int64_t i = 0; i < nsteps; ++i) {
+        cudaEvent_t* e = &ev[(size_t)i * (nk + 1)];
+        StepArgs a = base_args(ctx);
+        CK(cudaEventRecord(e[0], ctx->stream));
+        if (ctx->d == 1) {
+            if (ctx->cplx) {
+                a.tw_a = ctx->tw.get(ctx->nx);
+            } else {
+                a.tw_a = ctx->tw.get(ctx->nx / 2);
+                a.tw_b = ctx->tw.get(ctx->nx);
+            }
+            CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
+            CK(cudaEventRecord(e[1], ctx->stream));
+        } else {
+            a.pin = ctx->P;
+            a.pyin = ctx->Py;
+            a.qout = ctx->Q;
+            a.tw_a = ctx->tw.get(ctx->nx / 2);
+            a.tw_b = ctx->tw.get(ctx->nx);
+            CK(launch_k2_rows(a, MODE_STEP, ctx->nl, ctx->stream));
+            CK(cudaEventRecord(e[1], ctx->stream));
+            a.qin = ctx->Q;
+            a.pout = ctx->P;
+            a.pyout = ctx->Py;
+            a.tw_a = ctx->tw.get(ctx->ny);
+            CK(launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream));
+            CK(cudaEventRecord(e[2], ctx->stream));
+        }
+        CK(launch_advance(ctx->dstep, 1, ctx->stream));
+        ctx->launches += nk + 1;
+    }
+    ctx->step += nsteps;
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k <= nk; ++k) out_ms[k] = 0.0;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        cudaEvent_t* e = &ev[(size_t)i * (nk + 1)];
+        for (int k = 0; k < nk; ++k) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e[k], e[k + 1]));
+            out_ms[k] += ms / nsteps;
+            out_ms[nk] += ms / nsteps;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (nkernels) *nkernels = nk;
+    return read_status(ctx);
+}
+
 sft_status sft_draw_noise(sft_ctx* ctx, int64_t step, void* host_out, size_t bytes) {
     if (!ctx || !host_out || step < 0) return SFT_EINVAL;
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
@@ -759,6 +836,12 @@ sft_status sft_get_step(const sft_ctx* ctx, int64_t* step) {
 sft_status sft_launches_per_step(const sft_ctx* ctx, int* launches) {
     if (!ctx || !launches) return SFT_EINVAL;
     *launches = ctx->launches_per_step;
+    return SFT_OK;
+}
+
+sft_status sft_kernel_launches(const sft_ctx* ctx, int64_t* count) {
+    if (!ctx || !count) return SFT_EINVAL;
+    *count = ctx->launches;
     return SFT_OK;
 }
 
