@@ -17,7 +17,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsft.so")
+LIB_PATH = os.environ.get("SFT_LIB", os.path.join(_HERE, "libsft.so"))
 
 SFT_OK, SFT_EINVAL, SFT_ENOMEM, SFT_ECUDA, SFT_ENONFINITE, SFT_ETIMEOUT, SFT_EUNSUPPORTED, SFT_ECHECKPOINT = range(8)
 SFT_MODEL_A, SFT_MODEL_B, SFT_KPZ, SFT_CGL = 0, 1, 2, 3

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -64,6 +65,7 @@ struct sft_ctx {
     int launches_per_step = 0;
     int ckpt_segment = 100;
     long long launches = 0;
+    bool pipe_cols = false;  // pipelined (bulk-copy) column pass
     std::string err;
 };
 
@@ -200,6 +202,11 @@ static sft_status prime(sft_ctx* ctx) {
     return SFT_OK;
 }
 
+static cudaError_t launch_cols_step(const sft_ctx* ctx, const StepArgs& a) {
+    if (ctx->pipe_cols) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
+    return launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream);
+}
+
 // Enqueue the kernels of one step (k_in_chunk = k).
 static sft_status enqueue_step(sft_ctx* ctx, int k) {
     StepArgs a = base_args(ctx);
@@ -224,7 +231,7 @@ static sft_status enqueue_step(sft_ctx* ctx, int k) {
     a.pout = ctx->P;
     a.pyout = ctx->Py;
     a.tw_a = ctx->tw.get(ctx->ny);
-    CK(launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream));
+    CK(launch_cols_step(ctx, a));
     return SFT_OK;
 }
 
@@ -346,7 +353,9 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     }
     long long qmax = 0;
     for (int i = 0; i < ctx->d; ++i) qmax += (long long)(cfg->n[i] / 2) * (cfg->n[i] / 2);
-    const long long nq = qmax + 1;
+    long long nq = qmax + 1;  // d = 3: one entry per |a|^2
+    if (ctx->d == 1) nq = ctx->nx / 2 + 1;
+    if (ctx->d == 2) nq = (long long)(ctx->nx / 2 + 1) * (ctx->ny / 2 + 1);
     if (ok) ok = dalloc((void**)&ctx->tab, (size_t)nq * (ctx->cplx ? 2 : 1) * sizeof(float4));
     if (ok) ok = dalloc((void**)&ctx->dstep, 4 * sizeof(long long)) && dalloc((void**)&ctx->dstatus, sizeof(unsigned));
     ctx->nshells = (int)isqrt_ceil(qmax) + 1;
@@ -381,6 +390,8 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     t.model = cfg->model;
     t.scheme = cfg->scheme;
     t.complex_field = ctx->cplx;
+    t.d = ctx->d;
+    t.hy = ctx->ny / 2 + 1;
     for (int i = 0; i < 8; ++i) t.p[i] = cfg->p[i];
     t.h = cfg->h;
     t.dk = 2.0 * M_PI / (ctx->nx * cfg->dx[0]);
@@ -404,6 +415,13 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
         }
     }
     ctx->launches_per_step = ctx->d == 1 ? 1 : 2;
+    {
+        // column-pass variant: the multi-block kernel by default; SFT_COLUMN_PASS=pipelined selects
+        // the persistent bulk-copy pipelined kernel where it is built
+        const char* v = getenv("SFT_COLUMN_PASS");
+        const bool pipe = v && strcmp(v, "pipelined") == 0;
+        ctx->pipe_cols = ctx->d == 2 && pipe && k2_pipe_supported(ctx->nx, ctx->ny, ctx->cplx);
+    }
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cleanup(SFT_ECUDA);
     *out = ctx;
     return SFT_OK;
@@ -463,6 +481,7 @@ static sft_status read_status(sft_ctx* ctx) {
     CK(cudaMemcpyAsync(&st, ctx->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(&bad, ctx->dstep + 2, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (st & 2u) return fail(ctx, SFT_ETIMEOUT, "a bounded device-side wait ran out; the step was abandoned");
     if (st & 1u) {
         char buf[128];
         snprintf(buf, sizeof buf, "non-finite state first seen at step %lld", bad);
@@ -794,7 +813,7 @@ sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, in
             a.pout = ctx->P;
             a.pyout = ctx->Py;
             a.tw_a = ctx->tw.get(ctx->ny);
-            CK(launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream));
+            CK(launch_cols_step(ctx, a));
             CK(cudaEventRecord(e[2], ctx->stream));
         }
         CK(launch_advance(ctx->dstep, 1, ctx->stream));

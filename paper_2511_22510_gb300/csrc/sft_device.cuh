@@ -3,7 +3,7 @@
 // Box-Muller recipe (bit-reproducible: only correctly rounded IEEE operations
 // through the __f*_rn intrinsics, never contracted), and a shared-memory
 // Stockham FFT engine in which a team of T threads holds a line of N complex
-// values, E = 16 per thread, with warp/named-barrier synchronisation.
+// values (E per thread), with warp/named-barrier synchronisation.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -112,22 +112,39 @@ __device__ __forceinline__ float2 normal_pair_for_index(uint64_t seed, uint64_t 
 }
 
 // ------------------------------------------------------------- FFT engine
-// Compile-time plan: E = min(16, N) values per thread, T = N / E threads per
-// line; radix schedule 16, 16, ..., then the remainder (2, 4 or 8).
-template <int N>
+// Compile-time plan for an N-point line: E values per thread (32 for lines of
+// 512 points and more, else up to 16), T = N / E threads per line, and the
+// radix of every Stockham pass; every radix divides E, so each thread runs
+// E / R butterflies per pass.  Lines of 1024 points take two radix-32 passes
+// and a single shared-memory exchange.
+#ifndef SFT_EMAX
+#define SFT_EMAX 16
+#endif
+template <int N, int EM = SFT_EMAX>
 struct FftPlan {
     static_assert(N >= 2 && (N & (N - 1)) == 0, "power of two");
-    static constexpr int E = N < 16 ? N : 16;
-    static constexpr int T = N / E;
     static constexpr int log2(int v) { return v <= 1 ? 0 : 1 + log2(v / 2); }
     static constexpr int L = log2(N);
-    static constexpr int P = N <= 16 ? 1 : (L + 3) / 4;  // passes
-    static constexpr int radix(int p) { return N <= 16 ? N : (p < L / 4 ? 16 : (1 << (L % 4))); }
-    // padded exchange buffer (complex elements): pos(i) = i + i/16
-    static constexpr int BUF = P > 1 ? N + N / 16 : 1;
+    static constexpr int E = N <= 16 ? N : (N >= 512 ? EM : (N <= 32 && EM >= 32 ? N : 16));
+    static constexpr int T = N / E;
+    static constexpr int R0 = E;  // first radix
+    // remaining log2 after the first pass, split into radix-E passes and a remainder
+    static constexpr int LE = log2(E);
+    static constexpr int LR = L - log2(R0);
+    static constexpr int P = 1 + (LR + LE - 1) / LE;
+    static constexpr int radix(int p) {
+        return p == 0 ? R0 : (p < P - 1 ? E : (LR % LE == 0 ? E : (1 << (LR % LE))));
+    }
+    // padded exchange buffer: one pad element per R0 (first-pass radix) elements
+    static constexpr int PAD = R0 >= 16 ? R0 : 16;
+    static constexpr int BUF = N + N / PAD + 1;
 };
 
-__device__ __forceinline__ int xpos(int i) { return i + (i >> 4); }
+// padded position of element i in an exchange buffer of plan N
+template <int N, int EM = SFT_EMAX>
+__device__ __forceinline__ int xpos(int i) {
+    return i + i / FftPlan<N, EM>::PAD;
+}
 
 // Team barrier: teams of T <= 32 threads live inside one warp and use the
 // warp barrier (all lanes of the warp must take part); larger teams use a
@@ -142,27 +159,36 @@ __device__ __forceinline__ void team_sync() {
     }
 }
 
-// cos / sin of 2 pi m / 16
-__device__ constexpr float kCos16[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
-                                        0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
-                                        -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
-                                        0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
-__device__ constexpr float kSin16[16] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
-                                        1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
-                                        0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
-                                        -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f};
+// cos / sin of 2 pi m / 32
+__device__ constexpr float kCos32[32] = {
+    1.0f, 0.98078528040323044f, 0.92387953251128674f, 0.83146961230254524f, 0.70710678118654752f,
+    0.55557023301960218f, 0.38268343236508977f, 0.19509032201612826f, 0.0f, -0.19509032201612826f,
+    -0.38268343236508977f, -0.55557023301960218f, -0.70710678118654752f, -0.83146961230254524f,
+    -0.92387953251128674f, -0.98078528040323044f, -1.0f, -0.98078528040323044f, -0.92387953251128674f,
+    -0.83146961230254524f, -0.70710678118654752f, -0.55557023301960218f, -0.38268343236508977f,
+    -0.19509032201612826f, 0.0f, 0.19509032201612826f, 0.38268343236508977f, 0.55557023301960218f,
+    0.70710678118654752f, 0.83146961230254524f, 0.92387953251128674f, 0.98078528040323044f};
 
 // z * W_R^m with W_R = e^{-2 pi i / R} (forward) or its conjugate (inverse);
-// m and R are compile-time constants after unrolling.
+// m and R are compile-time constants after unrolling.  Angles are counted in
+// 32nds of a turn; quarter turns are swaps, odd multiples of 1/8 turn use the
+// (a +- b)/sqrt2 form.
 template <bool INV>
 __device__ __forceinline__ float2 twiddle_const(float2 z, int m, int R) {
-    const int q = (m * 16 / R) & 15;  // angle in sixteenths of a turn
+    const int q = (m * 32 / R) & 31;
     if (q == 0) return z;
-    if (q == 8) return make_float2(-z.x, -z.y);
-    if (q == 4) return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
-    if (q == 12) return INV ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
-    const float c = kCos16[q];
-    const float s = INV ? kSin16[q] : -kSin16[q];
+    if (q == 16) return make_float2(-z.x, -z.y);
+    if (q == 8) return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+    if (q == 24) return INV ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
+    const float c = kCos32[q];
+    const float sn = kCos32[(q + 24) & 31];  // sin(2 pi q / 32) = cos(2 pi (q - 8) / 32)
+    const float s = INV ? sn : -sn;
+    if ((q & 7) == 4) {
+        const float r = 0.70710678118654752f;
+        // c = +-r, s = +-r
+        return make_float2(r * ((c > 0 ? z.x : -z.x) - (s > 0 ? z.y : -z.y)),
+                           r * ((s > 0 ? z.x : -z.x) + (c > 0 ? z.y : -z.y)));
+    }
     return make_float2(z.x * c - z.y * s, z.x * s + z.y * c);
 }
 
@@ -176,7 +202,7 @@ __device__ constexpr int bitrev(int k) {
     return r;
 }
 
-// In-register DFT of R values (R = 1, 2, 4, 8, 16): radix-2 decimation in
+// In-register DFT of R values (R = 1, 2, 4, ..., 32): radix-2 decimation in
 // frequency, then the bit-reversal permutation (resolved at compile time).
 template <int R, bool INV>
 __device__ __forceinline__ void dft_reg(float2* x) {
@@ -205,11 +231,11 @@ __device__ __forceinline__ void dft_reg(float2* x) {
 // x[t + T e]; after the last pass it holds X[t + T e] in natural order.
 // Passes other than the last exchange through the padded team buffer `buf`.
 // tw: table of W_N^m = e^{-2 pi i m / N}, m in [0, N).
-template <int N, bool INV, int PASS, int NS>
+template <int N, bool INV, int PASS, int NS, int EM>
 struct StockhamPass {
-    static __device__ __forceinline__ void run(float2 (&v)[FftPlan<N>::E], float2* buf, int t,
+    static __device__ __forceinline__ void run(float2 (&v)[FftPlan<N, EM>::E], float2* buf, int t,
                                                const float2* __restrict__ tw) {
-        using PL = FftPlan<N>;
+        using PL = FftPlan<N, EM>;
         constexpr int E = PL::E, T = PL::T;
         constexpr int R = PL::radix(PASS);
         constexpr int NB = E / R;
@@ -224,7 +250,7 @@ struct StockhamPass {
                 if constexpr (FIRST)
                     x[b][r] = v[b + r * NB];
                 else
-                    x[b][r] = buf[xpos(j + r * (N / R))];
+                    x[b][r] = buf[xpos<N, EM>(j + r * (N / R))];
             }
             if constexpr (!FIRST) {
                 const int k = j % NS;
@@ -250,19 +276,19 @@ struct StockhamPass {
                 const int k = j % NS;
                 const int base = (j / NS) * NS * R + k;
 #pragma unroll
-                for (int s = 0; s < R; ++s) buf[xpos(base + s * NS)] = x[b][s];
+                for (int s = 0; s < R; ++s) buf[xpos<N, EM>(base + s * NS)] = x[b][s];
             }
             team_sync<T>();
-            StockhamPass<N, INV, PASS + 1, NS * R>::run(v, buf, t, tw);
+            StockhamPass<N, INV, PASS + 1, NS * R, EM>::run(v, buf, t, tw);
         }
     }
 };
 
 // Unnormalised N-point FFT of a line held by a team (forward: e^{-2 pi i}).
-template <int N, bool INV>
-__device__ __forceinline__ void fft_line(float2 (&v)[FftPlan<N>::E], float2* buf, int t,
+template <int N, bool INV, int EM = SFT_EMAX>
+__device__ __forceinline__ void fft_line(float2 (&v)[FftPlan<N, EM>::E], float2* buf, int t,
                                          const float2* __restrict__ tw) {
-    StockhamPass<N, INV, 0, 1>::run(v, buf, t, tw);
+    StockhamPass<N, INV, 0, 1, EM>::run(v, buf, t, tw);
 }
 
 }  // namespace sft

@@ -61,17 +61,32 @@ struct StepArgs {
 cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s);
+cudaError_t launch_k2_cols_pipe(const StepArgs& a, int nl, cudaStream_t s);
+bool k2_pipe_supported(int nx, int ny, int complex_field);
 bool k1_supported(int nx, int complex_field);
 bool k2_supported(int nx, int ny, int complex_field);
 
 // coefficient tables (FP64 on the device, stored as float)
+// Table layouts (entry index -> k^2 / dk^2):
+//   d = 1: entry i = |a|            -> i^2
+//   d = 2: entry i * (ny/2 + 1) + j,  i = |a_x|, j = |a_y|  -> i^2 + j^2
+//   d = 3: entry q = |a|^2          -> q
 struct TableArgs {
     int model, scheme, complex_field;
+    int d, hy;  // hy = ny/2 + 1 (d = 2)
     double p[8];
     double h, dk, noise_norm;
     long long nq;
     float4* out;
 };
+__host__ __device__ inline long long table_k2_index(int d, int hy, long long entry) {
+    if (d == 1) return entry * entry;
+    if (d == 2) {
+        const long long i = entry / hy, j = entry % hy;
+        return i * i + j * j;
+    }
+    return entry;
+}
 cudaError_t launch_build_table(const TableArgs& t, cudaStream_t s);
 
 // initial condition (Philox tag 1) into a real-space buffer

@@ -13,7 +13,7 @@ struct LineCfg {
     static constexpr int T = PL::T;
     static constexpr int LINES = T >= 128 ? 1 : 128 / T;
     static constexpr int THREADS = LINES * T;
-    static constexpr int XB = M + M / 16 + 1;
+    static constexpr int XB = PL::BUF;
     static constexpr size_t smem() { return sizeof(float2) * (size_t)LINES * XB; }
 };
 
@@ -80,13 +80,13 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
         fft_line<M, false>(z, xb, t, twM);
         team_sync<T>();
 #pragma unroll
-        for (int e = 0; e < E; ++e) xb[xpos(t + T * e)] = z[e];
+        for (int e = 0; e < E; ++e) xb[xpos<M>(t + T * e)] = z[e];
         team_sync<T>();
         float2 Xq[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int k = t + T * e;
-            Xq[e] = r2c_post(z[e], cconj(xb[xpos((M - k) & (M - 1))]), __ldg(&twN[k]));
+            Xq[e] = r2c_post(z[e], cconj(xb[xpos<M>((M - k) & (M - 1))]), __ldg(&twN[k]));
         }
         const float2 z0 = xb[0];
         const float2 XqM = make_float2(z0.x - z0.y, 0.f);
@@ -105,20 +105,23 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
             const bool first = (a.scheme == 2) && (step == *a.first_step);
             float2* fp = a.fprev + (size_t)rr * (M + 1);
             const uint32_t rep = (uint32_t)(a.rep0 + rr);
+            float2 zn0, zn1;
             // modes k = t + T e, then (thread 0) the Nyquist mode k = M
 #pragma unroll
             for (int e = 0; e <= E; ++e) {
+                if (e < E && (e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
                 if (e == E && t != 0) break;
                 const int k = (e < E) ? t + T * e : M;
                 const float2 xq = (e < E) ? Xq[e] : XqM;
                 const bool inm = !a.dealias || 3 * k < NX;
                 const int q = k * k;
                 const float2 F = inm ? cscale(xq, nl_prefactor(a, q).x) : czero();
-                const Coefs co = load_coefs<false>(a.tab, q, first);
+                const Coefs co = load_coefs<false>(a.tab, k, first);
                 const float2 phv = ph[k];
                 const float2 Fp = (a.scheme == 2) ? fp[k] : czero();
                 const bool selfc = (k == 0 || k == M);
-                const float2 eta = fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
+                const float2 eta = (e < E) ? eta_of((e & 1) ? zn1 : zn0, selfc)
+                                           : fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
                 float2 o = setd_update<false>(co, phv, F, Fp, eta);
                 if (selfc) o.y = 0.f;
                 if (valid) {
@@ -182,16 +185,17 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k1_cplx(const StepArgs a)
         float2* fp = a.fprev + (size_t)rr * N;
         const uint32_t rep = (uint32_t)(a.rep0 + rr);
         const float2 s = make_float2(a.s0, a.s0i);
+        float2 zn0, zn1;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
+            if ((e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
             const int k = t + T * e;
             const int ks = signed_idx(k, N);
             const bool inm = !a.dealias || 3 * abs(ks) < N;
             const float2 F = inm ? cmul(s, z[e]) : czero();
-            const Coefs co = load_coefs<true>(a.tab, ks * ks, first);
+            const Coefs co = load_coefs<true>(a.tab, abs(ks), first);
             const float2 Fp = (a.scheme == 2) ? fp[k] : czero();
-            const float2 eta = fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, false);
-            const float2 o = setd_update<true>(co, raw[e], F, Fp, eta);
+            const float2 o = setd_update<true>(co, raw[e], F, Fp, eta_of((e & 1) ? zn1 : zn0, false));
             if (valid) {
                 ph[k] = o;
                 if (a.scheme == 2) fp[k] = F;

@@ -15,36 +15,44 @@
 // the even/odd split (z[m] = x[2m] + i x[2m+1]).
 #include "sft_step_common.cuh"
 
+#ifndef SFT_CTA
+#define SFT_CTA 128
+#endif
+#ifndef SFT_MINB
+#define SFT_MINB 4  // minimum resident blocks per SM requested from the register allocator
+#endif
+#ifndef SFT_RPB
+#define SFT_RPB 4  // replicas per column-pass block: the column's table and twiddle reads then hit L1
+#endif
+
 namespace sft {
 
 template <int M>
 struct RowCfg {
     using PL = FftPlan<M>;
     static constexpr int T = PL::T;
-    static constexpr int ROWS = T >= 256 ? 1 : 256 / T;
+    static constexpr int ROWS = T >= SFT_CTA ? 1 : SFT_CTA / T;
     static constexpr int THREADS = ROWS * T;
-    static constexpr int TS = M + 1;               // odd row stride of the spectral tile
-    static constexpr int XB = M + M / 16 + 1;       // padded exchange buffer per team
-    static constexpr size_t smem(int ntile) { return sizeof(float2) * ((size_t)ntile * ROWS * TS + (size_t)ROWS * XB); }
+    // odd row stride of the spectral tile; a row also serves as its team's FFT exchange buffer
+    static constexpr int TS = PL::BUF | 1;
+    static constexpr size_t smem(int ntile) { return sizeof(float2) * (size_t)ntile * ROWS * TS; }
 };
 
 template <int M, int NL, int MODE>
-__global__ void __launch_bounds__(RowCfg<M>::THREADS) k2_rows_real(const StepArgs a) {
+__global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_MINB) k2_rows_real(const StepArgs a) {
     using C = RowCfg<M>;
     using PL = FftPlan<M>;
-    constexpr int T = PL::T, E = PL::E, ROWS = C::ROWS, TS = C::TS, XB = C::XB;
+    constexpr int T = PL::T, E = PL::E, ROWS = C::ROWS, TS = C::TS;
     constexpr bool GRAD = (NL == NL_GRAD2) && (MODE == MODE_STEP);
-    constexpr int NTILE = GRAD ? 2 : 1;
     extern __shared__ float2 sm[];
     float2* tile = sm;
-    float2* xbuf = sm + NTILE * ROWS * TS;
     const int team = threadIdx.x / T, t = threadIdx.x % T;
     const int rep = blockIdx.y;
     const int ny = a.ny, hx = a.hx, ncols = a.ncols;
     const int y0 = blockIdx.x * ROWS;
     const int y = y0 + team;
     const bool yok = y < ny;
-    float2* xb = xbuf + team * XB;
+    float2* xb = tile + team * TS;  // the team's own tile row doubles as its exchange buffer
     const float2* __restrict__ twM = a.tw_a;
     const float2* __restrict__ twN = a.tw_b;
     float2 z[E];
@@ -112,18 +120,22 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS) k2_rows_real(const StepArg
         fft_line<M, false>(z, xb, t, twM);
         team_sync<T>();
 #pragma unroll
-        for (int e = 0; e < E; ++e) xb[xpos(t + T * e)] = z[e];
+        for (int e = 0; e < E; ++e) xb[xpos<M>(t + T * e)] = z[e];
         team_sync<T>();
         float2* trow = tile + team * TS;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int k = t + T * e;
-            if (k < ncols) trow[k] = r2c_post(z[e], cconj(xb[xpos((M - k) & (M - 1))]), __ldg(&twN[k]));
+            z[e] = r2c_post(z[e], cconj(xb[xpos<M>((M - k) & (M - 1))]), __ldg(&twN[k]));
         }
-        if (t == 0 && M < ncols) {
-            const float2 z0 = xb[0];
-            trow[M] = make_float2(z0.x - z0.y, 0.f);
+        const float2 z0 = xb[0];
+        team_sync<T>();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            if (k < ncols) trow[k] = z[e];
         }
+        if (t == 0 && M < ncols) trow[M] = make_float2(z0.x - z0.y, 0.f);
         __syncthreads();
         for (int f = threadIdx.x; f < ROWS * ncols; f += blockDim.x) {
             const int c = f / ROWS, yy = f % ROWS;
@@ -136,9 +148,9 @@ template <int NY>
 struct ColCfg {
     using PL = FftPlan<NY>;
     static constexpr int T = PL::T;
-    static constexpr int COLS = T >= 256 ? 1 : 256 / T;
+    static constexpr int COLS = T >= SFT_CTA ? 1 : SFT_CTA / T;
     static constexpr int THREADS = COLS * T;
-    static constexpr int XB = NY + NY / 16 + 1;
+    static constexpr int XB = PL::BUF;
     static constexpr size_t smem() { return sizeof(float2) * (size_t)COLS * XB; }
 };
 
@@ -172,21 +184,23 @@ __device__ __forceinline__ void emit_p(const StepArgs& a, const float2 (&out)[Ff
 }
 
 template <int NY, int NL, int MODE>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS) k2_cols_real(const StepArgs a) {
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(const StepArgs a) {
     using C = ColCfg<NY>;
     using PL = FftPlan<NY>;
     constexpr int T = PL::T, E = PL::E, COLS = C::COLS, XB = C::XB;
     extern __shared__ float2 sm[];
     const int team = threadIdx.x / T, t = threadIdx.x % T;
-    const int rep = blockIdx.y;
     const int c = blockIdx.x * COLS + team;
     const bool valid = c < a.hx;
     const int cc = valid ? c : a.hx - 1;
     const int M = a.nx / 2;
     float2* xb = sm + team * XB;
-    const size_t colbase = ((size_t)rep * a.hx + cc) * NY;
     const float2* __restrict__ tw = a.tw_a;
     const bool plane = (cc == 0 || cc == M);
+    for (int ri = 0; ri < SFT_RPB; ++ri) {
+    const int rep = blockIdx.y * SFT_RPB + ri;
+    if (rep >= a.R) break;
+    const size_t colbase = ((size_t)rep * a.hx + cc) * NY;
     float2 v[E];
 
     if constexpr (MODE == MODE_FWD) {
@@ -196,13 +210,13 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS) k2_cols_real(const StepAr
         fft_line<NY, false>(v, xb, t, tw);
         team_sync<T>();
 #pragma unroll
-        for (int e = 0; e < E; ++e) xb[xpos(t + T * e)] = v[e];
+        for (int e = 0; e < E; ++e) xb[xpos<NY>(t + T * e)] = v[e];
         team_sync<T>();
         if (plane) {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int ay = t + T * e;
-                if (2 * ay > NY) v[e] = cconj(xb[xpos(NY - ay)]);
+                if (2 * ay > NY) v[e] = cconj(xb[xpos<NY>(NY - ay)]);
                 if (ay == 0 || 2 * ay == NY) v[e].y = 0.f;
             }
         }
@@ -232,34 +246,34 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS) k2_cols_real(const StepAr
         float2 out[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
+            if ((e & 1) == 0)
+                team_normal_pair<T>(a.seed, (uint64_t)cc * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
+                                    out[e + 1]);
             const int ay = t + T * e;
             const int ays = signed_idx(ay, NY);
             const int q = cc * cc + ays * ays;
             const bool inm = !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < NY);
             float2 F = czero();
             if (has_f && inm) F = cscale(v[e], nl_prefactor(a, q).x);
-            const Coefs co = load_coefs<false>(a.tab, q, first);
+            const Coefs co = load_coefs<false>(a.tab, cc * (NY / 2 + 1) + abs(ays), first);
             const float2 ph = a.phi[colbase + ay];
             float2 Fp = czero();
             if (a.scheme == 2 && has_f) Fp = a.fprev[colbase + ay];
-            const bool partner = plane && 2 * ay > NY;
             const bool selfc = plane && (ay == 0 || 2 * ay == NY);
-            const float2 eta = partner ? czero()
-                                       : fourier_noise(a.seed, (uint64_t)cc * NY + ay, (uint32_t)step,
-                                                       (uint32_t)(a.rep0 + rep), selfc);
-            out[e] = setd_update<false>(co, ph, F, Fp, eta);
+            // partners on the self-conjugate planes are overwritten by the fix-up below
+            out[e] = setd_update<false>(co, ph, F, Fp, eta_of(out[e], selfc));
             if (a.scheme == 2 && has_f && valid) a.fprev[colbase + ay] = F;
         }
         if (plane || T < 32) {
             team_sync<T>();
 #pragma unroll
-            for (int e = 0; e < E; ++e) xb[xpos(t + T * e)] = out[e];
+            for (int e = 0; e < E; ++e) xb[xpos<NY>(t + T * e)] = out[e];
             team_sync<T>();
             if (plane) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int ay = t + T * e;
-                    if (2 * ay > NY) out[e] = cconj(xb[xpos(NY - ay)]);
+                    if (2 * ay > NY) out[e] = cconj(xb[xpos<NY>(NY - ay)]);
                     if (ay == 0 || 2 * ay == NY) out[e].y = 0.f;
                 }
             }
@@ -280,6 +294,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS) k2_cols_real(const StepAr
         for (int e = 0; e < E; ++e) out[e] = has_p ? a.phi[colbase + t + T * e] : czero();
         emit_p<NY, NL>(a, out, has_p, cc, colbase, xb, t);
     }
+    }  // replicas
 }
 
 // ----------------------------------------------------------------- launchers
@@ -311,7 +326,7 @@ static cudaError_t run_cols(const StepArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid((a.hx + C::COLS - 1) / C::COLS, a.R);
+    dim3 grid((a.hx + C::COLS - 1) / C::COLS, (a.R + SFT_RPB - 1) / SFT_RPB);
     k2_cols_real<NY, NL, MODE><<<grid, C::THREADS, sm, s>>>(a);
     return cudaGetLastError();
 }

@@ -71,7 +71,8 @@ __device__ void phi12_cplx(double2 z, double2& p1, double2& p2) {
     }
 }
 
-// One entry per q = |a|^2 (isotropic lattice, k^2 = dk^2 q):
+// One entry per class of modes with equal |k| (isotropic lattice; see the
+// table layouts in sft_internal.h), k^2 = dk^2 |a|^2:
 //   z = c h, f1 = e^z;
 //   SETD-EM: A = h phi1(z), B = 0, g = nf sqrt(2 D h) e^{z/2}      (f3 G dW)
 //   SETD1:   A = h phi1(z), B = 0, g = nf sqrt(2 D h phi1(2 Re z))  (f4 G, exact I1)
@@ -81,7 +82,7 @@ __device__ void phi12_cplx(double2 z, double2& p1, double2& p2) {
 __global__ void k_build_table(const TableArgs t) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= t.nq) return;
-    const double k2 = t.dk * t.dk * (double)q;
+    const double k2 = t.dk * t.dk * (double)table_k2_index(t.d, t.hy, q);
     const double* p = t.p;
     double2 c = make_double2(0.0, 0.0);
     double D = 0.0;

@@ -64,6 +64,43 @@ __device__ __forceinline__ float2 fourier_noise(uint64_t seed, uint64_t j, uint3
     return make_float2(z.x * r2, z.y * r2);
 }
 
+// Normal pairs of two modes a team holds, j(e) = jbase + t + T e and j(e+1)
+// (jbase even, T even or 1, e even), with one Philox call per counter: the two
+// modes 2m, 2m+1 of counter m sit in lanes t, t^1 (or slots e, e+1 when
+// T = 1).  The even lane draws the counter of its mode at e, the odd lane the
+// counter of its mode at e+1; each keeps one Box-Muller pair and hands the
+// other to its partner lane with one shuffle.  Every lane of the warp must
+// call this (warp shuffles).
+template <int T>
+__device__ __forceinline__ void team_normal_pair(uint64_t seed, uint64_t jbase, int t, int e, uint32_t step,
+                                                 uint32_t replica, float2& z0, float2& z1) {
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    if constexpr (T == 1) {
+        const uint64_t j = jbase + e;
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 1), step, replica, 0u), key);
+        z0 = recipe_bm_pair(w.x, w.y);
+        z1 = recipe_bm_pair(w.z, w.w);
+    } else {
+        const bool odd = (t & 1) != 0;
+        const uint64_t j = jbase + t + (uint64_t)T * (e + (odd ? 1 : 0));
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 1), step, replica, 0u), key);
+        const float2 p0 = recipe_bm_pair(w.x, w.y), p1 = recipe_bm_pair(w.z, w.w);
+        const float2 send = odd ? p0 : p1;
+        float2 recv;
+        recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+        recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+        z0 = odd ? recv : p0;
+        z1 = odd ? p1 : recv;
+    }
+}
+
+// eta from a normal pair: self-conjugate modes real N(0,1), others (z0 + i z1)/sqrt2.
+__device__ __forceinline__ float2 eta_of(float2 z, bool selfc) {
+    if (selfc) return make_float2(z.x, 0.f);
+    const float r2 = 0x1.6a09e6p-1f;
+    return make_float2(z.x * r2, z.y * r2);
+}
+
 __device__ __forceinline__ long long current_step(const StepArgs& a) { return *a.step_base + a.k_in_chunk; }
 
 __device__ __forceinline__ void flag_nonfinite(const StepArgs& a, float2 v, long long step) {

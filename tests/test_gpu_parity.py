@@ -159,6 +159,22 @@ def test_full_size_model_b_1024(sft, oracle_mod):
     g.close()
 
 
+@pytest.mark.parametrize("w", [
+    W.model_b_1024(replicas=3, scheme=2, h=0.025, sigma0=0.3),
+    W.kpz_2d(n=[1024, 1024], replicas=2, sigma0=0.5),
+], ids=["model_b_1024_setd2_R3", "kpz_1024_R2"])
+def test_pipelined_column_pass_parity(sft, oracle_mod, w):
+    """Lattices with 1024-point columns run the bulk-copy pipelined column pass;
+    several replicas exercise its (column, replica) work distribution."""
+    g, o = start_pair(sft, oracle_mod, w)
+    g.step(3)
+    o.step(3)
+    got = g.field()
+    for r in range(w.replicas):
+        assert rel_l2(got[r], o.field(r)) <= 1e-5
+    g.close()
+
+
 def test_model_b_zero_mode_bitwise(sft):
     w = W.model_b_1024(n=[64, 64], replicas=2, sigma0=0.3)
     g = gpu_stepper(sft, w)
