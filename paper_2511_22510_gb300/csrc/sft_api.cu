@@ -3,6 +3,7 @@
 // observables, checkpoints and error reporting.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -52,8 +53,9 @@ struct sft_ctx {
     double* dshell = nullptr;
     double* drough = nullptr;
     Twiddles tw;
-    // tangent
-    float2 *dphi = nullptr, *dseed = nullptr;
+    // tangent / adjoint
+    float2 *dphi = nullptr, *dseed = nullptr, *dP = nullptr, *dQ = nullptr;
+    bool dp_valid = false;
     // host mirrors
     long long step = 0;
     long long first_step = -1;
@@ -125,10 +127,10 @@ static StepArgs base_args(const sft_ctx* c) {
 // ------------------------------------------------------------ transforms
 // state <- forward transform of the real-space buffer (c->real / c->cfield),
 // for R replicas starting at replica r0.
-static sft_status forward_from_buffer(sft_ctx* ctx, int r0, int R) {
+static sft_status forward_from_buffer(sft_ctx* ctx, int r0, int R, float2* dst = nullptr) {
     StepArgs a = base_args(ctx);
     a.R = R;
-    a.phi = ctx->phi + (size_t)r0 * ctx->nmodes;
+    a.phi = (dst ? dst : ctx->phi) + (size_t)r0 * ctx->nmodes;
     a.real_io = ctx->real + (size_t)r0 * ctx->sites;
     a.cplx_io = ctx->cfield ? ctx->cfield + (size_t)r0 * ctx->sites : nullptr;
     if (ctx->d == 1) {
@@ -151,7 +153,7 @@ static sft_status forward_from_buffer(sft_ctx* ctx, int r0, int R) {
         a.tw_a = ctx->tw.get(ctx->ny);
         CK(launch_k2_cols(a, MODE_FWD, ctx->nl, ctx->stream));
     }
-    ctx->p_valid = false;
+    if (!dst) ctx->p_valid = false;
     return SFT_OK;
 }
 
@@ -205,6 +207,30 @@ static sft_status prime(sft_ctx* ctx) {
 static cudaError_t launch_cols_step(const sft_ctx* ctx, const StepArgs& a) {
     if (ctx->pipe_cols) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
     return launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream);
+}
+
+// One primal step with explicit intermediates: reads P from pin, leaves the
+// next step's P in pout (2-D); used by the adjoint's segment recompute.
+static sft_status enqueue_step_io(sft_ctx* ctx, const float2* pin, float2* pout) {
+    StepArgs a = base_args(ctx);
+    if (ctx->d == 1) {
+        a.tw_a = ctx->tw.get(ctx->nx / 2);
+        a.tw_b = ctx->tw.get(ctx->nx);
+        CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
+    } else {
+        a.pin = pin;
+        a.qout = ctx->Q;
+        a.tw_a = ctx->tw.get(ctx->nx / 2);
+        a.tw_b = ctx->tw.get(ctx->nx);
+        CK(launch_k2_rows(a, MODE_STEP, ctx->nl, ctx->stream));
+        a.qin = ctx->Q;
+        a.pout = pout;
+        a.tw_a = ctx->tw.get(ctx->ny);
+        CK(launch_cols_step(ctx, a));
+    }
+    CK(launch_advance(ctx->dstep, 1, ctx->stream));
+    ctx->launches += ctx->launches_per_step + 1;
+    return SFT_OK;
 }
 
 // Enqueue the kernels of one step (k_in_chunk = k).
@@ -681,12 +707,221 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
     return SFT_OK;
 }
 
-sft_status sft_tangent_step(sft_ctx* ctx, const void*, int64_t, void*) {
-    return fail(ctx, SFT_EUNSUPPORTED, "tangent not built yet");
+static sft_status diff_supported(sft_ctx* ctx) {
+    if (ctx->cplx || ctx->nl != NL_CUBIC || ctx->cfg.scheme == SFT_SETD2 || ctx->d > 2)
+        return fail(ctx, SFT_EUNSUPPORTED,
+                    "tangent/adjoint are built for real fields with the cubic term (Model A/B), SETD-EM or SETD1, "
+                    "d <= 2");
+    const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
+    if (!ctx->dphi) {
+        CK(cudaMalloc(&ctx->dphi, ms));
+        CK(cudaMemsetAsync(ctx->dphi, 0, ms, ctx->stream));
+    }
+    if (!ctx->dseed) CK(cudaMalloc(&ctx->dseed, ms));
+    if (ctx->d == 2 && !ctx->dP) {
+        CK(cudaMalloc(&ctx->dP, ms));
+        CK(cudaMalloc(&ctx->dQ, ms));
+        CK(cudaMemsetAsync(ctx->dP, 0, ms, ctx->stream));
+        CK(cudaMemsetAsync(ctx->dQ, 0, ms, ctx->stream));
+    }
+    return SFT_OK;
 }
-sft_status sft_adjoint(sft_ctx* ctx, const void*, int64_t, void*) {
-    return fail(ctx, SFT_EUNSUPPORTED, "adjoint not built yet");
+
+static sft_status set_step_counter(sft_ctx* ctx, long long step) {
+    ctx->step = step;
+    CK(cudaMemcpyAsync(ctx->dstep, &step, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+    return SFT_OK;
 }
+
+// dst spectrum <- forward transform of R real-space fields at a device pointer
+static sft_status spectrum_from_device_field(sft_ctx* ctx, const void* dev_field, float2* dst) {
+    const size_t rs = (size_t)ctx->R * ctx->sites * sizeof(float);
+    CK(cudaMemcpyAsync(ctx->real, dev_field, rs, cudaMemcpyDeviceToDevice, ctx->stream));
+    sft_status s = forward_from_buffer(ctx, 0, ctx->R, dst);
+    if (s != SFT_OK) return s;
+    ctx->launches += ctx->d == 1 ? 1 : 2;
+    return SFT_OK;
+}
+
+static sft_status device_field_from_spectrum(sft_ctx* ctx, const float2* src, void* dev_field) {
+    sft_status s = inverse_to_buffer(ctx, src, 0, ctx->R);
+    if (s != SFT_OK) return s;
+    ctx->launches += ctx->d == 1 ? 1 : 2;
+    CK(cudaMemcpyAsync(dev_field, ctx->real, (size_t)ctx->R * ctx->sites * sizeof(float), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    return SFT_OK;
+}
+
+sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps, void* dphi_out_dev) {
+    if (!ctx || nsteps < 0) return SFT_EINVAL;
+    sft_status s = diff_supported(ctx);
+    if (s != SFT_OK) return s;
+    const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
+    if (dphi0_dev) {
+        s = spectrum_from_device_field(ctx, dphi0_dev, ctx->dphi);
+        if (s != SFT_OK) return s;
+        CK(cudaMemcpyAsync(ctx->dseed, ctx->dphi, ms, cudaMemcpyDeviceToDevice, ctx->stream));
+        ctx->dp_valid = false;
+    }
+    if (!ctx->p_valid) {
+        s = prime(ctx);
+        if (s != SFT_OK) return s;
+    }
+    if (ctx->d == 2 && !ctx->dp_valid) {
+        StepArgs a = base_args(ctx);
+        a.phi = ctx->dphi;
+        a.pout = ctx->dP;
+        a.tw_a = ctx->tw.get(ctx->ny);
+        CK(launch_k2_cols(a, MODE_PRIME, ctx->nl, ctx->stream));
+        ctx->launches += 1;
+        ctx->dp_valid = true;
+    }
+    for (int64_t i = 0; i < nsteps; ++i) {
+        StepArgs a = base_args(ctx);
+        a.dphi = ctx->dphi;
+        if (ctx->d == 1) {
+            a.tw_a = ctx->tw.get(ctx->nx / 2);
+            a.tw_b = ctx->tw.get(ctx->nx);
+            CK(launch_k1_line(a, MODE_TAN, ctx->nl, ctx->stream));
+            ctx->launches += 1;
+        } else {
+            a.pin = ctx->P;
+            a.dpin = ctx->dP;
+            a.qout = ctx->Q;
+            a.dqout = ctx->dQ;
+            a.tw_a = ctx->tw.get(ctx->nx / 2);
+            a.tw_b = ctx->tw.get(ctx->nx);
+            CK(launch_k2_rows(a, MODE_TAN, ctx->nl, ctx->stream));
+            a.qin = ctx->Q;
+            a.dqin = ctx->dQ;
+            a.pout = ctx->P;
+            a.dpout = ctx->dP;
+            a.tw_a = ctx->tw.get(ctx->ny);
+            CK(launch_k2_cols(a, MODE_TAN, ctx->nl, ctx->stream));
+            ctx->launches += 2;
+        }
+        CK(launch_advance(ctx->dstep, 1, ctx->stream));
+        ctx->launches += 1;
+    }
+    ctx->step += nsteps;
+    if (dphi_out_dev) {
+        s = device_field_from_spectrum(ctx, ctx->dphi, dphi_out_dev);
+        if (s != SFT_OK) return s;
+    }
+    return read_status(ctx);
+}
+
+sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* grad_dev) {
+    if (!ctx || !cot_dev || !grad_dev || nsteps < 1) return SFT_EINVAL;
+    sft_status s = diff_supported(ctx);
+    if (s != SFT_OK) return s;
+    const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
+    const int64_t K = ctx->ckpt_segment;
+    const int64_t nseg = (nsteps + K - 1) / K;
+    const long long step0 = ctx->step;
+    float2 *ckpt = nullptr, *traj = nullptr, *phiN = nullptr;
+    auto release = [&]() {
+        if (ckpt) cudaFree(ckpt);
+        if (traj) cudaFree(traj);
+        if (phiN) cudaFree(phiN);
+    };
+#define CKA(call)                                                                                     \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            release();                                                                                \
+            return fail(ctx, SFT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+        }                                                                                             \
+    } while (0)
+#define SKA(expr)                   \
+    do {                            \
+        sft_status s_ = (expr);     \
+        if (s_ != SFT_OK) {         \
+            release();              \
+            return s_;              \
+        }                           \
+    } while (0)
+    if (cudaMalloc(&ckpt, ms * (size_t)nseg) != cudaSuccess || cudaMalloc(&traj, ms * (size_t)(K + 1)) != cudaSuccess ||
+        cudaMalloc(&phiN, ms) != cudaSuccess) {
+        release();
+        return fail(ctx, SFT_ENOMEM, "adjoint checkpoint buffers");
+    }
+    // forward sweep: state at the start of every segment
+    for (int64_t sg = 0; sg < nseg; ++sg) {
+        CKA(cudaMemcpyAsync(ckpt + (size_t)sg * ctx->R * ctx->nmodes, ctx->phi, ms, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+        SKA(step_impl(ctx, std::min<int64_t>(K, nsteps - sg * K), true));
+    }
+    CKA(cudaMemcpyAsync(phiN, ctx->phi, ms, cudaMemcpyDeviceToDevice, ctx->stream));
+    // lambda_N
+    SKA(spectrum_from_device_field(ctx, cot_dev, ctx->dphi));
+    bool w_valid = false;
+    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+        const int64_t n0 = sg * K, len = std::min<int64_t>(K, nsteps - n0);
+        // recompute the segment, keeping each step's primal input
+        CKA(cudaMemcpyAsync(ctx->phi, ckpt + (size_t)sg * ctx->R * ctx->nmodes, ms, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+        SKA(set_step_counter(ctx, step0 + n0));
+        if (ctx->d == 2) {
+            StepArgs a = base_args(ctx);
+            a.pout = traj;
+            a.tw_a = ctx->tw.get(ctx->ny);
+            CKA(launch_k2_cols(a, MODE_PRIME, ctx->nl, ctx->stream));
+        }
+        for (int64_t i = 0; i < len; ++i) {
+            float2* slot = traj + (size_t)i * ctx->R * ctx->nmodes;
+            if (ctx->d == 1) {
+                CKA(cudaMemcpyAsync(slot, ctx->phi, ms, cudaMemcpyDeviceToDevice, ctx->stream));
+                SKA(enqueue_step_io(ctx, nullptr, nullptr));
+            } else {
+                SKA(enqueue_step_io(ctx, slot, slot + (size_t)ctx->R * ctx->nmodes));
+            }
+        }
+        // reverse sweep over the segment
+        for (int64_t i = len - 1; i >= 0; --i) {
+            float2* slot = traj + (size_t)i * ctx->R * ctx->nmodes;
+            StepArgs a = base_args(ctx);
+            a.dphi = ctx->dphi;
+            if (ctx->d == 1) {
+                a.phi = slot;
+                a.tw_a = ctx->tw.get(ctx->nx / 2);
+                a.tw_b = ctx->tw.get(ctx->nx);
+                CKA(launch_k1_line(a, MODE_ADJ, ctx->nl, ctx->stream));
+                ctx->launches += 1;
+            } else {
+                if (!w_valid) {
+                    a.dpout = ctx->dP;
+                    a.tw_a = ctx->tw.get(ctx->ny);
+                    CKA(launch_k2_cols(a, MODE_ADJ_PRIME, ctx->nl, ctx->stream));
+                    w_valid = true;
+                }
+                a.pin = slot;
+                a.dpin = ctx->dP;
+                a.dqout = ctx->dQ;
+                a.tw_a = ctx->tw.get(ctx->nx / 2);
+                a.tw_b = ctx->tw.get(ctx->nx);
+                CKA(launch_k2_rows(a, MODE_ADJ, ctx->nl, ctx->stream));
+                a.dqin = ctx->dQ;
+                a.dpout = ctx->dP;
+                a.tw_a = ctx->tw.get(ctx->ny);
+                CKA(launch_k2_cols(a, MODE_ADJ, ctx->nl, ctx->stream));
+                ctx->launches += 2;
+            }
+        }
+    }
+    SKA(device_field_from_spectrum(ctx, ctx->dphi, grad_dev));
+    // the primal ends at step0 + nsteps, as after nsteps of sft_step
+    CKA(cudaMemcpyAsync(ctx->phi, phiN, ms, cudaMemcpyDeviceToDevice, ctx->stream));
+    SKA(set_step_counter(ctx, step0 + nsteps));
+    ctx->p_valid = false;
+    ctx->dp_valid = false;
+    s = read_status(ctx);
+    release();
+#undef CKA
+#undef SKA
+    return s;
+}
+
 sft_status sft_set_checkpoint_interval(sft_ctx* ctx, int segment) {
     if (!ctx || segment < 1) return SFT_EINVAL;
     ctx->ckpt_segment = segment;
@@ -869,8 +1104,9 @@ const char* sft_last_error(const sft_ctx* ctx) { return ctx ? ctx->err.c_str() :
 void sft_destroy(sft_ctx* ctx) {
     if (!ctx) return;
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
-    void* bufs[] = {ctx->phi, ctx->fprev, ctx->P, ctx->Q, ctx->Py, ctx->snap, ctx->real, ctx->cfield, ctx->tab,
-                    ctx->dstep, ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev, ctx->dphi, ctx->dseed};
+    void* bufs[] = {ctx->phi,   ctx->fprev,  ctx->P,      ctx->Q,      ctx->Py,     ctx->snap, ctx->real,
+                    ctx->cfield, ctx->tab,   ctx->dstep,  ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev,
+                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

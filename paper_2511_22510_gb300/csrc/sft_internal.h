@@ -7,7 +7,7 @@
 namespace sft {
 
 enum Nonlinearity { NL_CUBIC = 0, NL_GRAD2 = 1, NL_CGL = 2, NL_NONE = 3 };
-enum KernelMode { MODE_STEP = 0, MODE_FWD = 1, MODE_INV = 2, MODE_TAN = 3, MODE_ADJ = 4, MODE_PRIME = 5 };
+enum KernelMode { MODE_STEP = 0, MODE_FWD = 1, MODE_INV = 2, MODE_TAN = 3, MODE_ADJ = 4, MODE_PRIME = 5, MODE_ADJ_PRIME = 6 };
 
 // Everything a step kernel needs, passed by value.
 struct StepArgs {

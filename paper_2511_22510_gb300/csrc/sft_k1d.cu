@@ -17,6 +17,26 @@ struct LineCfg {
     static constexpr size_t smem() { return sizeof(float2) * (size_t)LINES * XB; }
 };
 
+// R2C post-processing of a line held by a team: Xq[e] = X[t + T e] for the
+// N/2 = M lowest modes, XqM = the Nyquist mode (valid in every thread).
+template <int M>
+__device__ __forceinline__ void line_post(float2 (&z)[FftPlan<M>::E], float2* xb, int t,
+                                          const float2* __restrict__ twN, float2 (&Xq)[FftPlan<M>::E], float2& XqM) {
+    using PL = FftPlan<M>;
+    constexpr int T = PL::T, E = PL::E;
+    team_sync<T>();
+#pragma unroll
+    for (int e = 0; e < E; ++e) xb[xpos<M>(t + T * e)] = z[e];
+    team_sync<T>();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = t + T * e;
+        Xq[e] = r2c_post(z[e], cconj(xb[xpos<M>((M - k) & (M - 1))]), __ldg(&twN[k]));
+    }
+    const float2 z0 = xb[0];
+    XqM = make_float2(z0.x - z0.y, 0.f);
+}
+
 // Real field, N = 2M points.  Mode k of replica r sits at phi[r * (M + 1) + k].
 template <int M, int NL, int MODE>
 __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a) {
@@ -34,6 +54,88 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
     const float2* __restrict__ twN = a.tw_b;
     float2* ph = a.phi + (size_t)rr * (M + 1);
     float2 z[E];
+
+    if constexpr (MODE == MODE_TAN || MODE == MODE_ADJ) {
+        // TAN: primal step plus dphi <- f1 dphi + A M s DFT[3 psi^2 dpsi] (dpsi = IDFT(M dphi)).
+        // ADJ: lam <- f1 lam + M DFT[3 psi^2 w], w = IDFT(A s M lam), psi from the primal state phi.
+        static_assert(NL == NL_CUBIC, "tangent/adjoint: cubic term");
+        float2* dp = a.dphi + (size_t)rr * (M + 1);
+        const float sc = a.scale;
+        float2 zd[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            const bool i1 = !a.dealias || 3 * k < NX, i2 = !a.dealias || 3 * (M - k) < NX;
+            const float2 tw = __ldg(&twN[k]);
+            z[e] = c2r_pre(i1 ? cscale(ph[k], sc) : czero(), i2 ? cscale(ph[M - k], sc) : czero(), tw);
+            float w1 = sc, w2 = sc;
+            if constexpr (MODE == MODE_ADJ) {
+                w1 *= __ldg(&a.tab[k]).y * nl_prefactor(a, k * k).x;
+                w2 *= __ldg(&a.tab[M - k]).y * nl_prefactor(a, (M - k) * (M - k)).x;
+            }
+            zd[e] = c2r_pre(i1 ? cscale(dp[k], w1) : czero(), i2 ? cscale(dp[M - k], w2) : czero(), tw);
+        }
+        fft_line<M, true>(z, xb, t, twM);
+        fft_line<M, true>(zd, xb, t, twM);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float2 p = z[e];
+            zd[e] = make_float2(3.f * p.x * p.x * zd[e].x, 3.f * p.y * p.y * zd[e].y);
+            z[e] = make_float2(p.x * p.x * p.x, p.y * p.y * p.y);
+        }
+        fft_line<M, false>(zd, xb, t, twM);
+        float2 dXq[E];
+        float2 dXqM;
+        line_post<M>(zd, xb, t, twN, dXq, dXqM);
+        if constexpr (MODE == MODE_ADJ) {
+#pragma unroll
+            for (int e = 0; e <= E; ++e) {
+                if (e == E && t != 0) break;
+                const int k = (e < E) ? t + T * e : M;
+                const bool inm = !a.dealias || 3 * k < NX;
+                const float2 v = inm ? ((e < E) ? dXq[e] : dXqM) : czero();
+                const float f1 = __ldg(&a.tab[k]).x;
+                float2 o = make_float2(f1 * dp[k].x + v.x, f1 * dp[k].y + v.y);
+                if (k == 0 || k == M) o.y = 0.f;
+                if (valid) dp[k] = o;
+            }
+            return;
+        } else {
+            fft_line<M, false>(z, xb, t, twM);
+            float2 Xq[E];
+            float2 XqM;
+            line_post<M>(z, xb, t, twN, Xq, XqM);
+            const long long step = current_step(a);
+            const uint32_t rep = (uint32_t)(a.rep0 + rr);
+            float2 zn0, zn1;
+#pragma unroll
+            for (int e = 0; e <= E; ++e) {
+                if (e < E && (e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
+                if (e == E && t != 0) break;
+                const int k = (e < E) ? t + T * e : M;
+                const bool inm = !a.dealias || 3 * k < NX;
+                const float sq = nl_prefactor(a, k * k).x;
+                const float2 F = inm ? cscale((e < E) ? Xq[e] : XqM, sq) : czero();
+                const float2 dF = inm ? cscale((e < E) ? dXq[e] : dXqM, sq) : czero();
+                const Coefs co = load_coefs<false>(a.tab, k, false);
+                const bool selfc = (k == 0 || k == M);
+                const float2 eta = (e < E) ? eta_of((e & 1) ? zn1 : zn0, selfc)
+                                           : fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
+                float2 o = setd_update<false>(co, ph[k], F, czero(), eta);
+                float2 d = setd_update<false>(co, dp[k], dF, czero(), czero());
+                if (selfc) {
+                    o.y = 0.f;
+                    d.y = 0.f;
+                }
+                if (valid) {
+                    ph[k] = o;
+                    dp[k] = d;
+                    flag_nonfinite(a, o, step);
+                }
+            }
+            return;
+        }
+    }
 
     if constexpr (MODE == MODE_FWD) {
         const float* src = a.real_io + (size_t)rr * NX;
@@ -239,6 +341,8 @@ static cudaError_t k1r_for(const StepArgs& a, int mode, int nl, cudaStream_t s) 
     if (mode == MODE_INV) return run_k1_real<M, NL_CUBIC, MODE_INV>(a, s);
     if (mode == MODE_STEP && nl == NL_CUBIC) return run_k1_real<M, NL_CUBIC, MODE_STEP>(a, s);
     if (mode == MODE_STEP && nl == NL_GRAD2) return run_k1_real<M, NL_GRAD2, MODE_STEP>(a, s);
+    if (mode == MODE_TAN && nl == NL_CUBIC) return run_k1_real<M, NL_CUBIC, MODE_TAN>(a, s);
+    if (mode == MODE_ADJ && nl == NL_CUBIC) return run_k1_real<M, NL_CUBIC, MODE_ADJ>(a, s);
     return cudaErrorInvalidValue;
 }
 

@@ -27,6 +27,33 @@
 
 namespace sft {
 
+// R2C post-processing of one row held by a team (z = FFT_M of the packed real
+// line) into the spectral row trow[0..ncols); xb is the team's exchange buffer
+// (it may alias trow).
+template <int M>
+__device__ __forceinline__ void row_post(float2 (&z)[FftPlan<M>::E], float2* xb, float2* trow, int ncols, int t,
+                                         const float2* __restrict__ twN) {
+    using PL = FftPlan<M>;
+    constexpr int T = PL::T, E = PL::E;
+    team_sync<T>();
+#pragma unroll
+    for (int e = 0; e < E; ++e) xb[xpos<M>(t + T * e)] = z[e];
+    team_sync<T>();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = t + T * e;
+        z[e] = r2c_post(z[e], cconj(xb[xpos<M>((M - k) & (M - 1))]), __ldg(&twN[k]));
+    }
+    const float2 z0 = xb[0];
+    team_sync<T>();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = t + T * e;
+        if (k < ncols) trow[k] = z[e];
+    }
+    if (t == 0 && M < ncols) trow[M] = make_float2(z0.x - z0.y, 0.f);
+}
+
 template <int M>
 struct RowCfg {
     using PL = FftPlan<M>;
@@ -44,6 +71,7 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_MINB) k2_rows_real(con
     using PL = FftPlan<M>;
     constexpr int T = PL::T, E = PL::E, ROWS = C::ROWS, TS = C::TS;
     constexpr bool GRAD = (NL == NL_GRAD2) && (MODE == MODE_STEP);
+    static_assert(!((MODE == MODE_TAN || MODE == MODE_ADJ) && NL != NL_CUBIC), "tangent/adjoint: cubic term");
     extern __shared__ float2 sm[];
     float2* tile = sm;
     const int team = threadIdx.x / T, t = threadIdx.x % T;
@@ -57,6 +85,57 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_MINB) k2_rows_real(con
     const float2* __restrict__ twN = a.tw_b;
     float2 z[E];
 
+    if constexpr (MODE == MODE_TAN || MODE == MODE_ADJ) {
+        // tangent: q' = 3 psi^2 dpsi next to q = psi^3; adjoint: v = 3 psi^2 w.
+        // tile 0: primal P (psi), tile 1: tangent dP (dpsi) or adjoint W.
+        for (int f = threadIdx.x; f < ROWS * (M + 1); f += blockDim.x) {
+            const int c = f / ROWS, yy = f % ROWS;
+            float2 v0 = czero(), v1 = czero();
+            if (c < ncols && y0 + yy < ny) {
+                const size_t off = ((size_t)rep * hx + c) * ny + y0 + yy;
+                v0 = a.pin[off];
+                v1 = a.dpin[off];
+            }
+            tile[yy * TS + c] = v0;
+            tile[ROWS * TS + yy * TS + c] = v1;
+        }
+        __syncthreads();
+        const float2* trow = tile + team * TS;
+        float2* drow = tile + ROWS * TS + team * TS;
+        float2 zd[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            const float2 tw = __ldg(&twN[k]);
+            z[e] = c2r_pre(trow[k], trow[M - k], tw);
+            zd[e] = c2r_pre(drow[k], drow[M - k], tw);
+        }
+        fft_line<M, true>(z, xb, t, twM);
+        fft_line<M, true>(zd, xb, t, twM);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float2 p = z[e];
+            zd[e] = make_float2(3.f * p.x * p.x * zd[e].x, 3.f * p.y * p.y * zd[e].y);
+            if constexpr (MODE == MODE_TAN) z[e] = make_float2(p.x * p.x * p.x, p.y * p.y * p.y);
+        }
+        fft_line<M, false>(zd, xb, t, twM);
+        // second output first: its post-processing uses tile row 0 as the exchange buffer
+        row_post<M>(zd, xb, drow, ncols, t, twN);
+        if constexpr (MODE == MODE_TAN) {
+            fft_line<M, false>(z, xb, t, twM);
+            row_post<M>(z, xb, tile + team * TS, ncols, t, twN);
+        }
+        __syncthreads();
+        for (int f = threadIdx.x; f < ROWS * ncols; f += blockDim.x) {
+            const int c = f / ROWS, yy = f % ROWS;
+            if (y0 + yy < ny) {
+                const size_t off = ((size_t)rep * hx + c) * ny + y0 + yy;
+                a.dqout[off] = tile[ROWS * TS + yy * TS + c];
+                if constexpr (MODE == MODE_TAN) a.qout[off] = tile[yy * TS + c];
+            }
+        }
+        return;
+    }
     if constexpr (MODE == MODE_FWD) {
         const float* src = a.real_io + ((size_t)rep * ny + (yok ? y : 0)) * (2 * M);
 #pragma unroll
@@ -153,6 +232,29 @@ struct ColCfg {
     static constexpr int XB = PL::BUF;
     static constexpr size_t smem() { return sizeof(float2) * (size_t)COLS * XB; }
 };
+
+// Hermitian fix-up of one column held by a team on the planes a_x in {0, nx/2}:
+// partners (a_y > ny/2) take the conjugate of a_y' = ny - a_y, self-conjugate
+// modes drop their imaginary part.  Warp-uniform when teams share a warp.
+template <int NY>
+__device__ __forceinline__ void fixup_plane(float2 (&out)[FftPlan<NY>::E], float2* xb, int t, bool plane) {
+    using PL = FftPlan<NY>;
+    constexpr int T = PL::T, E = PL::E;
+    if (plane || T < 32) {
+        team_sync<T>();
+#pragma unroll
+        for (int e = 0; e < E; ++e) xb[xpos<NY>(t + T * e)] = out[e];
+        team_sync<T>();
+        if (plane) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ay = t + T * e;
+                if (2 * ay > NY) out[e] = cconj(xb[xpos<NY>(NY - ay)]);
+                if (ay == 0 || 2 * ay == NY) out[e].y = 0.f;
+            }
+        }
+    }
+}
 
 // P <- IFFT_y(M phi / N^2) for one column (and, for KPZ, P_y <- IFFT_y(i k_y M phi / N^2)):
 // the dealiased input of the next row pass.
@@ -286,6 +388,98 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(co
             }
         }
         emit_p<NY, NL>(a, out, valid && cc < a.ncols, cc, colbase, xb, t);
+    } else if constexpr (MODE == MODE_TAN) {
+        // primal step as in MODE_STEP, plus the tangent dphi <- f1 dphi + A M s DFT[q'] (no noise)
+        if (!valid && T >= 32) return;
+        const long long step = current_step(a);
+        const bool has_f = valid && cc < a.ncols;
+        float2 dv[E];
+        if (has_f || T < 32) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                v[e] = has_f ? a.qin[colbase + t + T * e] : czero();
+                dv[e] = has_f ? a.dqin[colbase + t + T * e] : czero();
+            }
+            fft_line<NY, false>(v, xb, t, tw);
+            fft_line<NY, false>(dv, xb, t, tw);
+        }
+        float2 out[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if ((e & 1) == 0)
+                team_normal_pair<T>(a.seed, (uint64_t)cc * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
+                                    out[e + 1]);
+            const int ay = t + T * e;
+            const int ays = signed_idx(ay, NY);
+            const int q = cc * cc + ays * ays;
+            const bool inm = !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < NY);
+            const float sq = nl_prefactor(a, q).x;
+            const float2 F = (has_f && inm) ? cscale(v[e], sq) : czero();
+            const float2 dF = (has_f && inm) ? cscale(dv[e], sq) : czero();
+            const Coefs co = load_coefs<false>(a.tab, cc * (NY / 2 + 1) + abs(ays), false);
+            const bool selfc = plane && (ay == 0 || 2 * ay == NY);
+            out[e] = setd_update<false>(co, a.phi[colbase + ay], F, czero(), eta_of(out[e], selfc));
+            dv[e] = setd_update<false>(co, a.dphi[colbase + ay], dF, czero(), czero());
+        }
+        fixup_plane<NY>(out, xb, t, plane);
+        fixup_plane<NY>(dv, xb, t, plane);
+        if (valid) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                a.phi[colbase + t + T * e] = out[e];
+                a.dphi[colbase + t + T * e] = dv[e];
+                flag_nonfinite(a, out[e], step);
+            }
+        }
+        emit_p<NY, NL>(a, out, valid && cc < a.ncols, cc, colbase, xb, t);
+        StepArgs b = a;
+        b.pout = a.dpout;
+        emit_p<NY, NL>(b, dv, valid && cc < a.ncols, cc, colbase, xb, t);
+    } else if constexpr (MODE == MODE_ADJ || MODE == MODE_ADJ_PRIME) {
+        // adjoint: lam <- f1 lam + M DFT[v] (v from the row pass), then W = IDFT_y(A s M lam / N^2)
+        if (!valid && T >= 32) return;
+        const bool has_f = valid && cc < a.ncols;
+        float2 lam[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) lam[e] = a.dphi[colbase + t + T * e];
+        if constexpr (MODE == MODE_ADJ) {
+            if (has_f || T < 32) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[e] = has_f ? a.dqin[colbase + t + T * e] : czero();
+                fft_line<NY, false>(v, xb, t, tw);
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ay = t + T * e;
+                const int ays = signed_idx(ay, NY);
+                const bool inm = !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < NY);
+                const float f1 = __ldg(&a.tab[cc * (NY / 2 + 1) + abs(ays)]).x;
+                const float2 dv = (has_f && inm) ? v[e] : czero();
+                lam[e] = make_float2(f1 * lam[e].x + dv.x, f1 * lam[e].y + dv.y);
+            }
+            fixup_plane<NY>(lam, xb, t, plane);
+            if (valid) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) a.dphi[colbase + t + T * e] = lam[e];
+            }
+        }
+        const bool has_p = valid && cc < a.ncols;
+        if (has_p || T < 32) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ay = t + T * e;
+                const int ays = signed_idx(ay, NY);
+                const int q = cc * cc + ays * ays;
+                const bool inm = !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < NY);
+                const Coefs co = load_coefs<false>(a.tab, cc * (NY / 2 + 1) + abs(ays), false);
+                v[e] = (has_p && inm) ? cscale(lam[e], co.A.x * nl_prefactor(a, q).x * a.scale) : czero();
+            }
+            fft_line<NY, true>(v, xb, t, tw);
+            if (has_p) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) a.dpout[colbase + t + T * e] = v[e];
+            }
+        }
     } else if constexpr (MODE == MODE_PRIME) {
         if (!valid && T >= 32) return;
         const bool has_p = valid && cc < a.ncols;
@@ -301,7 +495,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(co
 template <int M, int NL, int MODE>
 static cudaError_t run_rows(const StepArgs& a, cudaStream_t s) {
     using C = RowCfg<M>;
-    constexpr int NTILE = (NL == NL_GRAD2 && MODE == MODE_STEP) ? 2 : 1;
+    constexpr int NTILE = ((NL == NL_GRAD2 && MODE == MODE_STEP) || MODE == MODE_TAN || MODE == MODE_ADJ) ? 2 : 1;
     const size_t sm = C::smem(NTILE);
     static bool attr = false;
     if (!attr) {
@@ -337,6 +531,8 @@ static cudaError_t rows_for(const StepArgs& a, int mode, int nl, cudaStream_t s)
     if (mode == MODE_INV) return run_rows<M, NL_CUBIC, MODE_INV>(a, s);
     if (mode == MODE_STEP && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_STEP>(a, s);
     if (mode == MODE_STEP && nl == NL_GRAD2) return run_rows<M, NL_GRAD2, MODE_STEP>(a, s);
+    if (mode == MODE_TAN && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_TAN>(a, s);
+    if (mode == MODE_ADJ && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_ADJ>(a, s);
     return cudaErrorInvalidValue;
 }
 
@@ -348,6 +544,9 @@ static cudaError_t cols_for(const StepArgs& a, int mode, int nl, cudaStream_t s)
     if (mode == MODE_STEP && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_STEP>(a, s);
     if (mode == MODE_PRIME && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_PRIME>(a, s);
     if (mode == MODE_PRIME && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_PRIME>(a, s);
+    if (mode == MODE_TAN && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_TAN>(a, s);
+    if (mode == MODE_ADJ && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_ADJ>(a, s);
+    if (mode == MODE_ADJ_PRIME && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_ADJ_PRIME>(a, s);
     return cudaErrorInvalidValue;
 }
 
