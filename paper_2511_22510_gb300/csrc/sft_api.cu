@@ -124,6 +124,24 @@ static StepArgs base_args(const sft_ctx* c) {
     return a;
 }
 
+// Row pass: in 3-D the pair (z, y) is the row index of the x-major layout.
+static cudaError_t launch_rows(const sft_ctx* ctx, StepArgs a, int mode) {
+    a.ny = ctx->ny * ctx->nz;
+    a.nz = 1;
+    return launch_k2_rows(a, mode, ctx->nl, ctx->stream);
+}
+
+// Second pass: columns (2-D) or a_x planes (3-D).
+static cudaError_t launch_second(const sft_ctx* ctx, const StepArgs& a, int mode) {
+    if (ctx->d == 3) return launch_k3_planes(a, mode, ctx->nl, ctx->stream);
+    return launch_k2_cols(a, mode, ctx->nl, ctx->stream);
+}
+
+static cudaError_t launch_cols_step(const sft_ctx* ctx, const StepArgs& a) {
+    if (ctx->pipe_cols) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
+    return launch_second(ctx, a, MODE_STEP);
+}
+
 // ------------------------------------------------------------ transforms
 // state <- forward transform of the real-space buffer (c->real / c->cfield),
 // for R replicas starting at replica r0.
@@ -148,10 +166,10 @@ static sft_status forward_from_buffer(sft_ctx* ctx, int r0, int R, float2* dst =
         a.qout = ctx->Q + (size_t)r0 * ctx->nmodes;
         a.tw_a = ctx->tw.get(ctx->nx / 2);
         a.tw_b = ctx->tw.get(ctx->nx);
-        CK(launch_k2_rows(a, MODE_FWD, ctx->nl, ctx->stream));
+        CK(launch_rows(ctx, a, MODE_FWD));
         a.qin = a.qout;
         a.tw_a = ctx->tw.get(ctx->ny);
-        CK(launch_k2_cols(a, MODE_FWD, ctx->nl, ctx->stream));
+        CK(launch_second(ctx, a, MODE_FWD));
     }
     if (!dst) ctx->p_valid = false;
     return SFT_OK;
@@ -178,11 +196,11 @@ static sft_status inverse_to_buffer(sft_ctx* ctx, const float2* src, int r0, int
         a.ncols = ctx->hx;
         a.pout = ctx->Q + (size_t)r0 * ctx->nmodes;
         a.tw_a = ctx->tw.get(ctx->ny);
-        CK(launch_k2_cols(a, MODE_INV, ctx->nl, ctx->stream));
+        CK(launch_second(ctx, a, MODE_INV));
         a.pin = a.pout;
         a.tw_a = ctx->tw.get(ctx->nx / 2);
         a.tw_b = ctx->tw.get(ctx->nx);
-        CK(launch_k2_rows(a, MODE_INV, ctx->nl, ctx->stream));
+        CK(launch_rows(ctx, a, MODE_INV));
     }
     return SFT_OK;
 }
@@ -198,16 +216,12 @@ static sft_status prime(sft_ctx* ctx) {
     a.pout = ctx->P;
     a.pyout = ctx->Py;
     a.tw_a = ctx->tw.get(ctx->ny);
-    CK(launch_k2_cols(a, MODE_PRIME, ctx->nl, ctx->stream));
+    CK(launch_second(ctx, a, MODE_PRIME));
     ctx->launches += 1;
     ctx->p_valid = true;
     return SFT_OK;
 }
 
-static cudaError_t launch_cols_step(const sft_ctx* ctx, const StepArgs& a) {
-    if (ctx->pipe_cols) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
-    return launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream);
-}
 
 // One primal step with explicit intermediates: reads P from pin, leaves the
 // next step's P in pout (2-D); used by the adjoint's segment recompute.
@@ -222,7 +236,7 @@ static sft_status enqueue_step_io(sft_ctx* ctx, const float2* pin, float2* pout)
         a.qout = ctx->Q;
         a.tw_a = ctx->tw.get(ctx->nx / 2);
         a.tw_b = ctx->tw.get(ctx->nx);
-        CK(launch_k2_rows(a, MODE_STEP, ctx->nl, ctx->stream));
+        CK(launch_rows(ctx, a, MODE_STEP));
         a.qin = ctx->Q;
         a.pout = pout;
         a.tw_a = ctx->tw.get(ctx->ny);
@@ -252,7 +266,7 @@ static sft_status enqueue_step(sft_ctx* ctx, int k) {
     a.qout = ctx->Q;
     a.tw_a = ctx->tw.get(ctx->nx / 2);
     a.tw_b = ctx->tw.get(ctx->nx);
-    CK(launch_k2_rows(a, MODE_STEP, ctx->nl, ctx->stream));
+    CK(launch_rows(ctx, a, MODE_STEP));
     a.qin = ctx->Q;
     a.pout = ctx->P;
     a.pyout = ctx->Py;
@@ -322,7 +336,9 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
     if (cfg->d == 1 && !k1_supported(cfg->n[0], cplx)) return why = "1-D size outside the built plans", SFT_EUNSUPPORTED;
     if (cfg->d == 2 && !k2_supported(cfg->n[0], cfg->n[1], cplx))
         return why = "2-D size/field outside the built plans", SFT_EUNSUPPORTED;
-    if (cfg->d == 3) return why = "3-D lattices are not built", SFT_EUNSUPPORTED;
+    if (cfg->d == 3 && (cplx || cfg->model == SFT_KPZ || !k3_supported(cfg->n[0], cfg->n[1], cfg->n[2], cplx)))
+        return why = "3-D lattices are built for real fields with the cubic term and 16..128 points per axis",
+               SFT_EUNSUPPORTED;
     return SFT_OK;
 }
 
@@ -862,11 +878,11 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
         CKA(cudaMemcpyAsync(ctx->phi, ckpt + (size_t)sg * ctx->R * ctx->nmodes, ms, cudaMemcpyDeviceToDevice,
                             ctx->stream));
         SKA(set_step_counter(ctx, step0 + n0));
-        if (ctx->d == 2) {
+        if (ctx->d >= 2) {
             StepArgs a = base_args(ctx);
             a.pout = traj;
             a.tw_a = ctx->tw.get(ctx->ny);
-            CKA(launch_k2_cols(a, MODE_PRIME, ctx->nl, ctx->stream));
+            CKA(launch_second(ctx, a, MODE_PRIME));
         }
         for (int64_t i = 0; i < len; ++i) {
             float2* slot = traj + (size_t)i * ctx->R * ctx->nmodes;
@@ -1042,7 +1058,7 @@ sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, in
             a.qout = ctx->Q;
             a.tw_a = ctx->tw.get(ctx->nx / 2);
             a.tw_b = ctx->tw.get(ctx->nx);
-            CK(launch_k2_rows(a, MODE_STEP, ctx->nl, ctx->stream));
+            CK(launch_rows(ctx, a, MODE_STEP));
             CK(cudaEventRecord(e[1], ctx->stream));
             a.qin = ctx->Q;
             a.pout = ctx->P;

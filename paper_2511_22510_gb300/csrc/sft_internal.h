@@ -62,6 +62,8 @@ cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2_cols_pipe(const StepArgs& a, int nl, cudaStream_t s);
+cudaError_t launch_k3_planes(const StepArgs& a, int mode, int nl, cudaStream_t s);
+bool k3_supported(int nx, int ny, int nz, int complex_field);
 bool k2_pipe_supported(int nx, int ny, int complex_field);
 bool k1_supported(int nx, int complex_field);
 bool k2_supported(int nx, int ny, int complex_field);

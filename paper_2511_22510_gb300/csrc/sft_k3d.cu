@@ -1,0 +1,213 @@
+// sft_k3d.cu -- plane pass of the 3-D step (real fields, cubic term).
+//
+// Layout (x-major): spectrum phi[a_x][a_z][a_y], each a_x plane N x N
+// contiguous.  The x-direction (row) pass is the 2-D row pass with the pair
+// (z, y) as the row index.  This kernel holds one a_x plane of one replica in
+// shared memory and does, in order:
+//   y-FFT of the rows, z-FFT of the columns  -> DFT[q] on the plane;
+//   SETD update per mode (Philox noise, counter index (a_x nz + a_z) ny + a_y);
+//   Hermitian fix-up on the planes a_x in {0, nx/2}: the mode (a_z, a_y) is a
+//   partner when (a_z, a_y) is lexicographically above (-a_z, -a_y) mod N;
+//   dealiased inverse z- and y-FFTs -> the next step's row-pass input.
+#include "sft_step_common.cuh"
+
+namespace sft {
+
+template <int N>
+struct PlaneCfg {
+    using PL = FftPlan<N>;
+    static constexpr int T = PL::T;
+    static constexpr int TEAMS = T >= 256 ? 1 : 256 / T;
+    static constexpr int THREADS = TEAMS * T;
+    static constexpr int RS = N + 1;  // odd row stride of the plane
+    static constexpr int XB = PL::BUF;
+    static constexpr int ITERS = (N + TEAMS - 1) / TEAMS;  // lines per team per phase
+    static constexpr size_t smem() { return sizeof(float2) * ((size_t)N * RS + (size_t)TEAMS * XB); }
+};
+
+// FFT of every row (ROW = true) or column of the plane held in shared memory.
+template <int N, bool ROW, bool INV>
+__device__ __forceinline__ void plane_fft(float2* S, float2* xb, int team, int t, const float2* __restrict__ tw) {
+    using C = PlaneCfg<N>;
+    using PL = FftPlan<N>;
+    constexpr int T = PL::T, E = PL::E;
+    for (int it = 0; it < C::ITERS; ++it) {
+        const int line = team + it * C::TEAMS;
+        const int l = line < N ? line : N - 1;
+        float2 v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = ROW ? S[l * C::RS + t + T * e] : S[(t + T * e) * C::RS + l];
+        fft_line<N, INV>(v, xb, t, tw);
+        if (line < N) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if (ROW)
+                    S[l * C::RS + t + T * e] = v[e];
+                else
+                    S[(t + T * e) * C::RS + l] = v[e];
+            }
+        }
+        team_sync<T>();
+    }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs a) {
+    using C = PlaneCfg<N>;
+    using PL = FftPlan<N>;
+    constexpr int T = PL::T, E = PL::E, RS = C::RS;
+    extern __shared__ float2 sm[];
+    float2* S = sm;
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    float2* xb = sm + (size_t)N * RS + (size_t)team * C::XB;
+    const int c = blockIdx.x, rep = blockIdx.y;
+    const int M = a.nx / 2;
+    const size_t base = ((size_t)rep * a.hx + c) * (size_t)N * N;
+    const float2* __restrict__ tw = a.tw_a;
+    const bool plane = (c == 0 || c == M);
+
+    if constexpr (MODE == MODE_FWD || MODE == MODE_STEP) {
+        const bool has_f = (MODE == MODE_FWD) || c < a.ncols;
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x)
+            S[(f / N) * RS + f % N] = has_f ? a.qin[base + f] : czero();
+        __syncthreads();
+        if (has_f) {
+            plane_fft<N, true, false>(S, xb, team, t, tw);
+            __syncthreads();
+            plane_fft<N, false, false>(S, xb, team, t, tw);
+            __syncthreads();
+        }
+    } else {
+        // INV / PRIME: the (masked) state goes straight to the inverse transforms
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x) S[(f / N) * RS + f % N] = a.phi[base + f];
+        __syncthreads();
+    }
+
+    if constexpr (MODE == MODE_STEP) {
+        const long long step = current_step(a);
+        const bool first = (a.scheme == 2) && (step == *a.first_step);
+        const bool has_f = c < a.ncols;
+        for (int it = 0; it < C::ITERS; ++it) {
+            const int line = team + it * C::TEAMS;
+            const int az = line < N ? line : N - 1;
+            const int azs = signed_idx(az, N);
+#pragma unroll
+            for (int e = 0; e < E; e += 2) {
+                float2 zz[2];
+                team_normal_pair<T>(a.seed, ((uint64_t)c * N + az) * N, t, e, (uint32_t)step,
+                                    (uint32_t)(a.rep0 + rep), zz[0], zz[1]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ay = t + T * (e + h);
+                    const int ays = signed_idx(ay, N);
+                    const int q = c * c + ays * ays + azs * azs;
+                    const bool inm = !a.dealias || (3 * c < a.nx && 3 * abs(ays) < N && 3 * abs(azs) < N);
+                    const float2 F = (has_f && inm) ? cscale(S[az * RS + ay], nl_prefactor(a, q).x) : czero();
+                    const Coefs co = load_coefs<false>(a.tab, q, first);
+                    const size_t idx = base + (size_t)az * N + ay;
+                    float2 Fp = czero();
+                    if (a.scheme == 2 && has_f) Fp = a.fprev[idx];
+                    const int mz = (N - az) % N, my = (N - ay) % N;
+                    const bool selfc = plane && az == mz && ay == my;
+                    float2 o = setd_update<false>(co, a.phi[idx], F, Fp, eta_of(zz[h], selfc));
+                    if (selfc) o.y = 0.f;
+                    if (line < N) {
+                        if (a.scheme == 2 && has_f) a.fprev[idx] = F;
+                        S[az * RS + ay] = o;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (plane) {
+            // partners take the conjugate of their canonical mode (canonical entries are not written here)
+            for (int f = threadIdx.x; f < N * N; f += blockDim.x) {
+                const int az = f / N, ay = f % N;
+                const int mz = (N - az) % N, my = (N - ay) % N;
+                if (az > mz || (az == mz && ay > my)) S[az * RS + ay] = cconj(S[mz * RS + my]);
+            }
+            __syncthreads();
+        }
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x) {
+            const int az = f / N, ay = f % N;
+            const float2 o = S[az * RS + ay];
+            a.phi[base + f] = o;
+            flag_nonfinite(a, o, step);
+        }
+    }
+    if constexpr (MODE == MODE_FWD) {
+        if (plane) {
+            for (int f = threadIdx.x; f < N * N; f += blockDim.x) {
+                const int az = f / N, ay = f % N;
+                const int mz = (N - az) % N, my = (N - ay) % N;
+                if (az > mz || (az == mz && ay > my)) S[az * RS + ay] = cconj(S[mz * RS + my]);
+                if (az == mz && ay == my) S[az * RS + ay].y = 0.f;
+            }
+            __syncthreads();
+        }
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x) a.phi[base + f] = S[(f / N) * RS + f % N];
+        return;
+    } else {
+        // inverse transforms of M phi / N^3 (INV: no mask) -> row-pass input
+        const bool emit = (MODE == MODE_INV) || c < a.ncols;
+        if (!emit) return;  // whole block
+        __syncthreads();
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x) {
+            const int az = f / N, ay = f % N;
+            const bool inm = (MODE == MODE_INV) || !a.dealias ||
+                             (3 * c < a.nx && 3 * abs(signed_idx(ay, N)) < N && 3 * abs(signed_idx(az, N)) < N);
+            const float2 o = S[az * RS + ay];
+            S[az * RS + ay] = inm ? cscale(o, a.scale) : czero();
+        }
+        __syncthreads();
+        plane_fft<N, false, true>(S, xb, team, t, tw);
+        __syncthreads();
+        plane_fft<N, true, true>(S, xb, team, t, tw);
+        __syncthreads();
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x) a.pout[base + f] = S[(f / N) * RS + f % N];
+    }
+}
+
+template <int N, int MODE>
+static cudaError_t run_planes(const StepArgs& a, cudaStream_t s) {
+    using C = PlaneCfg<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k3_planes<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k3_planes<N, MODE><<<dim3(a.hx, a.R), C::THREADS, C::smem(), s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t planes_for(const StepArgs& a, int mode, cudaStream_t s) {
+    switch (mode) {
+        case MODE_STEP: return run_planes<N, MODE_STEP>(a, s);
+        case MODE_FWD: return run_planes<N, MODE_FWD>(a, s);
+        case MODE_INV: return run_planes<N, MODE_INV>(a, s);
+        case MODE_PRIME: return run_planes<N, MODE_PRIME>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool k3_supported(int nx, int ny, int nz, int complex_field) {
+    if (complex_field || ny != nz) return false;
+    auto ok = [](int n) { return n == 16 || n == 32 || n == 64 || n == 128; };
+    return ok(ny) && nx >= 16 && nx <= 4096 && (nx & (nx - 1)) == 0;
+}
+
+cudaError_t launch_k3_planes(const StepArgs& a, int mode, int nl, cudaStream_t s) {
+    if (nl != NL_CUBIC) return cudaErrorInvalidValue;
+    switch (a.ny) {
+        case 16: return planes_for<16>(a, mode, s);
+        case 32: return planes_for<32>(a, mode, s);
+        case 64: return planes_for<64>(a, mode, s);
+        case 128: return planes_for<128>(a, mode, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sft

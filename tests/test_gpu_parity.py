@@ -66,19 +66,22 @@ def rel_l2(a, b):
     W.model_b_1024(n=[32, 32], replicas=2),
     W.kpz_1d(64, replicas=2),
     W.cgl_2048(n=[32], d=1, dx=[0.5], replicas=2),
-], ids=["2d16", "2d32", "1d64", "cgl1d32"])
+    W.model_a_128_3d(n=[16, 16, 16], replicas=2),
+], ids=["2d16", "2d32", "1d64", "cgl1d32", "3d16"])
 def test_noise_normals_bit_identical(sft, oracle_mod, w):
     g = gpu_stepper(sft, w)
     o = oracle_for(oracle_mod, w)
     hx = g.hx
     ny = w.n[1] if w.d > 1 else 1
+    nz = w.n[2] if w.d > 2 else 1
     nx = w.n[0]
-    # self-conjugate stored modes of a real field (App. B): a_x in {0, nx/2} and a_y in {0, ny/2}
-    selfc = np.zeros((hx, ny), dtype=bool)
+    # self-conjugate stored modes of a real field (App. B): a_x in {0, nx/2}, a_z in {0, nz/2}, a_y in {0, ny/2}
+    selfc = np.zeros((hx, nz, ny), dtype=bool)
     if not w.complex_field:
         for ax in (0, nx // 2):
-            for ay in ({0, ny // 2} if ny > 1 else {0}):
-                selfc[ax, ay] = True
+            for az in ({0, nz // 2} if nz > 1 else {0}):
+                for ay in ({0, ny // 2} if ny > 1 else {0}):
+                    selfc[ax, az, ay] = True
     selfc = selfc.reshape(g.spec_shape[1:])
     r2 = np.float32(float.fromhex('0x1.6a09e6p-1'))
     for step in (0, 7, 123456):
@@ -100,8 +103,9 @@ def test_noise_normals_bit_identical(sft, oracle_mod, w):
 # ------------------------------------------------------------------ transforms
 @pytest.mark.parametrize("w", [
     W.model_a_64(n=[64, 64], replicas=3), W.model_a_64(n=[256, 256]), W.kpz_1d(1024, replicas=2, sigma0=1.0),
-    W.cgl_2048(n=[128], d=1, dx=[0.5], replicas=2),
-], ids=["2d64", "2d256", "1d1024", "cgl1d"])
+    W.cgl_2048(n=[128], d=1, dx=[0.5], replicas=2), W.model_a_128_3d(n=[32, 32, 32], replicas=2),
+    W.model_a_128_3d(n=[128, 128, 128], replicas=1),
+], ids=["2d64", "2d256", "1d1024", "cgl1d", "3d32", "3d128"])
 def test_forward_transform_and_roundtrip(sft, oracle_mod, w):
     w = w.with_(sigma0=1.0)
     g, o = start_pair(sft, oracle_mod, w)
@@ -130,6 +134,10 @@ CASES = [
     ("model_a_1d_128", W.model_a_64(d=1, n=[128], dx=[1.0], replicas=2), 100),
     ("cgl_1d_64_setd2", W.cgl_2048(n=[64], d=1, dx=[0.5], replicas=2, p=[2.0, -0.5, 1e-3]), 100),
     ("model_a_16_nodealias", W.model_a_64(n=[16, 16], dealias=0), 100),
+    ("model_a_3d_16_setd1", W.model_a_128_3d(n=[16, 16, 16], replicas=2, sigma0=0.3), 60),
+    ("model_a_3d_32_setd2", W.model_a_128_3d(n=[32, 32, 32], replicas=1, sigma0=0.3, scheme=2), 30),
+    ("model_b_3d_32_em", W.model_a_128_3d(n=[32, 32, 32], model=1, p=[1.0, -0.5, 1.0, 0.2], scheme=0, h=0.02,
+                                          sigma0=0.3), 30),
 ]
 
 
@@ -171,6 +179,18 @@ def test_pipelined_column_pass_parity(sft, oracle_mod, w):
     o.step(3)
     got = g.field()
     for r in range(w.replicas):
+        assert rel_l2(got[r], o.field(r)) <= 1e-5
+    g.close()
+
+
+def test_full_size_model_a_128_3d(sft, oracle_mod):
+    """The 3-D linear-response lattice (Model A 128^3) for a few steps."""
+    w = W.model_a_128_3d(replicas=2, sigma0=0.3)
+    g, o = start_pair(sft, oracle_mod, w)
+    g.step(3)
+    o.step(3)
+    got = g.field()
+    for r in range(2):
         assert rel_l2(got[r], o.field(r)) <= 1e-5
     g.close()
 
