@@ -128,12 +128,17 @@ static StepArgs base_args(const sft_ctx* c) {
 static cudaError_t launch_rows(const sft_ctx* ctx, StepArgs a, int mode) {
     a.ny = ctx->ny * ctx->nz;
     a.nz = 1;
+    if (ctx->cplx) {
+        a.tw_a = ctx->tw.get(ctx->nx);
+        return launch_k2c_rows(a, mode, ctx->stream);
+    }
     return launch_k2_rows(a, mode, ctx->nl, ctx->stream);
 }
 
 // Second pass: columns (2-D) or a_x planes (3-D).
 static cudaError_t launch_second(const sft_ctx* ctx, const StepArgs& a, int mode) {
     if (ctx->d == 3) return launch_k3_planes(a, mode, ctx->nl, ctx->stream);
+    if (ctx->cplx) return launch_k2c_cols(a, mode, ctx->stream);
     return launch_k2_cols(a, mode, ctx->nl, ctx->stream);
 }
 
@@ -334,8 +339,8 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
     if (cfg->dealias != 0 && cfg->dealias != 1) return why = "dealias must be 0 or 1", SFT_EINVAL;
     const int cplx = cfg->model == SFT_CGL;
     if (cfg->d == 1 && !k1_supported(cfg->n[0], cplx)) return why = "1-D size outside the built plans", SFT_EUNSUPPORTED;
-    if (cfg->d == 2 && !k2_supported(cfg->n[0], cfg->n[1], cplx))
-        return why = "2-D size/field outside the built plans", SFT_EUNSUPPORTED;
+    if (cfg->d == 2 && !(cplx ? k2c_supported(cfg->n[0], cfg->n[1]) : k2_supported(cfg->n[0], cfg->n[1], 0)))
+        return why = "2-D size outside the built plans", SFT_EUNSUPPORTED;
     if (cfg->d == 3 && (cplx || cfg->model == SFT_KPZ || !k3_supported(cfg->n[0], cfg->n[1], cfg->n[2], cplx)))
         return why = "3-D lattices are built for real fields with the cubic term and 16..128 points per axis",
                SFT_EUNSUPPORTED;
@@ -364,8 +369,11 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     ctx->nl = cfg->model == SFT_KPZ ? NL_GRAD2 : (ctx->cplx ? NL_CGL : NL_CUBIC);
     ctx->hx = ctx->cplx ? ctx->nx : ctx->nx / 2 + 1;
     ctx->mx = 0;
-    for (int c = 0; c < ctx->hx; ++c)
-        if (!cfg->dealias || 3 * c < ctx->nx) ctx->mx = c + 1;
+    for (int c = 0; c < ctx->hx; ++c) {
+        // real fields: the first mx x-modes; complex fields: the mx x-modes with 3|a_x| < nx (compact order)
+        const int cs = ctx->cplx && 2 * c >= ctx->nx ? ctx->nx - c : c;
+        if (!cfg->dealias || 3 * cs < ctx->nx) ctx->mx = ctx->cplx ? ctx->mx + 1 : c + 1;
+    }
     ctx->sites = (long long)ctx->nx * ctx->ny * ctx->nz;
     ctx->nmodes = (long long)ctx->hx * ctx->ny * ctx->nz;
     ctx->R = cfg->replicas;

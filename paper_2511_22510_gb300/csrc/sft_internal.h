@@ -63,6 +63,9 @@ cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2_cols_pipe(const StepArgs& a, int nl, cudaStream_t s);
 cudaError_t launch_k3_planes(const StepArgs& a, int mode, int nl, cudaStream_t s);
+cudaError_t launch_k2c_rows(const StepArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_k2c_cols(const StepArgs& a, int mode, cudaStream_t s);
+bool k2c_supported(int nx, int ny);
 bool k3_supported(int nx, int ny, int nz, int complex_field);
 bool k2_pipe_supported(int nx, int ny, int complex_field);
 bool k1_supported(int nx, int complex_field);

@@ -1,0 +1,281 @@
+// sft_k2c.cu -- two-pass 2-D step for complex fields (complex Ginzburg-Landau).
+//
+// Layout (x-major): spectrum phi[a_x][a_y] over the full a_x in [0, nx).  The
+// intermediates P, Q keep only the x-columns inside the dealiasing band, in
+// compact order: column cx < m holds a_x = cx, column cx >= m holds
+// a_x = cx + (nx - ncols) (the negative indices), with ncols = 2m - 1
+// (ncols = nx without dealiasing).
+//   row pass:    P --IFFT_x--> A(x, y) --(|A|^2 A)--> FFT_x --> Q
+//   column pass: Q --FFT_y--> F = M s DFT[|A|^2 A], s = -(1 + i beta);
+//                phi <- f1 phi + A F + B F_prev + g eta (complex coefficients,
+//                complex noise on every mode); P <- IFFT_y(M phi / N^2)
+#include "sft_step_common.cuh"
+
+namespace sft {
+
+__device__ __forceinline__ bool cmask_x(int ax, int nx, int ncols) {
+    const int m = (ncols + 1) / 2;
+    return ax < m || ax >= nx - ncols / 2;
+}
+__device__ __forceinline__ int ccomp_x(int ax, int nx, int ncols) {
+    const int m = (ncols + 1) / 2;
+    return ax < m ? ax : ax - (nx - ncols);
+}
+
+template <int N>
+struct CRowCfg {
+    using PL = FftPlan<N>;
+    static constexpr int T = PL::T;
+    static constexpr int ROWS = T >= 128 ? 4 : (T >= 32 ? 128 / T : 128 / T);
+    static constexpr int THREADS = ROWS * T;
+    static constexpr int TS = PL::BUF | 1;  // a row is also its team's exchange buffer
+    static constexpr size_t smem() { return sizeof(float2) * (size_t)ROWS * TS; }
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(CRowCfg<N>::THREADS) k2_rows_cplx(const StepArgs a) {
+    using C = CRowCfg<N>;
+    using PL = FftPlan<N>;
+    constexpr int T = PL::T, E = PL::E, ROWS = C::ROWS, TS = C::TS;
+    extern __shared__ float2 sm[];
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const int rep = blockIdx.y;
+    const int ny = a.ny, hx = a.hx, ncols = a.ncols, nx = N;
+    const int y0 = blockIdx.x * ROWS;
+    const int y = y0 + team;
+    const bool yok = y < ny;
+    float2* trow = sm + team * TS;
+    const float2* __restrict__ tw = a.tw_a;
+    float2 z[E];
+    if constexpr (MODE == MODE_FWD) {
+        const float2* src = a.cplx_io + ((size_t)rep * ny + (yok ? y : 0)) * N;
+#pragma unroll
+        for (int e = 0; e < E; ++e) z[e] = yok ? src[t + T * e] : czero();
+    } else {
+        for (int f = threadIdx.x; f < ROWS * ncols; f += blockDim.x) {
+            const int c = f / ROWS, yy = f % ROWS;
+            sm[yy * TS + c] = (y0 + yy < ny) ? a.pin[((size_t)rep * hx + c) * ny + y0 + yy] : czero();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int ax = t + T * e;
+            z[e] = cmask_x(ax, nx, ncols) ? trow[ccomp_x(ax, nx, ncols)] : czero();
+        }
+        fft_line<N, true>(z, trow, t, tw);
+        if constexpr (MODE == MODE_INV) {
+            if (yok) {
+                float2* dst = a.cplx_io + ((size_t)rep * ny + y) * N;
+#pragma unroll
+                for (int e = 0; e < E; ++e) dst[t + T * e] = z[e];
+            }
+            return;
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) z[e] = cscale(z[e], z[e].x * z[e].x + z[e].y * z[e].y);
+        }
+    }
+    if constexpr (MODE != MODE_INV) {
+        fft_line<N, false>(z, trow, t, tw);
+        team_sync<T>();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int ax = t + T * e;
+            if (cmask_x(ax, nx, ncols)) trow[ccomp_x(ax, nx, ncols)] = z[e];
+        }
+        __syncthreads();
+        for (int f = threadIdx.x; f < ROWS * ncols; f += blockDim.x) {
+            const int c = f / ROWS, yy = f % ROWS;
+            if (y0 + yy < ny) a.qout[((size_t)rep * hx + c) * ny + y0 + yy] = sm[yy * TS + c];
+        }
+    }
+}
+
+template <int NY>
+struct CColCfg {
+    using PL = FftPlan<NY>;
+    static constexpr int T = PL::T;
+    static constexpr int COLS = T >= 128 ? 1 : 128 / T;
+    static constexpr int THREADS = COLS * T;
+    static constexpr int XB = PL::BUF;
+    static constexpr size_t smem() { return sizeof(float2) * (size_t)COLS * XB; }
+};
+
+template <int NY, int MODE>
+__global__ void __launch_bounds__(CColCfg<NY>::THREADS) k2_cols_cplx(const StepArgs a) {
+    using C = CColCfg<NY>;
+    using PL = FftPlan<NY>;
+    constexpr int T = PL::T, E = PL::E, COLS = C::COLS, XB = C::XB;
+    extern __shared__ float2 sm[];
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const int rep = blockIdx.y;
+    const int c = blockIdx.x * COLS + team;  // a_x
+    const bool valid = c < a.hx;
+    const int ax = valid ? c : a.hx - 1;
+    const int nx = a.nx, ncols = a.ncols;
+    float2* xb = sm + team * XB;
+    const float2* __restrict__ tw = a.tw_a;
+    const size_t colbase = ((size_t)rep * a.hx + ax) * NY;
+    const bool inx = !a.dealias || cmask_x(ax, nx, ncols);
+    const size_t cbase = ((size_t)rep * a.hx + (inx ? ccomp_x(ax, nx, ncols) : 0)) * NY;
+    if (!valid && T >= 32) return;
+    float2 v[E];
+    if constexpr (MODE == MODE_FWD) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = a.qin[colbase + t + T * e];
+        fft_line<NY, false>(v, xb, t, tw);
+        if (valid) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) a.phi[colbase + t + T * e] = v[e];
+        }
+        return;
+    } else if constexpr (MODE == MODE_INV) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = cscale(a.phi[colbase + t + T * e], a.scale);
+        fft_line<NY, true>(v, xb, t, tw);
+        if (valid) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) a.pout[colbase + t + T * e] = v[e];
+        }
+        return;
+    } else {
+        float2 out[E];
+        const int axs = signed_idx(ax, nx);
+        if constexpr (MODE == MODE_STEP) {
+            const long long step = current_step(a);
+            const bool first = (a.scheme == 2) && (step == *a.first_step);
+            const bool has_f = valid && inx;
+            if (has_f || T < 32) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[e] = has_f ? a.qin[cbase + t + T * e] : czero();
+                fft_line<NY, false>(v, xb, t, tw);
+            }
+            const float2 s = make_float2(a.s0, a.s0i);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if ((e & 1) == 0)
+                    team_normal_pair<T>(a.seed, (uint64_t)ax * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep),
+                                        out[e], out[e + 1]);
+                const int ay = t + T * e;
+                const int ays = signed_idx(ay, NY);
+                const bool inm = has_f && (!a.dealias || 3 * abs(ays) < NY);
+                const float2 F = inm ? cmul(s, v[e]) : czero();
+                const Coefs co = load_coefs<true>(a.tab, abs(axs) * (NY / 2 + 1) + abs(ays), first);
+                float2 Fp = czero();
+                if (a.scheme == 2 && has_f) Fp = a.fprev[colbase + ay];
+                out[e] = setd_update<true>(co, a.phi[colbase + ay], F, Fp, eta_of(out[e], false));
+                if (a.scheme == 2 && has_f && valid) a.fprev[colbase + ay] = F;
+            }
+            if (valid) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    a.phi[colbase + t + T * e] = out[e];
+                    flag_nonfinite(a, out[e], step);
+                }
+            }
+        } else {  // MODE_PRIME
+#pragma unroll
+            for (int e = 0; e < E; ++e) out[e] = a.phi[colbase + t + T * e];
+        }
+        const bool has_p = valid && inx;
+        if (has_p || T < 32) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ay = t + T * e;
+                const bool inm = has_p && (!a.dealias || 3 * abs(signed_idx(ay, NY)) < NY);
+                v[e] = inm ? cscale(out[e], a.scale) : czero();
+            }
+            fft_line<NY, true>(v, xb, t, tw);
+            if (has_p) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) a.pout[cbase + t + T * e] = v[e];
+            }
+        }
+    }
+}
+
+template <int N, int MODE>
+static cudaError_t run_crows(const StepArgs& a, cudaStream_t s) {
+    using C = CRowCfg<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k2_rows_cplx<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k2_rows_cplx<N, MODE><<<dim3((a.ny + C::ROWS - 1) / C::ROWS, a.R), C::THREADS, C::smem(), s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NY, int MODE>
+static cudaError_t run_ccols(const StepArgs& a, cudaStream_t s) {
+    using C = CColCfg<NY>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k2_cols_cplx<NY, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k2_cols_cplx<NY, MODE><<<dim3((a.hx + C::COLS - 1) / C::COLS, a.R), C::THREADS, C::smem(), s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t crows_for(const StepArgs& a, int mode, cudaStream_t s) {
+    switch (mode) {
+        case MODE_STEP: return run_crows<N, MODE_STEP>(a, s);
+        case MODE_FWD: return run_crows<N, MODE_FWD>(a, s);
+        case MODE_INV: return run_crows<N, MODE_INV>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NY>
+static cudaError_t ccols_for(const StepArgs& a, int mode, cudaStream_t s) {
+    switch (mode) {
+        case MODE_STEP: return run_ccols<NY, MODE_STEP>(a, s);
+        case MODE_FWD: return run_ccols<NY, MODE_FWD>(a, s);
+        case MODE_INV: return run_ccols<NY, MODE_INV>(a, s);
+        case MODE_PRIME: return run_ccols<NY, MODE_PRIME>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool k2c_supported(int nx, int ny) {
+    auto ok = [](int n) { return n >= 16 && n <= 4096 && (n & (n - 1)) == 0; };
+    return ok(nx) && ok(ny);
+}
+
+cudaError_t launch_k2c_rows(const StepArgs& a, int mode, cudaStream_t s) {
+    switch (a.nx) {
+        case 16: return crows_for<16>(a, mode, s);
+        case 32: return crows_for<32>(a, mode, s);
+        case 64: return crows_for<64>(a, mode, s);
+        case 128: return crows_for<128>(a, mode, s);
+        case 256: return crows_for<256>(a, mode, s);
+        case 512: return crows_for<512>(a, mode, s);
+        case 1024: return crows_for<1024>(a, mode, s);
+        case 2048: return crows_for<2048>(a, mode, s);
+        case 4096: return crows_for<4096>(a, mode, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_k2c_cols(const StepArgs& a, int mode, cudaStream_t s) {
+    switch (a.ny) {
+        case 16: return ccols_for<16>(a, mode, s);
+        case 32: return ccols_for<32>(a, mode, s);
+        case 64: return ccols_for<64>(a, mode, s);
+        case 128: return ccols_for<128>(a, mode, s);
+        case 256: return ccols_for<256>(a, mode, s);
+        case 512: return ccols_for<512>(a, mode, s);
+        case 1024: return ccols_for<1024>(a, mode, s);
+        case 2048: return ccols_for<2048>(a, mode, s);
+        case 4096: return ccols_for<4096>(a, mode, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sft

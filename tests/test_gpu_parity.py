@@ -67,7 +67,8 @@ def rel_l2(a, b):
     W.kpz_1d(64, replicas=2),
     W.cgl_2048(n=[32], d=1, dx=[0.5], replicas=2),
     W.model_a_128_3d(n=[16, 16, 16], replicas=2),
-], ids=["2d16", "2d32", "1d64", "cgl1d32", "3d16"])
+    W.cgl_2048(n=[16, 16], replicas=2),
+], ids=["2d16", "2d32", "1d64", "cgl1d32", "3d16", "cgl2d16"])
 def test_noise_normals_bit_identical(sft, oracle_mod, w):
     g = gpu_stepper(sft, w)
     o = oracle_for(oracle_mod, w)
@@ -104,8 +105,8 @@ def test_noise_normals_bit_identical(sft, oracle_mod, w):
 @pytest.mark.parametrize("w", [
     W.model_a_64(n=[64, 64], replicas=3), W.model_a_64(n=[256, 256]), W.kpz_1d(1024, replicas=2, sigma0=1.0),
     W.cgl_2048(n=[128], d=1, dx=[0.5], replicas=2), W.model_a_128_3d(n=[32, 32, 32], replicas=2),
-    W.model_a_128_3d(n=[128, 128, 128], replicas=1),
-], ids=["2d64", "2d256", "1d1024", "cgl1d", "3d32", "3d128"])
+    W.model_a_128_3d(n=[128, 128, 128], replicas=1), W.cgl_2048(n=[64, 64], replicas=2),
+], ids=["2d64", "2d256", "1d1024", "cgl1d", "3d32", "3d128", "cgl2d64"])
 def test_forward_transform_and_roundtrip(sft, oracle_mod, w):
     w = w.with_(sigma0=1.0)
     g, o = start_pair(sft, oracle_mod, w)
@@ -134,6 +135,9 @@ CASES = [
     ("model_a_1d_128", W.model_a_64(d=1, n=[128], dx=[1.0], replicas=2), 100),
     ("cgl_1d_64_setd2", W.cgl_2048(n=[64], d=1, dx=[0.5], replicas=2, p=[2.0, -0.5, 1e-3]), 100),
     ("model_a_16_nodealias", W.model_a_64(n=[16, 16], dealias=0), 100),
+    ("cgl_2d_64_setd2", W.cgl_2048(n=[64, 64], replicas=2, p=[2.0, -0.5, 1e-3]), 100),
+    ("cgl_2d_128_em", W.cgl_2048(n=[128, 128], scheme=0, h=0.02, p=[2.0, -0.5, 1e-3]), 50),
+    ("cgl_2d_32_setd1_nodealias", W.cgl_2048(n=[32, 32], scheme=1, dealias=0, p=[0.5, 0.3, 1e-2]), 60),
     ("model_a_3d_16_setd1", W.model_a_128_3d(n=[16, 16, 16], replicas=2, sigma0=0.3), 60),
     ("model_a_3d_32_setd2", W.model_a_128_3d(n=[32, 32, 32], replicas=1, sigma0=0.3, scheme=2), 30),
     ("model_b_3d_32_em", W.model_a_128_3d(n=[32, 32, 32], model=1, p=[1.0, -0.5, 1.0, 0.2], scheme=0, h=0.02,
@@ -192,6 +196,16 @@ def test_full_size_model_a_128_3d(sft, oracle_mod):
     got = g.field()
     for r in range(2):
         assert rel_l2(got[r], o.field(r)) <= 1e-5
+    g.close()
+
+
+def test_full_size_cgl_2048(sft, oracle_mod):
+    """The CGL lattice (2048^2, dx = 0.5, SETD2) for two steps."""
+    w = W.cgl_2048(replicas=1)
+    g, o = start_pair(sft, oracle_mod, w)
+    g.step(2)
+    o.step(2)
+    assert rel_l2(g.field()[0], o.field(0)) <= 1e-5
     g.close()
 
 
