@@ -133,6 +133,13 @@ def sft_create(cfg: sft_config):
     return ctx
 
 
+def sft_create_batch(cfgs):
+    arr = (sft_config * len(cfgs))(*cfgs)
+    ctx = C.c_void_p()
+    _check(None, load_library().sft_create_batch(arr, len(cfgs), C.byref(ctx)))
+    return ctx
+
+
 def sft_destroy(ctx):
     load_library().sft_destroy(ctx)
 
@@ -240,6 +247,52 @@ def sft_profile(ctx, nsteps: int):
 
 
 # ---------------------------------------------------------------- convenience
+class Batch:
+    """Several configurations (same model and scheme, uneven lattice sizes)
+    advanced together: 1-D members in one persistent launch, the others on a
+    parallel branch of the same CUDA graph.  Replicas are numbered member by
+    member."""
+
+    def __init__(self, cfgs):
+        self.cfgs = list(cfgs)
+        self.ctx = sft_create_batch(self.cfgs)
+        self.R = sum(c.replicas for c in self.cfgs)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sft_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        sft_step(self.ctx, n)
+
+    def step_plain(self, n=1):
+        sft_step_plain(self.ctx, n)
+
+    def sync(self):
+        sft_sync(self.ctx)
+
+    def set_field(self, replica: int, field: np.ndarray):
+        sft_set_field(self.ctx, replica, np.ascontiguousarray(field, dtype=np.float32))
+
+    def field(self, replica: int, shape) -> np.ndarray:
+        out = np.zeros(shape, dtype=np.float32)
+        sft_get_field(self.ctx, replica, out)
+        return out
+
+    def init_random(self, sigma):
+        sft_init_random(self.ctx, sigma)
+
+    def roughness(self) -> np.ndarray:
+        return sft_observe(self.ctx, SFT_OBS_ROUGHNESS, self.R)
+
+
 class Stepper:
     """R replicas of one field behind one sft context.
 

@@ -68,6 +68,18 @@ struct sft_ctx {
     int ckpt_segment = 100;
     long long launches = 0;
     bool pipe_cols = false;  // pipelined (bulk-copy) column pass
+    // batch context: members advanced together (1-D lattices of uneven sizes in one persistent launch)
+    bool is_batch = false;
+    std::vector<sft_ctx*> members;
+    std::vector<long long> rep_offset;  // global replica index of each member's replica 0
+    std::vector<int> solo;              // members stepped by their own kernels on a forked branch
+    BatchMember* d_members = nullptr;
+    BatchItem* d_items = nullptr;
+    int nitems = 0;
+    int* d_head = nullptr;
+    int batch_blocks = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
 };
 
@@ -210,9 +222,28 @@ static sft_status inverse_to_buffer(sft_ctx* ctx, const float2* src, int r0, int
     return SFT_OK;
 }
 
+// Advance the step counter(s) read by the step kernels (a batch: its own and
+// those of the members that run their own kernels).
+static cudaError_t advance_all(sft_ctx* ctx, int by) {
+    cudaError_t e = launch_advance(ctx->dstep, by, ctx->stream);
+    for (int m : ctx->solo)
+        if (e == cudaSuccess) e = launch_advance(ctx->members[m]->dstep, by, ctx->stream);
+    return e;
+}
+static int advances_per_chunk(const sft_ctx* ctx) { return 1 + (int)ctx->solo.size(); }
+
 // P (and P_y) <- dealiased inverse y-transform of the state, the input of the
 // next row pass.
 static sft_status prime(sft_ctx* ctx) {
+    if (ctx->is_batch) {
+        for (int m : ctx->solo) {
+            sft_status s = prime(ctx->members[m]);
+            if (s != SFT_OK) return fail(ctx, s, ctx->members[m]->err);
+            ctx->launches += 1;
+        }
+        ctx->p_valid = true;
+        return SFT_OK;
+    }
     if (ctx->d == 1) {
         ctx->p_valid = true;
         return SFT_OK;
@@ -252,8 +283,38 @@ static sft_status enqueue_step_io(sft_ctx* ctx, const float2* pin, float2* pout)
     return SFT_OK;
 }
 
+static sft_status enqueue_step(sft_ctx* ctx, int k);
+
+// One step of a batch: queue reset + the persistent 1-D kernel on the batch
+// stream, the other members' own kernels on a forked branch, joined at the end.
+static sft_status enqueue_batch_step(sft_ctx* ctx, int k) {
+    if (!ctx->solo.empty()) {
+        CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+        for (int m : ctx->solo) {
+            sft_ctx* mb = ctx->members[m];
+            cudaStream_t keep = mb->stream;
+            mb->stream = ctx->side;
+            sft_status s = enqueue_step(mb, k);
+            mb->stream = keep;
+            if (s != SFT_OK) return fail(ctx, s, mb->err);
+        }
+    }
+    if (ctx->nitems > 0) {
+        CK(cudaMemsetAsync(ctx->d_head, 0, sizeof(int), ctx->stream));
+        CK(launch_k1_batch(ctx->d_members, ctx->d_items, ctx->nitems, ctx->d_head, ctx->nl, k, ctx->batch_blocks,
+                           ctx->stream));
+    }
+    if (!ctx->solo.empty()) {
+        CK(cudaEventRecord(ctx->ev_join, ctx->side));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    }
+    return SFT_OK;
+}
+
 // Enqueue the kernels of one step (k_in_chunk = k).
 static sft_status enqueue_step(sft_ctx* ctx, int k) {
+    if (ctx->is_batch) return enqueue_batch_step(ctx, k);
     StepArgs a = base_args(ctx);
     a.k_in_chunk = k;
     if (ctx->d == 1) {
@@ -286,7 +347,7 @@ static sft_status capture_graph(sft_ctx* ctx) {
     sft_status st = SFT_OK;
     for (int k = 0; k < kGraphChunk && st == SFT_OK; ++k) st = enqueue_step(ctx, k);
     if (st == SFT_OK) {
-        cudaError_t e = launch_advance(ctx->dstep, kGraphChunk, ctx->stream);
+        cudaError_t e = advance_all(ctx, kGraphChunk);
         if (e != cudaSuccess) st = fail(ctx, SFT_ECUDA, cudaGetErrorString(e));
     }
     cudaError_t ee = cudaStreamEndCapture(ctx->stream, &g);
@@ -478,11 +539,117 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
 }
 
 sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
-    if (out) *out = nullptr;
-    if (!cfgs || count < 1 || !out) return SFT_EINVAL;
-    if (count == 1) return sft_create(cfgs, out);
-    return SFT_EUNSUPPORTED;
+    if (!out) return SFT_EINVAL;
+    *out = nullptr;
+    if (!cfgs || count < 1) return SFT_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        std::string why;
+        sft_status vs = validate(&cfgs[i], why);
+        if (vs != SFT_OK) {
+            fprintf(stderr, "sft_create_batch: member %d: %s\n", i, why.c_str());
+            return vs;
+        }
+        if (cfgs[i].model != cfgs[0].model || cfgs[i].scheme != cfgs[0].scheme) {
+            fprintf(stderr, "sft_create_batch: members must share the model and the scheme\n");
+            return SFT_EUNSUPPORTED;
+        }
+    }
+    sft_ctx* ctx = new (std::nothrow) sft_ctx();
+    if (!ctx) return SFT_ENOMEM;
+    auto cleanup = [&](sft_status s) {
+        sft_destroy(ctx);
+        return s;
+    };
+    ctx->is_batch = true;
+    ctx->cfg = cfgs[0];
+    ctx->d = cfgs[0].d;
+    ctx->cplx = cfgs[0].model == SFT_CGL;
+    ctx->nl = cfgs[0].model == SFT_KPZ ? NL_GRAD2 : (ctx->cplx ? NL_CGL : NL_CUBIC);
+    if (cfgs[0].stream) {
+        ctx->stream = (cudaStream_t)cfgs[0].stream;
+    } else {
+        if (cudaStreamCreate(&ctx->stream) != cudaSuccess) return cleanup(SFT_ECUDA);
+        ctx->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(SFT_ECUDA);
+    if (cudaMalloc(&ctx->dstep, 4 * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&ctx->dstatus, sizeof(unsigned)) != cudaSuccess || cudaMalloc(&ctx->d_head, sizeof(int)) != cudaSuccess)
+        return cleanup(SFT_ENOMEM);
+    long long init[4] = {0, -1, (long long)0x7fffffffffffffffLL, 0};
+    if (cudaMemcpy(ctx->dstep, init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(ctx->dstatus, 0, sizeof(unsigned)) != cudaSuccess)
+        return cleanup(SFT_ECUDA);
+    std::vector<BatchMember> hm;
+    std::vector<std::pair<int, BatchItem>> items;  // (M, item)
+    long long roff = 0;
+    for (int i = 0; i < count; ++i) {
+        sft_config c = cfgs[i];
+        c.stream = ctx->stream;
+        sft_ctx* m = nullptr;
+        sft_status st = sft_create(&c, &m);
+        if (st != SFT_OK) return cleanup(st);
+        ctx->members.push_back(m);
+        ctx->rep_offset.push_back(roff);
+        roff += m->R;
+        const int M = m->nx / 2;
+        const int lines = (m->d == 1 && !m->cplx) ? batch_lines_per_item(M) : 0;
+        if (lines > 0) {
+            BatchMember bm{};
+            bm.a = base_args(m);
+            bm.a.tw_a = m->tw.get(m->nx / 2);
+            bm.a.tw_b = m->tw.get(m->nx);
+            bm.a.step_base = ctx->dstep;  // one counter for every member of the persistent launch
+            bm.a.status = ctx->dstatus;
+            bm.a.bad_step = ctx->dstep + 2;
+            bm.M = M;
+            for (int r0 = 0; r0 < m->R; r0 += lines)
+                items.push_back({M, BatchItem{(int)hm.size(), r0}});
+            hm.push_back(bm);
+        } else {
+            ctx->solo.push_back(i);
+        }
+    }
+    ctx->R = (int)roff;
+    // largest lattices first, so the long items do not finish last
+    std::stable_sort(items.begin(), items.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::vector<BatchItem> hi;
+    for (auto& it : items) hi.push_back(it.second);
+    ctx->nitems = (int)hi.size();
+    if (!hm.empty()) {
+        if (cudaMalloc(&ctx->d_members, hm.size() * sizeof(BatchMember)) != cudaSuccess ||
+            cudaMalloc(&ctx->d_items, hi.size() * sizeof(BatchItem)) != cudaSuccess)
+            return cleanup(SFT_ENOMEM);
+        if (cudaMemcpy(ctx->d_members, hm.data(), hm.size() * sizeof(BatchMember), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(ctx->d_items, hi.data(), hi.size() * sizeof(BatchItem), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(SFT_ECUDA);
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        ctx->batch_blocks = std::max(1, std::min(nsm, ctx->nitems));
+    }
+    ctx->launches_per_step = ctx->nitems > 0 ? 1 : 0;
+    for (int m : ctx->solo) ctx->launches_per_step += ctx->members[m]->launches_per_step;
+    *out = ctx;
+    return SFT_OK;
 }
+
+// batch: global replica -> (member, local replica)
+static sft_ctx* member_of(sft_ctx* ctx, int replica, int* local) {
+    for (size_t i = 0; i < ctx->members.size(); ++i) {
+        const long long o = ctx->rep_offset[i];
+        if (replica >= o && replica < o + ctx->members[i]->R) {
+            *local = (int)(replica - o);
+            return ctx->members[i];
+        }
+    }
+    return nullptr;
+}
+
+static size_t field_bytes(const sft_ctx* m) { return (size_t)m->sites * (m->cplx ? sizeof(float2) : sizeof(float)); }
 
 static sft_status check_replica(sft_ctx* ctx, int replica, size_t bytes, size_t per, int* r0, int* R) {
     if (replica < -1 || replica >= ctx->R) return fail(ctx, SFT_EINVAL, "replica out of range");
@@ -494,6 +661,26 @@ static sft_status check_replica(sft_ctx* ctx, int replica, size_t bytes, size_t 
 
 sft_status sft_set_field(sft_ctx* ctx, int replica, const void* host, size_t bytes) {
     if (!ctx || !host) return SFT_EINVAL;
+    if (ctx->is_batch) {
+        if (replica >= 0) {
+            int local = 0;
+            sft_ctx* m = member_of(ctx, replica, &local);
+            if (!m) return fail(ctx, SFT_EINVAL, "replica out of range");
+            sft_status st = sft_set_field(m, local, host, bytes);
+            return st == SFT_OK ? SFT_OK : fail(ctx, st, m->err);
+        }
+        size_t total = 0;
+        for (sft_ctx* m : ctx->members) total += field_bytes(m) * m->R;
+        if (bytes != total) return fail(ctx, SFT_EINVAL, "buffer size does not match the batch");
+        const char* p = (const char*)host;
+        for (sft_ctx* m : ctx->members) {
+            sft_status st = sft_set_field(m, -1, p, field_bytes(m) * m->R);
+            if (st != SFT_OK) return fail(ctx, st, m->err);
+            p += field_bytes(m) * m->R;
+        }
+        ctx->p_valid = false;
+        return SFT_OK;
+    }
     const size_t per = (size_t)ctx->sites * (ctx->cplx ? sizeof(float2) : sizeof(float));
     int r0, R;
     sft_status s = check_replica(ctx, replica, bytes, per, &r0, &R);
@@ -512,6 +699,14 @@ sft_status sft_set_field(sft_ctx* ctx, int replica, const void* host, size_t byt
 
 sft_status sft_init_random(sft_ctx* ctx, double sigma) {
     if (!ctx || !(sigma >= 0)) return SFT_EINVAL;
+    if (ctx->is_batch) {
+        for (sft_ctx* m : ctx->members) {
+            sft_status st = sft_init_random(m, sigma);
+            if (st != SFT_OK) return fail(ctx, st, m->err);
+        }
+        ctx->p_valid = false;
+        return SFT_OK;
+    }
     CK(launch_init_random(ctx->real, ctx->cfield, ctx->sites, ctx->R, ctx->rep0, ctx->cfg.seed, (float)sigma,
                           ctx->stream));
     ctx->launches += 1;
@@ -526,6 +721,10 @@ sft_status sft_init_random(sft_ctx* ctx, double sigma) {
 }
 
 static sft_status read_status(sft_ctx* ctx) {
+    for (sft_ctx* m : ctx->members) {
+        sft_status s = read_status(m);
+        if (s != SFT_OK) return fail(ctx, s, m->err);
+    }
     unsigned st = 0;
     long long bad = 0;
     CK(cudaMemcpyAsync(&st, ctx->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
@@ -548,6 +747,25 @@ sft_status sft_sync(sft_ctx* ctx) {
 
 sft_status sft_get_field(sft_ctx* ctx, int replica, void* host_out, size_t bytes) {
     if (!ctx || !host_out) return SFT_EINVAL;
+    if (ctx->is_batch) {
+        if (replica >= 0) {
+            int local = 0;
+            sft_ctx* m = member_of(ctx, replica, &local);
+            if (!m) return fail(ctx, SFT_EINVAL, "replica out of range");
+            sft_status st = sft_get_field(m, local, host_out, bytes);
+            return st == SFT_OK ? SFT_OK : fail(ctx, st, m->err);
+        }
+        size_t total = 0;
+        for (sft_ctx* m : ctx->members) total += field_bytes(m) * m->R;
+        if (bytes != total) return fail(ctx, SFT_EINVAL, "buffer size does not match the batch");
+        char* p = (char*)host_out;
+        for (sft_ctx* m : ctx->members) {
+            sft_status st = sft_get_field(m, -1, p, field_bytes(m) * m->R);
+            if (st != SFT_OK) return fail(ctx, st, m->err);
+            p += field_bytes(m) * m->R;
+        }
+        return read_status(ctx);
+    }
     const size_t per = (size_t)ctx->sites * (ctx->cplx ? sizeof(float2) : sizeof(float));
     int r0, R;
     sft_status s = check_replica(ctx, replica, bytes, per, &r0, &R);
@@ -562,6 +780,7 @@ sft_status sft_get_field(sft_ctx* ctx, int replica, void* host_out, size_t bytes
 
 sft_status sft_get_spectrum(sft_ctx* ctx, void* host_out, size_t bytes) {
     if (!ctx || !host_out) return SFT_EINVAL;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     if (bytes != (size_t)ctx->R * ctx->nmodes * sizeof(float2)) return fail(ctx, SFT_EINVAL, "spectrum size mismatch");
     CK(cudaMemcpyAsync(host_out, ctx->phi, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     return read_status(ctx);
@@ -569,6 +788,7 @@ sft_status sft_get_spectrum(sft_ctx* ctx, void* host_out, size_t bytes) {
 
 sft_status sft_set_spectrum(sft_ctx* ctx, const void* host_in, size_t bytes) {
     if (!ctx || !host_in) return SFT_EINVAL;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     if (bytes != (size_t)ctx->R * ctx->nmodes * sizeof(float2)) return fail(ctx, SFT_EINVAL, "spectrum size mismatch");
     CK(cudaMemcpyAsync(ctx->phi, host_in, bytes, cudaMemcpyHostToDevice, ctx->stream));
     ctx->p_valid = false;
@@ -596,8 +816,8 @@ static sft_status step_impl(sft_ctx* ctx, int64_t nsteps, bool use_graph) {
                 sft_status s = enqueue_step(ctx, k);
                 if (s != SFT_OK) return s;
             }
-            CK(launch_advance(ctx->dstep, kGraphChunk, ctx->stream));
-            ctx->launches += (long long)kGraphChunk * ctx->launches_per_step + 1;
+            CK(advance_all(ctx, kGraphChunk));
+            ctx->launches += (long long)kGraphChunk * ctx->launches_per_step + advances_per_chunk(ctx);
             left -= kGraphChunk;
             ctx->warmed = true;
         }
@@ -607,17 +827,18 @@ static sft_status step_impl(sft_ctx* ctx, int64_t nsteps, bool use_graph) {
         }
         while (left >= kGraphChunk) {
             CK(cudaGraphLaunch(ctx->graph, ctx->stream));
-            ctx->launches += (long long)kGraphChunk * ctx->launches_per_step + 1;
+            ctx->launches += (long long)kGraphChunk * ctx->launches_per_step + advances_per_chunk(ctx);
             left -= kGraphChunk;
         }
     }
     for (int64_t i = 0; i < left; ++i) {
         sft_status s = enqueue_step(ctx, 0);
         if (s != SFT_OK) return s;
-        CK(launch_advance(ctx->dstep, 1, ctx->stream));
-        ctx->launches += ctx->launches_per_step + 1;
+        CK(advance_all(ctx, 1));
+        ctx->launches += ctx->launches_per_step + advances_per_chunk(ctx);
     }
     ctx->step += nsteps;
+    for (sft_ctx* m : ctx->members) m->step += nsteps;
     return SFT_OK;
 }
 
@@ -627,6 +848,20 @@ sft_status sft_step_plain(sft_ctx* ctx, int64_t nsteps) { return step_impl(ctx, 
 sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, size_t* written) {
     if (!ctx) return SFT_EINVAL;
     if (written) *written = 0;
+    if (ctx->is_batch) {
+        if (kind != SFT_OBS_ROUGHNESS)
+            return fail(ctx, SFT_EUNSUPPORTED, "a batch of uneven lattices supports the per-replica roughness only");
+        if (!host_out || cap < (size_t)ctx->R) return fail(ctx, SFT_EINVAL, "output too small");
+        size_t w = 0;
+        for (sft_ctx* m : ctx->members) {
+            size_t wm = 0;
+            sft_status st = sft_observe(m, kind, host_out + w, cap - w, &wm);
+            if (st != SFT_OK) return fail(ctx, st, m->err);
+            w += wm;
+        }
+        if (written) *written = w;
+        return SFT_OK;
+    }
     const int ns = ctx->nshells;
     if (kind == SFT_OBS_NSHELLS) {
         if (!host_out || cap < 1) return fail(ctx, SFT_EINVAL, "output too small");
@@ -778,6 +1013,7 @@ static sft_status device_field_from_spectrum(sft_ctx* ctx, const float2* src, vo
 
 sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps, void* dphi_out_dev) {
     if (!ctx || nsteps < 0) return SFT_EINVAL;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     sft_status s = diff_supported(ctx);
     if (s != SFT_OK) return s;
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
@@ -837,6 +1073,7 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
 
 sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* grad_dev) {
     if (!ctx || !cot_dev || !grad_dev || nsteps < 1) return SFT_EINVAL;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     sft_status s = diff_supported(ctx);
     if (s != SFT_OK) return s;
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
@@ -989,6 +1226,7 @@ static uint64_t config_hash(const sft_config& c) {
 
 sft_status sft_checkpoint(sft_ctx* ctx, void* host_buf, size_t cap, size_t* written) {
     if (!ctx) return SFT_EINVAL;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     const size_t need = sizeof(CkptHeader) + ms * (ctx->fprev ? 2 : 1);
     if (written) *written = need;
@@ -1012,6 +1250,7 @@ sft_status sft_checkpoint(sft_ctx* ctx, void* host_buf, size_t cap, size_t* writ
 
 sft_status sft_restore(sft_ctx* ctx, const void* host_buf, size_t bytes) {
     if (!ctx || !host_buf) return SFT_EINVAL;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     CkptHeader hd{};
     if (bytes < sizeof hd) return fail(ctx, SFT_ECHECKPOINT, "checkpoint truncated");
     memcpy(&hd, host_buf, sizeof hd);
@@ -1039,6 +1278,51 @@ sft_status sft_restore(sft_ctx* ctx, const void* host_buf, size_t bytes) {
 // or the line kernel in 1-D) followed by the mean whole-step duration.
 sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, int* nkernels) {
     if (!ctx || !out_ms || nsteps < 1) return SFT_EINVAL;
+    if (ctx->is_batch) {
+        // out: [persistent 1-D kernel, the other members' kernels, step]
+        if (cap < 3) return fail(ctx, SFT_EINVAL, "output too small");
+        if (!ctx->p_valid) {
+            sft_status s = prime(ctx);
+            if (s != SFT_OK) return s;
+        }
+        cudaEvent_t e0, e1, e2;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventCreate(&e2));
+        double t1 = 0, t2 = 0;
+        for (int64_t i = 0; i < nsteps; ++i) {
+            CK(cudaEventRecord(e0, ctx->stream));
+            if (ctx->nitems > 0) {
+                CK(cudaMemsetAsync(ctx->d_head, 0, sizeof(int), ctx->stream));
+                CK(launch_k1_batch(ctx->d_members, ctx->d_items, ctx->nitems, ctx->d_head, ctx->nl, 0,
+                                   ctx->batch_blocks, ctx->stream));
+            }
+            CK(cudaEventRecord(e1, ctx->stream));
+            for (int m : ctx->solo) {
+                sft_status s = enqueue_step(ctx->members[m], 0);
+                if (s != SFT_OK) return fail(ctx, s, ctx->members[m]->err);
+            }
+            CK(cudaEventRecord(e2, ctx->stream));
+            CK(advance_all(ctx, 1));
+            ctx->launches += ctx->launches_per_step + advances_per_chunk(ctx);
+            CK(cudaEventSynchronize(e2));
+            float a = 0, b = 0;
+            CK(cudaEventElapsedTime(&a, e0, e1));
+            CK(cudaEventElapsedTime(&b, e1, e2));
+            t1 += a;
+            t2 += b;
+        }
+        ctx->step += nsteps;
+        for (sft_ctx* m : ctx->members) m->step += nsteps;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(e2);
+        out_ms[0] = t1 / nsteps;
+        out_ms[1] = t2 / nsteps;
+        out_ms[2] = (t1 + t2) / nsteps;
+        if (nkernels) *nkernels = 2;
+        return read_status(ctx);
+    }
     const int nk = ctx->d == 1 ? 1 : 2;
     if (cap < nk + 1) return fail(ctx, SFT_EINVAL, "output too small");
     if (!ctx->p_valid) {
@@ -1097,6 +1381,7 @@ sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, in
 
 sft_status sft_draw_noise(sft_ctx* ctx, int64_t step, void* host_out, size_t bytes) {
     if (!ctx || !host_out || step < 0) return SFT_EINVAL;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (bytes != ms) return fail(ctx, SFT_EINVAL, "noise buffer size mismatch");
     CK(launch_draw_noise(ctx->nx, ctx->ny, ctx->nz, ctx->hx, ctx->cplx, ctx->R, ctx->rep0, ctx->cfg.seed, step,
@@ -1128,6 +1413,13 @@ const char* sft_last_error(const sft_ctx* ctx) { return ctx ? ctx->err.c_str() :
 void sft_destroy(sft_ctx* ctx) {
     if (!ctx) return;
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    for (sft_ctx* m : ctx->members) sft_destroy(m);
+    if (ctx->d_members) cudaFree(ctx->d_members);
+    if (ctx->d_items) cudaFree(ctx->d_items);
+    if (ctx->d_head) cudaFree(ctx->d_head);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     void* bufs[] = {ctx->phi,   ctx->fprev,  ctx->P,      ctx->Q,      ctx->Py,     ctx->snap, ctx->real,
                     ctx->cfield, ctx->tab,   ctx->dstep,  ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev,
                     ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ};

@@ -71,6 +71,19 @@ bool k2_pipe_supported(int nx, int ny, int complex_field);
 bool k1_supported(int nx, int complex_field);
 bool k2_supported(int nx, int ny, int complex_field);
 
+// batches of 1-D lattices of uneven sizes advanced by one persistent launch
+struct BatchMember {
+    StepArgs a;  // the member's arguments (step_base shared by the batch)
+    int M;       // half length: the member's lattice has 2M points
+};
+struct BatchItem {
+    int member;  // index into the member table
+    int r0;      // first replica of the item
+};
+int batch_lines_per_item(int M);
+cudaError_t launch_k1_batch(const BatchMember* members, const BatchItem* items, int nitems, int* head, int nl,
+                            int k_in_chunk, int blocks, cudaStream_t s);
+
 // coefficient tables (FP64 on the device, stored as float)
 // Table layouts (entry index -> k^2 / dk^2):
 //   d = 1: entry i = |a|            -> i^2

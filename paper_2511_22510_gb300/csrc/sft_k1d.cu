@@ -37,6 +37,74 @@ __device__ __forceinline__ void line_post(float2 (&z)[FftPlan<M>::E], float2* xb
     XqM = make_float2(z0.x - z0.y, 0.f);
 }
 
+// One SETD step of one real 1-D replica held by a team of T threads (Sec. IV
+// boxed algorithm): inverse transform of the masked state, nonlinearity,
+// forward transform, update with Philox noise.  r: replica (clamped when the
+// team is idle, valid = false); xb: the team's exchange buffer.
+template <int M, int NL>
+__device__ __forceinline__ void line_step(const StepArgs& a, int r, bool valid, int t, float2* xb) {
+    using PL = FftPlan<M>;
+    constexpr int T = PL::T, E = PL::E;
+    constexpr int NX = 2 * M;
+    const float2* __restrict__ twM = a.tw_a;
+    const float2* __restrict__ twN = a.tw_b;
+    float2* ph = a.phi + (size_t)r * (M + 1);
+    const float sc = a.scale;
+    float2 z[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = t + T * e;
+        float2 X = ph[k], Xm = ph[M - k];
+        X = (!a.dealias || 3 * k < NX) ? cscale(X, sc) : czero();
+        Xm = (!a.dealias || 3 * (M - k) < NX) ? cscale(Xm, sc) : czero();
+        if constexpr (NL == NL_GRAD2) {
+            X = cscale(cmuli(X), a.dk * (float)k);
+            Xm = cscale(cmuli(Xm), k == 0 ? 0.f : a.dk * (float)(M - k));
+        }
+        z[e] = c2r_pre(X, Xm, __ldg(&twN[k]));
+    }
+    fft_line<M, true>(z, xb, t, twM);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if constexpr (NL == NL_GRAD2)
+            z[e] = make_float2(z[e].x * z[e].x, z[e].y * z[e].y);
+        else
+            z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
+    }
+    fft_line<M, false>(z, xb, t, twM);
+    float2 Xq[E];
+    float2 XqM;
+    line_post<M>(z, xb, t, twN, Xq, XqM);
+    const long long step = current_step(a);
+    const bool first = (a.scheme == 2) && (step == *a.first_step);
+    float2* fp = a.fprev + (size_t)r * (M + 1);
+    const uint32_t rep = (uint32_t)(a.rep0 + r);
+    float2 zn0, zn1;
+    // modes k = t + T e, then (thread 0) the Nyquist mode k = M
+#pragma unroll
+    for (int e = 0; e <= E; ++e) {
+        if (e < E && (e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
+        if (e == E && t != 0) break;
+        const int k = (e < E) ? t + T * e : M;
+        const float2 xq = (e < E) ? Xq[e] : XqM;
+        const bool inm = !a.dealias || 3 * k < NX;
+        const float2 F = inm ? cscale(xq, nl_prefactor(a, k * k).x) : czero();
+        const Coefs co = load_coefs<false>(a.tab, k, first);
+        const float2 phv = ph[k];
+        const float2 Fp = (a.scheme == 2) ? fp[k] : czero();
+        const bool selfc = (k == 0 || k == M);
+        const float2 eta = (e < E) ? eta_of((e & 1) ? zn1 : zn0, selfc)
+                                   : fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
+        float2 o = setd_update<false>(co, phv, F, Fp, eta);
+        if (selfc) o.y = 0.f;
+        if (valid) {
+            ph[k] = o;
+            if (a.scheme == 2) fp[k] = F;
+            flag_nonfinite(a, o, step);
+        }
+    }
+}
+
 // Real field, N = 2M points.  Mode k of replica r sits at phi[r * (M + 1) + k].
 template <int M, int NL, int MODE>
 __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a) {
@@ -137,6 +205,10 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
         }
     }
 
+    if constexpr (MODE == MODE_STEP) {
+        line_step<M, NL>(a, rr, valid, t, xb);
+        return;
+    }
     if constexpr (MODE == MODE_FWD) {
         const float* src = a.real_io + (size_t)rr * NX;
 #pragma unroll
@@ -390,6 +462,114 @@ cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s) 
         case 16384: return k1r_for<16384>(a, mode, nl, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// ------------------------------------------------------------------ batches
+// One persistent launch advances every replica of every 1-D member of a batch
+// by one step: each block takes work items (member, first replica) from a
+// device queue (largest lattices first) and runs the size's line_step with as
+// many teams as fit its 512 threads.  Lattices up to 16384 points (line
+// teams of at most 512 threads).
+constexpr int kBatchThreads = 512;
+template <int M>
+struct BatchLines {
+    static constexpr int T = FftPlan<M>::T;
+    static constexpr int LINES = kBatchThreads / T;
+    static constexpr int XB = FftPlan<M>::BUF;
+};
+
+template <int M, int NL>
+__device__ __forceinline__ void batch_lines(const StepArgs& a, int r0, float2* sm) {
+    using B = BatchLines<M>;
+    const int team = threadIdx.x / B::T, t = threadIdx.x % B::T;
+    if (team >= B::LINES) return;  // whole teams idle
+    const int r = r0 + team;
+    const bool valid = r < a.R;
+    line_step<M, NL>(a, valid ? r : a.R - 1, valid, t, sm + team * B::XB);
+}
+
+template <int NL>
+__global__ void __launch_bounds__(kBatchThreads, 1)
+    k1_batch(const BatchMember* __restrict__ members, const BatchItem* __restrict__ items, int nitems, int* head,
+             int k_in_chunk) {
+    extern __shared__ float2 sm[];
+    __shared__ int cur;
+    for (;;) {
+        if (threadIdx.x == 0) cur = atomicAdd(head, 1);
+        __syncthreads();
+        const int it = cur;
+        __syncthreads();
+        if (it >= nitems) break;
+        const BatchItem w = items[it];
+        StepArgs a = members[w.member].a;
+        a.k_in_chunk = k_in_chunk;
+        switch (members[w.member].M) {
+            case 16: batch_lines<16, NL>(a, w.r0, sm); break;
+            case 32: batch_lines<32, NL>(a, w.r0, sm); break;
+            case 64: batch_lines<64, NL>(a, w.r0, sm); break;
+            case 128: batch_lines<128, NL>(a, w.r0, sm); break;
+            case 256: batch_lines<256, NL>(a, w.r0, sm); break;
+            case 512: batch_lines<512, NL>(a, w.r0, sm); break;
+            case 1024: batch_lines<1024, NL>(a, w.r0, sm); break;
+            case 2048: batch_lines<2048, NL>(a, w.r0, sm); break;
+            case 4096: batch_lines<4096, NL>(a, w.r0, sm); break;
+            case 8192: batch_lines<8192, NL>(a, w.r0, sm); break;
+            default: break;
+        }
+        __syncthreads();
+    }
+}
+
+int batch_lines_per_item(int M) {
+    switch (M) {
+        case 16: return BatchLines<16>::LINES;
+        case 32: return BatchLines<32>::LINES;
+        case 64: return BatchLines<64>::LINES;
+        case 128: return BatchLines<128>::LINES;
+        case 256: return BatchLines<256>::LINES;
+        case 512: return BatchLines<512>::LINES;
+        case 1024: return BatchLines<1024>::LINES;
+        case 2048: return BatchLines<2048>::LINES;
+        case 4096: return BatchLines<4096>::LINES;
+        case 8192: return BatchLines<8192>::LINES;
+        default: return 0;
+    }
+}
+
+size_t batch_smem_bytes() {
+    size_t b = 0;
+    auto upd = [&](size_t v) { b = v > b ? v : b; };
+    upd(sizeof(float2) * BatchLines<16>::LINES * BatchLines<16>::XB);
+    upd(sizeof(float2) * BatchLines<32>::LINES * BatchLines<32>::XB);
+    upd(sizeof(float2) * BatchLines<64>::LINES * BatchLines<64>::XB);
+    upd(sizeof(float2) * BatchLines<128>::LINES * BatchLines<128>::XB);
+    upd(sizeof(float2) * BatchLines<256>::LINES * BatchLines<256>::XB);
+    upd(sizeof(float2) * BatchLines<512>::LINES * BatchLines<512>::XB);
+    upd(sizeof(float2) * BatchLines<1024>::LINES * BatchLines<1024>::XB);
+    upd(sizeof(float2) * BatchLines<2048>::LINES * BatchLines<2048>::XB);
+    upd(sizeof(float2) * BatchLines<4096>::LINES * BatchLines<4096>::XB);
+    upd(sizeof(float2) * BatchLines<8192>::LINES * BatchLines<8192>::XB);
+    return b;
+}
+
+cudaError_t launch_k1_batch(const BatchMember* members, const BatchItem* items, int nitems, int* head, int nl,
+                            int k_in_chunk, int blocks, cudaStream_t s) {
+    static bool attr[2] = {false, false};
+    const size_t sm = batch_smem_bytes();
+    const int which = nl == NL_GRAD2 ? 1 : 0;
+    if (!attr[which]) {
+        cudaError_t e = which ? cudaFuncSetAttribute(k1_batch<NL_GRAD2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)sm)
+                              : cudaFuncSetAttribute(k1_batch<NL_CUBIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)sm);
+        if (e != cudaSuccess) return e;
+        attr[which] = true;
+    }
+    if (which)
+        k1_batch<NL_GRAD2><<<blocks, kBatchThreads, sm, s>>>(members, items, nitems, head, k_in_chunk);
+    else
+        k1_batch<NL_CUBIC><<<blocks, kBatchThreads, sm, s>>>(members, items, nitems, head, k_in_chunk);
+    return cudaGetLastError();
 }
 
 }  // namespace sft
