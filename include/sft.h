@@ -213,6 +213,30 @@ sft_status sft_launches_per_step(const sft_ctx* ctx, int* launches);
  * graph replays included). */
 sft_status sft_kernel_launches(const sft_ctx* ctx, int64_t* count);
 
+/* No counterpart in the paper: an entry point for callers that cannot allocate
+ * device memory (an embedding runtime that owns the allocator, a plug-in that
+ * must not grow its footprint after start-up, a real-time loop where an
+ * allocation could stall).  Advances nsteps SETD steps of a 2-D real field
+ * (Model A, Model B or KPZ; n[0] == n[1] <= 512) without a context and without
+ * calling cudaMalloc or cudaFree.
+ *   cfg:       configuration as for sft_create (d = 2); cfg->stream is used.
+ *   phi_dev:   DEVICE state, in/out, spectrum layout of sft_get_spectrum
+ *              (R * (n0/2 + 1) * n1 complex float pairs), owned by the caller.
+ *   fprev_dev: DEVICE SETD2 history of the same size (in/out), or NULL for
+ *              SETD-EM and SETD1.
+ *   history_valid: 1 if fprev_dev holds F of the step before step0 (a
+ *              continued SETD2 run); 0 makes the first step use SETD1.
+ *   step0:     index of the first step (the noise counter).
+ * All other scratch -- intermediates, coefficient table, twiddles, counters --
+ * lives in one fixed device array of about 7 MiB that every GPU loading this
+ * library holds until exit; sizes beyond it (R * (n0/2 + 1) * n1 > 262144 modes,
+ * or n > 512) return SFT_EINVAL.  The first call on a device looks that array
+ * up and must come before any stream capture.  Calls share the array: calls
+ * that overlap on the GPU race.  Synchronises cfg->stream; returns
+ * SFT_ENONFINITE if the state became non-finite. */
+sft_status sft_step2d_noalloc(const sft_config* cfg, void* phi_dev, void* fprev_dev, int history_valid,
+                              int64_t step0, int64_t nsteps);
+
 const char* sft_last_error(const sft_ctx* ctx);
 void sft_destroy(sft_ctx* ctx);
 

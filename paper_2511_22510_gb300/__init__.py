@@ -33,7 +33,8 @@ ABI_FUNCTIONS = [
     "sft_create", "sft_create_batch", "sft_set_field", "sft_init_random", "sft_get_field", "sft_get_spectrum",
     "sft_set_spectrum", "sft_step", "sft_step_plain", "sft_sync", "sft_observe", "sft_tangent_step",
     "sft_adjoint", "sft_set_checkpoint_interval", "sft_checkpoint", "sft_restore", "sft_get_step",
-    "sft_launches_per_step", "sft_kernel_launches", "sft_draw_noise", "sft_profile", "sft_last_error", "sft_destroy",
+    "sft_launches_per_step", "sft_kernel_launches", "sft_draw_noise", "sft_profile", "sft_step2d_noalloc",
+    "sft_last_error", "sft_destroy",
 ]
 
 
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH):
     L.sft_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.sft_draw_noise.argtypes = [vp, i64, vp, sz]
     L.sft_kernel_launches.argtypes = [vp, C.POINTER(i64)]
+    L.sft_step2d_noalloc.argtypes = [C.POINTER(sft_config), vp, vp, C.c_int, i64, i64]
     L.sft_profile.argtypes = [vp, i64, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
     L.sft_last_error.argtypes = [vp]
     L.sft_last_error.restype = C.c_char_p
@@ -218,6 +220,13 @@ def sft_get_step(ctx) -> int:
     v = C.c_int64()
     _check(ctx, load_library().sft_get_step(ctx, C.byref(v)))
     return v.value
+
+
+def sft_step2d_noalloc(cfg: sft_config, phi_dev_ptr: int, fprev_dev_ptr: Optional[int], history_valid: int,
+                       step0: int, nsteps: int):
+    """Context-free 2-D step on caller-owned device buffers; allocates nothing."""
+    _check(None, load_library().sft_step2d_noalloc(C.byref(cfg), phi_dev_ptr, fprev_dev_ptr, int(history_valid),
+                                                   int(step0), int(nsteps)))
 
 
 def sft_kernel_launches(ctx) -> int:

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "sft.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sft_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(sft_[a-z_0-9]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
