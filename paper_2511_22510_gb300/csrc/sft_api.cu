@@ -967,17 +967,16 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
 }
 
 static sft_status diff_supported(sft_ctx* ctx) {
-    if (ctx->cplx || ctx->nl != NL_CUBIC || ctx->cfg.scheme == SFT_SETD2 || ctx->d > 2)
+    if (ctx->cplx || ctx->nl != NL_CUBIC || ctx->cfg.scheme == SFT_SETD2)
         return fail(ctx, SFT_EUNSUPPORTED,
-                    "tangent/adjoint are built for real fields with the cubic term (Model A/B), SETD-EM or SETD1, "
-                    "d <= 2");
+                    "tangent/adjoint are built for real fields with the cubic term (Model A/B), SETD-EM or SETD1");
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (!ctx->dphi) {
         CK(cudaMalloc(&ctx->dphi, ms));
         CK(cudaMemsetAsync(ctx->dphi, 0, ms, ctx->stream));
     }
     if (!ctx->dseed) CK(cudaMalloc(&ctx->dseed, ms));
-    if (ctx->d == 2 && !ctx->dP) {
+    if (ctx->d >= 2 && !ctx->dP) {
         CK(cudaMalloc(&ctx->dP, ms));
         CK(cudaMalloc(&ctx->dQ, ms));
         CK(cudaMemsetAsync(ctx->dP, 0, ms, ctx->stream));
@@ -1027,12 +1026,12 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
         s = prime(ctx);
         if (s != SFT_OK) return s;
     }
-    if (ctx->d == 2 && !ctx->dp_valid) {
+    if (ctx->d >= 2 && !ctx->dp_valid) {
         StepArgs a = base_args(ctx);
         a.phi = ctx->dphi;
         a.pout = ctx->dP;
         a.tw_a = ctx->tw.get(ctx->ny);
-        CK(launch_k2_cols(a, MODE_PRIME, ctx->nl, ctx->stream));
+        CK(launch_second(ctx, a, MODE_PRIME));
         ctx->launches += 1;
         ctx->dp_valid = true;
     }
@@ -1051,13 +1050,20 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
             a.dqout = ctx->dQ;
             a.tw_a = ctx->tw.get(ctx->nx / 2);
             a.tw_b = ctx->tw.get(ctx->nx);
-            CK(launch_k2_rows(a, MODE_TAN, ctx->nl, ctx->stream));
+            CK(launch_rows(ctx, a, MODE_TAN));
             a.qin = ctx->Q;
             a.dqin = ctx->dQ;
             a.pout = ctx->P;
             a.dpout = ctx->dP;
             a.tw_a = ctx->tw.get(ctx->ny);
-            CK(launch_k2_cols(a, MODE_TAN, ctx->nl, ctx->stream));
+            if (ctx->d == 3) {
+                // the plane pass runs the primal step, then the (noise-free) tangent update
+                CK(launch_second(ctx, a, MODE_STEP));
+                CK(launch_second(ctx, a, MODE_TAN));
+                ctx->launches += 1;
+            } else {
+                CK(launch_k2_cols(a, MODE_TAN, ctx->nl, ctx->stream));
+            }
             ctx->launches += 2;
         }
         CK(launch_advance(ctx->dstep, 1, ctx->stream));
@@ -1153,7 +1159,7 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
                 if (!w_valid) {
                     a.dpout = ctx->dP;
                     a.tw_a = ctx->tw.get(ctx->ny);
-                    CKA(launch_k2_cols(a, MODE_ADJ_PRIME, ctx->nl, ctx->stream));
+                    CKA(launch_second(ctx, a, MODE_ADJ_PRIME));
                     w_valid = true;
                 }
                 a.pin = slot;
@@ -1161,11 +1167,11 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
                 a.dqout = ctx->dQ;
                 a.tw_a = ctx->tw.get(ctx->nx / 2);
                 a.tw_b = ctx->tw.get(ctx->nx);
-                CKA(launch_k2_rows(a, MODE_ADJ, ctx->nl, ctx->stream));
+                CKA(launch_rows(ctx, a, MODE_ADJ));
                 a.dqin = ctx->dQ;
                 a.dpout = ctx->dP;
                 a.tw_a = ctx->tw.get(ctx->ny);
-                CKA(launch_k2_cols(a, MODE_ADJ, ctx->nl, ctx->stream));
+                CKA(launch_second(ctx, a, MODE_ADJ));
                 ctx->launches += 2;
             }
         }

@@ -66,10 +66,16 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
     const float2* __restrict__ tw = a.tw_a;
     const bool plane = (c == 0 || c == M);
 
-    if constexpr (MODE == MODE_FWD || MODE == MODE_STEP) {
+    // modes: STEP (primal, with noise); TAN (tangent only: dphi <- f1 dphi + A M s DFT[q']);
+    // ADJ (lam <- f1 lam + M DFT[v], then W = IDFT(A s M lam / N^3)); ADJ_PRIME (W from lam only)
+    constexpr bool DIFF = (MODE == MODE_TAN || MODE == MODE_ADJ || MODE == MODE_ADJ_PRIME);
+    const float2* qsrc = DIFF ? a.dqin : a.qin;
+    float2* state = DIFF ? a.dphi : a.phi;
+    float2* pdst = DIFF ? a.dpout : a.pout;
+    if constexpr (MODE == MODE_FWD || MODE == MODE_STEP || MODE == MODE_TAN || MODE == MODE_ADJ) {
         const bool has_f = (MODE == MODE_FWD) || c < a.ncols;
         for (int f = threadIdx.x; f < N * N; f += blockDim.x)
-            S[(f / N) * RS + f % N] = has_f ? a.qin[base + f] : czero();
+            S[(f / N) * RS + f % N] = has_f ? qsrc[base + f] : czero();
         __syncthreads();
         if (has_f) {
             plane_fft<N, true, false>(S, xb, team, t, tw);
@@ -78,14 +84,14 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
             __syncthreads();
         }
     } else {
-        // INV / PRIME: the (masked) state goes straight to the inverse transforms
-        for (int f = threadIdx.x; f < N * N; f += blockDim.x) S[(f / N) * RS + f % N] = a.phi[base + f];
+        // INV / PRIME / ADJ_PRIME: the state goes straight to the inverse transforms
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x) S[(f / N) * RS + f % N] = state[base + f];
         __syncthreads();
     }
 
-    if constexpr (MODE == MODE_STEP) {
+    if constexpr (MODE == MODE_STEP || MODE == MODE_TAN || MODE == MODE_ADJ) {
         const long long step = current_step(a);
-        const bool first = (a.scheme == 2) && (step == *a.first_step);
+        const bool first = (MODE == MODE_STEP) && (a.scheme == 2) && (step == *a.first_step);
         const bool has_f = c < a.ncols;
         for (int it = 0; it < C::ITERS; ++it) {
             const int line = team + it * C::TEAMS;
@@ -93,28 +99,36 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
             const int azs = signed_idx(az, N);
 #pragma unroll
             for (int e = 0; e < E; e += 2) {
-                float2 zz[2];
-                team_normal_pair<T>(a.seed, ((uint64_t)c * N + az) * N, t, e, (uint32_t)step,
-                                    (uint32_t)(a.rep0 + rep), zz[0], zz[1]);
+                float2 zz[2] = {czero(), czero()};
+                if constexpr (MODE == MODE_STEP)
+                    team_normal_pair<T>(a.seed, ((uint64_t)c * N + az) * N, t, e, (uint32_t)step,
+                                        (uint32_t)(a.rep0 + rep), zz[0], zz[1]);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int ay = t + T * (e + h);
                     const int ays = signed_idx(ay, N);
                     const int q = c * c + ays * ays + azs * azs;
                     const bool inm = !a.dealias || (3 * c < a.nx && 3 * abs(ays) < N && 3 * abs(azs) < N);
-                    const float2 F = (has_f && inm) ? cscale(S[az * RS + ay], nl_prefactor(a, q).x) : czero();
+                    const float2 Fh = (has_f && inm) ? S[az * RS + ay] : czero();
                     const Coefs co = load_coefs<false>(a.tab, q, first);
                     const size_t idx = base + (size_t)az * N + ay;
-                    float2 Fp = czero();
-                    if (a.scheme == 2 && has_f) Fp = a.fprev[idx];
                     const int mz = (N - az) % N, my = (N - ay) % N;
                     const bool selfc = plane && az == mz && ay == my;
-                    float2 o = setd_update<false>(co, a.phi[idx], F, Fp, eta_of(zz[h], selfc));
-                    if (selfc) o.y = 0.f;
-                    if (line < N) {
-                        if (a.scheme == 2 && has_f) a.fprev[idx] = F;
-                        S[az * RS + ay] = o;
+                    float2 o;
+                    if constexpr (MODE == MODE_STEP) {
+                        const float2 F = cscale(Fh, nl_prefactor(a, q).x);
+                        float2 Fp = czero();
+                        if (a.scheme == 2 && has_f) Fp = a.fprev[idx];
+                        o = setd_update<false>(co, state[idx], F, Fp, eta_of(zz[h], selfc));
+                        if (line < N && a.scheme == 2 && has_f) a.fprev[idx] = F;
+                    } else if constexpr (MODE == MODE_TAN) {
+                        o = setd_update<false>(co, state[idx], cscale(Fh, nl_prefactor(a, q).x), czero(), czero());
+                    } else {
+                        const float2 l = state[idx];
+                        o = make_float2(co.f1.x * l.x + Fh.x, co.f1.x * l.y + Fh.y);
                     }
+                    if (selfc) o.y = 0.f;
+                    if (line < N) S[az * RS + ay] = o;
                 }
             }
         }
@@ -131,8 +145,8 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
         for (int f = threadIdx.x; f < N * N; f += blockDim.x) {
             const int az = f / N, ay = f % N;
             const float2 o = S[az * RS + ay];
-            a.phi[base + f] = o;
-            flag_nonfinite(a, o, step);
+            state[base + f] = o;
+            if (MODE == MODE_STEP) flag_nonfinite(a, o, step);
         }
     }
     if constexpr (MODE == MODE_FWD) {
@@ -148,23 +162,28 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
         for (int f = threadIdx.x; f < N * N; f += blockDim.x) a.phi[base + f] = S[(f / N) * RS + f % N];
         return;
     } else {
-        // inverse transforms of M phi / N^3 (INV: no mask) -> row-pass input
+        // inverse transforms of M phi / N^3 (INV: no mask; adjoint: times A s) -> row-pass input
         const bool emit = (MODE == MODE_INV) || c < a.ncols;
         if (!emit) return;  // whole block
         __syncthreads();
         for (int f = threadIdx.x; f < N * N; f += blockDim.x) {
             const int az = f / N, ay = f % N;
-            const bool inm = (MODE == MODE_INV) || !a.dealias ||
-                             (3 * c < a.nx && 3 * abs(signed_idx(ay, N)) < N && 3 * abs(signed_idx(az, N)) < N);
+            const int ays = signed_idx(ay, N), azs = signed_idx(az, N);
+            const bool inm = (MODE == MODE_INV) || !a.dealias || (3 * c < a.nx && 3 * abs(ays) < N && 3 * abs(azs) < N);
+            float w = a.scale;
+            if constexpr (MODE == MODE_ADJ || MODE == MODE_ADJ_PRIME) {
+                const int q = c * c + ays * ays + azs * azs;
+                w *= __ldg(&a.tab[q]).y * nl_prefactor(a, q).x;
+            }
             const float2 o = S[az * RS + ay];
-            S[az * RS + ay] = inm ? cscale(o, a.scale) : czero();
+            S[az * RS + ay] = inm ? cscale(o, w) : czero();
         }
         __syncthreads();
         plane_fft<N, false, true>(S, xb, team, t, tw);
         __syncthreads();
         plane_fft<N, true, true>(S, xb, team, t, tw);
         __syncthreads();
-        for (int f = threadIdx.x; f < N * N; f += blockDim.x) a.pout[base + f] = S[(f / N) * RS + f % N];
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x) pdst[base + f] = S[(f / N) * RS + f % N];
     }
 }
 
@@ -189,6 +208,9 @@ static cudaError_t planes_for(const StepArgs& a, int mode, cudaStream_t s) {
         case MODE_FWD: return run_planes<N, MODE_FWD>(a, s);
         case MODE_INV: return run_planes<N, MODE_INV>(a, s);
         case MODE_PRIME: return run_planes<N, MODE_PRIME>(a, s);
+        case MODE_TAN: return run_planes<N, MODE_TAN>(a, s);
+        case MODE_ADJ: return run_planes<N, MODE_ADJ>(a, s);
+        case MODE_ADJ_PRIME: return run_planes<N, MODE_ADJ_PRIME>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -37,6 +37,9 @@ CASES = [
     ("model_a_64", W.model_a_64(n=[64, 64], replicas=2, sigma0=0.3, h=0.02)),
     ("model_b_32_em", W.model_b_1024(n=[32, 32], replicas=2, sigma0=0.3, scheme=0, h=0.02)),
     ("model_a_1d_256", W.model_a_64(d=1, n=[256], dx=[1.0], replicas=3, sigma0=0.3, h=0.02)),
+    ("model_a_3d_16", W.model_a_128_3d(n=[16, 16, 16], replicas=2, sigma0=0.3, h=0.02)),
+    ("model_b_3d_16_em", W.model_a_128_3d(n=[16, 16, 16], model=1, p=[1.0, -0.5, 1.0, 0.2], scheme=0, h=0.02,
+                                          sigma0=0.3)),
 ]
 
 
@@ -131,3 +134,51 @@ def test_adjoint_dot_product_and_parity(env, oracle_mod, name, w):
     assert np.array_equal(g2.spectrum(), g3.spectrum())
     for x in (g1, g2, g3):
         x.close()
+
+
+def test_fluctuation_dissipation_model_a_3d(env):
+    """Equilibrium Model A (Gamma = 1, D = T): the response to an impulse in the
+    mode k0 obeys R(k0, tau) = -(1/T) dC(k0, tau)/dtau (the time-domain form of
+    the FDT of Sec. V.A), checked in integrated form
+    int_0^tau R = (C(k0, 0) - C(k0, tau)) / T over an ensemble of replicas, with
+    the tangent on the same noise paths as the correlations.  Tolerance: 4
+    standard errors (batch means over replica groups) plus the O(h) bias."""
+    m, torch = env
+    T = 1.0
+    w = W.model_a_128_3d(n=[16, 16, 16], replicas=512, p=[1.0, 0.5, 1.0, T], h=0.01)
+    g = m.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed)
+    g.init_random(0.5)
+    g.step(1500)
+    ns = g.nshells()
+    g.observe(m.SFT_OBS_MARK)
+    N = 16
+    x = np.arange(N)
+    seed = np.cos(2 * np.pi * x / N)[None, None, None, :] * np.ones((w.replicas, N, N, N))
+    din = torch.from_numpy(seed.astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    taus, resp, corr = [0.0], [1.0], []
+    c0 = m.sft_observe(g.ctx, m.SFT_OBS_SK_REPLICAS, w.replicas * ns).reshape(w.replicas, ns)[:, 1]
+    corr.append(c0)
+    chunk = 5
+    first = True
+    for i in range(40):
+        m.sft_tangent_step(g.ctx, din.data_ptr() if first else None, chunk, None)
+        first = False
+        taus.append((i + 1) * chunk * w.h)
+        resp.append(g.observe(m.SFT_OBS_RESPONSE)[1])
+        # two-time correlation per replica in shell 1 (|a| = 1: exactly the modes +-k0 on each axis)
+        ck = m.sft_observe(g.ctx, m.SFT_OBS_CKT, 2 * ns)
+        corr.append(ck[1])
+    taus = np.array(taus)
+    resp = np.array(resp)
+    cmean0 = float(np.mean(corr[0]))
+    ctau = np.array([cmean0] + [float(c) for c in corr[1:]])
+    integ = np.concatenate([[0.0], np.cumsum(0.5 * (resp[1:] + resp[:-1]) * np.diff(taus))])
+    lhs = integ
+    rhs = (ctau[0] - ctau) / T
+    # statistical error of C(0) - C(tau): scale from the spread of C(0) over replica groups
+    groups = corr[0].reshape(16, -1).mean(axis=1)
+    sem = float(np.std(groups) / np.sqrt(16))
+    for j in (10, 20, 40):
+        assert abs(lhs[j] - rhs[j]) <= 4 * sem + 0.03 * abs(rhs[j]) + 0.02 * taus[j], (taus[j], lhs[j], rhs[j], sem)
+    g.close()
