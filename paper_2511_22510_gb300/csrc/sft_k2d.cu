@@ -13,6 +13,7 @@
 // so every step moves the state once through HBM plus two dealiased
 // intermediates.  Real-length-N transforms use the N/2-point complex FFT with
 // the even/odd split (z[m] = x[2m] + i x[2m+1]).
+#include "sft_async.cuh"
 #include "sft_step_common.cuh"
 
 #ifndef SFT_CTA
@@ -60,8 +61,11 @@ struct RowCfg {
     static constexpr int T = PL::T;
     static constexpr int ROWS = T >= SFT_CTA ? 1 : SFT_CTA / T;
     static constexpr int THREADS = ROWS * T;
-    // odd row stride of the spectral tile; a row also serves as its team's FFT exchange buffer
-    static constexpr int TS = PL::BUF | 1;
+    // row stride of the spectral tile (a row also serves as its team's FFT exchange buffer):
+    // the transposing tile loads/stores of a half-warp touch ROWS rows x 16/ROWS columns, which
+    // fall on distinct banks when TS = 16/ROWS (mod 16); an odd stride when ROWS >= 16
+    static constexpr int TSM = ROWS >= 16 ? 1 : 16 / ROWS;
+    static constexpr int TS = ROWS >= 16 ? (PL::BUF | 1) : ((PL::BUF + 15) / 16) * 16 + TSM;
     static constexpr size_t smem(int ntile) { return sizeof(float2) * (size_t)ntile * ROWS * TS; }
 };
 
