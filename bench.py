@@ -50,6 +50,10 @@ def parse_args():
     ap.add_argument("--h", type=float, default=0.05)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--workload", default="model_b_1024",
+                    choices=["model_b_1024", "model_a_64", "kpz_ensemble", "cgl_2048", "model_a_128_3d",
+                             "model_a_128_3d_tangent"],
+                    help="model_b_1024 is the headline; the others print their own line for the other workloads")
     return ap.parse_args()
 
 
@@ -380,10 +384,103 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_other(args):
+    """Throughput of the other workloads (one GPU): batched/graph path against the
+    plain form (one replica or one member at a time, host-launched, no graph)."""
+    import torch
+    import paper_2511_22510_gb300 as sft
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    K = max(args.steps // 10, 20)
+
+    def timed(fn):
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": K, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "vs_baseline": None}
+    if args.workload == "kpz_ensemble":
+        lengths = W.kpz_ensemble_lengths()
+        counts = {L: lengths.count(L) for L in sorted(set(lengths))}
+        members = [W.kpz_1d(L, replicas=c) for L, c in counts.items()] + [W.kpz_2d(replicas=64)]
+        cfgs = [sft.make_config(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, w.dealias,
+                                stream=stream.cuda_stream) for w in members]
+        sites = sum(w.sites * w.replicas for w in members)
+        batch = sft.Batch(cfgs)
+        batch.step(32)
+        batch.sync()
+        ms = timed(lambda: batch.step(K))
+        value = sites * K / (ms * 1e-3) / 1e9
+        prof = sft.sft_profile(batch.ctx, 10)
+        batch.close()
+        singles = [sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed,
+                               stream=stream.cuda_stream) for w in members]
+        for g in singles:
+            g.step_plain(2)
+        Kp = max(K // 4, 5)
+
+        def plain_all():
+            for g in singles:
+                g.step_plain(Kp)
+        msp = timed(plain_all)
+        plain = sites * Kp / (msp * 1e-3) / 1e9
+        for g in singles:
+            g.close()
+        line.update({"value": value, "ms_per_step": ms / K,
+                     "config": {"workload": "kpz_ensemble", "members": {str(L): c for L, c in counts.items()},
+                                "plus": "64 x 256^2", "note": "lines up to 16384 points in one persistent launch; 32768 and 65536 points and the 2-D members on a parallel graph branch"},
+                     "batched_kernels_ms": {"k1_batch": prof[0], "other_members": prof[1]},
+                     "plain": {"value": plain, "unit": UNIT, "batched_speedup": value / plain,
+                               "form": "each member's own kernels launched from the host, no graph"}})
+    else:
+        if args.workload == "model_a_64":
+            w = W.model_a_64(replicas=1024)
+        elif args.workload == "cgl_2048":
+            w = W.cgl_2048(replicas=4)
+        else:
+            w = W.model_a_128_3d(replicas=32)
+        g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, stream=stream.cuda_stream)
+        g.init_random(max(w.sigma0, 0.1))
+        if args.workload == "model_a_128_3d_tangent":
+            seed = torch.zeros((w.replicas,) + w.shape, dtype=torch.float32, device="cuda")
+            seed[..., 1] = 1.0
+            torch.cuda.synchronize()
+            sft.sft_tangent_step(g.ctx, seed.data_ptr(), 4, None)
+            ms = timed(lambda: sft.sft_tangent_step(g.ctx, None, K, None))
+        else:
+            g.step(32)
+            g.sync()
+            ms = timed(lambda: g.step(K))
+        value = w.sites * w.replicas * K / (ms * 1e-3) / 1e9
+        prof = sft.sft_profile(g.ctx, 10)
+        g.close()
+        p1 = sft.Stepper(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, stream=stream.cuda_stream)
+        p1.init_random(0.1)
+        p1.step_plain(2)
+        msp = timed(lambda: p1.step_plain(K))
+        plain = w.sites * K / (msp * 1e-3) / 1e9
+        p1.close()
+        line.update({"value": value, "ms_per_step": ms / K,
+                     "config": {"workload": args.workload, "lattice": "x".join(str(n) for n in w.n),
+                                "replicas": w.replicas, "scheme": scheme_name(w.scheme), "h": w.h},
+                     "kernels_ms": list(map(float, prof)),
+                     "plain": {"value": plain, "unit": UNIT, "replicas": 1, "graph": False,
+                               "batched_speedup": value / plain}})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "model_b_1024":
+        run_other(args)
     else:
         run_gpu(args)
 

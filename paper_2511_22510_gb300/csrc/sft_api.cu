@@ -967,9 +967,10 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
 }
 
 static sft_status diff_supported(sft_ctx* ctx) {
-    if (ctx->cplx || ctx->nl != NL_CUBIC || ctx->cfg.scheme == SFT_SETD2)
+    if (ctx->cplx || ctx->nl != NL_CUBIC || ctx->cfg.scheme == SFT_SETD2 || (ctx->d == 1 && ctx->nx > 32768))
         return fail(ctx, SFT_EUNSUPPORTED,
-                    "tangent/adjoint are built for real fields with the cubic term (Model A/B), SETD-EM or SETD1");
+                    "tangent/adjoint are built for real fields with the cubic term (Model A/B), SETD-EM or SETD1 "
+                    "(1-D up to 32768 points)");
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (!ctx->dphi) {
         CK(cudaMalloc(&ctx->dphi, ms));

@@ -59,6 +59,7 @@ struct StepArgs {
 // launchers (return cudaGetLastError of the launch); each picks the template
 // instance for the lattice size and returns cudaErrorInvalidValue if none.
 cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s);
+cudaError_t launch_k1_cluster(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2_cols_pipe(const StepArgs& a, int nl, cudaStream_t s);

@@ -428,10 +428,11 @@ static cudaError_t k1c_for(const StepArgs& a, int mode, cudaStream_t s) {
 
 bool k1_supported(int nx, int complex_field) {
     if ((nx & (nx - 1)) != 0) return false;
-    return complex_field ? (nx >= 16 && nx <= 16384) : (nx >= 32 && nx <= 32768);
+    return complex_field ? (nx >= 16 && nx <= 16384) : (nx >= 32 && nx <= 65536);
 }
 
 cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s) {
+    if (nl != NL_CGL && a.nx == 65536) return launch_k1_cluster(a, mode, nl, s);
     if (nl == NL_CGL) {
         switch (a.nx) {
             case 16: return k1c_for<16>(a, mode, s);

@@ -181,10 +181,13 @@ __device__ __forceinline__ int shell_of(long long q) {
     return (int)j;
 }
 
-__global__ void k_observe(const ObsArgs o) {
+// Shell sums go through a per-block shared array when it fits (local = true),
+// else straight to the global accumulators.
+__global__ void k_observe(const ObsArgs o, bool local) {
     extern __shared__ double acc[];
     const int r = blockIdx.y;
-    for (int j = threadIdx.x; j < o.nshells; j += blockDim.x) acc[j] = 0.0;
+    if (local)
+        for (int j = threadIdx.x; j < o.nshells; j += blockDim.x) acc[j] = 0.0;
     __shared__ double rough;
     if (threadIdx.x == 0) rough = 0.0;
     __syncthreads();
@@ -214,12 +217,16 @@ __global__ void k_observe(const ObsArgs o) {
             const float2 u = o.ref[idx];
             val = (double)u.x * u.x + (double)u.y * u.y;
         }
-        atomicAdd(&acc[shell_of(q)], w * val * o.norm);
+        if (local)
+            atomicAdd(&acc[shell_of(q)], w * val * o.norm);
+        else
+            atomicAdd(&o.shell_sum[(size_t)r * o.nshells + shell_of(q)], w * val * o.norm);
     }
     if (o.rough) atomicAdd(&rough, my_rough);
     __syncthreads();
-    for (int j = threadIdx.x; j < o.nshells; j += blockDim.x)
-        if (acc[j] != 0.0) atomicAdd(&o.shell_sum[(size_t)r * o.nshells + j], acc[j]);
+    if (local)
+        for (int j = threadIdx.x; j < o.nshells; j += blockDim.x)
+            if (acc[j] != 0.0) atomicAdd(&o.shell_sum[(size_t)r * o.nshells + j], acc[j]);
     if (threadIdx.x == 0 && o.rough) atomicAdd(&o.rough[r], rough);
 }
 
@@ -229,12 +236,13 @@ cudaError_t launch_observe(const ObsArgs& o, cudaStream_t s) {
     int blocks = (int)(nb < 1184 ? nb : 1184);
     if (blocks < 1) blocks = 1;
     dim3 grid(blocks, o.R);
-    const size_t sm = sizeof(double) * (size_t)o.nshells;
+    const bool local = sizeof(double) * (size_t)o.nshells <= 96 * 1024;
+    const size_t sm = local ? sizeof(double) * (size_t)o.nshells : 0;
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_observe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    k_observe<<<grid, 256, sm, s>>>(o);
+    k_observe<<<grid, 256, sm, s>>>(o, local);
     return cudaGetLastError();
 }
 

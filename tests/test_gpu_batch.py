@@ -23,7 +23,8 @@ def sft():
 
 
 MEMBERS = [W.kpz_1d(1024, replicas=5), W.kpz_1d(2048, replicas=3), W.kpz_1d(16384, replicas=2),
-           W.kpz_1d(4096, replicas=17), W.kpz_2d(n=[64, 64], replicas=2), W.kpz_1d(32768, replicas=1)]
+           W.kpz_1d(4096, replicas=17), W.kpz_2d(n=[64, 64], replicas=2), W.kpz_1d(32768, replicas=1),
+           W.kpz_1d(65536, replicas=2)]
 
 
 def cfg_of(sft, w, replica0=0):

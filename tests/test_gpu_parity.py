@@ -132,6 +132,8 @@ CASES = [
     ("kpz_2d_32", W.kpz_2d(n=[32, 32], replicas=2), 100),
     ("kpz_1d_256", W.kpz_1d(256, replicas=3), 100),
     ("kpz_1d_4096", W.kpz_1d(4096, replicas=1), 50),
+    ("kpz_1d_65536_cluster_R3", W.kpz_1d(65536, replicas=3, sigma0=0.2), 30),
+    ("model_a_1d_65536_setd2", W.model_a_64(d=1, n=[65536], dx=[1.0], scheme=2, sigma0=0.3), 30),
     ("model_a_1d_128", W.model_a_64(d=1, n=[128], dx=[1.0], replicas=2), 100),
     ("cgl_1d_64_setd2", W.cgl_2048(n=[64], d=1, dx=[0.5], replicas=2, p=[2.0, -0.5, 1e-3]), 100),
     ("model_a_16_nodealias", W.model_a_64(n=[16, 16], dealias=0), 100),
@@ -303,4 +305,20 @@ def test_structure_factor_twotime_roughness(sft, oracle_mod):
     assert np.allclose(ck[:ns], oc2, rtol=3e-5, atol=1e-9 * np.abs(oc2).max())
     rough = g.observe(sft.SFT_OBS_ROUGHNESS)
     assert np.allclose(rough, o.roughness(), rtol=2e-5)
+    g.close()
+
+
+def test_observables_large_shell_count(sft, oracle_mod):
+    """A 65536-point line has 32769 shells: the shell sums no longer fit shared
+    memory and accumulate in global memory instead."""
+    w = W.kpz_1d(65536, replicas=2, sigma0=0.3)
+    g, o = start_pair(sft, oracle_mod, w)
+    g.step(5)
+    o.step(5)
+    ns = g.nshells()
+    sk = g.observe(sft.SFT_OBS_SK)
+    ov, oc = o.shells(0)
+    assert ns == len(ov) and np.array_equal(sk[ns:], oc)
+    assert np.allclose(sk[:ns], ov, rtol=2e-5, atol=1e-12 * np.abs(ov).max())
+    assert np.allclose(g.observe(sft.SFT_OBS_ROUGHNESS), o.roughness(), rtol=2e-5)
     g.close()
