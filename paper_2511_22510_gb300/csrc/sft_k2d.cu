@@ -16,11 +16,28 @@
 #include "sft_async.cuh"
 #include "sft_step_common.cuh"
 
-#ifndef SFT_CTA
-#define SFT_CTA 128
+// Launch shape of the row pass: SFT_ROW_CTA threads per block (16 values per
+// thread), SFT_ROW_MINB resident blocks per SM requested from the register
+// allocator.
+#ifndef SFT_ROW_CTA
+#define SFT_ROW_CTA 128
 #endif
-#ifndef SFT_MINB
-#define SFT_MINB 4  // minimum resident blocks per SM requested from the register allocator
+#ifndef SFT_ROW_MINB
+#define SFT_ROW_MINB 4
+#endif
+// Column pass on columns of 512 points and more: SFT_COL_EMAX values per
+// thread, SFT_COL_CTA threads per block and SFT_COL_THREADS_SM resident threads
+// per SM (more warps in flight hide the HBM and L1 latency of the streaming
+// update better than longer per-thread FFT radices).  Shorter columns use 16
+// values per thread, 128-thread blocks and 4 blocks per SM.
+#ifndef SFT_COL_EMAX
+#define SFT_COL_EMAX 8
+#endif
+#ifndef SFT_COL_CTA
+#define SFT_COL_CTA 256
+#endif
+#ifndef SFT_COL_THREADS_SM
+#define SFT_COL_THREADS_SM 768
 #endif
 #ifndef SFT_RPB
 #define SFT_RPB 4  // replicas per column-pass block: the column's table and twiddle reads then hit L1
@@ -59,7 +76,7 @@ template <int M>
 struct RowCfg {
     using PL = FftPlan<M>;
     static constexpr int T = PL::T;
-    static constexpr int ROWS = T >= SFT_CTA ? 1 : SFT_CTA / T;
+    static constexpr int ROWS = T >= SFT_ROW_CTA ? 1 : SFT_ROW_CTA / T;
     static constexpr int THREADS = ROWS * T;
     // row stride of the spectral tile (a row also serves as its team's FFT exchange buffer):
     // the transposing tile loads/stores of a half-warp touch ROWS rows x 16/ROWS columns, which
@@ -70,7 +87,7 @@ struct RowCfg {
 };
 
 template <int M, int NL, int MODE>
-__global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_MINB) k2_rows_real(const StepArgs a) {
+__global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_ROW_MINB) k2_rows_real(const StepArgs a) {
     using C = RowCfg<M>;
     using PL = FftPlan<M>;
     constexpr int T = PL::T, E = PL::E, ROWS = C::ROWS, TS = C::TS;
@@ -227,12 +244,18 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_MINB) k2_rows_real(con
     }
 }
 
+constexpr int kColEM = SFT_COL_EMAX;
+
 template <int NY>
 struct ColCfg {
-    using PL = FftPlan<NY>;
+    static constexpr bool WIDE = NY >= 512;
+    using PL = FftPlan<NY, kColEM>;
     static constexpr int T = PL::T;
-    static constexpr int COLS = T >= SFT_CTA ? 1 : SFT_CTA / T;
+    static constexpr int CTA = WIDE ? SFT_COL_CTA : 128;
+    static constexpr int COLS = T >= CTA ? 1 : CTA / T;
     static constexpr int THREADS = COLS * T;
+    static constexpr int PER_SM = WIDE ? SFT_COL_THREADS_SM : 512;
+    static constexpr int MINB = PER_SM / THREADS > 1 ? PER_SM / THREADS : 1;
     static constexpr int XB = PL::BUF;
     static constexpr size_t smem() { return sizeof(float2) * (size_t)COLS * XB; }
 };
@@ -241,19 +264,19 @@ struct ColCfg {
 // partners (a_y > ny/2) take the conjugate of a_y' = ny - a_y, self-conjugate
 // modes drop their imaginary part.  Warp-uniform when teams share a warp.
 template <int NY>
-__device__ __forceinline__ void fixup_plane(float2 (&out)[FftPlan<NY>::E], float2* xb, int t, bool plane) {
-    using PL = FftPlan<NY>;
+__device__ __forceinline__ void fixup_plane(float2 (&out)[FftPlan<NY, kColEM>::E], float2* xb, int t, bool plane) {
+    using PL = FftPlan<NY, kColEM>;
     constexpr int T = PL::T, E = PL::E;
     if (plane || T < 32) {
         team_sync<T>();
 #pragma unroll
-        for (int e = 0; e < E; ++e) xb[xpos<NY>(t + T * e)] = out[e];
+        for (int e = 0; e < E; ++e) xb[xpos<NY, kColEM>(t + T * e)] = out[e];
         team_sync<T>();
         if (plane) {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int ay = t + T * e;
-                if (2 * ay > NY) out[e] = cconj(xb[xpos<NY>(NY - ay)]);
+                if (2 * ay > NY) out[e] = cconj(xb[xpos<NY, kColEM>(NY - ay)]);
                 if (ay == 0 || 2 * ay == NY) out[e].y = 0.f;
             }
         }
@@ -263,9 +286,9 @@ __device__ __forceinline__ void fixup_plane(float2 (&out)[FftPlan<NY>::E], float
 // P <- IFFT_y(M phi / N^2) for one column (and, for KPZ, P_y <- IFFT_y(i k_y M phi / N^2)):
 // the dealiased input of the next row pass.
 template <int NY, int NL>
-__device__ __forceinline__ void emit_p(const StepArgs& a, const float2 (&out)[FftPlan<NY>::E], bool has_p, int cc,
+__device__ __forceinline__ void emit_p(const StepArgs& a, const float2 (&out)[FftPlan<NY, kColEM>::E], bool has_p, int cc,
                                        size_t colbase, float2* xb, int t) {
-    using PL = FftPlan<NY>;
+    using PL = FftPlan<NY, kColEM>;
     constexpr int T = PL::T, E = PL::E;
     if (!(has_p || T < 32)) return;
     float2 v[E];
@@ -278,8 +301,8 @@ __device__ __forceinline__ void emit_p(const StepArgs& a, const float2 (&out)[Ff
         v[e] = (has_p && inm) ? cscale(out[e], a.scale) : czero();
         if constexpr (NL == NL_GRAD2) vy[e] = cscale(cmuli(v[e]), a.dk * (float)odd_idx(ay, NY));
     }
-    fft_line<NY, true>(v, xb, t, a.tw_a);
-    if constexpr (NL == NL_GRAD2) fft_line<NY, true>(vy, xb, t, a.tw_a);
+    fft_line<NY, true, kColEM>(v, xb, t, a.tw_a);
+    if constexpr (NL == NL_GRAD2) fft_line<NY, true, kColEM>(vy, xb, t, a.tw_a);
     if (has_p) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -290,9 +313,9 @@ __device__ __forceinline__ void emit_p(const StepArgs& a, const float2 (&out)[Ff
 }
 
 template <int NY, int NL, int MODE>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(const StepArgs a) {
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS, ColCfg<NY>::MINB) k2_cols_real(const StepArgs a) {
     using C = ColCfg<NY>;
-    using PL = FftPlan<NY>;
+    using PL = FftPlan<NY, kColEM>;
     constexpr int T = PL::T, E = PL::E, COLS = C::COLS, XB = C::XB;
     extern __shared__ float2 sm[];
     const int team = threadIdx.x / T, t = threadIdx.x % T;
@@ -313,16 +336,16 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(co
         if (!valid && T >= 32) return;
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = a.qin[colbase + t + T * e];
-        fft_line<NY, false>(v, xb, t, tw);
+        fft_line<NY, false, kColEM>(v, xb, t, tw);
         team_sync<T>();
 #pragma unroll
-        for (int e = 0; e < E; ++e) xb[xpos<NY>(t + T * e)] = v[e];
+        for (int e = 0; e < E; ++e) xb[xpos<NY, kColEM>(t + T * e)] = v[e];
         team_sync<T>();
         if (plane) {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int ay = t + T * e;
-                if (2 * ay > NY) v[e] = cconj(xb[xpos<NY>(NY - ay)]);
+                if (2 * ay > NY) v[e] = cconj(xb[xpos<NY, kColEM>(NY - ay)]);
                 if (ay == 0 || 2 * ay == NY) v[e].y = 0.f;
             }
         }
@@ -334,7 +357,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(co
         if (!valid && T >= 32) return;
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = cscale(a.phi[colbase + t + T * e], a.scale);
-        fft_line<NY, true>(v, xb, t, tw);
+        fft_line<NY, true, kColEM>(v, xb, t, tw);
         if (valid) {
 #pragma unroll
             for (int e = 0; e < E; ++e) a.pout[colbase + t + T * e] = v[e];
@@ -347,7 +370,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(co
         if (has_f || T < 32) {
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = has_f ? a.qin[colbase + t + T * e] : czero();
-            fft_line<NY, false>(v, xb, t, tw);
+            fft_line<NY, false, kColEM>(v, xb, t, tw);
         }
         float2 out[E];
 #pragma unroll
@@ -373,13 +396,13 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(co
         if (plane || T < 32) {
             team_sync<T>();
 #pragma unroll
-            for (int e = 0; e < E; ++e) xb[xpos<NY>(t + T * e)] = out[e];
+            for (int e = 0; e < E; ++e) xb[xpos<NY, kColEM>(t + T * e)] = out[e];
             team_sync<T>();
             if (plane) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int ay = t + T * e;
-                    if (2 * ay > NY) out[e] = cconj(xb[xpos<NY>(NY - ay)]);
+                    if (2 * ay > NY) out[e] = cconj(xb[xpos<NY, kColEM>(NY - ay)]);
                     if (ay == 0 || 2 * ay == NY) out[e].y = 0.f;
                 }
             }
@@ -404,8 +427,8 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(co
                 v[e] = has_f ? a.qin[colbase + t + T * e] : czero();
                 dv[e] = has_f ? a.dqin[colbase + t + T * e] : czero();
             }
-            fft_line<NY, false>(v, xb, t, tw);
-            fft_line<NY, false>(dv, xb, t, tw);
+            fft_line<NY, false, kColEM>(v, xb, t, tw);
+            fft_line<NY, false, kColEM>(dv, xb, t, tw);
         }
         float2 out[E];
 #pragma unroll
@@ -450,7 +473,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(co
             if (has_f || T < 32) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[e] = has_f ? a.dqin[colbase + t + T * e] : czero();
-                fft_line<NY, false>(v, xb, t, tw);
+                fft_line<NY, false, kColEM>(v, xb, t, tw);
             }
 #pragma unroll
             for (int e = 0; e < E; ++e) {
@@ -478,7 +501,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, SFT_MINB) k2_cols_real(co
                 const Coefs co = load_coefs<false>(a.tab, cc * (NY / 2 + 1) + abs(ays), false);
                 v[e] = (has_p && inm) ? cscale(lam[e], co.A.x * nl_prefactor(a, q).x * a.scale) : czero();
             }
-            fft_line<NY, true>(v, xb, t, tw);
+            fft_line<NY, true, kColEM>(v, xb, t, tw);
             if (has_p) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) a.dpout[colbase + t + T * e] = v[e];

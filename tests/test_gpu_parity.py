@@ -130,6 +130,9 @@ CASES = [
     ("model_b_64_setd2", W.model_b_1024(n=[64, 64], scheme=2, h=0.025, sigma0=0.3), 100),
     ("model_b_128_setd1_R3", W.model_b_1024(n=[128, 128], replicas=3, sigma0=0.3), 40),
     ("kpz_2d_32", W.kpz_2d(n=[32, 32], replicas=2), 100),
+    ("kpz_2d_512", W.kpz_2d(n=[512, 512], replicas=2), 10),
+    ("model_a_2048_setd1", W.model_a_64(n=[2048, 2048], replicas=1, sigma0=0.3), 3),
+    ("model_b_4096_setd2", W.model_b_1024(n=[4096, 4096], scheme=2, h=0.025, sigma0=0.3), 2),
     ("kpz_1d_256", W.kpz_1d(256, replicas=3), 100),
     ("kpz_1d_4096", W.kpz_1d(4096, replicas=1), 50),
     ("kpz_1d_65536_cluster_R3", W.kpz_1d(65536, replicas=3, sigma0=0.2), 30),
