@@ -52,10 +52,13 @@ __global__ void __launch_bounds__(CRowCfg<N>::THREADS) k2_rows_cplx(const StepAr
 #pragma unroll
         for (int e = 0; e < E; ++e) z[e] = yok ? src[t + T * e] : czero();
     } else {
-        for (int f = threadIdx.x; f < ROWS * ncols; f += blockDim.x) {
-            const int c = f / ROWS, yy = f % ROWS;
-            sm[yy * TS + c] = (y0 + yy < ny) ? a.pin[((size_t)rep * hx + c) * ny + y0 + yy] : czero();
-        }
+        block_copy<C::THREADS, ROWS * N>(
+            ROWS * ncols,
+            [&](int f) {
+                const int c = f / ROWS, yy = f % ROWS;
+                return (y0 + yy < ny) ? a.pin[((size_t)rep * hx + c) * ny + y0 + yy] : czero();
+            },
+            [&](int f, float2 v) { sm[(f % ROWS) * TS + f / ROWS] = v; });
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -84,10 +87,12 @@ __global__ void __launch_bounds__(CRowCfg<N>::THREADS) k2_rows_cplx(const StepAr
             if (cmask_x(ax, nx, ncols)) trow[ccomp_x(ax, nx, ncols)] = z[e];
         }
         __syncthreads();
-        for (int f = threadIdx.x; f < ROWS * ncols; f += blockDim.x) {
-            const int c = f / ROWS, yy = f % ROWS;
-            if (y0 + yy < ny) a.qout[((size_t)rep * hx + c) * ny + y0 + yy] = sm[yy * TS + c];
-        }
+        block_copy<C::THREADS, ROWS * N>(
+            ROWS * ncols, [&](int f) { return sm[(f % ROWS) * TS + f / ROWS]; },
+            [&](int f, float2 v) {
+                const int c = f / ROWS, yy = f % ROWS;
+                if (y0 + yy < ny) a.qout[((size_t)rep * hx + c) * ny + y0 + yy] = v;
+            });
     }
 }
 

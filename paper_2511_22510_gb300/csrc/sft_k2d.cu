@@ -72,8 +72,9 @@ __device__ __forceinline__ void row_post(float2 (&z)[FftPlan<M>::E], float2* xb,
     if (t == 0 && M < ncols) trow[M] = make_float2(z0.x - z0.y, 0.f);
 }
 
-template <int M>
+template <int M_>
 struct RowCfg {
+    static constexpr int M = M_;
     using PL = FftPlan<M>;
     static constexpr int T = PL::T;
     static constexpr int ROWS = T >= SFT_ROW_CTA ? 1 : SFT_ROW_CTA / T;
@@ -85,6 +86,35 @@ struct RowCfg {
     static constexpr int TS = ROWS >= 16 ? (PL::BUF | 1) : ((PL::BUF + 15) / 16) * 16 + TSM;
     static constexpr size_t smem(int ntile) { return sizeof(float2) * (size_t)ntile * ROWS * TS; }
 };
+
+// Spectral tile of a row-pass block: tile[yy][c] = src[rowbase + c ny + y0 + yy]
+// for the ROWS rows y0 + yy and the columns c < ncols; columns ncols..M are
+// zero (outside the dealiasing band).
+template <class C>
+__device__ __forceinline__ void load_tile(float2* tile, const float2* __restrict__ src, size_t rowbase, int ncols,
+                                          int ny, int y0) {
+    constexpr int ROWS = C::ROWS, TS = C::TS, NEL = C::ROWS * (C::M + 1);
+    block_copy<C::THREADS, NEL>(
+        NEL,
+        [&](int f) {
+            const int c = f / ROWS, yy = f % ROWS;
+            return (c < ncols && y0 + yy < ny) ? src[rowbase + (size_t)c * ny + y0 + yy] : czero();
+        },
+        [&](int f, float2 v) { tile[(f % ROWS) * TS + f / ROWS] = v; });
+}
+
+// dst[rowbase + c ny + y0 + yy] = tile[yy][c] for c < ncols
+template <class C>
+__device__ __forceinline__ void store_tile(const float2* tile, float2* __restrict__ dst, size_t rowbase, int ncols,
+                                           int ny, int y0) {
+    constexpr int ROWS = C::ROWS, TS = C::TS;
+    block_copy<C::THREADS, C::ROWS * (C::M + 1)>(
+        ROWS * ncols, [&](int f) { return tile[(f % ROWS) * TS + f / ROWS]; },
+        [&](int f, float2 v) {
+            const int c = f / ROWS, yy = f % ROWS;
+            if (y0 + yy < ny) dst[rowbase + (size_t)c * ny + y0 + yy] = v;
+        });
+}
 
 template <int M, int NL, int MODE>
 __global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_ROW_MINB) k2_rows_real(const StepArgs a) {
@@ -101,6 +131,7 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_ROW_MINB) k2_rows_real
     const int y0 = blockIdx.x * ROWS;
     const int y = y0 + team;
     const bool yok = y < ny;
+    const size_t rowbase = (size_t)rep * hx * ny;
     float2* xb = tile + team * TS;  // the team's own tile row doubles as its exchange buffer
     const float2* __restrict__ twM = a.tw_a;
     const float2* __restrict__ twN = a.tw_b;
@@ -109,17 +140,8 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_ROW_MINB) k2_rows_real
     if constexpr (MODE == MODE_TAN || MODE == MODE_ADJ) {
         // tangent: q' = 3 psi^2 dpsi next to q = psi^3; adjoint: v = 3 psi^2 w.
         // tile 0: primal P (psi), tile 1: tangent dP (dpsi) or adjoint W.
-        for (int f = threadIdx.x; f < ROWS * (M + 1); f += blockDim.x) {
-            const int c = f / ROWS, yy = f % ROWS;
-            float2 v0 = czero(), v1 = czero();
-            if (c < ncols && y0 + yy < ny) {
-                const size_t off = ((size_t)rep * hx + c) * ny + y0 + yy;
-                v0 = a.pin[off];
-                v1 = a.dpin[off];
-            }
-            tile[yy * TS + c] = v0;
-            tile[ROWS * TS + yy * TS + c] = v1;
-        }
+        load_tile<C>(tile, a.pin, rowbase, ncols, ny, y0);
+        load_tile<C>(tile + ROWS * TS, a.dpin, rowbase, ncols, ny, y0);
         __syncthreads();
         const float2* trow = tile + team * TS;
         float2* drow = tile + ROWS * TS + team * TS;
@@ -147,14 +169,8 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_ROW_MINB) k2_rows_real
             row_post<M>(z, xb, tile + team * TS, ncols, t, twN);
         }
         __syncthreads();
-        for (int f = threadIdx.x; f < ROWS * ncols; f += blockDim.x) {
-            const int c = f / ROWS, yy = f % ROWS;
-            if (y0 + yy < ny) {
-                const size_t off = ((size_t)rep * hx + c) * ny + y0 + yy;
-                a.dqout[off] = tile[ROWS * TS + yy * TS + c];
-                if constexpr (MODE == MODE_TAN) a.qout[off] = tile[yy * TS + c];
-            }
-        }
+        store_tile<C>(tile + ROWS * TS, a.dqout, rowbase, ncols, ny, y0);
+        if constexpr (MODE == MODE_TAN) store_tile<C>(tile, a.qout, rowbase, ncols, ny, y0);
         return;
     }
     if constexpr (MODE == MODE_FWD) {
@@ -165,17 +181,8 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_ROW_MINB) k2_rows_real
             z[e] = yok ? *reinterpret_cast<const float2*>(src + 2 * m) : czero();
         }
     } else {
-        for (int f = threadIdx.x; f < ROWS * (M + 1); f += blockDim.x) {
-            const int c = f / ROWS, yy = f % ROWS;
-            float2 v = czero(), vy = czero();
-            if (c < ncols && y0 + yy < ny) {
-                const size_t off = ((size_t)rep * hx + c) * ny + y0 + yy;
-                v = a.pin[off];
-                if constexpr (GRAD) vy = a.pyin[off];
-            }
-            tile[yy * TS + c] = v;
-            if constexpr (GRAD) tile[ROWS * TS + yy * TS + c] = vy;
-        }
+        load_tile<C>(tile, a.pin, rowbase, ncols, ny, y0);
+        if constexpr (GRAD) load_tile<C>(tile + ROWS * TS, a.pyin, rowbase, ncols, ny, y0);
         __syncthreads();
         const float2* trow = tile + team * TS;
         if constexpr (GRAD) {
@@ -237,10 +244,7 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, SFT_ROW_MINB) k2_rows_real
         }
         if (t == 0 && M < ncols) trow[M] = make_float2(z0.x - z0.y, 0.f);
         __syncthreads();
-        for (int f = threadIdx.x; f < ROWS * ncols; f += blockDim.x) {
-            const int c = f / ROWS, yy = f % ROWS;
-            if (y0 + yy < ny) a.qout[((size_t)rep * hx + c) * ny + y0 + yy] = tile[yy * TS + c];
-        }
+        store_tile<C>(tile, a.qout, rowbase, ncols, ny, y0);
     }
 }
 

@@ -74,8 +74,9 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
     float2* pdst = DIFF ? a.dpout : a.pout;
     if constexpr (MODE == MODE_FWD || MODE == MODE_STEP || MODE == MODE_TAN || MODE == MODE_ADJ) {
         const bool has_f = (MODE == MODE_FWD) || c < a.ncols;
-        for (int f = threadIdx.x; f < N * N; f += blockDim.x)
-            S[(f / N) * RS + f % N] = has_f ? qsrc[base + f] : czero();
+        block_copy<C::THREADS, N * N>(
+            N * N, [&](int f) { return has_f ? qsrc[base + f] : czero(); },
+            [&](int f, float2 v) { S[(f / N) * RS + f % N] = v; });
         __syncthreads();
         if (has_f) {
             plane_fft<N, true, false>(S, xb, team, t, tw);
@@ -85,7 +86,8 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
         }
     } else {
         // INV / PRIME / ADJ_PRIME: the state goes straight to the inverse transforms
-        for (int f = threadIdx.x; f < N * N; f += blockDim.x) S[(f / N) * RS + f % N] = state[base + f];
+        block_copy<C::THREADS, N * N>(
+            N * N, [&](int f) { return state[base + f]; }, [&](int f, float2 v) { S[(f / N) * RS + f % N] = v; });
         __syncthreads();
     }
 
@@ -159,7 +161,8 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
             }
             __syncthreads();
         }
-        for (int f = threadIdx.x; f < N * N; f += blockDim.x) a.phi[base + f] = S[(f / N) * RS + f % N];
+        block_copy<C::THREADS, N * N>(
+            N * N, [&](int f) { return S[(f / N) * RS + f % N]; }, [&](int f, float2 v) { a.phi[base + f] = v; });
         return;
     } else {
         // inverse transforms of M phi / N^3 (INV: no mask; adjoint: times A s) -> row-pass input
@@ -183,7 +186,8 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
         __syncthreads();
         plane_fft<N, true, true>(S, xb, team, t, tw);
         __syncthreads();
-        for (int f = threadIdx.x; f < N * N; f += blockDim.x) pdst[base + f] = S[(f / N) * RS + f % N];
+        block_copy<C::THREADS, N * N>(
+            N * N, [&](int f) { return S[(f / N) * RS + f % N]; }, [&](int f, float2 v) { pdst[base + f] = v; });
     }
 }
 

@@ -101,6 +101,31 @@ __device__ __forceinline__ float2 eta_of(float2 z, bool selfc) {
     return make_float2(z.x * r2, z.y * r2);
 }
 
+// Block-wide copy of the elements f in [0, n), n <= NMAX: thread i takes
+// f = i, i + THREADS, ... (THREADS = blockDim.x).  Loads are issued in batches
+// of up to 24 per thread before the matching stores, so a whole batch of
+// global loads is in flight at once; a loop with one load and one dependent
+// store per trip would wait a full memory latency per trip.
+template <int THREADS, int NMAX, class Load, class Store>
+__device__ __forceinline__ void block_copy(int n, Load&& load, Store&& store) {
+    constexpr int NIT = (NMAX + THREADS - 1) / THREADS;
+    constexpr int B = NIT <= 24 ? NIT : 16;
+#pragma unroll
+    for (int i0 = 0; i0 < NIT; i0 += B) {
+        decltype(load(0)) v[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int f = (int)threadIdx.x + (i0 + u) * THREADS;
+            if (i0 + u < NIT && f < n) v[u] = load(f);
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int f = (int)threadIdx.x + (i0 + u) * THREADS;
+            if (i0 + u < NIT && f < n) store(f, v[u]);
+        }
+    }
+}
+
 __device__ __forceinline__ long long current_step(const StepArgs& a) { return *a.step_base + a.k_in_chunk; }
 
 __device__ __forceinline__ void flag_nonfinite(const StepArgs& a, float2 v, long long step) {
