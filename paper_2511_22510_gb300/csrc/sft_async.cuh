@@ -59,6 +59,10 @@ __device__ __forceinline__ void cp_async_8(void* dst_smem, const void* src) {
 __device__ __forceinline__ void cp_async_16(void* dst_smem, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
 }
+// 16-byte copy that bypasses L1 (streamed data read once)
+__device__ __forceinline__ void cp_async_16_cg(void* dst_smem, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 

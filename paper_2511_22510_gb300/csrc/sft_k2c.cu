@@ -9,6 +9,7 @@
 //   column pass: Q --FFT_y--> F = M s DFT[|A|^2 A], s = -(1 + i beta);
 //                phi <- f1 phi + A F + B F_prev + g eta (complex coefficients,
 //                complex noise on every mode); P <- IFFT_y(M phi / N^2)
+#include "sft_async.cuh"
 #include "sft_step_common.cuh"
 
 namespace sft {
@@ -96,6 +97,10 @@ __global__ void __launch_bounds__(CRowCfg<N>::THREADS) k2_rows_cplx(const StepAr
     }
 }
 
+// Replicas per column-pass block: the column's coefficient and twiddle reads
+// then hit the caches for every replica after the first.
+constexpr int kCRpb = 4;
+
 template <int NY>
 struct CColCfg {
     using PL = FftPlan<NY>;
@@ -103,97 +108,119 @@ struct CColCfg {
     static constexpr int COLS = T >= 128 ? 1 : 128 / T;
     static constexpr int THREADS = COLS * T;
     static constexpr int XB = PL::BUF;
+    // the step stages each column's state and SETD2 history behind the exchange
+    // buffers, at a 16-byte aligned offset
+    static constexpr int SOFF = (COLS * XB + 1) / 2 * 2;
     static constexpr size_t smem() { return sizeof(float2) * (size_t)COLS * XB; }
+    static constexpr size_t smem_step() { return sizeof(float2) * ((size_t)SOFF + 2 * (size_t)COLS * NY); }
 };
 
+template <int NY, int T>
+__device__ __forceinline__ void stage_ccolumn(float2* dst, const float2* src, int t) {
+#pragma unroll
+    for (int i = t; i < NY / 2; i += T) cp_async_16_cg(dst + 2 * i, src + 2 * i);
+}
+
 template <int NY, int MODE>
-__global__ void __launch_bounds__(CColCfg<NY>::THREADS) k2_cols_cplx(const StepArgs a) {
+__global__ void __launch_bounds__(CColCfg<NY>::THREADS, 512 / CColCfg<NY>::THREADS) k2_cols_cplx(const StepArgs a) {
     using C = CColCfg<NY>;
     using PL = FftPlan<NY>;
     constexpr int T = PL::T, E = PL::E, COLS = C::COLS, XB = C::XB;
     extern __shared__ float2 sm[];
     const int team = threadIdx.x / T, t = threadIdx.x % T;
-    const int rep = blockIdx.y;
     const int c = blockIdx.x * COLS + team;  // a_x
     const bool valid = c < a.hx;
     const int ax = valid ? c : a.hx - 1;
     const int nx = a.nx, ncols = a.ncols;
     float2* xb = sm + team * XB;
     const float2* __restrict__ tw = a.tw_a;
-    const size_t colbase = ((size_t)rep * a.hx + ax) * NY;
     const bool inx = !a.dealias || cmask_x(ax, nx, ncols);
-    const size_t cbase = ((size_t)rep * a.hx + (inx ? ccomp_x(ax, nx, ncols) : 0)) * NY;
+    const int axs = signed_idx(ax, nx);
     if (!valid && T >= 32) return;
-    float2 v[E];
-    if constexpr (MODE == MODE_FWD) {
+    for (int ri = 0; ri < kCRpb; ++ri) {
+        const int rep = blockIdx.y * kCRpb + ri;
+        if (rep >= a.R) break;
+        const size_t colbase = ((size_t)rep * a.hx + ax) * NY;
+        const size_t cbase = ((size_t)rep * a.hx + (inx ? ccomp_x(ax, nx, ncols) : 0)) * NY;
+        float2 v[E];
+        if constexpr (MODE == MODE_FWD) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = a.qin[colbase + t + T * e];
-        fft_line<NY, false>(v, xb, t, tw);
-        if (valid) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) a.phi[colbase + t + T * e] = v[e];
-        }
-        return;
-    } else if constexpr (MODE == MODE_INV) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = cscale(a.phi[colbase + t + T * e], a.scale);
-        fft_line<NY, true>(v, xb, t, tw);
-        if (valid) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) a.pout[colbase + t + T * e] = v[e];
-        }
-        return;
-    } else {
-        float2 out[E];
-        const int axs = signed_idx(ax, nx);
-        if constexpr (MODE == MODE_STEP) {
-            const long long step = current_step(a);
-            const bool first = (a.scheme == 2) && (step == *a.first_step);
-            const bool has_f = valid && inx;
-            if (has_f || T < 32) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) v[e] = has_f ? a.qin[cbase + t + T * e] : czero();
-                fft_line<NY, false>(v, xb, t, tw);
-            }
-            const float2 s = make_float2(a.s0, a.s0i);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if ((e & 1) == 0)
-                    team_normal_pair<T>(a.seed, (uint64_t)ax * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep),
-                                        out[e], out[e + 1]);
-                const int ay = t + T * e;
-                const int ays = signed_idx(ay, NY);
-                const bool inm = has_f && (!a.dealias || 3 * abs(ays) < NY);
-                const float2 F = inm ? cmul(s, v[e]) : czero();
-                const Coefs co = load_coefs<true>(a.tab, abs(axs) * (NY / 2 + 1) + abs(ays), first);
-                float2 Fp = czero();
-                if (a.scheme == 2 && has_f) Fp = a.fprev[colbase + ay];
-                out[e] = setd_update<true>(co, a.phi[colbase + ay], F, Fp, eta_of(out[e], false));
-                if (a.scheme == 2 && has_f && valid) a.fprev[colbase + ay] = F;
-            }
+            for (int e = 0; e < E; ++e) v[e] = a.qin[colbase + t + T * e];
+            fft_line<NY, false>(v, xb, t, tw);
             if (valid) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    a.phi[colbase + t + T * e] = out[e];
-                    flag_nonfinite(a, out[e], step);
-                }
+                for (int e = 0; e < E; ++e) a.phi[colbase + t + T * e] = v[e];
             }
-        } else {  // MODE_PRIME
+        } else if constexpr (MODE == MODE_INV) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) out[e] = a.phi[colbase + t + T * e];
-        }
-        const bool has_p = valid && inx;
-        if (has_p || T < 32) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int ay = t + T * e;
-                const bool inm = has_p && (!a.dealias || 3 * abs(signed_idx(ay, NY)) < NY);
-                v[e] = inm ? cscale(out[e], a.scale) : czero();
-            }
+            for (int e = 0; e < E; ++e) v[e] = cscale(a.phi[colbase + t + T * e], a.scale);
             fft_line<NY, true>(v, xb, t, tw);
-            if (has_p) {
+            if (valid) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) a.pout[cbase + t + T * e] = v[e];
+                for (int e = 0; e < E; ++e) a.pout[colbase + t + T * e] = v[e];
+            }
+        } else {
+            float2 out[E];
+            if constexpr (MODE == MODE_STEP) {
+                const long long step = current_step(a);
+                const bool first = (a.scheme == 2) && (step == *a.first_step);
+                const bool has_f = valid && inx;
+                // the state column (and SETD2 history) streams into shared memory during the FFT of Q
+                float2* sphi = sm + C::SOFF + team * NY;
+                float2* sfp = sm + C::SOFF + (COLS + team) * NY;
+                team_sync<T>();  // this team's reads of the staging rows (previous replica) are complete
+                if (valid) {
+                    stage_ccolumn<NY, T>(sphi, a.phi + colbase, t);
+                    if (a.scheme == 2 && has_f) stage_ccolumn<NY, T>(sfp, a.fprev + colbase, t);
+                }
+                cp_async_commit();
+                if (has_f || T < 32) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) v[e] = has_f ? a.qin[cbase + t + T * e] : czero();
+                    fft_line<NY, false>(v, xb, t, tw);
+                }
+                cp_async_wait_all();
+                team_sync<T>();
+                const float2 s = make_float2(a.s0, a.s0i);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & 1) == 0)
+                        team_normal_pair<T>(a.seed, (uint64_t)ax * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep),
+                                            out[e], out[e + 1]);
+                    const int ay = t + T * e;
+                    const int ays = signed_idx(ay, NY);
+                    const bool inm = has_f && (!a.dealias || 3 * abs(ays) < NY);
+                    const float2 F = inm ? cmul(s, v[e]) : czero();
+                    const Coefs co = load_coefs<true>(a.tab, abs(axs) * (NY / 2 + 1) + abs(ays), first);
+                    float2 Fp = czero();
+                    if (a.scheme == 2 && has_f) Fp = sfp[ay];
+                    out[e] = setd_update<true>(co, sphi[ay], F, Fp, eta_of(out[e], false));
+                    if (a.scheme == 2 && has_f && valid) a.fprev[colbase + ay] = F;
+                }
+                if (valid) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        a.phi[colbase + t + T * e] = out[e];
+                        flag_nonfinite(a, out[e], step);
+                    }
+                }
+            } else {  // MODE_PRIME
+#pragma unroll
+                for (int e = 0; e < E; ++e) out[e] = a.phi[colbase + t + T * e];
+            }
+            const bool has_p = valid && inx;
+            if (has_p || T < 32) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int ay = t + T * e;
+                    const bool inm = has_p && (!a.dealias || 3 * abs(signed_idx(ay, NY)) < NY);
+                    v[e] = inm ? cscale(out[e], a.scale) : czero();
+                }
+                fft_line<NY, true>(v, xb, t, tw);
+                if (has_p) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) a.pout[cbase + t + T * e] = v[e];
+                }
             }
         }
     }
@@ -216,14 +243,14 @@ static cudaError_t run_crows(const StepArgs& a, cudaStream_t s) {
 template <int NY, int MODE>
 static cudaError_t run_ccols(const StepArgs& a, cudaStream_t s) {
     using C = CColCfg<NY>;
+    const size_t sm = MODE == MODE_STEP ? C::smem_step() : C::smem();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k2_cols_cplx<NY, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem());
+        cudaError_t e = cudaFuncSetAttribute(k2_cols_cplx<NY, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k2_cols_cplx<NY, MODE><<<dim3((a.hx + C::COLS - 1) / C::COLS, a.R), C::THREADS, C::smem(), s>>>(a);
+    k2_cols_cplx<NY, MODE><<<dim3((a.hx + C::COLS - 1) / C::COLS, (a.R + kCRpb - 1) / kCRpb), C::THREADS, sm, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -261,8 +261,19 @@ struct ColCfg {
     static constexpr int PER_SM = WIDE ? SFT_COL_THREADS_SM : 512;
     static constexpr int MINB = PER_SM / THREADS > 1 ? PER_SM / THREADS : 1;
     static constexpr int XB = PL::BUF;
+    // the step stages each column's state (and SETD2 history) in shared memory
+    // behind the exchange buffers, at a 16-byte aligned offset
+    static constexpr int SOFF = (COLS * XB + 1) / 2 * 2;
     static constexpr size_t smem() { return sizeof(float2) * (size_t)COLS * XB; }
+    static constexpr size_t smem_step() { return sizeof(float2) * ((size_t)SOFF + 2 * (size_t)COLS * NY); }
 };
+
+// Asynchronous copy of one column (NY values) into shared memory, 16 bytes per copy.
+template <int NY, int T>
+__device__ __forceinline__ void stage_column(float2* dst, const float2* src, int t) {
+#pragma unroll
+    for (int i = t; i < NY / 2; i += T) cp_async_16_cg(dst + 2 * i, src + 2 * i);
+}
 
 // Hermitian fix-up of one column held by a team on the planes a_x in {0, nx/2}:
 // partners (a_y > ny/2) take the conjugate of a_y' = ny - a_y, self-conjugate
@@ -371,11 +382,22 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, ColCfg<NY>::MINB) k2_cols
         const long long step = current_step(a);
         const bool first = (a.scheme == 2) && (step == *a.first_step);
         const bool has_f = valid && cc < a.ncols;
+        // the state column (and SETD2 history) streams into shared memory while the FFT of Q runs
+        float2* sphi = sm + C::SOFF + team * NY;
+        float2* sfp = sm + C::SOFF + (COLS + team) * NY;
+        team_sync<T>();  // this team's reads of the staging rows (previous replica) are complete
+        if (valid) {
+            stage_column<NY, T>(sphi, a.phi + colbase, t);
+            if (a.scheme == 2 && has_f) stage_column<NY, T>(sfp, a.fprev + colbase, t);
+        }
+        cp_async_commit();
         if (has_f || T < 32) {
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = has_f ? a.qin[colbase + t + T * e] : czero();
             fft_line<NY, false, kColEM>(v, xb, t, tw);
         }
+        cp_async_wait_all();
+        team_sync<T>();
         float2 out[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -389,9 +411,9 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, ColCfg<NY>::MINB) k2_cols
             float2 F = czero();
             if (has_f && inm) F = cscale(v[e], nl_prefactor(a, q).x);
             const Coefs co = load_coefs<false>(a.tab, cc * (NY / 2 + 1) + abs(ays), first);
-            const float2 ph = a.phi[colbase + ay];
+            const float2 ph = sphi[ay];
             float2 Fp = czero();
-            if (a.scheme == 2 && has_f) Fp = a.fprev[colbase + ay];
+            if (a.scheme == 2 && has_f) Fp = sfp[ay];
             const bool selfc = plane && (ay == 0 || 2 * ay == NY);
             // partners on the self-conjugate planes are overwritten by the fix-up below
             out[e] = setd_update<false>(co, ph, F, Fp, eta_of(out[e], selfc));
@@ -543,7 +565,7 @@ static cudaError_t run_rows(const StepArgs& a, cudaStream_t s) {
 template <int NY, int NL, int MODE>
 static cudaError_t run_cols(const StepArgs& a, cudaStream_t s) {
     using C = ColCfg<NY>;
-    const size_t sm = C::smem();
+    const size_t sm = MODE == MODE_STEP ? C::smem_step() : C::smem();
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k2_cols_real<NY, NL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
