@@ -324,6 +324,8 @@ def run_gpu(args):
                    "l2": "working set %.0f MB > 129 MB L2, no flush" % (
                        R * (w.n[0] // 2 + 1) * w.n[1] * 8 * 3 / 1e6)},
         "roofline": roofline,
+        "plan": dict(zip(("row_shape", "col_shape", "replicas_per_col_block", "pipelined_cols"),
+                         sft.sft_get_plan(g.ctx))),
         "step_roofline": {"bytes_per_site_step": step_bytes_site, "achieved_GBps": step_achieved,
                           "frac": step_achieved / peak,
                           "survey_24B_frac": 24.0 * value / peak},

@@ -154,6 +154,24 @@ sft_status sft_step(sft_ctx* ctx, int64_t nsteps);
  * the plain unbatched form used for timing comparisons. */
 sft_status sft_step_plain(sft_ctx* ctx, int64_t nsteps);
 
+/* Schedule of the step's passes.  On the first step (or here, if no step has
+ * run yet) a plan autotuner times every variant built for the lattice with
+ * CUDA events on scratch copies of the state and keeps the fastest; the
+ * choice is cached per configuration for the process (SFT_AUTOTUNE=0 in the
+ * environment keeps the defaults).  out[0]: row-pass shape (0: 128-thread
+ * blocks at 4 per SM, 1: 256-thread blocks at 2 per SM); out[1]: 2-D column
+ * pass radix schedule and block shape (0: 8 values per thread, 256-thread
+ * blocks, 3 per SM; 1: same, 4 per SM; 2: 16 values per thread, 128-thread
+ * blocks, 4 per SM; columns shorter than 512 points have only 0); out[2]:
+ * replicas per column-pass block; out[3]: 1 when the pipelined bulk-copy
+ * column pass runs.  cap >= 4.  The schedule changes no result beyond
+ * rounding order: every variant computes the same step.  Not on batch
+ * contexts.  No counterpart in the paper (its code calls FFTW). */
+sft_status sft_get_plan(sft_ctx* ctx, int* out, int cap);
+/* Force a schedule (values as sft_get_plan, n >= 4); SFT_EINVAL for a
+ * variant not built for the lattice.  Synchronises the context stream. */
+sft_status sft_set_plan(sft_ctx* ctx, const int* plan, int n);
+
 /* Wait for the context stream and report the device status word. */
 sft_status sft_sync(sft_ctx* ctx);
 

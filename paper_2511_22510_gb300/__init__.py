@@ -34,7 +34,7 @@ ABI_FUNCTIONS = [
     "sft_set_spectrum", "sft_step", "sft_step_plain", "sft_sync", "sft_observe", "sft_tangent_step",
     "sft_adjoint", "sft_set_checkpoint_interval", "sft_checkpoint", "sft_restore", "sft_get_step",
     "sft_launches_per_step", "sft_kernel_launches", "sft_draw_noise", "sft_profile", "sft_step2d_noalloc",
-    "sft_last_error", "sft_destroy",
+    "sft_get_plan", "sft_set_plan", "sft_last_error", "sft_destroy",
 ]
 
 
@@ -88,6 +88,8 @@ def load_library(path: str = LIB_PATH):
     L.sft_kernel_launches.argtypes = [vp, C.POINTER(i64)]
     L.sft_step2d_noalloc.argtypes = [C.POINTER(sft_config), vp, vp, C.c_int, i64, i64]
     L.sft_profile.argtypes = [vp, i64, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
+    L.sft_get_plan.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
+    L.sft_set_plan.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
     L.sft_last_error.argtypes = [vp]
     L.sft_last_error.restype = C.c_char_p
     L.sft_destroy.argtypes = [vp]
@@ -233,6 +235,18 @@ def sft_kernel_launches(ctx) -> int:
     v = C.c_int64()
     _check(ctx, load_library().sft_kernel_launches(ctx, C.byref(v)))
     return v.value
+
+
+def sft_get_plan(ctx) -> list:
+    """[row shape, column shape, replicas per column block, pipelined column pass]"""
+    out = (C.c_int * 4)()
+    _check(ctx, load_library().sft_get_plan(ctx, out, 4))
+    return list(out)
+
+
+def sft_set_plan(ctx, plan: Sequence[int]):
+    v = (C.c_int * 4)(*[int(x) for x in plan])
+    _check(ctx, load_library().sft_set_plan(ctx, v, 4))
 
 
 def sft_launches_per_step(ctx) -> int:

@@ -8,7 +8,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/sft.h"
@@ -68,6 +71,10 @@ struct sft_ctx {
     int ckpt_segment = 100;
     long long launches = 0;
     bool pipe_cols = false;  // pipelined (bulk-copy) column pass
+    bool pipe_forced = false;  // chosen by SFT_COLUMN_PASS, not by the plan
+    // schedule of the step's passes (plan autotuner)
+    bool planned = false;
+    int row_shape = 0, col_shape = 0, rpb = 0;
     // batch context: members advanced together (1-D lattices of uneven sizes in one persistent launch)
     bool is_batch = false;
     std::vector<sft_ctx*> members;
@@ -133,6 +140,7 @@ static StepArgs base_args(const sft_ctx* c) {
     a.first_step = c->dstep + 1;
     a.status = c->dstatus;
     a.bad_step = c->dstep + 2;
+    a.rpb = c->rpb;
     return a;
 }
 
@@ -144,7 +152,7 @@ static cudaError_t launch_rows(const sft_ctx* ctx, StepArgs a, int mode) {
         a.tw_a = ctx->tw.get(ctx->nx);
         return launch_k2c_rows(a, mode, ctx->stream);
     }
-    return launch_k2_rows(a, mode, ctx->nl, ctx->stream);
+    return launch_k2_rows(a, mode, ctx->nl, ctx->stream, mode == MODE_STEP ? ctx->row_shape : 0);
 }
 
 // Second pass: columns (2-D) or a_x planes (3-D).
@@ -156,6 +164,7 @@ static cudaError_t launch_second(const sft_ctx* ctx, const StepArgs& a, int mode
 
 static cudaError_t launch_cols_step(const sft_ctx* ctx, const StepArgs& a) {
     if (ctx->pipe_cols) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
+    if (ctx->d == 2 && !ctx->cplx) return launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream, ctx->col_shape);
     return launch_second(ctx, a, MODE_STEP);
 }
 
@@ -338,6 +347,163 @@ static sft_status enqueue_step(sft_ctx* ctx, int k) {
     a.pyout = ctx->Py;
     a.tw_a = ctx->tw.get(ctx->ny);
     CK(launch_cols_step(ctx, a));
+    return SFT_OK;
+}
+
+// ------------------------------------------------------------ plan autotuner
+// The schedule of the step's passes -- the radix schedule and block shape of
+// the 2-D column pass, replicas per column block, the block shape of the row
+// pass and the pipelined column pass -- is chosen per lattice by timing every
+// variant built for it with CUDA events on scratch copies of the state (the
+// context's own state is left untouched), once per configuration in the
+// process.  SFT_AUTOTUNE=0 keeps the defaults.
+namespace {
+struct PlanKey {
+    int d, nx, ny, nz, R, nl, scheme, dealias, dev;
+    bool operator<(const PlanKey& o) const {
+        return std::tie(d, nx, ny, nz, R, nl, scheme, dealias, dev) <
+               std::tie(o.d, o.nx, o.ny, o.nz, o.R, o.nl, o.scheme, o.dealias, o.dev);
+    }
+};
+struct PlanChoice {
+    int row_shape, col_shape, rpb, pipe;
+};
+std::mutex g_plan_mu;
+std::map<PlanKey, PlanChoice> g_plans;
+constexpr int kRpbChoices[] = {2, 4, 8};
+constexpr int kPlanReps = 4;
+}  // namespace
+
+// mean time of kPlanReps launches after one untimed launch
+template <class F>
+static cudaError_t time_launch(cudaStream_t s, F&& launch, float* ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int i = 0; i < kPlanReps && e == cudaSuccess; ++i) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    *ms = t / kPlanReps;
+    return e;
+}
+
+static void apply_plan(sft_ctx* ctx, const PlanChoice& p) {
+    ctx->row_shape = p.row_shape;
+    ctx->col_shape = p.col_shape;
+    ctx->rpb = p.rpb;
+    if (!ctx->pipe_forced) ctx->pipe_cols = p.pipe != 0;
+}
+
+static sft_status prime(sft_ctx* ctx);
+
+static sft_status plan_step(sft_ctx* ctx) {
+    if (ctx->planned) return SFT_OK;
+    ctx->planned = true;
+    if (ctx->is_batch) {
+        for (int m : ctx->solo) {
+            sft_status s = plan_step(ctx->members[m]);
+            if (s != SFT_OK) return fail(ctx, s, ctx->members[m]->err);
+        }
+        return SFT_OK;
+    }
+    const char* env = getenv("SFT_AUTOTUNE");
+    if ((env && env[0] == '0') || ctx->cplx || ctx->d < 2) return SFT_OK;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    const PlanKey key{ctx->d, ctx->nx, ctx->ny, ctx->nz, ctx->R, ctx->nl, ctx->cfg.scheme, ctx->cfg.dealias, dev};
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        auto it = g_plans.find(key);
+        if (it != g_plans.end()) {
+            apply_plan(ctx, it->second);
+            return SFT_OK;
+        }
+    }
+    if (!ctx->p_valid) {
+        sft_status s = prime(ctx);
+        if (s != SFT_OK) return s;
+    }
+    PlanChoice best{0, 0, 0, 0};
+    // row pass: reads P, writes the scratch Q (the state is not touched)
+    StepArgs a = base_args(ctx);
+    a.pin = ctx->P;
+    a.pyin = ctx->Py;
+    a.qout = ctx->Q;
+    a.ny = ctx->ny * ctx->nz;
+    a.nz = 1;
+    a.tw_a = ctx->tw.get(ctx->nx / 2);
+    a.tw_b = ctx->tw.get(ctx->nx);
+    float best_ms = 1e30f;
+    for (int sh = 0; sh < k2_row_shapes(); ++sh) {
+        float ms = 0.f;
+        CK(time_launch(ctx->stream, [&] { return launch_k2_rows(a, MODE_STEP, ctx->nl, ctx->stream, sh); }, &ms));
+        if (ms < best_ms) best_ms = ms, best.row_shape = sh;
+    }
+    CK(launch_k2_rows(a, MODE_STEP, ctx->nl, ctx->stream, best.row_shape));  // Q as the chosen pass leaves it
+    if (ctx->d == 2) {
+        // column pass on copies of the state and history, writing a scratch P (and P_y); the
+        // intermediates use the state's layout (replica stride hx columns), so every scratch
+        // buffer has the state's size, as the context's own P, Q, P_y do
+        const size_t sb = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
+        const size_t pb = sb;
+        const bool grad = ctx->nl == NL_GRAD2, hist = ctx->cfg.scheme == SFT_SETD2;
+        float2 *tphi = nullptr, *tfp = nullptr, *tP = nullptr, *tPy = nullptr;
+        cudaError_t me = cudaMalloc(&tphi, sb);
+        if (me == cudaSuccess) me = cudaMalloc(&tP, pb);
+        if (me == cudaSuccess && hist) me = cudaMalloc(&tfp, sb);
+        if (me == cudaSuccess && grad) me = cudaMalloc(&tPy, pb);
+        if (me == cudaSuccess) {
+            StepArgs c = base_args(ctx);
+            c.qin = ctx->Q;
+            c.phi = tphi;
+            c.fprev = tfp;
+            c.pout = tP;
+            c.pyout = tPy;
+            c.tw_a = ctx->tw.get(ctx->ny);
+            cudaError_t e = cudaMemcpyAsync(tphi, ctx->phi, sb, cudaMemcpyDeviceToDevice, ctx->stream);
+            if (e == cudaSuccess && hist) e = cudaMemcpyAsync(tfp, ctx->fprev, sb, cudaMemcpyDeviceToDevice, ctx->stream);
+            best_ms = 1e30f;
+            for (int sh = 0; sh < k2_col_shapes(ctx->ny) && e == cudaSuccess; ++sh) {
+                for (int rpb : kRpbChoices) {
+                    c.rpb = rpb;
+                    float ms = 0.f;
+                    e = time_launch(ctx->stream, [&] { return launch_k2_cols(c, MODE_STEP, ctx->nl, ctx->stream, sh); },
+                                    &ms);
+                    if (e != cudaSuccess) break;
+                    if (ms < best_ms) best_ms = ms, best.col_shape = sh, best.rpb = rpb;
+                }
+            }
+            if (e == cudaSuccess && !ctx->pipe_forced && k2_pipe_supported(ctx->nx, ctx->ny, 0)) {
+                float ms = 0.f;
+                e = time_launch(ctx->stream, [&] { return launch_k2_cols_pipe(c, ctx->nl, ctx->stream); }, &ms);
+                if (e == cudaSuccess && ms < best_ms) best_ms = ms, best.pipe = 1;
+            }
+            cudaError_t se = cudaStreamSynchronize(ctx->stream);
+            if (e == cudaSuccess) e = se;
+            cudaFree(tphi);
+            cudaFree(tP);
+            if (tfp) cudaFree(tfp);
+            if (tPy) cudaFree(tPy);
+            if (e != cudaSuccess) return fail(ctx, SFT_ECUDA, std::string("plan autotuner: ") + cudaGetErrorString(e));
+        } else {
+            // not enough device memory for the scratch copies: keep the default column schedule
+            cudaGetLastError();
+            if (tphi) cudaFree(tphi);
+            if (tP) cudaFree(tP);
+            if (tfp) cudaFree(tfp);
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        g_plans[key] = best;
+    }
+    apply_plan(ctx, best);
     return SFT_OK;
 }
 
@@ -527,11 +693,14 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     }
     ctx->launches_per_step = ctx->d == 1 ? 1 : 2;
     {
-        // column-pass variant: the multi-block kernel by default; SFT_COLUMN_PASS=pipelined selects
-        // the persistent bulk-copy pipelined kernel where it is built
+        // column-pass variant: chosen by the plan autotuner unless SFT_COLUMN_PASS forces the
+        // persistent bulk-copy pipelined kernel ("pipelined", where it is built) or the
+        // multi-block kernel ("multiblock")
         const char* v = getenv("SFT_COLUMN_PASS");
-        const bool pipe = v && strcmp(v, "pipelined") == 0;
-        ctx->pipe_cols = ctx->d == 2 && pipe && k2_pipe_supported(ctx->nx, ctx->ny, ctx->cplx);
+        if (v && (strcmp(v, "pipelined") == 0 || strcmp(v, "multiblock") == 0)) {
+            ctx->pipe_forced = true;
+            ctx->pipe_cols = ctx->d == 2 && strcmp(v, "pipelined") == 0 && k2_pipe_supported(ctx->nx, ctx->ny, ctx->cplx);
+        }
     }
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cleanup(SFT_ECUDA);
     *out = ctx;
@@ -808,6 +977,10 @@ static sft_status step_impl(sft_ctx* ctx, int64_t nsteps, bool use_graph) {
         sft_status s = prime(ctx);
         if (s != SFT_OK) return s;
     }
+    if (!ctx->planned) {
+        sft_status s = plan_step(ctx);
+        if (s != SFT_OK) return s;
+    }
     int64_t left = nsteps;
     if (use_graph && left >= kGraphChunk) {
         if (!ctx->warmed) {
@@ -843,6 +1016,45 @@ static sft_status step_impl(sft_ctx* ctx, int64_t nsteps, bool use_graph) {
 }
 
 sft_status sft_step(sft_ctx* ctx, int64_t nsteps) { return step_impl(ctx, nsteps, true); }
+
+sft_status sft_get_plan(sft_ctx* ctx, int* out, int cap) {
+    if (!ctx || !out || cap < 4) return SFT_EINVAL;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
+    if (!ctx->p_valid) {
+        sft_status s = prime(ctx);
+        if (s != SFT_OK) return s;
+    }
+    sft_status s = plan_step(ctx);
+    if (s != SFT_OK) return s;
+    out[0] = ctx->row_shape;
+    out[1] = ctx->col_shape;
+    out[2] = ctx->rpb > 0 ? ctx->rpb : 4;
+    out[3] = ctx->pipe_cols ? 1 : 0;
+    return SFT_OK;
+}
+
+sft_status sft_set_plan(sft_ctx* ctx, const int* plan, int n) {
+    if (!ctx || !plan || n < 4) return SFT_EINVAL;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
+    const bool real2 = ctx->d >= 2 && !ctx->cplx;
+    if (plan[0] < 0 || plan[0] >= (real2 ? k2_row_shapes() : 1) || plan[1] < 0 ||
+        plan[1] >= (real2 && ctx->d == 2 ? k2_col_shapes(ctx->ny) : 1) || plan[2] < 1 || plan[2] > 64 ||
+        (plan[3] != 0 && !(ctx->d == 2 && k2_pipe_supported(ctx->nx, ctx->ny, ctx->cplx))))
+        return fail(ctx, SFT_EINVAL, "schedule outside the variants built for this lattice");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->planned = true;
+    ctx->row_shape = plan[0];
+    ctx->col_shape = plan[1];
+    ctx->rpb = plan[2];
+    ctx->pipe_cols = plan[3] != 0;
+    ctx->pipe_forced = true;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    ctx->warmed = false;  // the next chunk runs plain first (kernel attributes outside capture)
+    return SFT_OK;
+}
 sft_status sft_step_plain(sft_ctx* ctx, int64_t nsteps) { return step_impl(ctx, nsteps, false); }
 
 sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, size_t* written) {

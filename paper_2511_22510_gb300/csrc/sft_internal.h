@@ -54,14 +54,18 @@ struct StepArgs {
     const long long* first_step;  // SETD2: the step that uses SETD1 coefficients
     unsigned* status;             // bit 0: non-finite state
     long long* bad_step;
+    int rpb;                      // 2-D column pass: replicas per block (< 1: the default)
 };
 
 // launchers (return cudaGetLastError of the launch); each picks the template
 // instance for the lattice size and returns cudaErrorInvalidValue if none.
 cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k1_cluster(const StepArgs& a, int mode, int nl, cudaStream_t s);
-cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s);
-cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s);
+// shape: schedule variant of the step mode (0 = default; see k2_row_shapes / k2_col_shapes)
+cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape = 0);
+cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape = 0);
+int k2_row_shapes();        // schedule variants of the 2-D row pass
+int k2_col_shapes(int ny);  // schedule variants of the 2-D column pass for columns of ny points
 cudaError_t launch_k2_cols_pipe(const StepArgs& a, int nl, cudaStream_t s);
 cudaError_t launch_k3_planes(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2c_rows(const StepArgs& a, int mode, cudaStream_t s);

@@ -182,3 +182,61 @@ def test_fluctuation_dissipation_model_a_3d(env):
     for j in (10, 20, 40):
         assert abs(lhs[j] - rhs[j]) <= 4 * sem + 0.03 * abs(rhs[j]) + 0.02 * taus[j], (taus[j], lhs[j], rhs[j], sem)
     g.close()
+
+
+AUTOGRAD_CASES = [
+    ("model_a_32", W.model_a_64(n=[32, 32], replicas=2, sigma0=0.3, h=0.02)),
+    ("model_b_3d_16_em", W.model_a_128_3d(n=[16, 16, 16], model=1, p=[1.0, -0.5, 1.0, 0.2], scheme=0, h=0.02,
+                                          sigma0=0.3)),
+]
+
+
+@pytest.mark.parametrize("name,w", AUTOGRAD_CASES, ids=[c[0] for c in AUTOGRAD_CASES])
+def test_autograd_function(env, oracle_mod, name, w):
+    """torch.autograd over the tangent/adjoint pair: forward = J v (the oracle's
+    tangent), backward = J^T g (the oracle's adjoint); <J v, g> = <v, J^T g>;
+    the backward pass leaves the stepper where the forward left it."""
+    m, torch = env
+    from paper_2511_22510_gb300.response import propagate
+    f0 = W.initial_fields(w)
+    v0 = W.initial_fields(w.with_(sigma0=1.0), seed_offset=5).astype(np.float32)
+    gw = W.initial_fields(w.with_(sigma0=1.0), seed_offset=6).astype(np.float32)
+    nst = 15
+    g, o = make_pair(m, oracle_mod, w, f0)
+    m.sft_set_checkpoint_interval(g.ctx, 6)
+    v = torch.from_numpy(v0).cuda().requires_grad_(True)
+    out = propagate(v, g, nst)
+    after_forward = g.spectrum()
+    gt = torch.from_numpy(gw).cuda()
+    (out * gt).sum().backward()
+    assert np.array_equal(g.spectrum(), after_forward)
+    assert g.step_count == nst
+    jv = out.detach().cpu().numpy().astype(np.float64)
+    jtg = v.grad.cpu().numpy().astype(np.float64)
+    tan_o = o.tangent_step(v0.astype(np.float64), nst)
+    o2 = make_pair(m, oracle_mod, w, f0)[1]
+    adj_o = o2.adjoint(gw.astype(np.float64), nst)
+    for r in range(w.replicas):
+        assert rel(jv[r], tan_o[r]) <= 1e-5, (name, r)
+        assert rel(jtg[r], adj_o[r]) <= 1e-5, (name, r)
+        lhs = float(np.sum(jv[r] * gw[r]))
+        rhs = float(np.sum(v0[r] * jtg[r]))
+        assert abs(lhs - rhs) <= 2e-5 * (abs(lhs) + abs(rhs)), (name, lhs, rhs)
+    # linear in v, same noise path: a second propagation from the same start doubles with 2 v
+    g2, _ = make_pair(m, oracle_mod, w, f0)
+    out2 = propagate(2.0 * v.detach(), g2, nst)
+    assert rel(out2.cpu().numpy().astype(np.float64), 2.0 * jv) <= 1e-6
+    for x in (g, g2):
+        x.close()
+
+
+def test_autograd_rejects_host_tensors(env):
+    m, torch = env
+    from paper_2511_22510_gb300.response import propagate
+    w = W.model_a_64(n=[16, 16], replicas=1)
+    g = m.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed)
+    with pytest.raises(ValueError):
+        propagate(torch.zeros((1, 16, 16)), g, 1)
+    with pytest.raises(ValueError):
+        propagate(torch.zeros((2, 16, 16), device="cuda"), g, 1)
+    g.close()
