@@ -196,16 +196,18 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
         if (has_f || T < 32) {
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = has_f ? a.qin[colbase + t + T * e] : czero();
-            fft_line<NY, false, EM>(v, xb, t, tw);
         }
-        cp_async_wait_all();
-        team_sync<T>();
+        // the noise depends on no loaded value: drawn while the loads of Q are in flight
         float2 out[E];
 #pragma unroll
+        for (int e = 0; e < E; e += 2)
+            team_normal_pair<T>(a.seed, (uint64_t)cc * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
+                                out[e + 1]);
+        if (has_f || T < 32) fft_line<NY, false, EM>(v, xb, t, tw);
+        cp_async_wait_all();
+        team_sync<T>();
+#pragma unroll
         for (int e = 0; e < E; ++e) {
-            if ((e & 1) == 0)
-                team_normal_pair<T>(a.seed, (uint64_t)cc * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
-                                    out[e + 1]);
             const int ay = t + T * e;
             const int ays = signed_idx(ay, NY);
             const int q = cc * cc + ays * ays;
