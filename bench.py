@@ -436,7 +436,7 @@ def run_other(args):
             g.close()
         line.update({"value": value, "ms_per_step": ms / K,
                      "config": {"workload": "kpz_ensemble", "members": {str(L): c for L, c in counts.items()},
-                                "plus": "64 x 256^2", "note": "lines up to 16384 points in one persistent launch; 32768 and 65536 points and the 2-D members on a parallel graph branch"},
+                                "plus": "64 x 256^2", "note": "lines up to 16384 points in one persistent launch; 32768 and 65536 points and the 2-D members each on a parallel graph branch"},
                      "batched_kernels_ms": {"k1_batch": prof[0], "other_members": prof[1]},
                      "plain": {"value": plain, "unit": UNIT, "batched_speedup": value / plain,
                                "form": "each member's own kernels launched from the host, no graph"}})

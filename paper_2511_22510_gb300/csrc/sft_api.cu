@@ -85,8 +85,9 @@ struct sft_ctx {
     int nitems = 0;
     int* d_head = nullptr;
     int batch_blocks = 0;
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::vector<cudaStream_t> sides;   // one forked graph branch per solo member
+    std::vector<cudaEvent_t> ev_joins;
+    cudaEvent_t ev_fork = nullptr;
     std::string err;
 };
 
@@ -295,15 +296,17 @@ static sft_status enqueue_step_io(sft_ctx* ctx, const float2* pin, float2* pout)
 static sft_status enqueue_step(sft_ctx* ctx, int k);
 
 // One step of a batch: queue reset + the persistent 1-D kernel on the batch
-// stream, the other members' own kernels on a forked branch, joined at the end.
+// stream, every other member's own kernels on a forked branch of its own (so
+// members too large for the persistent kernel run side by side), all joined at
+// the end.
 static sft_status enqueue_batch_step(sft_ctx* ctx, int k) {
     if (!ctx->solo.empty()) {
         CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
-        CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-        for (int m : ctx->solo) {
-            sft_ctx* mb = ctx->members[m];
+        for (size_t i = 0; i < ctx->solo.size(); ++i) {
+            CK(cudaStreamWaitEvent(ctx->sides[i], ctx->ev_fork, 0));
+            sft_ctx* mb = ctx->members[ctx->solo[i]];
             cudaStream_t keep = mb->stream;
-            mb->stream = ctx->side;
+            mb->stream = ctx->sides[i];
             sft_status s = enqueue_step(mb, k);
             mb->stream = keep;
             if (s != SFT_OK) return fail(ctx, s, mb->err);
@@ -314,9 +317,9 @@ static sft_status enqueue_batch_step(sft_ctx* ctx, int k) {
         CK(launch_k1_batch(ctx->d_members, ctx->d_items, ctx->nitems, ctx->d_head, ctx->nl, k, ctx->batch_blocks,
                            ctx->stream));
     }
-    if (!ctx->solo.empty()) {
-        CK(cudaEventRecord(ctx->ev_join, ctx->side));
-        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    for (size_t i = 0; i < ctx->solo.size(); ++i) {
+        CK(cudaEventRecord(ctx->ev_joins[i], ctx->sides[i]));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_joins[i], 0));
     }
     return SFT_OK;
 }
@@ -740,10 +743,7 @@ sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
         if (cudaStreamCreate(&ctx->stream) != cudaSuccess) return cleanup(SFT_ECUDA);
         ctx->own_stream = true;
     }
-    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
-        return cleanup(SFT_ECUDA);
+    if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) return cleanup(SFT_ECUDA);
     if (cudaMalloc(&ctx->dstep, 4 * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&ctx->dstatus, sizeof(unsigned)) != cudaSuccess || cudaMalloc(&ctx->d_head, sizeof(int)) != cudaSuccess)
         return cleanup(SFT_ENOMEM);
@@ -799,6 +799,14 @@ sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         ctx->batch_blocks = std::max(1, std::min(nsm, ctx->nitems));
+    }
+    for (size_t i = 0; i < ctx->solo.size(); ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return cleanup(SFT_ECUDA);
+        ctx->sides.push_back(st);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return cleanup(SFT_ECUDA);
+        ctx->ev_joins.push_back(ev);
     }
     ctx->launches_per_step = ctx->nitems > 0 ? 1 : 0;
     for (int m : ctx->solo) ctx->launches_per_step += ctx->members[m]->launches_per_step;
@@ -1636,9 +1644,9 @@ void sft_destroy(sft_ctx* ctx) {
     if (ctx->d_members) cudaFree(ctx->d_members);
     if (ctx->d_items) cudaFree(ctx->d_items);
     if (ctx->d_head) cudaFree(ctx->d_head);
-    if (ctx->side) cudaStreamDestroy(ctx->side);
+    for (cudaStream_t st : ctx->sides) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : ctx->ev_joins) cudaEventDestroy(ev);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     void* bufs[] = {ctx->phi,   ctx->fprev,  ctx->P,      ctx->Q,      ctx->Py,     ctx->snap, ctx->real,
                     ctx->cfield, ctx->tab,   ctx->dstep,  ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev,
                     ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ};

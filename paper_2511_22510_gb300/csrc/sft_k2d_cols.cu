@@ -238,11 +238,13 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
             }
         }
         if (valid) {
+            float nf = 0.f;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 a.phi[colbase + t + T * e] = out[e];
-                flag_nonfinite(a, out[e], step);
+                nf = nonfinite_acc(nf, out[e]);
             }
+            flag_nonfinite_acc(a, nf, step);
         }
         emit_p<NY, NL, EM>(a, out, valid && cc < a.ncols, cc, colbase, xb, t);
     } else if constexpr (MODE == MODE_TAN) {

@@ -135,6 +135,19 @@ __device__ __forceinline__ void flag_nonfinite(const StepArgs& a, float2 v, long
     }
 }
 
+// Branch-free form of the check above for a set of values: x * 0 is NaN exactly
+// when x is infinite or NaN (and +-0 otherwise, which leaves acc unchanged), so
+// acc stays 0 while every value is finite; one flag_nonfinite_acc at the end.
+__device__ __forceinline__ float nonfinite_acc(float acc, float2 v) {
+    return __fmaf_rn(v.y, 0.f, __fmaf_rn(v.x, 0.f, acc));
+}
+__device__ __forceinline__ void flag_nonfinite_acc(const StepArgs& a, float acc, long long step) {
+    if (acc != acc) {
+        atomicOr(a.status, 1u);
+        atomicMin((unsigned long long*)a.bad_step, (unsigned long long)step);
+    }
+}
+
 // phi_new = f1 phi + A F + B F_prev + g eta   (complex arithmetic throughout;
 // for real fields the imaginary parts of the coefficients are zero).
 template <bool CPLX>
