@@ -142,6 +142,7 @@ static StepArgs base_args(const sft_ctx* c) {
     a.status = c->dstatus;
     a.bad_step = c->dstep + 2;
     a.rpb = c->rpb;
+    a.tw_c = c->tw.get(8192);
     return a;
 }
 
@@ -664,6 +665,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
         lens.push_back(ctx->nx);
     }
     if (ctx->d >= 2) lens.push_back(ctx->ny);
+    if (ctx->d == 1 && !ctx->cplx && ctx->nx == 65536) lens.push_back(8192);  // per-block FFT of the cluster kernel
     if (build_twiddles(ctx, lens) != SFT_OK) return cleanup(SFT_ECUDA);
     // FP64 coefficient tables
     TableArgs t{};

@@ -48,6 +48,7 @@ struct StepArgs {
     // twiddle tables for the transform lengths used by the kernel
     const float2* tw_a;  // table for the first transform length
     const float2* tw_b;  // table for the second transform length
+    const float2* tw_c;  // 1-D lines of 65536 points: table of the 8192-point per-block FFT
     // step bookkeeping
     const long long* step_base;  // device: step index of k_in_chunk = 0
     int k_in_chunk;

@@ -1,12 +1,23 @@
 // sft_k1d_cluster.cu -- whole-step kernel for 1-D real lattices of 65536 points.
 //
-// The half-length complex line (32768 values) does not fit one block's shared
-// memory in FP32, so one replica is held by a cluster of 4 blocks of 512
-// threads: the 2048 threads hold 16 values each in registers, and the padded
-// exchange buffer of the Stockham passes is split in four quarters, one in
-// each block's shared memory, addressed through distributed shared memory;
-// cluster-wide barriers replace the team barriers.  Same arithmetic as the
-// single-block line kernel (Sec. IV boxed algorithm).
+// The half-length complex line (M = 32768 values, packed z[m] = x[2m] + i x[2m+1])
+// does not fit one block's shared memory in FP32.  One replica is held by a
+// cluster of P = 4 blocks of 512 threads, and every M-point transform is split
+// four-step style into L = M / P = 8192-point FFTs that each block runs in its
+// own shared memory, plus one P-point stage across the blocks:
+//
+//   inverse, m = P l + p, n = n1 + L n2:
+//     T_p[n1] = W_M^{-p n1} IFFT_L(Z[P l + p])[n1]        (block p, local)
+//     y[n1 + L n2] = sum_p W_P^{-p n2} T_p[n1]             (block q: n1 in its quarter; reads T_p remotely)
+//   forward, k = P k1 + k2:
+//     U_k2[n1] = W_M^{n1 k2} sum_n2 q[n1 + L n2] W_P^{n2 k2} (the thread that holds q[n1 + L n2])
+//     Q[P k1 + k2] = FFT_L(U_k2)[k1]                        (block k2, after U_k2 is written into it)
+//
+// so distributed shared memory is touched only by the cross-block stage, the
+// redistribution before the forward FFT and the r2c partner reads, not by every
+// FFT pass.  Same arithmetic as the single-block line kernel otherwise (Sec. IV
+// boxed algorithm): dealias + scale, C2R, q(psi), R2C, SETD update with the
+// Philox Fourier noise.
 #include <cooperative_groups.h>
 
 #include "sft_step_common.cuh"
@@ -15,99 +26,49 @@ namespace cg = cooperative_groups;
 
 namespace sft {
 
-constexpr int kClM = 32768;  // half length
-constexpr int kCl = 4;       // blocks per cluster
+constexpr int kClL = 8192;  // points of the per-block FFT
 constexpr int kClThreads = 512;
-using ClPlan = FftPlan<kClM, 16>;
-static_assert(ClPlan::T == kCl * kClThreads, "one value group per thread");
-constexpr int kClQuarter = (ClPlan::BUF + kCl - 1) / kCl;
+using ClPlan = FftPlan<kClL, 16>;
+static_assert(ClPlan::T == kClThreads && ClPlan::E == 16, "16 values per thread, one line per block");
 
-struct DistBuf {
-    float2* part[kCl];
-    __device__ __forceinline__ float2& operator[](int p) const {
-        const int r = p / kClQuarter;
-        return part[r][p - r * kClQuarter];
-    }
-};
+__device__ __forceinline__ int clpos(int i) { return xpos<kClL, 16>(i); }
 
-__device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
-
-// Stockham pass over the distributed buffer (same plan and indexing as fft_line).
-template <bool INV, int PASS, int NS>
-__device__ __forceinline__ void cl_pass(float2 (&v)[ClPlan::E], const DistBuf& buf, int t,
-                                        const float2* __restrict__ tw) {
-    constexpr int N = kClM, E = ClPlan::E, T = ClPlan::T;
-    constexpr int R = ClPlan::radix(PASS);
-    constexpr int NB = E / R;
-    constexpr bool FIRST = (PASS == 0);
-    constexpr bool LAST = (NS * R == N);
-    float2 x[NB][R];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        const int j = t + T * b;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if constexpr (FIRST)
-                x[b][r] = v[b + r * NB];
-            else
-                x[b][r] = buf[xpos<N, 16>(j + r * (N / R))];
-        }
-        if constexpr (!FIRST) {
-            const int k = j % NS;
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(&tw[r * k * (N / (NS * R))]);
-                if (INV) w.y = -w.y;
-                x[b][r] = cmul(x[b][r], w);
-            }
-        }
-        dft_reg<R, INV>(x[b]);
-    }
-    if constexpr (LAST) {
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-            for (int s = 0; s < R; ++s) v[b + s * NB] = x[b][s];
-    } else {
-        cl_sync();
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const int j = t + T * b;
-            const int k = j % NS;
-            const int base = (j / NS) * NS * R + k;
-#pragma unroll
-            for (int s = 0; s < R; ++s) buf[xpos<N, 16>(base + s * NS)] = x[b][s];
-        }
-        cl_sync();
-        cl_pass<INV, PASS + 1, NS * R>(v, buf, t, tw);
-    }
-}
-
-template <int MODE, int NL>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k1_cluster(const StepArgs a) {
-    constexpr int M = kClM, NX = 2 * M, E = ClPlan::E, T = ClPlan::T;
+template <int P, int MODE, int NL>
+__global__ void __launch_bounds__(kClThreads, 1) k1_cluster(const StepArgs a) {
+    constexpr int L = kClL, M = P * L, NX = 2 * M, E = ClPlan::E, T = ClPlan::T;
+    constexpr int NI = L / (P * T);  // n1 values per thread in the cross-block stage
+    static_assert(NI * P == E, "cross-block stage keeps E values per thread");
     extern __shared__ float2 sm[];
     cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    DistBuf buf;
-#pragma unroll
-    for (int r = 0; r < kCl; ++r) buf.part[r] = cl.map_shared_rank(sm, r);
-    const int t = rank * kClThreads + threadIdx.x;
-    const int rr = blockIdx.x / kCl;  // replica
-    const float2* __restrict__ twM = a.tw_a;
-    const float2* __restrict__ twN = a.tw_b;
+    const int q = (int)cl.block_rank();  // block of the cluster
+    const int t = threadIdx.x;
+    const int rr = blockIdx.x / P;  // replica
+    const float2* __restrict__ twL = a.tw_c;  // W_L
+    const float2* __restrict__ twM = a.tw_a;  // W_M
+    const float2* __restrict__ twN = a.tw_b;  // W_NX
     float2* ph = a.phi + (size_t)rr * (M + 1);
-    float2 z[E];
-    cl_sync();  // every block of the cluster is running before remote shared memory is touched
+    float2* rem[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) rem[r] = cl.map_shared_rank(sm, r);
+    float2 y[E];  // y[i P + n2] = value at n = n1(i) + L n2, n1(i) = q L/P + t + T i
+    cl.sync();    // every block of the cluster is running before remote shared memory is touched
+
     if constexpr (MODE == MODE_FWD) {
         const float* src = a.real_io + (size_t)rr * NX;
 #pragma unroll
-        for (int e = 0; e < E; ++e) z[e] = *reinterpret_cast<const float2*>(src + 2 * (t + T * e));
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int n2 = 0; n2 < P; ++n2) {
+                const int n = q * (L / P) + t + T * i + L * n2;
+                y[i * P + n2] = *reinterpret_cast<const float2*>(src + 2 * n);
+            }
     } else {
+        // inverse, block-local part: T_p[n1] for p = q
+        float2 z[E];
         const float sc = a.scale;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const int k = t + T * e;
+            const int k = P * (t + T * e) + q;
             float2 X = ph[k], Xm = ph[M - k];
             if constexpr (MODE == MODE_STEP) {
                 X = (!a.dealias || 3 * k < NX) ? cscale(X, sc) : czero();
@@ -122,91 +83,155 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads) k1_clu
             }
             z[e] = c2r_pre(X, Xm, __ldg(&twN[k]));
         }
-        cl_pass<true, 0, 1>(z, buf, t, twM);
+        fft_line<L, true, 16>(z, sm, t, twL);
+        __syncthreads();  // the FFT's last reads of the buffer are done
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int n1 = t + T * e;
+            float2 w = __ldg(&twM[q * n1]);
+            w.y = -w.y;
+            sm[clpos(n1)] = cmul(z[e], w);
+        }
+        cl.sync();
+        // cross-block inverse P-point stage for this block's quarter of n1
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int n1 = q * (L / P) + t + T * i;
+            float2 x[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) x[p] = rem[p][clpos(n1)];
+            dft_reg<P, true>(x);
+#pragma unroll
+            for (int n2 = 0; n2 < P; ++n2) y[i * P + n2] = x[n2];
+        }
         if constexpr (MODE == MODE_INV) {
             float* dst = a.real_io + (size_t)rr * NX;
 #pragma unroll
-            for (int e = 0; e < E; ++e) *reinterpret_cast<float2*>(dst + 2 * (t + T * e)) = z[e];
-            cl_sync();
-            return;
+            for (int i = 0; i < NI; ++i)
+#pragma unroll
+                for (int n2 = 0; n2 < P; ++n2) {
+                    const int n = q * (L / P) + t + T * i + L * n2;
+                    *reinterpret_cast<float2*>(dst + 2 * n) = y[i * P + n2];
+                }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if constexpr (NL == NL_GRAD2)
+                    y[e] = make_float2(y[e].x * y[e].x, y[e].y * y[e].y);
+                else
+                    y[e] = make_float2(y[e].x * y[e].x * y[e].x, y[e].y * y[e].y * y[e].y);
+            }
         }
+    }
+
+    if constexpr (MODE != MODE_INV) {
+        // forward: U_k2[n1] for this thread's n1, written into block k2
+        cl.sync();  // every remote read of the cross-block inverse stage is done
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int n1 = q * (L / P) + t + T * i;
+            float2 x[P];
+#pragma unroll
+            for (int n2 = 0; n2 < P; ++n2) x[n2] = y[i * P + n2];
+            dft_reg<P, false>(x);
+#pragma unroll
+            for (int k2 = 0; k2 < P; ++k2) rem[k2][clpos(n1)] = cmul(x[k2], __ldg(&twM[n1 * k2]));
+        }
+        cl.sync();
+        float2 v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = sm[clpos(t + T * e)];
+        fft_line<L, false, 16>(v, sm, t, twL);  // v[e] = Q[P (t + T e) + q]
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) sm[clpos(t + T * e)] = v[e];
+        cl.sync();
+
+        // R2C post-processing and the update of the modes k in [q L, (q + 1) L) (block q)
+        auto Qat = [&](int k) -> float2 { return rem[k % P][clpos(k / P)]; };
+        float2 Xq[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            if constexpr (NL == NL_GRAD2)
-                z[e] = make_float2(z[e].x * z[e].x, z[e].y * z[e].y);
-            else
-                z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
+            const int k = q * L + t + T * e;
+            Xq[e] = r2c_post(Qat(k), cconj(Qat((M - k) & (M - 1))), __ldg(&twN[k]));
+        }
+        const float2 z0 = rem[0][clpos(0)];
+        const float2 XqM = make_float2(z0.x - z0.y, 0.f);
+        const bool last_owner = (q == 0 && t == 0);  // also handles the Nyquist mode k = M
+        if constexpr (MODE == MODE_FWD) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int k = q * L + t + T * e;
+                float2 o = Xq[e];
+                if (k == 0) o.y = 0.f;
+                ph[k] = o;
+            }
+            if (last_owner) ph[M] = XqM;
+        } else {
+            const long long step = current_step(a);
+            const bool first = (a.scheme == 2) && (step == *a.first_step);
+            float2* fp = a.fprev + (size_t)rr * (M + 1);
+            const uint32_t rep = (uint32_t)(a.rep0 + rr);
+            float2 zn0, zn1;
+            float nf = 0.f;
+#pragma unroll
+            for (int e = 0; e <= E; ++e) {
+                if (e < E && (e & 1) == 0)
+                    team_normal_pair<T>(a.seed, (uint64_t)q * L, t, e, (uint32_t)step, rep, zn0, zn1);
+                if (e == E && !last_owner) break;
+                const int k = (e < E) ? q * L + t + T * e : M;
+                const float2 xq = (e < E) ? Xq[e] : XqM;
+                const bool inm = !a.dealias || 3 * k < NX;
+                const float2 F = inm ? cscale(xq, nl_prefactor(a, k * k).x) : czero();
+                const Coefs co = load_coefs<false>(a.tab, k, first);
+                const float2 Fp = (a.scheme == 2) ? fp[k] : czero();
+                const bool selfc = (k == 0 || k == M);
+                const float2 eta = (e < E) ? eta_of((e & 1) ? zn1 : zn0, selfc)
+                                           : fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
+                float2 o = setd_update<false>(co, ph[k], F, Fp, eta);
+                if (selfc) o.y = 0.f;
+                ph[k] = o;
+                if (a.scheme == 2) fp[k] = F;
+                nf = nonfinite_acc(nf, o);
+            }
+            flag_nonfinite_acc(a, nf, step);
         }
     }
-    cl_pass<false, 0, 1>(z, buf, t, twM);
-    // R2C post-processing through the distributed buffer
-    cl_sync();
-#pragma unroll
-    for (int e = 0; e < E; ++e) buf[xpos<M, 16>(t + T * e)] = z[e];
-    cl_sync();
-    float2 Xq[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int k = t + T * e;
-        Xq[e] = r2c_post(z[e], cconj(buf[xpos<M, 16>((M - k) & (M - 1))]), __ldg(&twN[k]));
-    }
-    const float2 z0 = buf[0];
-    const float2 XqM = make_float2(z0.x - z0.y, 0.f);
-    if constexpr (MODE == MODE_FWD) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            float2 v = Xq[e];
-            if (t + T * e == 0) v.y = 0.f;
-            ph[t + T * e] = v;
-        }
-        if (t == 0) ph[M] = XqM;
-    } else {
-        const long long step = current_step(a);
-        const bool first = (a.scheme == 2) && (step == *a.first_step);
-        float2* fp = a.fprev + (size_t)rr * (M + 1);
-        const uint32_t rep = (uint32_t)(a.rep0 + rr);
-        float2 zn0, zn1;
-#pragma unroll
-        for (int e = 0; e <= E; ++e) {
-            if (e < E && (e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
-            if (e == E && t != 0) break;
-            const int k = (e < E) ? t + T * e : M;
-            const float2 xq = (e < E) ? Xq[e] : XqM;
-            const bool inm = !a.dealias || 3 * k < NX;
-            const float2 F = inm ? cscale(xq, nl_prefactor(a, k * k).x) : czero();
-            const Coefs co = load_coefs<false>(a.tab, k, first);
-            const float2 Fp = (a.scheme == 2) ? fp[k] : czero();
-            const bool selfc = (k == 0 || k == M);
-            const float2 eta = (e < E) ? eta_of((e & 1) ? zn1 : zn0, selfc)
-                                       : fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
-            float2 o = setd_update<false>(co, ph[k], F, Fp, eta);
-            if (selfc) o.y = 0.f;
-            ph[k] = o;
-            if (a.scheme == 2) fp[k] = F;
-            flag_nonfinite(a, o, step);
-        }
-    }
-    cl_sync();  // no block leaves while others may still read its shared memory
+    cl.sync();  // no block leaves while others may still read its shared memory
 }
 
-template <int MODE, int NL>
+template <int P, int MODE, int NL>
 static cudaError_t run_cluster(const StepArgs& a, cudaStream_t s) {
     static bool attr = false;
-    const size_t sm = sizeof(float2) * (size_t)kClQuarter;
+    const size_t sm = sizeof(float2) * (size_t)ClPlan::BUF;
+    if (!a.tw_a || !a.tw_b || !a.tw_c) return cudaErrorInvalidValue;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k1_cluster<MODE, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e =
+            cudaFuncSetAttribute(k1_cluster<P, MODE, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k1_cluster<MODE, NL><<<kCl * a.R, kClThreads, sm, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(P * a.R), 1, 1);
+    cfg.blockDim = dim3(kClThreads, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = P;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k1_cluster<P, MODE, NL>, a);
 }
 
 cudaError_t launch_k1_cluster(const StepArgs& a, int mode, int nl, cudaStream_t s) {
-    if (mode == MODE_FWD) return run_cluster<MODE_FWD, NL_CUBIC>(a, s);
-    if (mode == MODE_INV) return run_cluster<MODE_INV, NL_CUBIC>(a, s);
-    if (mode == MODE_STEP && nl == NL_CUBIC) return run_cluster<MODE_STEP, NL_CUBIC>(a, s);
-    if (mode == MODE_STEP && nl == NL_GRAD2) return run_cluster<MODE_STEP, NL_GRAD2>(a, s);
+    if (a.nx != 2 * 4 * kClL) return cudaErrorInvalidValue;
+    if (mode == MODE_FWD) return run_cluster<4, MODE_FWD, NL_CUBIC>(a, s);
+    if (mode == MODE_INV) return run_cluster<4, MODE_INV, NL_CUBIC>(a, s);
+    if (mode == MODE_STEP && nl == NL_CUBIC) return run_cluster<4, MODE_STEP, NL_CUBIC>(a, s);
+    if (mode == MODE_STEP && nl == NL_GRAD2) return run_cluster<4, MODE_STEP, NL_GRAD2>(a, s);
     return cudaErrorInvalidValue;
 }
 
