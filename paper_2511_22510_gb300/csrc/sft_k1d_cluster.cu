@@ -2,7 +2,8 @@
 //
 // The half-length complex line (M = 32768 values, packed z[m] = x[2m] + i x[2m+1])
 // does not fit one block's shared memory in FP32.  One replica is held by a
-// cluster of P = 4 blocks of 512 threads, and every M-point transform is split
+// cluster of P = 4 blocks of 1024 threads (8 values per thread, 64 registers,
+// so 32 warps per SM), and every M-point transform is split
 // four-step style into L = M / P = 8192-point FFTs that each block runs in its
 // own shared memory, plus one P-point stage across the blocks:
 //
@@ -27,11 +28,11 @@ namespace cg = cooperative_groups;
 namespace sft {
 
 constexpr int kClL = 8192;  // points of the per-block FFT
-constexpr int kClThreads = 512;
-using ClPlan = FftPlan<kClL, 16>;
-static_assert(ClPlan::T == kClThreads && ClPlan::E == 16, "16 values per thread, one line per block");
+constexpr int kClThreads = 1024;
+using ClPlan = FftPlan<kClL, 8>;
+static_assert(ClPlan::T == kClThreads && ClPlan::E == 8, "8 values per thread, one line per block");
 
-__device__ __forceinline__ int clpos(int i) { return xpos<kClL, 16>(i); }
+__device__ __forceinline__ int clpos(int i) { return xpos<kClL, 8>(i); }
 
 template <int P, int MODE, int NL>
 __global__ void __launch_bounds__(kClThreads, 1) k1_cluster(const StepArgs a) {
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k1_cluster(const StepArgs a) {
             }
             z[e] = c2r_pre(X, Xm, __ldg(&twN[k]));
         }
-        fft_line<L, true, 16>(z, sm, t, twL);
+        fft_line<L, true, 8>(z, sm, t, twL);
         __syncthreads();  // the FFT's last reads of the buffer are done
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k1_cluster(const StepArgs a) {
         float2 v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = sm[clpos(t + T * e)];
-        fft_line<L, false, 16>(v, sm, t, twL);  // v[e] = Q[P (t + T e) + q]
+        fft_line<L, false, 8>(v, sm, t, twL);  // v[e] = Q[P (t + T e) + q]
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < E; ++e) sm[clpos(t + T * e)] = v[e];
