@@ -158,8 +158,9 @@ sft_status sft_step_plain(sft_ctx* ctx, int64_t nsteps);
  * run yet) a plan autotuner times every variant built for the lattice with
  * CUDA events on scratch copies of the state and keeps the fastest; the
  * choice is cached per configuration for the process (SFT_AUTOTUNE=0 in the
- * environment keeps the defaults).  out[0]: row-pass shape (0: 128-thread
- * blocks at 4 per SM, 1: 256-thread blocks at 2 per SM); out[1]: 2-D column
+ * environment keeps the defaults; SFT_PLAN="row,col,rpb,pipe" fixes the
+ * schedule).  out[0]: row-pass shape (0: 128-thread blocks at 4 per SM, 1:
+ * 256-thread blocks at 2 per SM, 2: 512-thread blocks at 1 per SM); out[1]: 2-D column
  * pass radix schedule and block shape (0: 8 values per thread, 256-thread
  * blocks, 3 per SM; 1: same, 4 per SM; 2: 16 values per thread, 128-thread
  * blocks, 4 per SM; columns shorter than 512 points have only 0); out[2]:

@@ -418,6 +418,19 @@ static sft_status plan_step(sft_ctx* ctx) {
     }
     const char* env = getenv("SFT_AUTOTUNE");
     if ((env && env[0] == '0') || ctx->cplx || ctx->d < 2) return SFT_OK;
+    // SFT_PLAN="row,col,rpb,pipe" fixes the schedule (as sft_set_plan; e.g. to profile the one a timed run chose)
+    if (const char* fixed = getenv("SFT_PLAN")) {
+        int v[4];
+        if (sscanf(fixed, "%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3]) == 4) {
+            const bool ok = v[0] >= 0 && v[0] < k2_row_shapes() && v[1] >= 0 &&
+                            v[1] < (ctx->d == 2 ? k2_col_shapes(ctx->ny) : 1) && v[2] >= 1 && v[2] <= 64 &&
+                            (v[3] == 0 || (ctx->d == 2 && k2_pipe_supported(ctx->nx, ctx->ny, 0)));
+            if (!ok) return fail(ctx, SFT_EINVAL, "SFT_PLAN names a schedule not built for this lattice");
+            apply_plan(ctx, PlanChoice{v[0], v[1], v[2], v[3]});
+            return SFT_OK;
+        }
+        return fail(ctx, SFT_EINVAL, "SFT_PLAN must read row,col,rpb,pipe");
+    }
     int dev = 0;
     CK(cudaGetDevice(&dev));
     const PlanKey key{ctx->d, ctx->nx, ctx->ny, ctx->nz, ctx->R, ctx->nl, ctx->cfg.scheme, ctx->cfg.dealias, dev};

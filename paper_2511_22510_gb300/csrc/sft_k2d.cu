@@ -57,7 +57,9 @@ __device__ __forceinline__ void row_post(float2 (&z)[FftPlan<M>::E], float2* xb,
 
 // Schedules of the row pass of the step, chosen per lattice by the plan
 // autotuner: 0 = SFT_ROW_CTA threads per block at SFT_ROW_MINB blocks per SM;
-// 1 = 256-thread blocks (twice the rows per tile) at 2 blocks per SM.
+// 1 = 256-thread blocks (twice the rows per tile) at 2 blocks per SM;
+// 2 = 512-thread blocks at 1 per SM (16 rows per tile on 512-point rows: the
+// transposing tile reads whole 128-byte segments of every column).
 template <int SH>
 struct RowShape {
     static constexpr int CTA = SFT_ROW_CTA, MINB = SFT_ROW_MINB;
@@ -65,6 +67,10 @@ struct RowShape {
 template <>
 struct RowShape<1> {
     static constexpr int CTA = 256, MINB = 2;
+};
+template <>
+struct RowShape<2> {
+    static constexpr int CTA = 512, MINB = 1;
 };
 
 template <int M_, int SH = 0>
@@ -265,6 +271,7 @@ static cudaError_t run_rows(const StepArgs& a, cudaStream_t s) {
 template <int M, int NL>
 static cudaError_t rows_step(const StepArgs& a, cudaStream_t s, int shape) {
     if (shape == 1) return run_rows<M, NL, MODE_STEP, 1>(a, s);
+    if (shape == 2) return run_rows<M, NL, MODE_STEP, 2>(a, s);
     return run_rows<M, NL, MODE_STEP, 0>(a, s);
 }
 
@@ -279,7 +286,7 @@ static cudaError_t rows_for(const StepArgs& a, int mode, int nl, cudaStream_t s,
     return cudaErrorInvalidValue;
 }
 
-int k2_row_shapes() { return 2; }
+int k2_row_shapes() { return 3; }
 
 cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape) {
     switch (a.nx / 2) {

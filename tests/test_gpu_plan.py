@@ -53,7 +53,7 @@ def test_schedule_variants_agree(sft, name, w):
     ref.close()
     ncol = 3 if w.n[1] >= 512 else 1
     pipes = [0, 1] if (w.n[0], w.n[1]) in ((1024, 1024), (2048, 2048)) and w.model != W.KPZ else [0]
-    for row, col, rpb, pipe in itertools.product(range(2), range(ncol), (1, 2, 4, 8), pipes):
+    for row, col, rpb, pipe in itertools.product(range(3), range(ncol), (1, 2, 4, 8), pipes):
         if pipe and (col or rpb != 4):
             continue  # the pipelined column pass has one schedule
         g = stepper(sft, w)
@@ -74,7 +74,7 @@ def test_autotuner_leaves_state_and_caches(sft):
     g.set_field(f0)
     spec0 = g.spectrum()
     plan = sft.sft_get_plan(g.ctx)
-    assert 0 <= plan[0] < 2 and 0 <= plan[1] < 3 and plan[2] in (2, 4, 8) and plan[3] in (0, 1)
+    assert 0 <= plan[0] < 3 and 0 <= plan[1] < 3 and plan[2] in (2, 4, 8) and plan[3] in (0, 1)
     assert np.array_equal(g.spectrum(), spec0)
     assert g.step_count == 0
     g2 = stepper(sft, w)
@@ -86,7 +86,7 @@ def test_autotuner_leaves_state_and_caches(sft):
     for r in range(w.replicas):
         assert rel_l2(g.field(r), g2.field(r)) <= 2e-6
     with pytest.raises(sft.SftError):
-        sft.sft_set_plan(g.ctx, [2, 0, 4, 0])
+        sft.sft_set_plan(g.ctx, [3, 0, 4, 0])
     with pytest.raises(sft.SftError):
         sft.sft_set_plan(g.ctx, [0, 3, 4, 0])
     g.close()
