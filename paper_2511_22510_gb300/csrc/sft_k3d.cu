@@ -17,7 +17,10 @@ template <int N>
 struct PlaneCfg {
     using PL = FftPlan<N>;
     static constexpr int T = PL::T;
-    static constexpr int TEAMS = T >= 256 ? 1 : 256 / T;
+    // a 128^2 plane fills most of an SM's shared memory (one block per SM), so
+    // that block takes 512 threads; smaller planes run several 256-thread blocks
+    static constexpr int TT = N >= 128 ? 512 : 256;
+    static constexpr int TEAMS = T >= TT ? 1 : TT / T;
     static constexpr int THREADS = TEAMS * T;
     static constexpr int RS = N + 1;  // odd row stride of the plane
     static constexpr int XB = PL::BUF;
