@@ -142,7 +142,7 @@ static StepArgs base_args(const sft_ctx* c) {
     a.status = c->dstatus;
     a.bad_step = c->dstep + 2;
     a.rpb = c->rpb;
-    a.tw_c = c->tw.get(8192);
+    a.tw_c = (c->d == 1 && !c->cplx && k1_cluster_fft_len(c->nx)) ? c->tw.get(k1_cluster_fft_len(c->nx)) : nullptr;
     return a;
 }
 
@@ -678,7 +678,8 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
         lens.push_back(ctx->nx);
     }
     if (ctx->d >= 2) lens.push_back(ctx->ny);
-    if (ctx->d == 1 && !ctx->cplx && ctx->nx == 65536) lens.push_back(8192);  // per-block FFT of the cluster kernel
+    if (ctx->d == 1 && !ctx->cplx && k1_cluster_fft_len(ctx->nx))
+        lens.push_back(k1_cluster_fft_len(ctx->nx));  // per-block FFT of the cluster kernel
     if (build_twiddles(ctx, lens) != SFT_OK) return cleanup(SFT_ECUDA);
     // FP64 coefficient tables
     TableArgs t{};
@@ -779,7 +780,9 @@ sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
         ctx->rep_offset.push_back(roff);
         roff += m->R;
         const int M = m->nx / 2;
-        const int lines = (m->d == 1 && !m->cplx) ? batch_lines_per_item(M) : 0;
+        // lines the persistent kernel takes; longer ones that the cluster kernel runs better (few replicas) go solo
+        const int lines =
+            (m->d == 1 && !m->cplx && !k1_use_cluster(m->nx, m->R, MODE_STEP)) ? batch_lines_per_item(M) : 0;
         if (lines > 0) {
             BatchMember bm{};
             bm.a = base_args(m);

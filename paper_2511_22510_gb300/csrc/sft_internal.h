@@ -62,6 +62,8 @@ struct StepArgs {
 // instance for the lattice size and returns cudaErrorInvalidValue if none.
 cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k1_cluster(const StepArgs& a, int mode, int nl, cudaStream_t s);
+int k1_cluster_fft_len(int nx);            // per-block FFT length of the cluster kernel for lines of nx points (0: none)
+bool k1_use_cluster(int nx, int R, int mode);  // whether a 1-D launch of R replicas takes the cluster kernel
 // shape: schedule variant of the step mode (0 = default; see k2_row_shapes / k2_col_shapes)
 cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape = 0);
 cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape = 0);

@@ -432,7 +432,7 @@ bool k1_supported(int nx, int complex_field) {
 }
 
 cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s) {
-    if (nl != NL_CGL && a.nx == 65536) return launch_k1_cluster(a, mode, nl, s);
+    if (nl != NL_CGL && k1_use_cluster(a.nx, a.R, mode)) return launch_k1_cluster(a, mode, nl, s);
     if (nl == NL_CGL) {
         switch (a.nx) {
             case 16: return k1c_for<16>(a, mode, s);

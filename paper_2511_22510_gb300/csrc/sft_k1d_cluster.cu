@@ -1,11 +1,15 @@
-// sft_k1d_cluster.cu -- whole-step kernel for 1-D real lattices of 65536 points.
+// sft_k1d_cluster.cu -- whole-step kernel for long 1-D real lattices, one
+// replica per thread-block cluster.
 //
-// The half-length complex line (M = 32768 values, packed z[m] = x[2m] + i x[2m+1])
-// does not fit one block's shared memory in FP32.  One replica is held by a
-// cluster of P = 4 blocks of 1024 threads (8 values per thread, 64 registers,
-// so 32 warps per SM), and every M-point transform is split
-// four-step style into L = M / P = 8192-point FFTs that each block runs in its
-// own shared memory, plus one P-point stage across the blocks:
+// 65536 points: the half-length complex line (M = 32768 values, packed
+// z[m] = x[2m] + i x[2m+1]) does not fit one block's shared memory in FP32.
+// 16384 and 32768 points fit one block, but a block per replica leaves most SMs
+// idle when there are fewer replicas than SMs.  So one replica is held by a
+// cluster of P blocks of L / 8 threads (8 values per thread, 64 registers), and
+// every M-point transform is split four-step style into L = M / P-point FFTs
+// that each block runs in its own shared memory, plus one P-point stage across
+// the blocks (P, L) = (4, 8192), (2, 8192), (2, 4096) for 65536, 32768, 16384
+// points:
 //
 //   inverse, m = P l + p, n = n1 + L n2:
 //     T_p[n1] = W_M^{-p n1} IFFT_L(Z[P l + p])[n1]        (block p, local)
@@ -27,16 +31,16 @@ namespace cg = cooperative_groups;
 
 namespace sft {
 
-constexpr int kClL = 8192;  // points of the per-block FFT
-constexpr int kClThreads = 1024;
-using ClPlan = FftPlan<kClL, 8>;
-static_assert(ClPlan::T == kClThreads && ClPlan::E == 8, "8 values per thread, one line per block");
+template <int L>
+using ClPlan = FftPlan<L, 8>;
 
-__device__ __forceinline__ int clpos(int i) { return xpos<kClL, 8>(i); }
+template <int L>
+__device__ __forceinline__ int clpos(int i) { return xpos<L, 8>(i); }
 
-template <int P, int MODE, int NL>
-__global__ void __launch_bounds__(kClThreads, 1) k1_cluster(const StepArgs a) {
-    constexpr int L = kClL, M = P * L, NX = 2 * M, E = ClPlan::E, T = ClPlan::T;
+template <int P, int L, int MODE, int NL>
+__global__ void __launch_bounds__(ClPlan<L>::T, 1024 / ClPlan<L>::T) k1_cluster(const StepArgs a) {
+    constexpr int M = P * L, NX = 2 * M, E = ClPlan<L>::E, T = ClPlan<L>::T;
+    static_assert(E == 8, "8 values per thread");
     constexpr int NI = L / (P * T);  // n1 values per thread in the cross-block stage
     static_assert(NI * P == E, "cross-block stage keeps E values per thread");
     extern __shared__ float2 sm[];
@@ -91,7 +95,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k1_cluster(const StepArgs a) {
             const int n1 = t + T * e;
             float2 w = __ldg(&twM[q * n1]);
             w.y = -w.y;
-            sm[clpos(n1)] = cmul(z[e], w);
+            sm[clpos<L>(n1)] = cmul(z[e], w);
         }
         cl.sync();
         // cross-block inverse P-point stage for this block's quarter of n1
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k1_cluster(const StepArgs a) {
             const int n1 = q * (L / P) + t + T * i;
             float2 x[P];
 #pragma unroll
-            for (int p = 0; p < P; ++p) x[p] = rem[p][clpos(n1)];
+            for (int p = 0; p < P; ++p) x[p] = rem[p][clpos<L>(n1)];
             dft_reg<P, true>(x);
 #pragma unroll
             for (int n2 = 0; n2 < P; ++n2) y[i * P + n2] = x[n2];
@@ -136,27 +140,27 @@ __global__ void __launch_bounds__(kClThreads, 1) k1_cluster(const StepArgs a) {
             for (int n2 = 0; n2 < P; ++n2) x[n2] = y[i * P + n2];
             dft_reg<P, false>(x);
 #pragma unroll
-            for (int k2 = 0; k2 < P; ++k2) rem[k2][clpos(n1)] = cmul(x[k2], __ldg(&twM[n1 * k2]));
+            for (int k2 = 0; k2 < P; ++k2) rem[k2][clpos<L>(n1)] = cmul(x[k2], __ldg(&twM[n1 * k2]));
         }
         cl.sync();
         float2 v[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = sm[clpos(t + T * e)];
+        for (int e = 0; e < E; ++e) v[e] = sm[clpos<L>(t + T * e)];
         fft_line<L, false, 8>(v, sm, t, twL);  // v[e] = Q[P (t + T e) + q]
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < E; ++e) sm[clpos(t + T * e)] = v[e];
+        for (int e = 0; e < E; ++e) sm[clpos<L>(t + T * e)] = v[e];
         cl.sync();
 
         // R2C post-processing and the update of the modes k in [q L, (q + 1) L) (block q)
-        auto Qat = [&](int k) -> float2 { return rem[k % P][clpos(k / P)]; };
+        auto Qat = [&](int k) -> float2 { return rem[k % P][clpos<L>(k / P)]; };
         float2 Xq[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int k = q * L + t + T * e;
             Xq[e] = r2c_post(Qat(k), cconj(Qat((M - k) & (M - 1))), __ldg(&twN[k]));
         }
-        const float2 z0 = rem[0][clpos(0)];
+        const float2 z0 = rem[0][clpos<L>(0)];
         const float2 XqM = make_float2(z0.x - z0.y, 0.f);
         const bool last_owner = (q == 0 && t == 0);  // also handles the Nyquist mode k = M
         if constexpr (MODE == MODE_FWD) {
@@ -201,20 +205,20 @@ __global__ void __launch_bounds__(kClThreads, 1) k1_cluster(const StepArgs a) {
     cl.sync();  // no block leaves while others may still read its shared memory
 }
 
-template <int P, int MODE, int NL>
+template <int P, int L, int MODE, int NL>
 static cudaError_t run_cluster(const StepArgs& a, cudaStream_t s) {
     static bool attr = false;
-    const size_t sm = sizeof(float2) * (size_t)ClPlan::BUF;
+    const size_t sm = sizeof(float2) * (size_t)ClPlan<L>::BUF;
     if (!a.tw_a || !a.tw_b || !a.tw_c) return cudaErrorInvalidValue;
     if (!attr) {
         cudaError_t e =
-            cudaFuncSetAttribute(k1_cluster<P, MODE, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaFuncSetAttribute(k1_cluster<P, L, MODE, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(P * a.R), 1, 1);
-    cfg.blockDim = dim3(kClThreads, 1, 1);
+    cfg.blockDim = dim3(ClPlan<L>::T, 1, 1);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -224,16 +228,46 @@ static cudaError_t run_cluster(const StepArgs& a, cudaStream_t s) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k1_cluster<P, MODE, NL>, a);
+    return cudaLaunchKernelEx(&cfg, k1_cluster<P, L, MODE, NL>, a);
+}
+
+template <int P, int L>
+static cudaError_t cluster_for(const StepArgs& a, int mode, int nl, cudaStream_t s) {
+    if (mode == MODE_FWD) return run_cluster<P, L, MODE_FWD, NL_CUBIC>(a, s);
+    if (mode == MODE_INV) return run_cluster<P, L, MODE_INV, NL_CUBIC>(a, s);
+    if (mode == MODE_STEP && nl == NL_CUBIC) return run_cluster<P, L, MODE_STEP, NL_CUBIC>(a, s);
+    if (mode == MODE_STEP && nl == NL_GRAD2) return run_cluster<P, L, MODE_STEP, NL_GRAD2>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+int k1_cluster_fft_len(int nx) {
+    switch (nx) {
+        case 65536:
+        case 32768: return 8192;
+        case 16384: return 4096;
+        default: return 0;
+    }
+}
+
+bool k1_use_cluster(int nx, int R, int mode) {
+    if (nx == 65536) return true;
+    if (!k1_cluster_fft_len(nx) || !(mode == MODE_STEP || mode == MODE_FWD || mode == MODE_INV)) return false;
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 1;
+    }
+    return R < 2 * nsm;  // a block per replica would leave SMs idle
 }
 
 cudaError_t launch_k1_cluster(const StepArgs& a, int mode, int nl, cudaStream_t s) {
-    if (a.nx != 2 * 4 * kClL) return cudaErrorInvalidValue;
-    if (mode == MODE_FWD) return run_cluster<4, MODE_FWD, NL_CUBIC>(a, s);
-    if (mode == MODE_INV) return run_cluster<4, MODE_INV, NL_CUBIC>(a, s);
-    if (mode == MODE_STEP && nl == NL_CUBIC) return run_cluster<4, MODE_STEP, NL_CUBIC>(a, s);
-    if (mode == MODE_STEP && nl == NL_GRAD2) return run_cluster<4, MODE_STEP, NL_GRAD2>(a, s);
-    return cudaErrorInvalidValue;
+    switch (a.nx) {
+        case 65536: return cluster_for<4, 8192>(a, mode, nl, s);
+        case 32768: return cluster_for<2, 8192>(a, mode, nl, s);
+        case 16384: return cluster_for<2, 4096>(a, mode, nl, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace sft

@@ -136,6 +136,10 @@ CASES = [
     ("kpz_1d_256", W.kpz_1d(256, replicas=3), 100),
     ("kpz_1d_4096", W.kpz_1d(4096, replicas=1), 50),
     ("kpz_1d_65536_cluster_R3", W.kpz_1d(65536, replicas=3, sigma0=0.2), 30),
+    ("kpz_1d_16384_cluster_R3", W.kpz_1d(16384, replicas=3, sigma0=0.2), 30),
+    ("model_a_1d_32768_setd2_cluster", W.model_a_64(d=1, n=[32768], dx=[1.0], scheme=2, sigma0=0.3), 30),
+    # at twice the SM count in replicas the 16384-point lines take the one-block-per-replica kernel
+    ("kpz_1d_16384_single_block_R304", W.kpz_1d(16384, replicas=304, sigma0=0.2), 3),
     ("model_a_1d_65536_setd2", W.model_a_64(d=1, n=[65536], dx=[1.0], scheme=2, sigma0=0.3), 30),
     ("model_a_1d_128", W.model_a_64(d=1, n=[128], dx=[1.0], replicas=2), 100),
     ("cgl_1d_64_setd2", W.cgl_2048(n=[64], d=1, dx=[0.5], replicas=2, p=[2.0, -0.5, 1e-3]), 100),
