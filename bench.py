@@ -72,6 +72,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest value of x over the ranks of the process group (x itself
+    when there is none): the whole job takes as long as its slowest rank."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_replica0(rank, replicas_per_rank):
+    """Global index of a rank's first replica: ranks take disjoint Philox
+    replica counters, so N ranks of R replicas run one ensemble of N R."""
+    return rank * replicas_per_rank
+
+
 def algorithmic_bytes(w, scheme, ncols):
     """Algorithmic HBM bytes per replica of each kernel of one step of the
     two-pass design (x-major spectra, dealiased intermediates with ncols of the
@@ -256,7 +272,7 @@ def run_gpu(args):
     R = args.replicas
     stream = torch.cuda.Stream()
     g = sft.Stepper(w.d, w.n, w.dx, R, w.model, w.p, w.scheme, w.h, w.seed, stream=stream.cuda_stream,
-                    replica0=rank * R)
+                    replica0=rank_replica0(rank, R))
     f0 = W.initial_fields(w, replicas=R, seed_offset=rank).astype(np.float32)
     g.set_field(f0)
     ncols = sum(1 for c in range(w.n[0] // 2 + 1) if 3 * c < w.n[0])
@@ -292,10 +308,7 @@ def run_gpu(args):
         barrier()
     ms = ev0.elapsed_time(ev1)
     launches = sft.sft_kernel_launches(g.ctx) - l0
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
     units = w.sites * R * K * ws
     value = units / (ms_max * 1e-3) / 1e9
     clocks = clk.summary()
@@ -371,10 +384,8 @@ def run_gpu(args):
         sk = g.observe(sft.SFT_OBS_SK)
     b.record(stream)
     barrier()
-    te = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_val = w.sites * R * ws * OBS_EVERY * chunks / (float(te.item()) * 1e-3) / 1e9
+    te = max_over_ranks(a.elapsed_time(b), dist)
+    e2e_val = w.sites * R * ws * OBS_EVERY * chunks / (te * 1e-3) / 1e9
     line["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": f0.nbytes / OBS_EVERY,
                    "d2h_bytes_per_step": sk.nbytes / OBS_EVERY,
                    "note": "per chunk of 100 steps: set_field of all R fields from pinned host memory, "

@@ -336,6 +336,7 @@ typedef struct {
     double h;
     uint64_t seed;
     int dealias;
+    int replica0; /* global index of replica 0: Philox counter word 2 of replica r is replica0 + r */
 } or_config;
 
 typedef struct {
@@ -543,7 +544,8 @@ static void draw_noise(const or_state* st, int replica, int64_t step, cplx* eta)
         if (cl == 2) continue;
         uint64_t j = noise_index(st, i);
         float z[4];
-        normals_for_index(st->cfg.seed, (uint32_t)(j >> 1), (uint32_t)step, (uint32_t)replica, 0u, z);
+        normals_for_index(st->cfg.seed, (uint32_t)(j >> 1), (uint32_t)step, (uint32_t)(st->cfg.replica0 + replica),
+                          0u, z);
         int o = (int)(j & 1) * 2;
         if (cl == 1)
             eta[i] = (double)z[o];
@@ -679,12 +681,12 @@ int or_init_random(or_state* st, double sigma) {
         for (size_t s = 0; s < st->ntot; ++s) {
             float z[4];
             if (st->cplx_field) {
-                normals_for_index(st->cfg.seed, (uint32_t)(s >> 1), 0u, (uint32_t)r, 1u, z);
+                normals_for_index(st->cfg.seed, (uint32_t)(s >> 1), 0u, (uint32_t)(st->cfg.replica0 + r), 1u, z);
                 int o = (int)(s & 1) * 2;
                 buf[2 * s] = sigma * (double)z[o];
                 buf[2 * s + 1] = sigma * (double)z[o + 1];
             } else {
-                normals_for_index(st->cfg.seed, (uint32_t)(s >> 2), 0u, (uint32_t)r, 1u, z);
+                normals_for_index(st->cfg.seed, (uint32_t)(s >> 2), 0u, (uint32_t)(st->cfg.replica0 + r), 1u, z);
                 buf[s] = sigma * (double)z[s & 3];
             }
         }

@@ -329,3 +329,31 @@ def test_observables_large_shell_count(sft, oracle_mod):
     assert np.allclose(sk[:ns], ov, rtol=2e-5, atol=1e-12 * np.abs(ov).max())
     assert np.allclose(g.observe(sft.SFT_OBS_ROUGHNESS), o.roughness(), rtol=2e-5)
     g.close()
+
+
+def test_replica_offset_shards_one_ensemble(sft, oracle_mod):
+    """Two contexts of 2 replicas at replica offsets 0 and 2 (as bench.py gives
+    two ranks) reproduce one context of 4 bit for bit (same schedule), and each
+    matches the oracle at the same offset."""
+    w = W.model_b_1024(n=[64, 64], replicas=4, sigma0=0.3)
+    f0 = W.initial_fields(w).astype(np.float32)
+    whole = sft.Stepper(w.d, w.n, w.dx, 4, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
+    whole.set_field(f0)
+    sft.sft_set_plan(whole.ctx, [0, 0, 4, 0])
+    whole.step(20)
+    want = whole.field()
+    whole.close()
+    for r0 in (0, 2):
+        g = sft.Stepper(w.d, w.n, w.dx, 2, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias, replica0=r0)
+        g.set_field(f0[r0:r0 + 2])
+        sft.sft_set_plan(g.ctx, [0, 0, 4, 0])
+        g.step(20)
+        got = g.field()
+        g.close()
+        assert np.array_equal(got, want[r0:r0 + 2])
+        o = oracle_mod.Oracle(w.d, w.n, w.dx, 2, w.model, w.p, w.scheme, w.h, w.seed, replica0=r0)
+        for r in range(2):
+            o.set_field(r, f0[r0 + r].astype(np.float64))
+        o.step(20)
+        for r in range(2):
+            assert rel_l2(got[r], o.field(r)) <= 1e-5
