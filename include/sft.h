@@ -74,8 +74,16 @@ typedef enum {
  *   SFT_CGL:     p = {alpha, beta, eps}: complex field, c = 1 - (1 + i alpha) k^2,
  *                D_a = eps, F = -(1 + i beta) DFT[|A|^2 A]       (Sec. V.C with b = alpha,
  *                c = beta, D = eps)
+ *   SFT_CUSTOM:  the general Fourier-space form of Sec. IV,
+ *                d phi_a/dt = c_a phi_a + F_a + sqrt(2 D_a) eta_a,  F = s_a DFT[q(psi)],
+ *                with c, D and s given as tables over |a|^2 and q one of sft_nonlinearity
+ *                (see the SFT_CUSTOM fields of sft_config).
  * psi, grad h and A are the inverse transforms of the dealiased state. */
-typedef enum { SFT_MODEL_A = 0, SFT_MODEL_B = 1, SFT_KPZ = 2, SFT_CGL = 3 } sft_model;
+typedef enum { SFT_MODEL_A = 0, SFT_MODEL_B = 1, SFT_KPZ = 2, SFT_CGL = 3, SFT_CUSTOM = 4 } sft_model;
+
+/* Real-space nonlinearity q of SFT_CUSTOM: none; psi^3 (real field); sum_j (d_j psi)^2
+ * with the spectral gradient (real field); |A|^2 A (complex field). */
+typedef enum { SFT_NL_NONE = 0, SFT_NL_CUBIC = 1, SFT_NL_GRAD2 = 2, SFT_NL_CGL = 3 } sft_nonlinearity;
 
 /* Schemes of Sec. II: SETD-EM (Eq. SETD-EM), SETD1 (Eq. SETD1), SETD2 (Eq. SETD2). */
 typedef enum { SFT_SETD_EM = 0, SFT_SETD1 = 1, SFT_SETD2 = 2 } sft_scheme;
@@ -95,6 +103,21 @@ typedef struct {
     void* stream;      /* cudaStream_t, or NULL for the default stream */
     int replica0;      /* global index of replica 0 (Philox counter word 2): ranks that shard one
                           ensemble pass disjoint offsets; 0 for a stand-alone context */
+    /* SFT_CUSTOM only (ignored otherwise).  Host tables indexed by q = |a|^2 = sum_i a_i^2,
+     * q = 0 .. sum_i (n_i/2)^2, copied by sft_create (the caller keeps ownership):
+     * c_re/c_im the linear operator c_a (c_im NULL: real), noise_D the noise strength
+     * D_a >= 0, nl_re/nl_im the nonlinear prefactor s_a (NULL: zero).  A real field needs
+     * real c and s (Hermitian symmetry); complex_field = 1 takes SFT_NL_CGL or SFT_NL_NONE,
+     * a real field SFT_NL_NONE, SFT_NL_CUBIC or SFT_NL_GRAD2 (3-D: NONE or CUBIC).
+     * SFT_EINVAL for a missing c_re / noise_D, a negative D or a complex table on a real
+     * field. */
+    int custom_nl;         /* sft_nonlinearity */
+    int complex_field;
+    const double* c_re;
+    const double* c_im;
+    const double* noise_D;
+    const double* nl_re;
+    const double* nl_im;
 } sft_config;
 
 /* Observables for sft_observe (App. C; shells j = ceil(|a|), i.e. the shell

@@ -20,7 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("SFT_LIB", os.path.join(_HERE, "libsft.so"))
 
 SFT_OK, SFT_EINVAL, SFT_ENOMEM, SFT_ECUDA, SFT_ENONFINITE, SFT_ETIMEOUT, SFT_EUNSUPPORTED, SFT_ECHECKPOINT = range(8)
-SFT_MODEL_A, SFT_MODEL_B, SFT_KPZ, SFT_CGL = 0, 1, 2, 3
+SFT_MODEL_A, SFT_MODEL_B, SFT_KPZ, SFT_CGL, SFT_CUSTOM = 0, 1, 2, 3, 4
+SFT_NL_NONE, SFT_NL_CUBIC, SFT_NL_GRAD2, SFT_NL_CGL = 0, 1, 2, 3
 SFT_SETD_EM, SFT_SETD1, SFT_SETD2 = 0, 1, 2
 (SFT_OBS_SK, SFT_OBS_SK_REPLICAS, SFT_OBS_MARK, SFT_OBS_CKT, SFT_OBS_ROUGHNESS, SFT_OBS_RESPONSE,
  SFT_OBS_NSHELLS) = range(7)
@@ -49,7 +50,9 @@ class sft_config(C.Structure):
         ("d", C.c_int), ("n", C.c_int * 3), ("dx", C.c_double * 3), ("replicas", C.c_int),
         ("model", C.c_int), ("p", C.c_double * 8), ("scheme", C.c_int), ("h", C.c_double),
         ("seed", C.c_uint64), ("dealias", C.c_int), ("precision", C.c_int), ("stream", C.c_void_p),
-        ("replica0", C.c_int),
+        ("replica0", C.c_int), ("custom_nl", C.c_int), ("complex_field", C.c_int),
+        ("c_re", C.POINTER(C.c_double)), ("c_im", C.POINTER(C.c_double)), ("noise_D", C.POINTER(C.c_double)),
+        ("nl_re", C.POINTER(C.c_double)), ("nl_im", C.POINTER(C.c_double)),
     ]
 
 
@@ -111,7 +114,9 @@ def _check(ctx, status: int):
 # ---------------------------------------------------------------- thin wrappers
 def make_config(d: int, n: Sequence[int], dx: Sequence[float], replicas: int, model: int, p: Sequence[float],
                 scheme: int, h: float, seed: int, dealias: int = 1, stream: Optional[int] = None,
-                replica0: int = 0) -> sft_config:
+                replica0: int = 0, custom: Optional[dict] = None) -> sft_config:
+    """custom (SFT_CUSTOM): {"nl": SFT_NL_*, "complex_field": 0/1, "c": c(|a|^2), "D": D(|a|^2),
+    "s": s(|a|^2) or None}, arrays over q = 0 .. sum_i (n_i/2)^2 (complex c or s for complex fields)."""
     cfg = sft_config()
     cfg.d = d
     for i in range(3):
@@ -128,6 +133,28 @@ def make_config(d: int, n: Sequence[int], dx: Sequence[float], replicas: int, mo
     cfg.precision = 0
     cfg.stream = stream
     cfg.replica0 = replica0
+    if custom is not None:
+        keep = []
+
+        def put(name, arr):
+            if arr is None:
+                return
+            a = np.ascontiguousarray(arr, dtype=np.float64)
+            keep.append(a)
+            setattr(cfg, name, a.ctypes.data_as(C.POINTER(C.c_double)))
+
+        cfg.custom_nl = int(custom.get("nl", SFT_NL_NONE))
+        cfg.complex_field = int(custom.get("complex_field", 0))
+        c = np.asarray(custom["c"])
+        put("c_re", c.real)
+        put("c_im", c.imag if np.iscomplexobj(c) else None)
+        put("noise_D", np.asarray(custom["D"], dtype=np.float64))
+        sv = custom.get("s")
+        if sv is not None:
+            sv = np.asarray(sv)
+            put("nl_re", sv.real)
+            put("nl_im", sv.imag if np.iscomplexobj(sv) else None)
+        cfg._keep = keep  # the tables live until sft_create has copied them
     return cfg
 
 
@@ -325,13 +352,14 @@ class Stepper:
     arrays (see ``spectrum``).
     """
 
-    def __init__(self, d, n, dx, replicas, model, p, scheme, h, seed, dealias=1, stream=None, replica0=0):
-        self.cfg = make_config(d, n, dx, replicas, model, p, scheme, h, seed, dealias, stream, replica0)
+    def __init__(self, d, n, dx, replicas, model, p, scheme, h, seed, dealias=1, stream=None, replica0=0,
+                 custom=None):
+        self.cfg = make_config(d, n, dx, replicas, model, p, scheme, h, seed, dealias, stream, replica0, custom)
         self.ctx = sft_create(self.cfg)
         self.d, self.R = d, replicas
         self.n = [int(n[i]) for i in range(d)]
         self.shape = tuple(reversed(self.n))
-        self.complex_field = model == SFT_CGL
+        self.complex_field = model == SFT_CGL or (model == SFT_CUSTOM and bool(custom.get("complex_field", 0)))
         self.sites = int(np.prod(self.n))
         nx = self.n[0]
         self.hx = nx if self.complex_field else nx // 2 + 1

@@ -75,6 +75,7 @@ struct sft_ctx {
     // schedule of the step's passes (plan autotuner)
     bool planned = false;
     int row_shape = 0, col_shape = 0, rpb = 0;
+    uint64_t cust_hash = 0;  // SFT_CUSTOM: hash of the copied tables (checkpoint compatibility)
     // batch context: members advanced together (1-D lattices of uneven sizes in one persistent launch)
     bool is_batch = false;
     std::vector<sft_ctx*> members;
@@ -112,6 +113,30 @@ static long long isqrt_ceil(long long q) {
     return j;
 }
 
+// Field kind and nonlinearity of a configuration.  SFT_CUSTOM without a
+// nonlinearity runs the cubic (real) or |A|^2 A (complex) kernels with s = 0.
+static void model_kind(const sft_config* c, int* cplx, int* nl) {
+    if (c->model == SFT_CUSTOM) {
+        *cplx = c->complex_field ? 1 : 0;
+        if (c->custom_nl == SFT_NL_GRAD2)
+            *nl = NL_GRAD2;
+        else if (c->custom_nl == SFT_NL_CGL)
+            *nl = NL_CGL;
+        else
+            *nl = *cplx ? NL_CGL : NL_CUBIC;
+        return;
+    }
+    *cplx = c->model == SFT_CGL;
+    *nl = c->model == SFT_KPZ ? NL_GRAD2 : (*cplx ? NL_CGL : NL_CUBIC);
+}
+
+// Entries of the SFT_CUSTOM tables: |a|^2 = 0 .. sum_i (n_i/2)^2.
+static long long custom_len(const sft_config* c) {
+    long long q = 0;
+    for (int i = 0; i < c->d; ++i) q += (long long)(c->n[i] / 2) * (c->n[i] / 2);
+    return q + 1;
+}
+
 static StepArgs base_args(const sft_ctx* c) {
     StepArgs a{};
     a.nx = c->nx;
@@ -131,6 +156,7 @@ static StepArgs base_args(const sft_ctx* c) {
         case SFT_MODEL_A:
         case SFT_MODEL_B: a.s0 = (float)(-p[0] * p[2]); a.s0i = 0.f; break;
         case SFT_KPZ: a.s0 = (float)(0.5 * p[1]); a.s0i = 0.f; break;
+        case SFT_CUSTOM: a.s0 = 1.f; a.s0i = 0.f; break;  // s is folded into the coefficient table
         default: a.s0 = -1.f; a.s0i = (float)(-p[1]); break;
     }
     a.seed = c->cfg.seed;
@@ -577,15 +603,36 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
     if (cfg->replicas < 1) return why = "replicas must be >= 1", SFT_EINVAL;
     if (cfg->replica0 < 0) return why = "replica0 must be >= 0", SFT_EINVAL;
     if (!(cfg->h > 0) || !std::isfinite(cfg->h)) return why = "h must be positive and finite", SFT_EINVAL;
-    if (cfg->model < SFT_MODEL_A || cfg->model > SFT_CGL) return why = "unknown model", SFT_EINVAL;
+    if (cfg->model < SFT_MODEL_A || cfg->model > SFT_CUSTOM) return why = "unknown model", SFT_EINVAL;
     if (cfg->scheme < SFT_SETD_EM || cfg->scheme > SFT_SETD2) return why = "unknown scheme", SFT_EINVAL;
     if (cfg->precision != 0) return why = "only FP32 precision (0) is built", SFT_EUNSUPPORTED;
     if (cfg->dealias != 0 && cfg->dealias != 1) return why = "dealias must be 0 or 1", SFT_EINVAL;
-    const int cplx = cfg->model == SFT_CGL;
+    int cplx = 0, nlk = 0;
+    model_kind(cfg, &cplx, &nlk);
+    if (cfg->model == SFT_CUSTOM) {
+        const int nl = cfg->custom_nl;
+        if (nl < SFT_NL_NONE || nl > SFT_NL_CGL) return why = "unknown custom nonlinearity", SFT_EINVAL;
+        if (cplx ? !(nl == SFT_NL_CGL || nl == SFT_NL_NONE) : nl == SFT_NL_CGL)
+            return why = "custom nonlinearity does not match the field (|A|^2 A needs a complex field, psi^3 and "
+                         "grad^2 a real one)",
+                   SFT_EINVAL;
+        if (!cfg->c_re || !cfg->noise_D) return why = "SFT_CUSTOM needs the c_re and noise_D tables", SFT_EINVAL;
+        const long long n = custom_len(cfg);
+        for (long long q = 0; q < n; ++q) {
+            const double ci = cfg->c_im ? cfg->c_im[q] : 0.0, si = cfg->nl_im ? cfg->nl_im[q] : 0.0;
+            const double sr = cfg->nl_re ? cfg->nl_re[q] : 0.0;
+            if (!std::isfinite(cfg->c_re[q]) || !std::isfinite(ci) || !std::isfinite(sr) || !std::isfinite(si))
+                return why = "custom tables must be finite", SFT_EINVAL;
+            if (!(cfg->noise_D[q] >= 0.0) || !std::isfinite(cfg->noise_D[q]))
+                return why = "custom noise strength D must be finite and >= 0", SFT_EINVAL;
+            if (!cplx && (ci != 0.0 || si != 0.0))
+                return why = "a real field needs real c and s (Hermitian symmetry)", SFT_EINVAL;
+        }
+    }
     if (cfg->d == 1 && !k1_supported(cfg->n[0], cplx)) return why = "1-D size outside the built plans", SFT_EUNSUPPORTED;
     if (cfg->d == 2 && !(cplx ? k2c_supported(cfg->n[0], cfg->n[1]) : k2_supported(cfg->n[0], cfg->n[1], 0)))
         return why = "2-D size outside the built plans", SFT_EUNSUPPORTED;
-    if (cfg->d == 3 && (cplx || cfg->model == SFT_KPZ || !k3_supported(cfg->n[0], cfg->n[1], cfg->n[2], cplx)))
+    if (cfg->d == 3 && (cplx || nlk == NL_GRAD2 || !k3_supported(cfg->n[0], cfg->n[1], cfg->n[2], cplx)))
         return why = "3-D lattices are built for real fields with the cubic term and 16..128 points per axis",
                SFT_EUNSUPPORTED;
     return SFT_OK;
@@ -609,8 +656,9 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     ctx->nx = cfg->n[0];
     ctx->ny = cfg->d >= 2 ? cfg->n[1] : 1;
     ctx->nz = cfg->d >= 3 ? cfg->n[2] : 1;
-    ctx->cplx = cfg->model == SFT_CGL;
-    ctx->nl = cfg->model == SFT_KPZ ? NL_GRAD2 : (ctx->cplx ? NL_CGL : NL_CUBIC);
+    model_kind(cfg, &ctx->cplx, &ctx->nl);
+    ctx->cfg.c_re = ctx->cfg.c_im = ctx->cfg.noise_D = ctx->cfg.nl_re = ctx->cfg.nl_im = nullptr;  // host tables: copied below
+    if (cfg->model != SFT_CUSTOM) ctx->cfg.custom_nl = ctx->cfg.complex_field = 0;
     ctx->hx = ctx->cplx ? ctx->nx : ctx->nx / 2 + 1;
     ctx->mx = 0;
     for (int c = 0; c < ctx->hx; ++c) {
@@ -696,7 +744,40 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     t.noise_norm = nf;
     t.nq = nq;
     t.out = ctx->tab;
-    if (launch_build_table(t, ctx->stream) != cudaSuccess) return cleanup(SFT_ECUDA);
+    double* dcust = nullptr;
+    if (cfg->model == SFT_CUSTOM) {
+        // c_re, c_im, D, s_re, s_im over |a|^2, copied to the device for the FP64 table build
+        const long long n = custom_len(cfg);
+        std::vector<double> host((size_t)(5 * n), 0.0);
+        const bool with_s = cfg->custom_nl != SFT_NL_NONE;
+        uint64_t hsh = 1469598103934665603ULL;
+        for (long long q = 0; q < n; ++q) {
+            host[q] = cfg->c_re[q];
+            host[n + q] = cfg->c_im ? cfg->c_im[q] : 0.0;
+            host[2 * n + q] = cfg->noise_D[q];
+            host[3 * n + q] = (with_s && cfg->nl_re) ? cfg->nl_re[q] : 0.0;
+            host[4 * n + q] = (with_s && cfg->nl_im) ? cfg->nl_im[q] : 0.0;
+        }
+        const unsigned char* b = (const unsigned char*)host.data();
+        for (size_t i = 0; i < host.size() * sizeof(double); ++i) {
+            hsh ^= b[i];
+            hsh *= 1099511628211ULL;
+        }
+        ctx->cust_hash = hsh;
+        if (cudaMalloc(&dcust, host.size() * sizeof(double)) != cudaSuccess) return cleanup(SFT_ENOMEM);
+        if (cudaMemcpy(dcust, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(dcust);
+            return cleanup(SFT_ECUDA);
+        }
+        t.cust = dcust;
+        t.ncust = n;
+    }
+    const cudaError_t te = launch_build_table(t, ctx->stream);
+    if (dcust) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(dcust);
+    }
+    if (te != cudaSuccess) return cleanup(SFT_ECUDA);
     // shell counts with the half-spectrum weights
     ctx->counts.assign(ctx->nshells, 0.0);
     for (int ax = 0; ax < ctx->hx; ++ax) {
@@ -737,7 +818,9 @@ sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
             fprintf(stderr, "sft_create_batch: member %d: %s\n", i, why.c_str());
             return vs;
         }
-        if (cfgs[i].model != cfgs[0].model || cfgs[i].scheme != cfgs[0].scheme) {
+        if (cfgs[i].model != cfgs[0].model || cfgs[i].scheme != cfgs[0].scheme ||
+            (cfgs[0].model == SFT_CUSTOM &&
+             (cfgs[i].custom_nl != cfgs[0].custom_nl || cfgs[i].complex_field != cfgs[0].complex_field))) {
             fprintf(stderr, "sft_create_batch: members must share the model and the scheme\n");
             return SFT_EUNSUPPORTED;
         }
@@ -751,8 +834,8 @@ sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
     ctx->is_batch = true;
     ctx->cfg = cfgs[0];
     ctx->d = cfgs[0].d;
-    ctx->cplx = cfgs[0].model == SFT_CGL;
-    ctx->nl = cfgs[0].model == SFT_KPZ ? NL_GRAD2 : (ctx->cplx ? NL_CGL : NL_CUBIC);
+    model_kind(&cfgs[0], &ctx->cplx, &ctx->nl);
+    ctx->cfg.c_re = ctx->cfg.c_im = ctx->cfg.noise_D = ctx->cfg.nl_re = ctx->cfg.nl_im = nullptr;
     if (cfgs[0].stream) {
         ctx->stream = (cudaStream_t)cfgs[0].stream;
     } else {
@@ -1446,8 +1529,8 @@ struct CkptHeader {
     int64_t has_fprev;
 };
 
-static uint64_t config_hash(const sft_config& c) {
-    uint64_t h = 1469598103934665603ULL;
+static uint64_t config_hash(const sft_config& c, uint64_t tables) {
+    uint64_t h = 1469598103934665603ULL ^ tables;
     auto mix = [&](const void* p, size_t n) {
         const unsigned char* b = (const unsigned char*)p;
         for (size_t i = 0; i < n; ++i) {
@@ -1466,6 +1549,8 @@ static uint64_t config_hash(const sft_config& c) {
     mix(&c.seed, sizeof c.seed);
     mix(&c.dealias, sizeof c.dealias);
     mix(&c.precision, sizeof c.precision);
+    mix(&c.custom_nl, sizeof c.custom_nl);
+    mix(&c.complex_field, sizeof c.complex_field);
     return h;
 }
 
@@ -1480,7 +1565,7 @@ sft_status sft_checkpoint(sft_ctx* ctx, void* host_buf, size_t cap, size_t* writ
     CkptHeader hd{};
     memcpy(hd.magic, "SFTCKPT1", 8);
     hd.version = 1;
-    hd.cfg_hash = config_hash(ctx->cfg);
+    hd.cfg_hash = config_hash(ctx->cfg, ctx->cust_hash);
     hd.step = ctx->step;
     hd.first_step = ctx->first_step;
     hd.R = ctx->R;
@@ -1501,7 +1586,7 @@ sft_status sft_restore(sft_ctx* ctx, const void* host_buf, size_t bytes) {
     memcpy(&hd, host_buf, sizeof hd);
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (memcmp(hd.magic, "SFTCKPT1", 8) != 0 || hd.version != 1) return fail(ctx, SFT_ECHECKPOINT, "not a checkpoint");
-    if (hd.cfg_hash != config_hash(ctx->cfg) || hd.R != ctx->R || hd.nmodes != ctx->nmodes ||
+    if (hd.cfg_hash != config_hash(ctx->cfg, ctx->cust_hash) || hd.R != ctx->R || hd.nmodes != ctx->nmodes ||
         hd.has_fprev != (ctx->fprev ? 1 : 0))
         return fail(ctx, SFT_ECHECKPOINT, "checkpoint written for another configuration");
     if (bytes != sizeof hd + ms * (hd.has_fprev ? 2 : 1)) return fail(ctx, SFT_ECHECKPOINT, "checkpoint size mismatch");

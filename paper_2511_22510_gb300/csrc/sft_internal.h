@@ -104,6 +104,10 @@ struct TableArgs {
     double h, dk, noise_norm;
     long long nq;
     float4* out;
+    // SFT_CUSTOM: device copies of c_re, c_im, D, s_re, s_im over |a|^2 = 0 .. ncust-1 (consecutive blocks);
+    // the prefactor s is folded into A and B
+    const double* cust;
+    long long ncust;
 };
 __host__ __device__ inline long long table_k2_index(int d, int hy, long long entry) {
     if (d == 1) return entry * entry;

@@ -86,11 +86,19 @@ __global__ void k_build_table(const TableArgs t) {
     const double* p = t.p;
     double2 c = make_double2(0.0, 0.0);
     double D = 0.0;
+    double2 s = make_double2(1.0, 0.0);  // nonlinear prefactor folded into A, B (SFT_CUSTOM only)
     switch (t.model) {
         case 0: c.x = -p[0] * (p[1] + k2); D = p[0] * p[3]; break;
         case 1: c.x = -p[0] * k2 * (p[1] + k2); D = p[0] * p[3] * k2; break;
         case 2: c.x = -p[0] * k2; D = p[2]; break;
-        default: c.x = 1.0 - k2; c.y = -p[0] * k2; D = p[2]; break;
+        case 3: c.x = 1.0 - k2; c.y = -p[0] * k2; D = p[2]; break;
+        default: {  // tables over |a|^2 (general Fourier-space form, Sec. IV)
+            const long long a2 = table_k2_index(t.d, t.hy, q);
+            const long long n = t.ncust;
+            c = make_double2(t.cust[a2], t.cust[n + a2]);
+            D = t.cust[2 * n + a2];
+            s = make_double2(t.cust[3 * n + a2], t.cust[4 * n + a2]);
+        }
     }
     const double h = t.h;
     const double2 z = make_double2(c.x * h, c.y * h);
@@ -114,6 +122,8 @@ __global__ void k_build_table(const TableArgs t) {
             B = make_double2(-h * p2.x, -h * p2.y);
         }
     }
+    A = make_double2(A.x * s.x - A.y * s.y, A.x * s.y + A.y * s.x);
+    B = make_double2(B.x * s.x - B.y * s.y, B.x * s.y + B.y * s.x);
     if (t.complex_field) {
         t.out[2 * q] = make_float4((float)f1.x, (float)f1.y, (float)A.x, (float)A.y);
         t.out[2 * q + 1] = make_float4((float)B.x, (float)B.y, (float)g.x, (float)g.y);

@@ -3,6 +3,8 @@ include/sft.h declares; configuration validation needs no device."""
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -57,3 +59,36 @@ def test_unsupported_configs_report_unsupported(lib):
     with pytest.raises(lib.SftError) as ei:
         lib.sft_create(cfg)
     assert ei.value.status == lib.SFT_EUNSUPPORTED
+
+
+def _custom(lib, n=16, **over):
+    q = 2 * (n // 2) ** 2 + 1
+    tab = dict(nl=lib.SFT_NL_CUBIC, complex_field=0, c=-(0.5 + np.arange(q) * 0.01), D=np.full(q, 0.1),
+               s=np.full(q, -1.0))
+    tab.update(over)
+    return tab
+
+
+@pytest.mark.parametrize("over", [
+    dict(c=None), dict(D=None), dict(D=-np.ones(2 * 8 ** 2 + 1)), dict(nl=7),
+    dict(c=-(0.5 + 0.1j) * np.ones(2 * 8 ** 2 + 1)),          # complex c on a real field
+    dict(s=(-1.0 + 0.5j) * np.ones(2 * 8 ** 2 + 1)),          # complex s on a real field
+    dict(nl=3),                                               # |A|^2 A on a real field
+    dict(complex_field=1, nl=1),                              # psi^3 on a complex field
+    dict(c=np.full(2 * 8 ** 2 + 1, np.nan)),
+])
+def test_invalid_custom_models_rejected_before_any_device_call(lib, over):
+    tab = _custom(lib, **over)
+    if tab["c"] is None or tab["D"] is None:
+        cfg = lib.make_config(2, [16, 16], [1.0, 1.0], 1, lib.SFT_CUSTOM, [], 1, 0.01, 1,
+                              custom=dict(tab, c=np.zeros(1) if tab["c"] is None else tab["c"],
+                                          D=np.zeros(1) if tab["D"] is None else tab["D"]))
+        if tab["c"] is None:
+            cfg.c_re = None
+        else:
+            cfg.noise_D = None
+    else:
+        cfg = lib.make_config(2, [16, 16], [1.0, 1.0], 1, lib.SFT_CUSTOM, [], 1, 0.01, 1, custom=tab)
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_create(cfg)
+    assert ei.value.status == lib.SFT_EINVAL
