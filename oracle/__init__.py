@@ -66,6 +66,9 @@ def lib():
             L = C.CDLL(build())
             dp = C.POINTER(C.c_double)
             vp = C.c_void_p
+            L.or_sde0d.argtypes = [C.c_int, dp, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_int64, C.c_int64,
+                                   C.c_int64, dp, dp]
+            L.or_sde0d.restype = C.c_int
             L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
             L.or_bm_log.argtypes = [C.c_float]
             L.or_bm_log.restype = C.c_float
@@ -331,3 +334,21 @@ class Oracle:
         if rc != 0:
             raise ValueError("adjoint needs a real field and SETD-EM or SETD1")
         return out.reshape((self.R,) + self.shape)
+
+
+SDE_SAO, SDE_GBM = 0, 1
+SDE_EM, SDE_MILSTEIN, SDE_SETD_EM, SDE_SETD_MILSTEIN, SDE_SETD1 = 0, 1, 2, 3, 4
+
+
+def sde0d(kind, p, scheme, h, nsteps, u0, seed, substeps=1, step0=0, w0=None):
+    """0-d SDE ensemble (Sec. III): advances the paths u0 (array) by nsteps steps of
+    size h (each the sum of `substeps` fine Wiener increments); returns (u, W)."""
+    u = np.array(u0, dtype=np.float64, copy=True).reshape(-1)
+    w = np.zeros_like(u) if w0 is None else np.array(w0, dtype=np.float64, copy=True).reshape(-1)
+    pv = np.zeros(8)
+    pv[:len(p)] = p
+    rc = lib().or_sde0d(int(kind), _dptr(pv), int(scheme), float(h), int(substeps), int(seed), int(step0),
+                        int(nsteps), int(u.size), _dptr(u), _dptr(w))
+    if rc != 0:
+        raise ValueError("or_sde0d: invalid arguments")
+    return u, w

@@ -1078,3 +1078,69 @@ int or_step_noise(or_state* st, const double* eta_ri) {
     st->step++;
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* 0-d SDE ensembles (Sec. III): independent paths of the Ito SDE              */
+/*   du = c u dt + F(u) dt + G(u) dW                                          */
+/* kind 0, SAO (Eq. sao), p = {Gamma, T, b}: c = -Gamma, F = -Gamma b u^3,     */
+/*   G = sqrt(2 Gamma T);                                                      */
+/* kind 1, GBM (Eq. gbm), p = {lambda, mu, delta}: c = lambda - delta,         */
+/*   F = delta u, G = mu u.                                                    */
+/* Schemes (the update rules of the stability table of Sec. III):             */
+/*   0 EM:            u + (c u + F) h + G dW                                   */
+/*   1 Milstein:      EM + G G' (dW^2 - h) / 2                                 */
+/*   2 SETD-EM:       f1 u + f2 F + f3 G dW                       (Eq. SETD-EM) */
+/*   3 SETD-Milstein: f1 u + f2 F + f3 G [dW + G' (dW^2 - h)/2]   (Eq. SETD-Miltstein) */
+/*   4 SETD1:         f1 u + f2 F + f4 G N,  N = dW / sqrt(h)     (Eq. SETD1)  */
+/* f1 = e^{ch}, f2 = (e^{ch} - 1)/c, f3 = e^{ch/2}, f4 = sqrt((e^{2ch} - 1)/(2c)). */
+/* Wiener increments: step n of size h = K h_f is the sum over i < K of        */
+/* sqrt(h_f) z(p, (step0 + n) K + i), z(p, m) the normal p & 3 of             */
+/* Philox(ctr = (p >> 2, m, 0, 2), key = seed); runs with different K on one  */
+/* seed therefore follow one Wiener path.  w (optional) accumulates W.        */
+/* ------------------------------------------------------------------------- */
+int or_sde0d(int kind, const double* p, int scheme, double h, int substeps, uint64_t seed, int64_t step0,
+             int64_t nsteps, int64_t npaths, double* u, double* w) {
+    if (kind < 0 || kind > 1 || scheme < 0 || scheme > 4 || !(h > 0) || substeps < 1) return 1;
+    const double c = kind == 0 ? -p[0] : p[0] - p[2];
+    const double ch = c * h;
+    const double f1 = exp(ch);
+    const double f2 = c != 0.0 ? expm1(ch) / c : h;
+    const double f3 = exp(0.5 * ch);
+    const double f4 = c != 0.0 ? sqrt(expm1(2.0 * ch) / (2.0 * c)) : sqrt(h);
+    const double sqhf = sqrt(h / substeps);
+    for (int64_t pa = 0; pa < npaths; ++pa) {
+        double x = u[pa], wsum = w ? w[pa] : 0.0;
+        for (int64_t n = 0; n < nsteps; ++n) {
+            double dW = 0.0;
+            for (int i = 0; i < substeps; ++i) {
+                const int64_t m = (step0 + n) * substeps + i;
+                float z[4];
+                normals_for_index(seed, (uint32_t)(pa >> 2), (uint32_t)m, 0u, 2u, z);
+                dW += sqhf * (double)z[pa & 3];
+            }
+            double F, G, Gp;
+            if (kind == 0) {
+                F = -p[0] * p[2] * x * x * x;
+                G = sqrt(2.0 * p[0] * p[1]);
+                Gp = 0.0;
+            } else {
+                F = p[2] * x;
+                G = p[1] * x;
+                Gp = p[1];
+            }
+            double xn;
+            switch (scheme) {
+                case 0: xn = x + (c * x + F) * h + G * dW; break;
+                case 1: xn = x + (c * x + F) * h + G * dW + 0.5 * G * Gp * (dW * dW - h); break;
+                case 2: xn = f1 * x + f2 * F + f3 * G * dW; break;
+                case 3: xn = f1 * x + f2 * F + f3 * G * (dW + 0.5 * Gp * (dW * dW - h)); break;
+                default: xn = f1 * x + f2 * F + f4 * G * (dW / sqrt(h)); break;
+            }
+            x = xn;
+            wsum += dW;
+        }
+        u[pa] = x;
+        if (w) w[pa] = wsum;
+    }
+    return 0;
+}
