@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--workload", default="model_b_1024",
                     choices=["model_b_1024", "model_a_64", "kpz_ensemble", "cgl_2048", "model_a_128_3d",
-                             "model_a_128_3d_tangent"],
+                             "model_a_128_3d_tangent", "sde0d"],
                     help="model_b_1024 is the headline; the others print their own line for the other workloads")
     return ap.parse_args()
 
@@ -418,6 +418,19 @@ def run_other(args):
 
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": K, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "vs_baseline": None}
+    if args.workload == "sde0d":
+        # 0-d SDE ensemble of Sec. III: GBM (lambda = 2, mu = 1, delta = 1), SETD-Milstein, h = 2^-8, FP64
+        S, p, h = 1 << 22, [2.0, 1.0, 1.0], 2.0 ** -8
+        u = torch.ones(S, dtype=torch.float64, device="cuda")
+        sft.sft_sde0d(1, p, sft.SFT_SDE_SETD_MILSTEIN, h, 16, u.data_ptr(), S, seed=9, stream=stream.cuda_stream)
+        ms = timed(lambda: sft.sft_sde0d(1, p, sft.SFT_SDE_SETD_MILSTEIN, h, K, u.data_ptr(), S, seed=9, step0=16,
+                                         stream=stream.cuda_stream))
+        line.update({"metric": "Gpath-steps/s, 0-d SDE ensemble", "unit": "Gpath-steps/s", "dtype": "f64",
+                     "value": S * K / (ms * 1e-3) / 1e9, "ms_per_step": ms / K,
+                     "config": {"workload": "sde0d", "problem": "GBM lambda=2 mu=1 delta=1", "scheme": "SETD-Milstein",
+                                "paths": S, "h": h}})
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "kpz_ensemble":
         lengths = W.kpz_ensemble_lengths()
         counts = {L: lengths.count(L) for L in sorted(set(lengths))}

@@ -255,6 +255,39 @@ sft_status sft_launches_per_step(const sft_ctx* ctx, int* launches);
  * graph replays included). */
 sft_status sft_kernel_launches(const sft_ctx* ctx, int64_t* count);
 
+/* 0-d SDE ensembles (Sec. III): npaths independent paths of the Ito SDE
+ * du = c u dt + F(u) dt + G(u) dW,
+ *   SFT_SDE_SAO (Eq. sao), p = {Gamma, T, b}: c = -Gamma, F = -Gamma b u^3,
+ *                G = sqrt(2 Gamma T) (additive noise);
+ *   SFT_SDE_GBM (Eq. gbm), p = {lambda, mu, delta}: c = lambda - delta,
+ *                F = delta u, G = mu u (multiplicative; delta = 0 makes the
+ *                deterministic part of the SETD schemes exact),
+ * advanced by the update rules of the stability table of Sec. III:
+ *   EM u + (c u + F) h + G dW;  Milstein EM + G G' (dW^2 - h)/2;
+ *   SETD-EM f1 u + f2 F + f3 G dW;  SETD-Milstein f1 u + f2 F + f3 G [dW + G' (dW^2 - h)/2];
+ *   SETD1 f1 u + f2 F + f4 G dW/sqrt(h),
+ * f1 = e^{ch}, f2 = (e^{ch} - 1)/c, f3 = e^{ch/2}, f4 = sqrt((e^{2ch} - 1)/(2c)).
+ * Step n (counting from step0) of size h uses dW = sum_{i < substeps}
+ * sqrt(h/substeps) z_p((step0 + n) substeps + i), z_p(m) the normal p & 3 of
+ * Philox4x32-10(ctr = (p >> 2, m, 0, 2), key = seed): runs with different
+ * substeps (h) on one seed follow one Wiener path (strong-convergence studies).
+ *   u_dev: DEVICE array of npaths doubles, in/out.  w_dev: DEVICE array of
+ *   npaths doubles accumulating W (the sum of the dW), or NULL.  Both owned by
+ *   the caller.  stream: cudaStream_t or NULL.  FP64 state and coefficients.
+ * Enqueues one kernel and returns (no synchronisation); SFT_EINVAL for an
+ * unknown kind or scheme, h <= 0, substeps < 1, negative counts, a missing
+ * u_dev or more than 2^32 fine increments; SFT_ECUDA if the launch fails. */
+typedef enum { SFT_SDE_SAO = 0, SFT_SDE_GBM = 1 } sft_sde_kind;
+typedef enum {
+    SFT_SDE_EM = 0,
+    SFT_SDE_MILSTEIN = 1,
+    SFT_SDE_SETD_EM = 2,
+    SFT_SDE_SETD_MILSTEIN = 3,
+    SFT_SDE_SETD1 = 4
+} sft_sde_scheme;
+sft_status sft_sde0d(int kind, const double* p, int scheme, double h, int substeps, uint64_t seed, int64_t step0,
+                     int64_t nsteps, int64_t npaths, void* u_dev, void* w_dev, void* stream);
+
 /* No counterpart in the paper: an entry point for callers that cannot allocate
  * device memory (an embedding runtime that owns the allocator, a plug-in that
  * must not grow its footprint after start-up, a real-time loop where an

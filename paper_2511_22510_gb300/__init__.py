@@ -35,7 +35,7 @@ ABI_FUNCTIONS = [
     "sft_set_spectrum", "sft_step", "sft_step_plain", "sft_sync", "sft_observe", "sft_tangent_step",
     "sft_adjoint", "sft_set_checkpoint_interval", "sft_checkpoint", "sft_restore", "sft_get_step",
     "sft_launches_per_step", "sft_kernel_launches", "sft_draw_noise", "sft_profile", "sft_step2d_noalloc",
-    "sft_get_plan", "sft_set_plan", "sft_last_error", "sft_destroy",
+    "sft_get_plan", "sft_set_plan", "sft_sde0d", "sft_last_error", "sft_destroy",
 ]
 
 
@@ -92,6 +92,8 @@ def load_library(path: str = LIB_PATH):
     L.sft_step2d_noalloc.argtypes = [C.POINTER(sft_config), vp, vp, C.c_int, i64, i64]
     L.sft_profile.argtypes = [vp, i64, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
     L.sft_get_plan.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
+    L.sft_sde0d.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int, C.c_double, C.c_int, C.c_uint64, i64, i64, i64,
+                            vp, vp, vp]
     L.sft_set_plan.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
     L.sft_last_error.argtypes = [vp]
     L.sft_last_error.restype = C.c_char_p
@@ -274,6 +276,20 @@ def sft_get_plan(ctx) -> list:
 def sft_set_plan(ctx, plan: Sequence[int]):
     v = (C.c_int * 4)(*[int(x) for x in plan])
     _check(ctx, load_library().sft_set_plan(ctx, v, 4))
+
+
+SFT_SDE_SAO, SFT_SDE_GBM = 0, 1
+SFT_SDE_EM, SFT_SDE_MILSTEIN, SFT_SDE_SETD_EM, SFT_SDE_SETD_MILSTEIN, SFT_SDE_SETD1 = 0, 1, 2, 3, 4
+
+
+def sft_sde0d(kind: int, p: Sequence[float], scheme: int, h: float, nsteps: int, u_dev_ptr: int, npaths: int,
+              seed: int, substeps: int = 1, step0: int = 0, w_dev_ptr: Optional[int] = None,
+              stream: Optional[int] = None):
+    """0-d SDE ensemble (Sec. III) on device arrays of npaths doubles (u in/out, W accumulated)."""
+    pv = (C.c_double * 8)(*([float(x) for x in p] + [0.0] * (8 - len(p))))
+    st = load_library().sft_sde0d(int(kind), pv, int(scheme), float(h), int(substeps), int(seed), int(step0),
+                                  int(nsteps), int(npaths), u_dev_ptr, w_dev_ptr, stream)
+    _check(None, st)
 
 
 def sft_launches_per_step(ctx) -> int:
