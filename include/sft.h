@@ -203,6 +203,14 @@ sft_status sft_sync(sft_ctx* ctx);
  * *written receives the number of doubles written.  Synchronises. */
 sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, size_t* written);
 
+/* Width over boxes (Sec. V.B, the KPZ width w_ell): for every replica, the mean
+ * over the boxes of ell^d sites that tile the lattice of the variance of the
+ * real-space field in the box, w_ell^2 = < <h^2>_box - <h>_box^2 >_boxes (FP64
+ * sums).  ell = n gives the global width of SFT_OBS_ROUGHNESS, ell = 1 gives 0.
+ * ell must divide every n_i; host_out receives R doubles (cap >= R).  Real
+ * fields, not on batch contexts.  Synchronises. */
+sft_status sft_box_width(sft_ctx* ctx, int ell, double* host_out, size_t cap, size_t* written);
+
 /* Linear response by forward-mode differentiation of the step (tangent map),
  * advanced together with the primal on the same noise path:
  *   dphi <- f1 dphi + A dF + B dF(t-h),  dF = M s DFT[q'(psi) IDFT(M dphi)].

@@ -66,6 +66,8 @@ def lib():
             L = C.CDLL(build())
             dp = C.POINTER(C.c_double)
             vp = C.c_void_p
+            L.or_box_width.argtypes = [vp, C.c_int, dp]
+            L.or_box_width.restype = C.c_int
             L.or_sde0d.argtypes = [C.c_int, dp, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_int64, C.c_int64,
                                    C.c_int64, dp, dp]
             L.or_sde0d.restype = C.c_int
@@ -325,6 +327,13 @@ class Oracle:
     def response(self):
         out = np.zeros(self.nshells())
         lib().or_observe_response(self._p, _dptr(out))
+        return out
+
+    def box_width(self, ell):
+        """w_ell^2 per replica: mean over boxes of ell^d sites of the in-box variance (Sec. V.B)."""
+        out = np.zeros(self.R)
+        if lib().or_box_width(self._p, int(ell), _dptr(out)) != 0:
+            raise ValueError("box width: real field and a box size dividing every n_i")
         return out
 
     def adjoint(self, lam, nsteps):

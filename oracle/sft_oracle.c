@@ -1144,3 +1144,37 @@ int or_sde0d(int kind, const double* p, int scheme, double h, int substeps, uint
     }
     return 0;
 }
+
+/* Width over boxes (Sec. V.B): for replica r, the mean over the boxes of ell^d
+ * sites tiling the lattice of the variance of the real-space field in the box,
+ * <h^2>_box - <h>_box^2.  ell must divide every n_i.  out: R values. */
+int or_box_width(const or_state* st, int ell, double* out) {
+    if (st->cplx_field || ell < 1) return 1;
+    for (int ax = 0; ax < st->cfg.d; ++ax)
+        if (st->n[ax] % ell) return 1;
+    const int nx = st->n[0], ny = st->n[1], nz = st->n[2];
+    const int lx = ell, ly = st->cfg.d >= 2 ? ell : 1, lz = st->cfg.d >= 3 ? ell : 1;
+    const int bx = nx / lx, by = ny / ly, bz = nz / lz;
+    double* h = (double*)malloc(sizeof(double) * st->ntot);
+    for (int r = 0; r < st->cfg.replicas; ++r) {
+        or_get_field(st, r, h);
+        double acc = 0.0;
+        for (int kz = 0; kz < bz; ++kz)
+            for (int ky = 0; ky < by; ++ky)
+                for (int kx = 0; kx < bx; ++kx) {
+                    double s1 = 0.0, s2 = 0.0;
+                    for (int z = kz * lz; z < (kz + 1) * lz; ++z)
+                        for (int y = ky * ly; y < (ky + 1) * ly; ++y)
+                            for (int x = kx * lx; x < (kx + 1) * lx; ++x) {
+                                const double v = h[((size_t)z * ny + y) * nx + x];
+                                s1 += v;
+                                s2 += v * v;
+                            }
+                    const double n = (double)lx * ly * lz, m = s1 / n;
+                    acc += s2 / n - m * m;
+                }
+        out[r] = acc / ((double)bx * by * bz);
+    }
+    free(h);
+    return 0;
+}

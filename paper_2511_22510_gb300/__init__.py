@@ -35,7 +35,7 @@ ABI_FUNCTIONS = [
     "sft_set_spectrum", "sft_step", "sft_step_plain", "sft_sync", "sft_observe", "sft_tangent_step",
     "sft_adjoint", "sft_set_checkpoint_interval", "sft_checkpoint", "sft_restore", "sft_get_step",
     "sft_launches_per_step", "sft_kernel_launches", "sft_draw_noise", "sft_profile", "sft_step2d_noalloc",
-    "sft_get_plan", "sft_set_plan", "sft_sde0d", "sft_last_error", "sft_destroy",
+    "sft_get_plan", "sft_set_plan", "sft_sde0d", "sft_box_width", "sft_last_error", "sft_destroy",
 ]
 
 
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
     L.sft_step2d_noalloc.argtypes = [C.POINTER(sft_config), vp, vp, C.c_int, i64, i64]
     L.sft_profile.argtypes = [vp, i64, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
     L.sft_get_plan.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
+    L.sft_box_width.argtypes = [vp, C.c_int, C.POINTER(C.c_double), sz, C.POINTER(sz)]
     L.sft_sde0d.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int, C.c_double, C.c_int, C.c_uint64, i64, i64, i64,
                             vp, vp, vp]
     L.sft_set_plan.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
@@ -276,6 +277,15 @@ def sft_get_plan(ctx) -> list:
 def sft_set_plan(ctx, plan: Sequence[int]):
     v = (C.c_int * 4)(*[int(x) for x in plan])
     _check(ctx, load_library().sft_set_plan(ctx, v, 4))
+
+
+def sft_box_width(ctx, ell: int, replicas: int) -> np.ndarray:
+    """w_ell^2 per replica: mean over boxes of ell^d sites of the in-box variance."""
+    out = np.zeros(replicas)
+    n = C.c_size_t()
+    _check(ctx, load_library().sft_box_width(ctx, int(ell), out.ctypes.data_as(C.POINTER(C.c_double)), replicas,
+                                             C.byref(n)))
+    return out
 
 
 SFT_SDE_SAO, SFT_SDE_GBM = 0, 1

@@ -1023,6 +1023,31 @@ sft_status sft_sync(sft_ctx* ctx) {
     return read_status(ctx);
 }
 
+sft_status sft_box_width(sft_ctx* ctx, int ell, double* host_out, size_t cap, size_t* written) {
+    if (!ctx || !host_out) return SFT_EINVAL;
+    if (written) *written = 0;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
+    if (ctx->cplx) return fail(ctx, SFT_EUNSUPPORTED, "the box width is defined for real fields");
+    const int n[3] = {ctx->nx, ctx->ny, ctx->nz};
+    if (ell < 1) return fail(ctx, SFT_EINVAL, "box size must be >= 1");
+    for (int i = 0; i < ctx->d; ++i)
+        if (n[i] % ell != 0) return fail(ctx, SFT_EINVAL, "box size must divide every lattice size");
+    if (cap < (size_t)ctx->R) return fail(ctx, SFT_EINVAL, "output too small");
+    sft_status s = inverse_to_buffer(ctx, ctx->phi, 0, ctx->R);
+    if (s != SFT_OK) return s;
+    CK(cudaMemsetAsync(ctx->drough, 0, sizeof(double) * ctx->R, ctx->stream));
+    CK(launch_box_width(ctx->real, ctx->nx, ctx->ny, ctx->nz, ctx->d, ell, ctx->R, ctx->drough, ctx->stream));
+    ctx->launches += 1;
+    std::vector<double> acc(ctx->R);
+    CK(cudaMemcpyAsync(acc.data(), ctx->drough, sizeof(double) * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double nboxes = 1.0;
+    for (int i = 0; i < ctx->d; ++i) nboxes *= (double)(n[i] / ell);
+    for (int r = 0; r < ctx->R; ++r) host_out[r] = acc[r] / nboxes;
+    if (written) *written = (size_t)ctx->R;
+    return read_status(ctx);
+}
+
 sft_status sft_get_field(sft_ctx* ctx, int replica, void* host_out, size_t bytes) {
     if (!ctx || !host_out) return SFT_EINVAL;
     if (ctx->is_batch) {

@@ -139,6 +139,9 @@ struct ObsArgs {
     double* rough;      // [R] sum over a != 0 of |phi_a|^2 (full-spectrum weights)
 };
 cudaError_t launch_observe(const ObsArgs& o, cudaStream_t s);
+// per replica: sum over the boxes of ell^d sites of the height variance in the box (out zeroed by the caller)
+cudaError_t launch_box_width(const float* real, int nx, int ny, int nz, int d, int ell, int R, double* out,
+                             cudaStream_t s);
 cudaError_t launch_shell_counts(int nx, int ny, int nz, int hx, int complex_field, int nshells, double* counts,
                                 cudaStream_t s);
 

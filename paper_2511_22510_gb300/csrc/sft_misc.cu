@@ -297,4 +297,59 @@ cudaError_t launch_draw_noise(int nx, int ny, int nz, int hx, int cplx, int R, i
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- box width
+// KPZ width over boxes (Sec. V.B): block b of the flattened (replica, box) grid
+// sums h and h^2 over the ell^d sites of its box in FP64 and adds the box
+// variance <h^2> - <h>^2 to its replica's accumulator.
+__global__ void k_box_width(const float* __restrict__ real, int nx, int ny, int nz, int d, int ell, long long nboxes,
+                            double* out) {
+    const long long b = blockIdx.x;
+    const int r = (int)(b / nboxes);
+    const long long box = b % nboxes;
+    const int bx = nx / ell, by = d >= 2 ? ny / ell : 1;
+    const int x0 = (int)(box % bx) * ell, y0 = (int)((box / bx) % by) * ell, z0 = (int)(box / ((long long)bx * by)) * ell;
+    const int lx = ell, ly = d >= 2 ? ell : 1, lz = d >= 3 ? ell : 1;
+    const long long ncell = (long long)lx * ly * lz;
+    const float* base = real + (size_t)r * ((size_t)nx * ny * nz);
+    double s1 = 0.0, s2 = 0.0;
+    for (long long i = threadIdx.x; i < ncell; i += blockDim.x) {
+        const int x = x0 + (int)(i % lx), y = y0 + (int)((i / lx) % ly), z = z0 + (int)(i / ((long long)lx * ly));
+        const double h = base[((size_t)z * ny + y) * nx + x];
+        s1 += h;
+        s2 += h * h;
+    }
+    __shared__ double red[2][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = s1;
+        red[1][wid] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t1 += red[0][w];
+            t2 += red[1][w];
+        }
+        const double m = t1 / (double)ncell;
+        atomicAdd(&out[r], t2 / (double)ncell - m * m);
+    }
+}
+
+cudaError_t launch_box_width(const float* real, int nx, int ny, int nz, int d, int ell, int R, double* out,
+                             cudaStream_t s) {
+    long long nboxes = nx / ell;
+    if (d >= 2) nboxes *= ny / ell;
+    if (d >= 3) nboxes *= nz / ell;
+    const long long blocks = nboxes * R;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_box_width<<<(unsigned)blocks, 256, 0, s>>>(real, nx, ny, nz, d, ell, nboxes, out);
+    return cudaGetLastError();
+}
+
 }  // namespace sft
