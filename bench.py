@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--workload", default="model_b_1024",
                     choices=["model_b_1024", "model_a_64", "kpz_ensemble", "cgl_2048", "model_a_128_3d",
-                             "model_a_128_3d_tangent", "sde0d"],
+                             "model_a_128_3d_tangent", "sde0d", "dynamics"],
                     help="model_b_1024 is the headline; the others print their own line for the other workloads")
     return ap.parse_args()
 
@@ -429,6 +429,32 @@ def run_other(args):
                      "value": S * K / (ms * 1e-3) / 1e9, "ms_per_step": ms / K,
                      "config": {"workload": "sde0d", "problem": "GBM lambda=2 mu=1 delta=1", "scheme": "SETD-Milstein",
                                 "paths": S, "h": h}})
+        print(json.dumps(line), flush=True)
+        return
+    if args.workload == "dynamics":
+        # C(k, omega), chi(k, omega) and the FDT deviation (App. C) on Model A 256^2 x 64 (the paper's FDT set-up)
+        import time
+        w = W.model_a_64(n=[256, 256], replicas=64, h=0.01)
+        g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, stream=stream.cuda_stream)
+        g.init_random(0.1)
+        g.step(64)
+        g.sync()
+        ms_plain = timed(lambda: g.step(256))
+        M = 256
+        sft.sft_dyn_start(g.ctx, M, 1)
+        ms_rec = timed(lambda: g.step(M))
+        nm = (w.n[0] // 2 + 1) * w.n[1]
+        t0 = time.perf_counter()
+        _, _, dbar = sft.sft_dyn_result(g.ctx, nm, M)
+        ms_res = (time.perf_counter() - t0) * 1e3
+        g.close()
+        sites = w.sites * w.replicas
+        line.update({"value": sites * M / (ms_rec * 1e-3) / 1e9, "ms_per_step": ms_rec / M, "steps": M,
+                     "config": {"workload": "dynamics", "lattice": "256x256", "replicas": w.replicas, "M": M,
+                                "every": 1, "model": "Model A"},
+                     "plain": {"value": sites * 256 / (ms_plain * 1e-3) / 1e9, "unit": UNIT,
+                               "form": "the same stepper without recording"},
+                     "result_ms": ms_res, "fdt_dbar": dbar})
         print(json.dumps(line), flush=True)
         return
     if args.workload == "kpz_ensemble":

@@ -203,6 +203,27 @@ sft_status sft_sync(sft_ctx* ctx);
  * *written receives the number of doubles written.  Synchronises. */
 sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, size_t* written);
 
+/* Dynamic correlation C(k, omega) and noise-inferred susceptibility chi(k, omega)
+ * (App. C), 2-D real fields.  sft_dyn_start arms a recording: at the steps
+ * s0 + m every (s0 = the next step, m = 0 .. M-1) every mode of every replica
+ * writes its state phi_a and its nonlinear force F_a (the F of that step) to
+ * device buffers (2 R * n_modes * M complex floats, allocated here; step-major,
+ * so the recording steps write coalesced).  After
+ * M * every further steps sft_dyn_result transforms the series in time on the
+ * GPU (the paper's convention phi_b = sum_m e^{+2 pi i b m / M} phi_m, omega_b =
+ * 2 pi b / T, T = M every h, b signed with b = -M/2 .. M/2 - 1 at index
+ * (b mod M)) and reduces over the replicas (the ensemble):
+ *   C[a M + b]   = (L/N^2)^d T / M^2 <|phi_ab|^2>
+ *   chi[a M + b] = (L/N^2)^d T / M^2 / (2 D_a) <phi_ab conj(-i omega_b phi_ab - K_ab)>,
+ *                  K = c_a phi + F (the deterministic force),
+ * a the stored mode (x-major half-spectrum order, n_modes = (n0/2 + 1) n1),
+ * chi as (re, im) pairs, cap >= n_modes M; *dbar (if not NULL) receives the
+ * average |2 Im chi - (omega / D) C| over the modes with D_a > 0 and all
+ * frequencies (Eq. average-deviation).  The result ends the recording.
+ * M: power of two in [16, 16384]; every >= 1.  Synchronises. */
+sft_status sft_dyn_start(sft_ctx* ctx, int M, int every);
+sft_status sft_dyn_result(sft_ctx* ctx, double* C_out, double* chi_out, size_t cap, double* dbar);
+
 /* Width over boxes (Sec. V.B, the KPZ width w_ell): for every replica, the mean
  * over the boxes of ell^d sites that tile the lattice of the variance of the
  * real-space field in the box, w_ell^2 = < <h^2>_box - <h>_box^2 >_boxes (FP64

@@ -68,6 +68,8 @@ def lib():
             vp = C.c_void_p
             L.or_box_width.argtypes = [vp, C.c_int, dp]
             L.or_box_width.restype = C.c_int
+            L.or_force.argtypes = [vp, C.c_int, dp]
+            L.or_force.restype = C.c_int
             L.or_sde0d.argtypes = [C.c_int, dp, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_int64, C.c_int64,
                                    C.c_int64, dp, dp]
             L.or_sde0d.restype = C.c_int
@@ -328,6 +330,12 @@ class Oracle:
         out = np.zeros(self.nshells())
         lib().or_observe_response(self._p, _dptr(out))
         return out
+
+    def force(self, r):
+        """Nonlinear term F_a of replica r at the current state (full spectrum)."""
+        out = np.zeros(self.ntot, dtype=np.complex128)
+        lib().or_force(self._p, int(r), _dptr(out.view(np.float64)))
+        return out.reshape(self.shape)
 
     def box_width(self, ell):
         """w_ell^2 per replica: mean over boxes of ell^d sites of the in-box variance (Sec. V.B)."""

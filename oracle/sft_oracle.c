@@ -1178,3 +1178,12 @@ int or_box_width(const or_state* st, int ell, double* out) {
     free(h);
     return 0;
 }
+
+/* The nonlinear term F_a = M_a s_a DFT[q(psi)]_a of the current state of one
+ * replica (Sec. IV step 1-3, full spectrum): with c_a phi_a it is the
+ * deterministic force K_a of the noise-inferred susceptibility (App. C). */
+int or_force(or_state* st, int replica, double* out_ri) {
+    if (replica < 0 || replica >= st->cfg.replicas) return 1;
+    nonlinear_term(st, st->phi + (size_t)replica * st->ntot, (cplx*)out_ri);
+    return 0;
+}

@@ -35,7 +35,8 @@ ABI_FUNCTIONS = [
     "sft_set_spectrum", "sft_step", "sft_step_plain", "sft_sync", "sft_observe", "sft_tangent_step",
     "sft_adjoint", "sft_set_checkpoint_interval", "sft_checkpoint", "sft_restore", "sft_get_step",
     "sft_launches_per_step", "sft_kernel_launches", "sft_draw_noise", "sft_profile", "sft_step2d_noalloc",
-    "sft_get_plan", "sft_set_plan", "sft_sde0d", "sft_box_width", "sft_last_error", "sft_destroy",
+    "sft_get_plan", "sft_set_plan", "sft_sde0d", "sft_box_width", "sft_dyn_start", "sft_dyn_result", "sft_last_error",
+    "sft_destroy",
 ]
 
 
@@ -93,6 +94,8 @@ def load_library(path: str = LIB_PATH):
     L.sft_profile.argtypes = [vp, i64, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
     L.sft_get_plan.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
     L.sft_box_width.argtypes = [vp, C.c_int, C.POINTER(C.c_double), sz, C.POINTER(sz)]
+    L.sft_dyn_start.argtypes = [vp, C.c_int, C.c_int]
+    L.sft_dyn_result.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), sz, C.POINTER(C.c_double)]
     L.sft_sde0d.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int, C.c_double, C.c_int, C.c_uint64, i64, i64, i64,
                             vp, vp, vp]
     L.sft_set_plan.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
@@ -286,6 +289,21 @@ def sft_box_width(ctx, ell: int, replicas: int) -> np.ndarray:
     _check(ctx, load_library().sft_box_width(ctx, int(ell), out.ctypes.data_as(C.POINTER(C.c_double)), replicas,
                                              C.byref(n)))
     return out
+
+
+def sft_dyn_start(ctx, M: int, every: int = 1):
+    _check(ctx, load_library().sft_dyn_start(ctx, int(M), int(every)))
+
+
+def sft_dyn_result(ctx, nmodes: int, M: int):
+    """(C [nmodes, M], chi [nmodes, M] complex, dbar) of App. C; b at index b mod M."""
+    Cv = np.zeros(nmodes * M)
+    chi = np.zeros(2 * nmodes * M)
+    db = C.c_double()
+    dp = C.POINTER(C.c_double)
+    _check(ctx, load_library().sft_dyn_result(ctx, Cv.ctypes.data_as(dp), chi.ctypes.data_as(dp), nmodes * M,
+                                              C.byref(db)))
+    return Cv.reshape(nmodes, M), chi.view(np.complex128).reshape(nmodes, M), db.value
 
 
 SFT_SDE_SAO, SFT_SDE_GBM = 0, 1

@@ -76,6 +76,11 @@ struct sft_ctx {
     bool planned = false;
     int row_shape = 0, col_shape = 0, rpb = 0;
     uint64_t cust_hash = 0;  // SFT_CUSTOM: hash of the copied tables (checkpoint compatibility)
+    std::vector<double> cust_c, cust_D;  // SFT_CUSTOM: real c and D over |a|^2 (dynamic observables)
+    // recording for the dynamic observables
+    float2 *rec_phi = nullptr, *rec_F = nullptr;
+    long long rec_start = 0;
+    int rec_every = 1, rec_M = 0;
     // batch context: members advanced together (1-D lattices of uneven sizes in one persistent launch)
     bool is_batch = false;
     std::vector<sft_ctx*> members;
@@ -169,6 +174,12 @@ static StepArgs base_args(const sft_ctx* c) {
     a.bad_step = c->dstep + 2;
     a.rpb = c->rpb;
     a.tw_c = (c->d == 1 && !c->cplx && k1_cluster_fft_len(c->nx)) ? c->tw.get(k1_cluster_fft_len(c->nx)) : nullptr;
+    a.rec_phi = c->rec_phi;
+    a.rec_F = c->rec_F;
+    a.rec_start = c->rec_start;
+    a.rec_n = (long long)c->R * c->nmodes;
+    a.rec_every = c->rec_every;
+    a.rec_M = c->rec_M;
     return a;
 }
 
@@ -191,7 +202,7 @@ static cudaError_t launch_second(const sft_ctx* ctx, const StepArgs& a, int mode
 }
 
 static cudaError_t launch_cols_step(const sft_ctx* ctx, const StepArgs& a) {
-    if (ctx->pipe_cols) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
+    if (ctx->pipe_cols && !a.rec_phi) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
     if (ctx->d == 2 && !ctx->cplx) return launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream, ctx->col_shape);
     return launch_second(ctx, a, MODE_STEP);
 }
@@ -503,6 +514,7 @@ static sft_status plan_step(sft_ctx* ctx) {
         if (me == cudaSuccess && grad) me = cudaMalloc(&tPy, pb);
         if (me == cudaSuccess) {
             StepArgs c = base_args(ctx);
+            c.rec_phi = c.rec_F = nullptr;  // trial passes record nothing
             c.qin = ctx->Q;
             c.phi = tphi;
             c.fprev = tfp;
@@ -764,6 +776,8 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
             hsh *= 1099511628211ULL;
         }
         ctx->cust_hash = hsh;
+        ctx->cust_c.assign(host.begin(), host.begin() + n);
+        ctx->cust_D.assign(host.begin() + 2 * n, host.begin() + 3 * n);
         if (cudaMalloc(&dcust, host.size() * sizeof(double)) != cudaSuccess) return cleanup(SFT_ENOMEM);
         if (cudaMemcpy(dcust, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaFree(dcust);
@@ -1021,6 +1035,158 @@ sft_status sft_sync(sft_ctx* ctx) {
     if (!ctx) return SFT_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream));
     return read_status(ctx);
+}
+
+// ------------------------------------------------------------ dynamic observables
+static void drop_graph(sft_ctx* ctx) {
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    ctx->warmed = false;  // the next chunk runs plain first, then is captured with the new arguments
+}
+
+static void stop_recording(sft_ctx* ctx) {
+    if (ctx->rec_phi) cudaFree(ctx->rec_phi);
+    if (ctx->rec_F) cudaFree(ctx->rec_F);
+    ctx->rec_phi = ctx->rec_F = nullptr;
+    ctx->rec_M = 0;
+    drop_graph(ctx);
+}
+
+sft_status sft_dyn_start(sft_ctx* ctx, int M, int every) {
+    if (!ctx) return SFT_EINVAL;
+    if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
+    if (ctx->d != 2 || ctx->cplx)
+        return fail(ctx, SFT_EUNSUPPORTED, "dynamic observables are built for 2-D real fields");
+    if (M < 16 || M > 16384 || (M & (M - 1)) || every < 1)
+        return fail(ctx, SFT_EINVAL, "M must be a power of two in [16, 16384] and every >= 1");
+    CK(cudaStreamSynchronize(ctx->stream));
+    stop_recording(ctx);
+    const size_t n = (size_t)ctx->R * ctx->nmodes * M;
+    if (cudaMalloc(&ctx->rec_phi, n * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&ctx->rec_F, n * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        stop_recording(ctx);
+        return fail(ctx, SFT_ENOMEM, "no device memory for the recorded series");
+    }
+    CK(cudaMemsetAsync(ctx->rec_phi, 0, n * sizeof(float2), ctx->stream));
+    CK(cudaMemsetAsync(ctx->rec_F, 0, n * sizeof(float2), ctx->stream));
+    ctx->rec_start = ctx->step;
+    ctx->rec_every = every;
+    ctx->rec_M = M;
+    return SFT_OK;
+}
+
+sft_status sft_dyn_result(sft_ctx* ctx, double* C_out, double* chi_out, size_t cap, double* dbar) {
+    if (!ctx || !C_out || !chi_out) return SFT_EINVAL;
+    if (!ctx->rec_phi) return fail(ctx, SFT_EINVAL, "no recording: call sft_dyn_start first");
+    const int M = ctx->rec_M;
+    if (ctx->step < ctx->rec_start + (long long)M * ctx->rec_every)
+        return fail(ctx, SFT_EINVAL, "the recording is not complete: step M * every times after sft_dyn_start");
+    const long long nm = ctx->nmodes;
+    if (cap < (size_t)(nm * M)) return fail(ctx, SFT_EINVAL, "output too small");
+    CK(cudaStreamSynchronize(ctx->stream));
+    sft_status st = read_status(ctx);
+    if (st != SFT_OK) return st;
+    const size_t n = (size_t)ctx->R * nm * M;
+    // time transforms of every (replica, mode) series: the complex line FFT
+    std::vector<float2> tw(M);
+    for (int m = 0; m < M; ++m) {
+        const double ang = 2.0 * M_PI * (double)m / (double)M;
+        tw[m] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    }
+    float2 *dtw = nullptr, *Phi = nullptr, *Fw = nullptr;
+    double *dc = nullptr, *dD = nullptr, *dC = nullptr;
+    double2* dchi = nullptr;
+    auto release = [&]() {
+        for (void* p : {(void*)dtw, (void*)Phi, (void*)Fw, (void*)dc, (void*)dD, (void*)dC, (void*)dchi})
+            if (p) cudaFree(p);
+    };
+    if (cudaMalloc(&dtw, M * sizeof(float2)) != cudaSuccess || cudaMalloc(&Phi, n * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&Fw, n * sizeof(float2)) != cudaSuccess || cudaMalloc(&dc, nm * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dD, nm * sizeof(double)) != cudaSuccess || cudaMalloc(&dC, nm * M * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dchi, nm * M * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(ctx, SFT_ENOMEM, "no device memory for the time transforms");
+    }
+    // c_a and D_a of every stored mode (Sec. V model terms; tables for SFT_CUSTOM)
+    std::vector<double> hc(nm), hD(nm);
+    const double dk = 2.0 * M_PI / (ctx->nx * ctx->cfg.dx[0]);
+    const double* p = ctx->cfg.p;
+    for (int cc = 0; cc < ctx->hx; ++cc)
+        for (int ay = 0; ay < ctx->ny; ++ay) {
+            const long long ays = (2 * ay < ctx->ny) ? ay : ay - ctx->ny;
+            const long long q = (long long)cc * cc + ays * ays;
+            const double k2 = dk * dk * (double)q;
+            double c = 0.0, D = 0.0;
+            switch (ctx->cfg.model) {
+                case SFT_MODEL_A: c = -p[0] * (p[1] + k2); D = p[0] * p[3]; break;
+                case SFT_MODEL_B: c = -p[0] * k2 * (p[1] + k2); D = p[0] * p[3] * k2; break;
+                case SFT_KPZ: c = -p[0] * k2; D = p[2]; break;
+                default: c = ctx->cust_c[q]; D = ctx->cust_D[q]; break;
+            }
+            hc[(size_t)cc * ctx->ny + ay] = c;
+            hD[(size_t)cc * ctx->ny + ay] = D;
+        }
+    cudaError_t e = cudaMemcpyAsync(dtw, tw.data(), M * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dc, hc.data(), nm * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dD, hD.data(), nm * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+        // step-major record -> one contiguous series per (replica, mode), then its FFT in place
+        float2* ser = pass == 0 ? Phi : Fw;
+        e = launch_transpose_c(pass == 0 ? ctx->rec_phi : ctx->rec_F, ser, M, (long long)ctx->R * nm, ctx->stream);
+        StepArgs t{};
+        t.nx = M;
+        t.ny = t.nz = 1;
+        t.hx = M;
+        t.R = (int)(ctx->R * nm);
+        t.cplx_io = ser;
+        t.phi = ser;
+        t.tw_a = dtw;
+        if (e == cudaSuccess) e = launch_k1_line(t, MODE_FWD, NL_CGL, ctx->stream);
+        ctx->launches += 2;
+    }
+    DynArgs dv{};
+    dv.Phi = Phi;
+    dv.Fw = Fw;
+    dv.c = dc;
+    dv.D = dD;
+    dv.R = ctx->R;
+    dv.M = M;
+    dv.nmodes = nm;
+    dv.T = (double)M * ctx->rec_every * ctx->cfg.h;
+    double Ld = 1.0;
+    for (int i = 0; i < ctx->d; ++i) Ld *= ctx->cfg.dx[i] / ctx->cfg.n[i];  // (L / N^2)^d = (dx / N)^d
+    dv.norm = Ld * dv.T / ((double)M * M) / ctx->R;
+    dv.C = dC;
+    dv.chi = dchi;
+    if (e == cudaSuccess) e = launch_dyn_reduce(dv, ctx->stream);
+    ctx->launches += 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(C_out, dC, nm * M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(chi_out, dchi, nm * M * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    release();
+    if (e != cudaSuccess) return fail(ctx, SFT_ECUDA, std::string("dynamic observables: ") + cudaGetErrorString(e));
+    // average absolute deviation from the FDT over the modes with noise (Eq. average-deviation)
+    if (dbar) {
+        double acc = 0.0;
+        long long cnt = 0;
+        for (long long a = 0; a < nm; ++a) {
+            if (!(hD[a] > 0.0)) continue;
+            for (int b = 0; b < M; ++b) {
+                const int sb = b < M / 2 ? b : b - M;
+                const double w = 2.0 * M_PI * sb / dv.T;
+                acc += std::fabs(2.0 * chi_out[2 * (a * M + b) + 1] - w / hD[a] * C_out[a * M + b]);
+                ++cnt;
+            }
+        }
+        *dbar = cnt ? acc / (double)cnt : 0.0;
+    }
+    stop_recording(ctx);
+    return SFT_OK;
 }
 
 sft_status sft_box_width(sft_ctx* ctx, int ell, double* host_out, size_t cap, size_t* written) {
@@ -1772,6 +1938,8 @@ void sft_destroy(sft_ctx* ctx) {
     if (ctx->d_members) cudaFree(ctx->d_members);
     if (ctx->d_items) cudaFree(ctx->d_items);
     if (ctx->d_head) cudaFree(ctx->d_head);
+    if (ctx->rec_phi) cudaFree(ctx->rec_phi);
+    if (ctx->rec_F) cudaFree(ctx->rec_F);
     for (cudaStream_t st : ctx->sides) cudaStreamDestroy(st);
     for (cudaEvent_t ev : ctx->ev_joins) cudaEventDestroy(ev);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);

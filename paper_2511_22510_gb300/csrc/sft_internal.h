@@ -7,7 +7,16 @@
 namespace sft {
 
 enum Nonlinearity { NL_CUBIC = 0, NL_GRAD2 = 1, NL_CGL = 2, NL_NONE = 3 };
-enum KernelMode { MODE_STEP = 0, MODE_FWD = 1, MODE_INV = 2, MODE_TAN = 3, MODE_ADJ = 4, MODE_PRIME = 5, MODE_ADJ_PRIME = 6 };
+enum KernelMode {
+    MODE_STEP = 0,
+    MODE_FWD = 1,
+    MODE_INV = 2,
+    MODE_TAN = 3,
+    MODE_ADJ = 4,
+    MODE_PRIME = 5,
+    MODE_ADJ_PRIME = 6,
+    MODE_STEP_REC = 7  // the step, also recording the state and the nonlinear force (dynamic observables)
+};
 
 // Everything a step kernel needs, passed by value.
 struct StepArgs {
@@ -56,6 +65,13 @@ struct StepArgs {
     unsigned* status;             // bit 0: non-finite state
     long long* bad_step;
     int rpb;                      // 2-D column pass: replicas per block (< 1: the default)
+    // recording for the dynamic observables (2-D real fields): at steps rec_start + m rec_every,
+    // m < rec_M, mode j (state layout index, replicas included) writes phi_j and F_j to
+    // rec_*[m rec_n + j] (step-major, coalesced), rec_n = R n_modes
+    float2* rec_phi;
+    float2* rec_F;
+    long long rec_start, rec_n;
+    int rec_every, rec_M;
 };
 
 // launchers (return cudaGetLastError of the launch); each picks the template
@@ -142,6 +158,21 @@ cudaError_t launch_observe(const ObsArgs& o, cudaStream_t s);
 // per replica: sum over the boxes of ell^d sites of the height variance in the box (out zeroed by the caller)
 cudaError_t launch_box_width(const float* real, int nx, int ny, int nz, int d, int ell, int R, double* out,
                              cudaStream_t s);
+// dynamic observables: C_ab and chi_ab from the time transforms of the recorded series (see sft_dyn_result)
+struct DynArgs {
+    const float2* Phi;  // [R][nmodes][M] time transforms of phi (forward, e^{-i})
+    const float2* Fw;   // same for the nonlinear force F
+    const double* c;    // [nmodes] linear operator c_a (real fields)
+    const double* D;    // [nmodes] noise strength D_a
+    int R, M;
+    long long nmodes;
+    double T, norm;     // record duration, (L/N^2)^d T / M^2 / R
+    double* C;          // [nmodes][M] out
+    double2* chi;       // [nmodes][M] out
+};
+cudaError_t launch_dyn_reduce(const DynArgs& d, cudaStream_t s);
+// out[c rows + r] = in[r cols + c] (complex, tiled through shared memory)
+cudaError_t launch_transpose_c(const float2* in, float2* out, long long rows, long long cols, cudaStream_t s);
 cudaError_t launch_shell_counts(int nx, int ny, int nz, int hx, int complex_field, int nshells, double* counts,
                                 cudaStream_t s);
 

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
 #pragma unroll
             for (int e = 0; e < E; ++e) a.pout[colbase + t + T * e] = v[e];
         }
-    } else if constexpr (MODE == MODE_STEP) {
+    } else if constexpr (MODE == MODE_STEP || MODE == MODE_STEP_REC) {
         if (!valid && T >= 32) return;
         const long long step = current_step(a);
         const bool first = (a.scheme == 2) && (step == *a.first_step);
@@ -222,6 +222,14 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
             // partners on the self-conjugate planes are overwritten by the fix-up below
             out[e] = setd_update<false>(co, ph, F, Fp, eta_of(out[e], selfc));
             if (a.scheme == 2 && has_f && valid) a.fprev[colbase + ay] = F;
+            if constexpr (MODE == MODE_STEP_REC) {
+                const long long kk = step - a.rec_start;
+                if (valid && kk >= 0 && kk % a.rec_every == 0 && kk / a.rec_every < a.rec_M) {
+                    const size_t ri = (size_t)(kk / a.rec_every) * (size_t)a.rec_n + colbase + ay;
+                    a.rec_phi[ri] = ph;
+                    a.rec_F[ri] = F;
+                }
+            }
         }
         if (plane || T < 32) {
             team_sync<T>();
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
 template <int NY, int NL, int MODE, int SH = 0>
 static cudaError_t run_cols(const StepArgs& a, cudaStream_t s) {
     using C = ColCfg<NY, SH>;
-    const size_t sm = MODE == MODE_STEP ? C::smem_step() : C::smem();
+    const size_t sm = (MODE == MODE_STEP || MODE == MODE_STEP_REC) ? C::smem_step() : C::smem();
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k2_cols_real<NY, NL, MODE, SH>,
@@ -371,6 +379,7 @@ static cudaError_t run_cols(const StepArgs& a, cudaStream_t s) {
 
 template <int NY, int NL>
 static cudaError_t cols_step(const StepArgs& a, cudaStream_t s, int shape) {
+    if (a.rec_phi) return run_cols<NY, NL, MODE_STEP_REC, 0>(a, s);  // recording: the default schedule
     if constexpr (ColCfg<NY>::WIDE) {
         if (shape == 1) return run_cols<NY, NL, MODE_STEP, 1>(a, s);
         if (shape == 2) return run_cols<NY, NL, MODE_STEP, 2>(a, s);

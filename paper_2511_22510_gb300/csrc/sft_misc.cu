@@ -352,4 +352,64 @@ cudaError_t launch_box_width(const float* real, int nx, int ny, int nz, int d, i
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ dynamic observables
+// C_ab and chi_ab of App. C from the time transforms of the recorded series, one
+// thread per (mode a, frequency b), the ensemble sum over replicas in FP64.  The
+// paper's time transform is phi_b = sum_m e^{+2 pi i b m / M} phi_m: our forward
+// transform (e^{-i}) at index (M - b) mod M; omega_b = 2 pi b / T, b signed.
+//   C_ab   = norm sum_s |phi_ab|^2
+//   chi_ab = norm / (2 D_a) sum_s phi_ab conj(-i omega_b phi_ab - K_ab),  K = c_a phi + F
+__global__ void k_dyn_reduce(const DynArgs d) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= d.nmodes * d.M) return;
+    const long long a = i / d.M;
+    const int b = (int)(i % d.M);
+    const int bb = (d.M - b) % d.M;
+    const int sb = b < d.M / 2 ? b : b - d.M;
+    const double w = 2.0 * 3.14159265358979323846 * (double)sb / d.T;
+    const double ca = d.c[a];
+    double cs = 0.0, xr = 0.0, xi = 0.0;
+    for (int r = 0; r < d.R; ++r) {
+        const size_t idx = ((size_t)r * d.nmodes + a) * d.M + bb;
+        const float2 X = d.Phi[idx], Fb = d.Fw[idx];
+        const double x = X.x, y = X.y;
+        const double kx = ca * x + Fb.x, ky = ca * y + Fb.y;  // K = c phi + F
+        const double yr = w * y - kx, yi = -w * x - ky;        // -i omega phi - K
+        cs += x * x + y * y;
+        xr += x * yr + y * yi;  // phi conj(Y)
+        xi += y * yr - x * yi;
+    }
+    d.C[i] = cs * d.norm;
+    const double f = d.D[a] > 0.0 ? d.norm / (2.0 * d.D[a]) : 0.0;
+    d.chi[i] = make_double2(xr * f, xi * f);
+}
+
+cudaError_t launch_dyn_reduce(const DynArgs& d, cudaStream_t s) {
+    const long long n = d.nmodes * d.M;
+    k_dyn_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+// complex transpose through 32 x 32 shared-memory tiles (padded against bank conflicts)
+__global__ void k_transpose_c(const float2* __restrict__ in, float2* __restrict__ out, long long rows, long long cols) {
+    __shared__ float2 tile[32][33];
+    const long long c0 = (long long)blockIdx.x * 32, r0 = (long long)blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const long long r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[i][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const long long c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][i];
+    }
+}
+
+cudaError_t launch_transpose_c(const float2* in, float2* out, long long rows, long long cols, cudaStream_t s) {
+    const long long gx = (cols + 31) / 32, gy = (rows + 31) / 32;
+    if (gx > 0x7fffffffLL || gy > 65535) return cudaErrorInvalidValue;
+    k_transpose_c<<<dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, s>>>(in, out, rows, cols);
+    return cudaGetLastError();
+}
+
 }  // namespace sft
