@@ -69,6 +69,10 @@ typedef enum {
  *                F = -Gamma u DFT[psi^3]                        (Sec. V.A, Delta = 0)
  *   SFT_MODEL_B: p = {Gamma, r, u, T}:  c = -Gamma k^2 (r + k^2), D_a = Gamma T k^2,
  *                F = -Gamma u k^2 DFT[psi^3]                    (Sec. V.A, Delta = 2)
+ *   Model A/B with p[4] != 0: the r phi term is placed in F instead of c (the
+ *                variant of the Sec. V.A footnote, c = -Gamma k^Delta k^2 never
+ *                changes sign): F = -Gamma k^Delta (r phi + u DFT[psi^3]);
+ *                SETD-EM and SETD1 only (SFT_EUNSUPPORTED with SETD2).
  *   SFT_KPZ:     p = {nu, lambda, D}:   c = -nu k^2, D_a = D,
  *                F = (lambda/2) DFT[|grad h|^2]                 (Sec. V.B, noise sqrt(2D) eta)
  *   SFT_CGL:     p = {alpha, beta, eps}: complex field, c = 1 - (1 + i alpha) k^2,

@@ -412,17 +412,24 @@ static double mode_mask(const or_state* st, size_t idx) {
 
 /* Linear operator c, noise strength D and nonlinear prefactor s of mode idx
  * (Sec. V: Model A/B with Gamma, KPZ, CGL; CUSTOM from |a|^2 tables). */
+/* Model A/B with p[4] != 0 place the r phi term in F instead of c (the variant
+ * of the Sec. V.A footnote, so that c does not change sign with k^2). */
+static int r_in_F(const or_state* st) {
+    return (st->cfg.model == OR_MODEL_A || st->cfg.model == OR_MODEL_B) && st->cfg.p[4] != 0.0;
+}
+
 static void mode_operator(const or_state* st, size_t idx, cplx* c, double* D, cplx* s) {
     const double* p = st->cfg.p;
     double k2 = mode_k2(st, idx);
+    const double r = r_in_F(st) ? 0.0 : p[1];
     switch (st->cfg.model) {
-        case OR_MODEL_A: /* p = Gamma, r, u, T */
-            *c = -p[0] * (p[1] + k2);
+        case OR_MODEL_A: /* p = Gamma, r, u, T[, r in F] */
+            *c = -p[0] * (r + k2);
             *D = p[0] * p[3];
             *s = -p[0] * p[2];
             break;
         case OR_MODEL_B:
-            *c = -p[0] * k2 * (p[1] + k2);
+            *c = -p[0] * k2 * (r + k2);
             *D = p[0] * p[3] * k2;
             *s = -p[0] * p[2] * k2;
             break;
@@ -738,6 +745,8 @@ static void nonlinear_term(or_state* st, const cplx* phi, cplx* F) {
         double D;
         mode_operator(st, i, &c, &D, &s);
         F[i] = mode_mask(st, i) * s * q[i];
+        if (r_in_F(st)) /* the linear term -Gamma r k^Delta phi, no dealiasing needed */
+            F[i] += -st->cfg.p[0] * st->cfg.p[1] * (st->cfg.model == OR_MODEL_B ? mode_k2(st, i) : 1.0) * phi[i];
     }
 }
 

@@ -618,6 +618,8 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
     if (cfg->model < SFT_MODEL_A || cfg->model > SFT_CUSTOM) return why = "unknown model", SFT_EINVAL;
     if (cfg->scheme < SFT_SETD_EM || cfg->scheme > SFT_SETD2) return why = "unknown scheme", SFT_EINVAL;
     if (cfg->precision != 0) return why = "only FP32 precision (0) is built", SFT_EUNSUPPORTED;
+    if ((cfg->model == SFT_MODEL_A || cfg->model == SFT_MODEL_B) && cfg->p[4] != 0.0 && cfg->scheme == SFT_SETD2)
+        return why = "r placed in F (p[4] != 0) is built for SETD-EM and SETD1", SFT_EUNSUPPORTED;
     if (cfg->dealias != 0 && cfg->dealias != 1) return why = "dealias must be 0 or 1", SFT_EINVAL;
     int cplx = 0, nlk = 0;
     model_kind(cfg, &cplx, &nlk);

@@ -87,9 +87,13 @@ __global__ void k_build_table(const TableArgs t) {
     double2 c = make_double2(0.0, 0.0);
     double D = 0.0;
     double2 s = make_double2(1.0, 0.0);  // nonlinear prefactor folded into A, B (SFT_CUSTOM only)
+    // Model A/B with p[4] != 0: the r phi term is part of F (explicit), not of c; for SETD-EM and
+    // SETD1 it folds into f1 below: f1 phi + A (F_nl + s_r phi) = (f1 + A s_r) phi + A F_nl
+    const bool rf = (t.model == 0 || t.model == 1) && p[4] != 0.0;
+    const double rr = rf ? 0.0 : p[1];
     switch (t.model) {
-        case 0: c.x = -p[0] * (p[1] + k2); D = p[0] * p[3]; break;
-        case 1: c.x = -p[0] * k2 * (p[1] + k2); D = p[0] * p[3] * k2; break;
+        case 0: c.x = -p[0] * (rr + k2); D = p[0] * p[3]; break;
+        case 1: c.x = -p[0] * k2 * (rr + k2); D = p[0] * p[3] * k2; break;
         case 2: c.x = -p[0] * k2; D = p[2]; break;
         case 3: c.x = 1.0 - k2; c.y = -p[0] * k2; D = p[2]; break;
         default: {  // tables over |a|^2 (general Fourier-space form, Sec. IV)
@@ -122,13 +126,18 @@ __global__ void k_build_table(const TableArgs t) {
             B = make_double2(-h * p2.x, -h * p2.y);
         }
     }
+    double2 f1v = f1;
+    if (rf) {
+        const double sr = -p[0] * p[1] * (t.model == 1 ? k2 : 1.0);
+        f1v = make_double2(f1.x + A.x * sr, f1.y + A.y * sr);
+    }
     A = make_double2(A.x * s.x - A.y * s.y, A.x * s.y + A.y * s.x);
     B = make_double2(B.x * s.x - B.y * s.y, B.x * s.y + B.y * s.x);
     if (t.complex_field) {
-        t.out[2 * q] = make_float4((float)f1.x, (float)f1.y, (float)A.x, (float)A.y);
+        t.out[2 * q] = make_float4((float)f1v.x, (float)f1v.y, (float)A.x, (float)A.y);
         t.out[2 * q + 1] = make_float4((float)B.x, (float)B.y, (float)g.x, (float)g.y);
     } else {
-        t.out[q] = make_float4((float)f1.x, (float)A.x, (float)B.x, (float)g.x);
+        t.out[q] = make_float4((float)f1v.x, (float)A.x, (float)B.x, (float)g.x);
     }
 }
 

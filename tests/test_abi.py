@@ -92,3 +92,10 @@ def test_invalid_custom_models_rejected_before_any_device_call(lib, over):
     with pytest.raises(lib.SftError) as ei:
         lib.sft_create(cfg)
     assert ei.value.status == lib.SFT_EINVAL
+
+
+def test_r_in_F_with_setd2_unsupported(lib):
+    cfg = lib.make_config(2, [64, 64], [1.0, 1.0], 1, 0, [1, -0.5, 1, 0.5, 1.0], 2, 0.01, 1)
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_create(cfg)
+    assert ei.value.status == lib.SFT_EUNSUPPORTED

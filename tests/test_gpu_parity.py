@@ -130,6 +130,9 @@ CASES = [
     ("model_b_64_setd2", W.model_b_1024(n=[64, 64], scheme=2, h=0.025, sigma0=0.3), 100),
     ("model_b_128_setd1_R3", W.model_b_1024(n=[128, 128], replicas=3, sigma0=0.3), 40),
     ("kpz_2d_32", W.kpz_2d(n=[32, 32], replicas=2), 100),
+    ("model_a_64_r_in_F", W.model_a_64(p=[1.0, -0.5, 1.0, 0.5, 1.0], replicas=2, sigma0=0.3), 100),
+    ("model_b_64_r_in_F_em", W.model_b_1024(n=[64, 64], p=[1.0, -1.0, 1.0, 0.1, 1.0], scheme=0, h=0.02,
+                                            sigma0=0.3), 100),
     ("kpz_2d_512", W.kpz_2d(n=[512, 512], replicas=2), 10),
     ("model_a_2048_setd1", W.model_a_64(n=[2048, 2048], replicas=1, sigma0=0.3), 3),
     ("model_b_4096_setd2", W.model_b_1024(n=[4096, 4096], scheme=2, h=0.025, sigma0=0.3), 2),

@@ -525,3 +525,28 @@ def test_adjoint_dot_product_identity(oracle_mod, model):
         lhs = np.sum(lam[r] * tan[r])
         rhs = np.sum(grad[r] * d0[r])
         assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + 1e-300), (lhs, rhs)
+
+
+@pytest.mark.parametrize("model,scheme", [(0, 1), (1, 1), (0, 0), (1, 0)])
+def test_r_in_F_linear_closed_form(oracle_mod, model, scheme):
+    """Model A/B with r placed in F (p[4] = 1, the variant of the Sec. V.A
+    footnote), u = 0 and no noise: each mode follows
+    phi_n = (e^{c0 h} + h phi1(c0 h) s_r)^n phi_0, c0 = -Gamma k^Delta k^2,
+    s_r = -Gamma r k^Delta (the explicit r phi term of F)."""
+    G, r, h, n = 1.3, -0.7, 0.05, 12
+    N, L = 16, 16.0
+    o = oracle_mod.Oracle(2, [N, N], [L / N, L / N], 1, model, [G, r, 0.0, 0.0, 1.0], scheme, h, seed=5)
+    rng = np.random.default_rng(0)
+    f0 = rng.normal(size=(N, N))
+    o.set_field(0, f0)
+    o.step(n)
+    k = 2 * np.pi * np.fft.fftfreq(N, L / N)
+    k2 = k[:, None] ** 2 + k[None, :] ** 2
+    kd = k2 if model == 1 else np.ones_like(k2)
+    c0 = -G * kd * k2
+    z = c0 * h
+    phi1 = np.where(np.abs(z) > 1e-12, np.expm1(z) / np.where(z == 0, 1, z), 1.0)
+    f = np.exp(z) + h * phi1 * (-G * r * kd)
+    want = np.fft.fft2(f0) * f ** n
+    got = o.spectrum(0)
+    assert np.allclose(got, want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
