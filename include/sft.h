@@ -122,6 +122,12 @@ typedef struct {
     const double* noise_D;
     const double* nl_re;
     const double* nl_im;
+    /* Noise (Sec. IV step 2): 0 draws eta_a in Fourier space with the Hermitian
+     * structure of App. B; 1 draws iid N(0,1) per real-space site (Philox
+     * ctr = (site >> 2, step, replica, 3), normal site & 3) and takes
+     * eta_a = DFT[eta]_a / sqrt(N^d): one extra forward transform per step.
+     * 1 is built for 2-D real fields. */
+    int noise_space;
 } sft_config;
 
 /* Observables for sft_observe (App. C; shells j = ceil(|a|), i.e. the shell

@@ -55,7 +55,7 @@ class _Cfg(C.Structure):
         ("noise_D", C.POINTER(C.c_double)), ("nl_re", C.POINTER(C.c_double)),
         ("nl_im", C.POINTER(C.c_double)),
         ("scheme", C.c_int), ("h", C.c_double), ("seed", C.c_uint64),
-        ("dealias", C.c_int), ("replica0", C.c_int),
+        ("dealias", C.c_int), ("replica0", C.c_int), ("noise_space", C.c_int),
     ]
 
 
@@ -194,9 +194,10 @@ class Oracle:
 
     def __init__(self, d, n, dx, replicas, model, p, scheme, h, seed, dealias=1,
                  nl=NL_NONE, complex_field=0, c_re=None, c_im=None, noise_D=None,
-                 nl_re=None, nl_im=None, replica0=0):
+                 nl_re=None, nl_im=None, replica0=0, noise_space=0):
         cfg = _Cfg()
         cfg.replica0 = int(replica0)
+        cfg.noise_space = int(noise_space)
         cfg.d = d
         for i in range(3):
             cfg.n[i] = int(n[i]) if i < d else 1

@@ -337,6 +337,7 @@ typedef struct {
     uint64_t seed;
     int dealias;
     int replica0; /* global index of replica 0: Philox counter word 2 of replica r is replica0 + r */
+    int noise_space; /* 0: Fourier-space draw (App. B); 1: real-space draw, then the DFT (Sec. IV step 2) */
 } or_config;
 
 typedef struct {
@@ -564,8 +565,30 @@ static void draw_noise(const or_state* st, int replica, int64_t step, cplx* eta)
             if (herm_class(st, i) == 2) eta[i] = conj(eta[neg_index(st, i)]);
 }
 
+/* Real-space noise of one replica at one step (the alternative of Sec. IV
+ * step 2): eta(x) iid N(0, 1) per site -- site s = lin3(x) takes normal s & 3 of
+ * Philox tag 3, counter (s / 4, step, replica, 3) -- and eta_a = DFT[eta]_a / sqrt(N).
+ * The DFT of a real field is Hermitian; the self-conjugate modes are real
+ * N(0, 1) and every other mode has E|eta_a|^2 = 1, as in the Fourier draw. */
+static void fft_full(const or_state* st, cplx* a, int sign);
+static void draw_noise_real(const or_state* st, int replica, int64_t step, cplx* eta) {
+    for (size_t s = 0; s < st->ntot; ++s) {
+        float z[4];
+        normals_for_index(st->cfg.seed, (uint32_t)(s >> 2), (uint32_t)step, (uint32_t)(st->cfg.replica0 + replica),
+                          3u, z);
+        eta[s] = (double)z[s & 3];
+    }
+    fft_full(st, eta, -1);
+    const double inv_sqrt_n = 1.0 / sqrt((double)st->ntot);
+    for (size_t i = 0; i < st->ntot; ++i) eta[i] *= inv_sqrt_n;
+    hermitian_fixup(st, eta);
+}
+
 int or_noise(const or_state* st, int replica, int64_t step, double* eta_ri) {
-    draw_noise(st, replica, step, (cplx*)eta_ri);
+    if (st->cfg.noise_space)
+        draw_noise_real(st, replica, step, (cplx*)eta_ri);
+    else
+        draw_noise(st, replica, step, (cplx*)eta_ri);
     return 0;
 }
 
@@ -758,7 +781,10 @@ static void step_replica(or_state* st, int r, int first) {
     cplx* F = st->w3;
     nonlinear_term(st, phi, F);
     cplx* eta = st->w0;
-    draw_noise(st, r, st->step, eta);
+    if (st->cfg.noise_space)
+        draw_noise_real(st, r, st->step, eta);
+    else
+        draw_noise(st, r, st->step, eta);
     for (size_t i = 0; i < nt; ++i) {
         cplx f1, a, b, g;
         mode_coefs(st, i, first, &f1, &a, &b, &g);

@@ -53,7 +53,7 @@ class sft_config(C.Structure):
         ("seed", C.c_uint64), ("dealias", C.c_int), ("precision", C.c_int), ("stream", C.c_void_p),
         ("replica0", C.c_int), ("custom_nl", C.c_int), ("complex_field", C.c_int),
         ("c_re", C.POINTER(C.c_double)), ("c_im", C.POINTER(C.c_double)), ("noise_D", C.POINTER(C.c_double)),
-        ("nl_re", C.POINTER(C.c_double)), ("nl_im", C.POINTER(C.c_double)),
+        ("nl_re", C.POINTER(C.c_double)), ("nl_im", C.POINTER(C.c_double)), ("noise_space", C.c_int),
     ]
 
 
@@ -120,7 +120,7 @@ def _check(ctx, status: int):
 # ---------------------------------------------------------------- thin wrappers
 def make_config(d: int, n: Sequence[int], dx: Sequence[float], replicas: int, model: int, p: Sequence[float],
                 scheme: int, h: float, seed: int, dealias: int = 1, stream: Optional[int] = None,
-                replica0: int = 0, custom: Optional[dict] = None) -> sft_config:
+                replica0: int = 0, custom: Optional[dict] = None, noise_space: int = 0) -> sft_config:
     """custom (SFT_CUSTOM): {"nl": SFT_NL_*, "complex_field": 0/1, "c": c(|a|^2), "D": D(|a|^2),
     "s": s(|a|^2) or None}, arrays over q = 0 .. sum_i (n_i/2)^2 (complex c or s for complex fields)."""
     cfg = sft_config()
@@ -139,6 +139,7 @@ def make_config(d: int, n: Sequence[int], dx: Sequence[float], replicas: int, mo
     cfg.precision = 0
     cfg.stream = stream
     cfg.replica0 = replica0
+    cfg.noise_space = int(noise_space)
     if custom is not None:
         keep = []
 
@@ -397,8 +398,9 @@ class Stepper:
     """
 
     def __init__(self, d, n, dx, replicas, model, p, scheme, h, seed, dealias=1, stream=None, replica0=0,
-                 custom=None):
-        self.cfg = make_config(d, n, dx, replicas, model, p, scheme, h, seed, dealias, stream, replica0, custom)
+                 custom=None, noise_space=0):
+        self.cfg = make_config(d, n, dx, replicas, model, p, scheme, h, seed, dealias, stream, replica0, custom,
+                               noise_space)
         self.ctx = sft_create(self.cfg)
         self.d, self.R = d, replicas
         self.n = [int(n[i]) for i in range(d)]

@@ -80,6 +80,8 @@ struct sft_ctx {
     // recording for the dynamic observables
     float2 *rec_phi = nullptr, *rec_F = nullptr;
     long long rec_start = 0;
+    // real-space noise: the transformed draw of the current step (R x nmodes)
+    float2* noise_spec = nullptr;
     int rec_every = 1, rec_M = 0;
     // batch context: members advanced together (1-D lattices of uneven sizes in one persistent launch)
     bool is_batch = false;
@@ -202,7 +204,7 @@ static cudaError_t launch_second(const sft_ctx* ctx, const StepArgs& a, int mode
 }
 
 static cudaError_t launch_cols_step(const sft_ctx* ctx, const StepArgs& a) {
-    if (ctx->pipe_cols && !a.rec_phi) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
+    if (ctx->pipe_cols && !a.rec_phi && !a.noise_in) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
     if (ctx->d == 2 && !ctx->cplx) return launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream, ctx->col_shape);
     return launch_second(ctx, a, MODE_STEP);
 }
@@ -376,6 +378,17 @@ static sft_status enqueue_step(sft_ctx* ctx, int k) {
         }
         CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
         return SFT_OK;
+    }
+    if (ctx->noise_spec) {
+        // real-space noise (Sec. IV step 2): iid N(0, 1) per site into the real-space buffer, its
+        // forward transform into noise_spec (Q as scratch, overwritten by the row pass below);
+        // the column pass reads eta_a = DFT[eta]_a / sqrt(N^d)
+        CK(launch_noise_real(ctx->real, ctx->sites, ctx->R, ctx->rep0, ctx->cfg.seed, ctx->dstep, k, ctx->stream));
+        sft_status s = forward_from_buffer(ctx, 0, ctx->R, ctx->noise_spec);
+        if (s != SFT_OK) return s;
+        ctx->launches -= 2;  // counted per step in launches_per_step
+        a.noise_in = ctx->noise_spec;
+        a.noise_scale = (float)(1.0 / std::sqrt((double)ctx->sites));
     }
     a.pin = ctx->P;
     a.pyin = ctx->Py;
@@ -623,6 +636,9 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
     if (cfg->dealias != 0 && cfg->dealias != 1) return why = "dealias must be 0 or 1", SFT_EINVAL;
     int cplx = 0, nlk = 0;
     model_kind(cfg, &cplx, &nlk);
+    if (cfg->noise_space != 0 && cfg->noise_space != 1) return why = "noise_space must be 0 or 1", SFT_EINVAL;
+    if (cfg->noise_space == 1 && (cfg->d != 2 || cplx))
+        return why = "real-space noise is built for 2-D real fields", SFT_EUNSUPPORTED;
     if (cfg->model == SFT_CUSTOM) {
         const int nl = cfg->custom_nl;
         if (nl < SFT_NL_NONE || nl > SFT_NL_CGL) return why = "unknown custom nonlinearity", SFT_EINVAL;
@@ -701,6 +717,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     if (ok && ctx->d >= 2) ok = dalloc((void**)&ctx->P, ms);
     if (ok && ctx->d >= 2 && ctx->nl == NL_GRAD2) ok = dalloc((void**)&ctx->Py, ms);
     if (ok && cfg->scheme == SFT_SETD2) ok = dalloc((void**)&ctx->fprev, ms);
+    if (ok && cfg->noise_space == 1) ok = dalloc((void**)&ctx->noise_spec, ms);
     if (ok) {
         if (ctx->cplx)
             ok = dalloc((void**)&ctx->cfield, rs);
@@ -808,6 +825,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
         }
     }
     ctx->launches_per_step = ctx->d == 1 ? 1 : 2;
+    if (cfg->noise_space == 1) ctx->launches_per_step += 3;  // draw + forward transform of the noise
     {
         // column-pass variant: chosen by the plan autotuner unless SFT_COLUMN_PASS forces the
         // persistent bulk-copy pipelined kernel ("pipelined", where it is built) or the
@@ -833,6 +851,10 @@ sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
         if (vs != SFT_OK) {
             fprintf(stderr, "sft_create_batch: member %d: %s\n", i, why.c_str());
             return vs;
+        }
+        if (cfgs[i].noise_space != 0) {
+            fprintf(stderr, "sft_create_batch: member %d: real-space noise is built for single contexts\n", i);
+            return SFT_EUNSUPPORTED;
         }
         if (cfgs[i].model != cfgs[0].model || cfgs[i].scheme != cfgs[0].scheme ||
             (cfgs[0].model == SFT_CUSTOM &&
@@ -1061,6 +1083,7 @@ sft_status sft_dyn_start(sft_ctx* ctx, int M, int every) {
     if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     if (ctx->d != 2 || ctx->cplx)
         return fail(ctx, SFT_EUNSUPPORTED, "dynamic observables are built for 2-D real fields");
+    if (ctx->noise_spec) return fail(ctx, SFT_EUNSUPPORTED, "dynamic observables are built for the Fourier-space noise");
     if (M < 16 || M > 16384 || (M & (M - 1)) || every < 1)
         return fail(ctx, SFT_EINVAL, "M must be a power of two in [16, 16384] and every >= 1");
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1744,6 +1767,7 @@ static uint64_t config_hash(const sft_config& c, uint64_t tables) {
     mix(&c.precision, sizeof c.precision);
     mix(&c.custom_nl, sizeof c.custom_nl);
     mix(&c.complex_field, sizeof c.complex_field);
+    if (c.noise_space) mix(&c.noise_space, sizeof c.noise_space);
     return h;
 }
 
@@ -1947,7 +1971,7 @@ void sft_destroy(sft_ctx* ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     void* bufs[] = {ctx->phi,   ctx->fprev,  ctx->P,      ctx->Q,      ctx->Py,     ctx->snap, ctx->real,
                     ctx->cfield, ctx->tab,   ctx->dstep,  ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev,
-                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ};
+                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

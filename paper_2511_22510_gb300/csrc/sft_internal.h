@@ -15,7 +15,8 @@ enum KernelMode {
     MODE_ADJ = 4,
     MODE_PRIME = 5,
     MODE_ADJ_PRIME = 6,
-    MODE_STEP_REC = 7  // the step, also recording the state and the nonlinear force (dynamic observables)
+    MODE_STEP_REC = 7,  // the step, also recording the state and the nonlinear force (dynamic observables)
+    MODE_STEP_RSN = 8   // the step with the noise read from a transformed real-space draw
 };
 
 // Everything a step kernel needs, passed by value.
@@ -72,6 +73,8 @@ struct StepArgs {
     float2* rec_F;
     long long rec_start, rec_n;
     int rec_every, rec_M;
+    const float2* noise_in;  // real-space noise: DFT of the draw (state layout); eta = noise_scale * noise_in
+    float noise_scale;
 };
 
 // launchers (return cudaGetLastError of the launch); each picks the template
@@ -141,6 +144,10 @@ cudaError_t launch_init_random(float* real_out, float2* cplx_out, long long site
 // unit-variance Fourier noise of one step for every stored mode (diagnostics)
 cudaError_t launch_draw_noise(int nx, int ny, int nz, int hx, int cplx, int R, int rep0, uint64_t seed,
                               long long step, float2* out, cudaStream_t s);
+// real-space noise of one step: iid N(0,1) per site (Philox tag 3) into real_out;
+// the step is *step_base + k (graph replays) or, with step_base NULL, k
+cudaError_t launch_noise_real(float* real_out, long long sites, int R, int rep0, uint64_t seed,
+                              const long long* step_base, long long k, cudaStream_t s);
 // step counter advance (one thread)
 cudaError_t launch_advance(long long* step_base, int by, cudaStream_t s);
 

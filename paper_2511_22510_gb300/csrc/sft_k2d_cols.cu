@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
 #pragma unroll
             for (int e = 0; e < E; ++e) a.pout[colbase + t + T * e] = v[e];
         }
-    } else if constexpr (MODE == MODE_STEP || MODE == MODE_STEP_REC) {
+    } else if constexpr (MODE == MODE_STEP || MODE == MODE_STEP_REC || MODE == MODE_STEP_RSN) {
         if (!valid && T >= 32) return;
         const long long step = current_step(a);
         const bool first = (a.scheme == 2) && (step == *a.first_step);
@@ -199,10 +199,15 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
         }
         // the noise depends on no loaded value: drawn while the loads of Q are in flight
         float2 out[E];
+        if constexpr (MODE == MODE_STEP_RSN) {
 #pragma unroll
-        for (int e = 0; e < E; e += 2)
-            team_normal_pair<T>(a.seed, (uint64_t)cc * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
-                                out[e + 1]);
+            for (int e = 0; e < E; ++e) out[e] = cscale(a.noise_in[colbase + t + T * e], a.noise_scale);
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; e += 2)
+                team_normal_pair<T>(a.seed, (uint64_t)cc * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
+                                    out[e + 1]);
+        }
         if (has_f || T < 32) fft_line<NY, false, EM>(v, xb, t, tw);
         cp_async_wait_all();
         team_sync<T>();
@@ -220,7 +225,9 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
             if (a.scheme == 2 && has_f) Fp = sfp[ay];
             const bool selfc = plane && (ay == 0 || 2 * ay == NY);
             // partners on the self-conjugate planes are overwritten by the fix-up below
-            out[e] = setd_update<false>(co, ph, F, Fp, eta_of(out[e], selfc));
+            const float2 eta = (MODE == MODE_STEP_RSN) ? make_float2(out[e].x, selfc ? 0.f : out[e].y)
+                                                        : eta_of(out[e], selfc);
+            out[e] = setd_update<false>(co, ph, F, Fp, eta);
             if (a.scheme == 2 && has_f && valid) a.fprev[colbase + ay] = F;
             if constexpr (MODE == MODE_STEP_REC) {
                 const long long kk = step - a.rec_start;
@@ -362,7 +369,7 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
 template <int NY, int NL, int MODE, int SH = 0>
 static cudaError_t run_cols(const StepArgs& a, cudaStream_t s) {
     using C = ColCfg<NY, SH>;
-    const size_t sm = (MODE == MODE_STEP || MODE == MODE_STEP_REC) ? C::smem_step() : C::smem();
+    const size_t sm = (MODE == MODE_STEP || MODE == MODE_STEP_REC || MODE == MODE_STEP_RSN) ? C::smem_step() : C::smem();
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k2_cols_real<NY, NL, MODE, SH>,
@@ -380,6 +387,7 @@ static cudaError_t run_cols(const StepArgs& a, cudaStream_t s) {
 template <int NY, int NL>
 static cudaError_t cols_step(const StepArgs& a, cudaStream_t s, int shape) {
     if (a.rec_phi) return run_cols<NY, NL, MODE_STEP_REC, 0>(a, s);  // recording: the default schedule
+    if (a.noise_in) return run_cols<NY, NL, MODE_STEP_RSN, 0>(a, s);  // real-space noise: the default schedule
     if constexpr (ColCfg<NY>::WIDE) {
         if (shape == 1) return run_cols<NY, NL, MODE_STEP, 1>(a, s);
         if (shape == 2) return run_cols<NY, NL, MODE_STEP, 2>(a, s);

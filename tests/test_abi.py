@@ -99,3 +99,17 @@ def test_r_in_F_with_setd2_unsupported(lib):
     with pytest.raises(lib.SftError) as ei:
         lib.sft_create(cfg)
     assert ei.value.status == lib.SFT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("d,model,space,status", [
+    (2, 0, 2, "SFT_EINVAL"),          # no such noise space
+    (1, 0, 1, "SFT_EUNSUPPORTED"),    # real-space noise is built for 2-D real fields
+    (3, 0, 1, "SFT_EUNSUPPORTED"),
+    (2, 3, 1, "SFT_EUNSUPPORTED"),    # complex field (CGL)
+])
+def test_real_space_noise_limits(lib, d, model, space, status):
+    n = [16] * d
+    cfg = lib.make_config(d, n, [1.0] * d, 1, model, [1, -0.5, 1, 0.5], 1, 0.01, 1, noise_space=space)
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_create(cfg)
+    assert ei.value.status == getattr(lib, status)

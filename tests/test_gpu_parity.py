@@ -360,3 +360,54 @@ def test_replica_offset_shards_one_ensemble(sft, oracle_mod):
         o.step(20)
         for r in range(2):
             assert rel_l2(got[r], o.field(r)) <= 1e-5
+
+
+# ------------------------------------------------------------------ real-space noise
+RSN_CASES = [
+    ("model_a_64_setd1_R2", W.model_a_64(replicas=2, sigma0=0.3), 100),
+    ("model_b_64_setd2", W.model_b_1024(n=[64, 64], scheme=2, h=0.025, sigma0=0.3), 100),
+    ("kpz_2d_32_em", W.kpz_2d(n=[32, 32], replicas=2, scheme=0), 100),
+    ("model_b_128_setd1_R3", W.model_b_1024(n=[128, 128], replicas=3, sigma0=0.3), 40),
+    ("model_b_1024_setd1_R2", W.model_b_1024(replicas=2, h=0.05), 3),
+]
+
+
+@pytest.mark.parametrize("name,w,nsteps", RSN_CASES, ids=[c[0] for c in RSN_CASES])
+def test_real_space_noise_step_parity(sft, oracle_mod, name, w, nsteps):
+    """Sec. IV step 2, real-space draw: the per-site Philox draw, its forward
+    transform and the step that reads eta_a = DFT[eta]_a / sqrt(N^d) against the
+    oracle (FP64 DFT of the same normals); replica0 = 3 checks the replica word."""
+    R = w.replicas
+    f32 = W.initial_fields(w, replicas=R).astype(np.float32)
+    g = sft.Stepper(w.d, w.n, w.dx, R, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias, replica0=3,
+                    noise_space=1)
+    g.set_field(f32)
+    o = oracle_mod.Oracle(w.d, w.n, w.dx, R, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
+                          replica0=3, noise_space=1)
+    for r in range(R):
+        o.set_field(r, f32[r].astype(np.float64))
+    g.step(nsteps)
+    o.step(nsteps)
+    got = g.field()
+    for r in range(R):
+        assert rel_l2(got[r], o.field(r)) <= 1e-5, (name, r)
+    g.close()
+
+
+def test_real_space_noise_graph_and_plain_bit_identical(sft):
+    w = W.model_a_64(n=[64, 64], replicas=2, sigma0=0.3)
+    mk = lambda: sft.Stepper(w.d, w.n, w.dx, 2, w.model, w.p, w.scheme, w.h, w.seed, noise_space=1)
+    a, b = mk(), mk()
+    f = W.initial_fields(w).astype(np.float32)
+    a.set_field(f)
+    b.set_field(f)
+    a.step(53)
+    b.step_plain(53)
+    assert np.array_equal(a.spectrum().view(np.uint64), b.spectrum().view(np.uint64))
+    # the two noises are different streams: a Fourier-noise run ends elsewhere
+    c = sft.Stepper(w.d, w.n, w.dx, 2, w.model, w.p, w.scheme, w.h, w.seed)
+    c.set_field(f)
+    c.step(53)
+    assert rel_l2(c.field(), a.field()) > 1e-2
+    for s in (a, b, c):
+        s.close()

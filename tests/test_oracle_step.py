@@ -80,6 +80,54 @@ def test_noise_streams_distinct(oracle_mod):
     assert np.abs(a - b).max() > 0.1 and np.abs(a - c).max() > 0.1
 
 
+def test_real_space_noise_is_the_transformed_site_draw(oracle_mod):
+    """Sec. IV step 2, real-space alternative: eta(x) iid N(0, 1) per site and
+    eta_a = DFT[eta]_a / sqrt(N^d).  The inverse DFT (numpy) of the oracle's
+    eta_a times sqrt(N^d) gives back, site by site, normal s & 3 of the Philox
+    block (s / 4, step, replica, 3) (Philox pinned by its known answers); the
+    spectrum is Hermitian with real self-conjugate modes."""
+    nx, ny, R = 16, 8, 2
+    w = W.model_a_64(n=[nx, nx])
+    o = oracle_mod.Oracle(2, [nx, ny], [1.0, 1.0], R, w.model, w.p, w.scheme, w.h, 99, noise_space=1,
+                          replica0=5)
+    for r, step in ((0, 0), (1, 7)):
+        eta = o.noise(r, step)  # (ny, nx) full spectrum
+        site = np.fft.ifft2(eta) * math.sqrt(nx * ny)
+        assert np.abs(site.imag).max() < 1e-13
+        want = np.array([oracle_mod.normals4(99, s >> 2, step, 5 + r, 3)[s & 3] for s in range(nx * ny)],
+                        dtype=np.float64).reshape(ny, nx)
+        assert np.abs(site.real - want).max() < 1e-12
+        neg = np.conj(np.roll(eta[::-1, ::-1], 1, axis=(0, 1)))
+        assert np.array_equal(eta, neg)
+        for iy in (0, ny // 2):
+            for ix in (0, nx // 2):
+                assert eta[iy, ix].imag == 0.0
+
+
+def test_gaussian_model_a_structure_factor_real_space_noise(oracle_mod):
+    """Sec. IV step 2 / Sec. V.A: with the real-space draw the linear theory
+    C_ET(k) = T / (r + k^2) holds as with the Fourier draw (the two noises have
+    the same covariance); shell averages within 5 sigma."""
+    N, R = 16, 64
+    w = W.model_a_64(n=[N, N], dx=[0.5, 0.5], p=[1.0, 1.0, 0.0, 0.6], h=0.05)
+    o = make_oracle(oracle_mod, w, replicas=R, noise_space=1)
+    o.step(200)
+    acc = None
+    S = 20
+    for _ in range(S):
+        o.step(20)
+        v, _ = o.shells(0)
+        acc = v if acc is None else acc + v
+    v = acc / S
+    dk = 2 * np.pi / (N * 0.5)
+    KY, KX = spectral_k(w.shape, 0.5)
+    kk = np.sqrt(KX ** 2 + KY ** 2)
+    for j in range(1, 6):
+        sel = (kk > (j - 1) * dk + 1e-9) & (kk <= j * dk + 1e-9)
+        ref = np.mean(0.6 / (1.0 + kk[sel] ** 2))
+        assert abs(v[j] - ref) < 5 * ref / math.sqrt(sel.sum() * R * S / 4), (j, v[j], ref)
+
+
 # ------------------------------------------------------------ linear closed forms
 @pytest.mark.parametrize("scheme", [0, 1, 2])
 @pytest.mark.parametrize("model", [0, 1])
