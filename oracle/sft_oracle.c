@@ -400,15 +400,29 @@ static double mode_k2(const or_state* st, size_t idx) {
     double kx = axis_k(st, 0, ix), ky = axis_k(st, 1, iy), kz = axis_k(st, 2, iz);
     return kx * kx + ky * ky + kz * kz;
 }
+/* Dealiasing mask M_a (Sec. IV step 1): dealias = 1 truncates by the 2/3 rule;
+ * dealias = 2 (phase-shift dealiasing) keeps every mode but the Nyquist ones,
+ * whose shifted copies are not the spectrum of a real field. */
 static double mode_mask(const or_state* st, size_t idx) {
     if (!st->cfg.dealias) return 1.0;
     int i3[3];
     idx3(st, idx, &i3[0], &i3[1], &i3[2]);
     for (int ax = 0; ax < 3; ++ax) {
         int a = signed_index(i3[ax], st->n[ax]);
-        if (3 * abs(a) >= st->n[ax] && st->n[ax] > 1) return 0.0;
+        if (st->n[ax] > 1 && (st->cfg.dealias == 2 ? 2 * abs(a) == st->n[ax] : 3 * abs(a) >= st->n[ax])) return 0.0;
     }
     return 1.0;
+}
+
+/* Phase of a shift of the grid by half a cell along the axes in the bit set
+ * sigma: e^{+i pi sum_{ax in sigma} a_ax / n_ax}, a_ax the signed index. */
+static cplx half_cell_phase(const or_state* st, size_t idx, int sigma) {
+    int i3[3];
+    idx3(st, idx, &i3[0], &i3[1], &i3[2]);
+    double ang = 0.0;
+    for (int ax = 0; ax < 3; ++ax)
+        if (sigma & (1 << ax)) ang += OR_PI * (double)signed_index(i3[ax], st->n[ax]) / (double)st->n[ax];
+    return cos(ang) + I * sin(ang);
 }
 
 /* Linear operator c, noise strength D and nonlinear prefactor s of mode idx
@@ -599,7 +613,9 @@ static size_t tab_len(const or_config* cfg) {
 }
 
 or_state* or_create(const or_config* cfg) {
-    if (cfg->d < 1 || cfg->d > 3 || cfg->replicas < 1 || !(cfg->h > 0)) return NULL;
+    if (cfg->d < 1 || cfg->d > 3 || cfg->replicas < 1 || !(cfg->h > 0) || cfg->dealias < 0 || cfg->dealias > 2 ||
+        cfg->noise_space < 0 || cfg->noise_space > 1)
+        return NULL;
     or_state* st = (or_state*)calloc(1, sizeof(or_state));
     st->cfg = *cfg;
     st->n[0] = st->n[1] = st->n[2] = 1;
@@ -726,15 +742,13 @@ int or_init_random(or_state* st, double sigma) {
     return 0;
 }
 
-/* Real-space nonlinearity q of the masked state; psi/grad kept in w-buffers.
- * P = M phi, psi = IDFT(P) (Sec. IV step 1, Sec. V model terms). */
-static void nonlinear_term(or_state* st, const cplx* phi, cplx* F) {
+/* DFT of the real-space nonlinearity q of the masked state, evaluated on the
+ * grid shifted by half a cell along the axes in sigma (sigma = 0: the plain
+ * grid): P = M phi e^{i pi sigma.a/N}, psi = IDFT(P), Q_a = DFT[q(psi)]_a
+ * e^{-i pi sigma.a/N} (Sec. IV step 1, Sec. V model terms). */
+static void nonlinear_dft(or_state* st, const cplx* phi, int sigma, cplx* q) {
     size_t nt = st->ntot;
-    cplx *q = st->w1, *g = st->w2;
-    if (st->nl == OR_NL_NONE) {
-        memset(F, 0, nt * sizeof(cplx));
-        return;
-    }
+    cplx* g = st->w2;
     if (st->nl == OR_NL_GRAD2) {
         memset(q, 0, nt * sizeof(cplx));
         for (int ax = 0; ax < st->cfg.d; ++ax) {
@@ -742,6 +756,7 @@ static void nonlinear_term(or_state* st, const cplx* phi, cplx* F) {
                 int i3[3];
                 idx3(st, i, &i3[0], &i3[1], &i3[2]);
                 g[i] = I * axis_k_odd(st, ax, i3[ax]) * mode_mask(st, i) * phi[i];
+                if (sigma) g[i] *= half_cell_phase(st, i, sigma);
             }
             fft_full(st, g, +1);
             for (size_t i = 0; i < nt; ++i) {
@@ -750,7 +765,7 @@ static void nonlinear_term(or_state* st, const cplx* phi, cplx* F) {
             }
         }
     } else {
-        for (size_t i = 0; i < nt; ++i) q[i] = mode_mask(st, i) * phi[i];
+        for (size_t i = 0; i < nt; ++i) q[i] = mode_mask(st, i) * phi[i] * (sigma ? half_cell_phase(st, i, sigma) : 1.0);
         fft_full(st, q, +1);
         for (size_t i = 0; i < nt; ++i) {
             cplx v = q[i] / (double)nt;
@@ -763,6 +778,34 @@ static void nonlinear_term(or_state* st, const cplx* phi, cplx* F) {
         }
     }
     fft_full(st, q, -1);
+    if (sigma)
+        for (size_t i = 0; i < nt; ++i) q[i] *= conj(half_cell_phase(st, i, sigma));
+}
+
+/* F_a = M_a s_a Q_a, with Q the plain DFT of q (dealias 0 or 1) or, for
+ * phase-shift dealiasing (dealias = 2), the mean of Q over the 2^d grids
+ * shifted by half a cell along every subset of the axes: on a grid shifted
+ * along ax, the alias of output mode a from input modes with
+ * a_1 + a_2 + a_3 = a + j N carries the factor (-1)^{j_ax}, so the mean keeps
+ * only the terms whose j has every component even (phase shifts after
+ * Rogallo, cited in Sec. IV step 1). */
+static void nonlinear_term(or_state* st, const cplx* phi, cplx* F) {
+    size_t nt = st->ntot;
+    cplx* q = st->w1;
+    if (st->nl == OR_NL_NONE) {
+        memset(q, 0, nt * sizeof(cplx));
+    } else if (st->cfg.dealias == 2) {
+        cplx* acc = st->w0;  /* free here: the noise is drawn after the force */
+        memset(acc, 0, nt * sizeof(cplx));
+        const int nshift = 1 << st->cfg.d;
+        for (int sigma = 0; sigma < nshift; ++sigma) {
+            nonlinear_dft(st, phi, sigma, q);
+            for (size_t i = 0; i < nt; ++i) acc[i] += q[i] / (double)nshift;
+        }
+        memcpy(q, acc, nt * sizeof(cplx));
+    } else {
+        nonlinear_dft(st, phi, 0, q);
+    }
     for (size_t i = 0; i < nt; ++i) {
         cplx c, s;
         double D;
@@ -922,6 +965,7 @@ static void tangent_term(or_state* st, const cplx* phi, const cplx* dphi, cplx* 
 
 /* dphi0: real-space tangent seed (replicas x field), or NULL to continue. */
 int or_tangent_step(or_state* st, const double* dphi0, int64_t nsteps, double* dphi_out) {
+    if (st->cfg.dealias == 2) return -1; /* linearised about the truncated nonlinear term only */
     size_t nt = st->ntot;
     int R = st->cfg.replicas;
     if (dphi0) {
@@ -1012,7 +1056,7 @@ int or_observe_response(const or_state* st, double* out) {
 /* so its transpose is -i k.                                                  */
 /* ------------------------------------------------------------------------- */
 int or_adjoint(or_state* st, const double* lam_in, int64_t nsteps, double* grad_out) {
-    if (st->cplx_field || st->cfg.scheme == OR_SETD2) return -1;
+    if (st->cplx_field || st->cfg.scheme == OR_SETD2 || st->cfg.dealias == 2) return -1;
     size_t nt = st->ntot;
     int R = st->cfg.replicas;
     cplx* traj = (cplx*)malloc(nt * (size_t)R * (size_t)(nsteps > 0 ? nsteps : 1) * sizeof(cplx));
