@@ -52,7 +52,8 @@ def parse_args():
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--workload", default="model_b_1024",
                     choices=["model_b_1024", "model_a_64", "kpz_ensemble", "cgl_2048", "model_a_128_3d",
-                             "model_a_128_3d_tangent", "sde0d", "dynamics"],
+                             "model_a_128_3d_tangent", "sde0d", "dynamics", "model_b_1024_phase_shift",
+                             "model_b_1024_real_space_noise"],
                     help="model_b_1024 is the headline; the others print their own line for the other workloads")
     return ap.parse_args()
 
@@ -491,13 +492,20 @@ def run_other(args):
                      "plain": {"value": plain, "unit": UNIT, "batched_speedup": value / plain,
                                "form": "each member's own kernels launched from the host, no graph"}})
     else:
+        noise_space = 0
         if args.workload == "model_a_64":
             w = W.model_a_64(replicas=1024)
+        elif args.workload == "model_b_1024_phase_shift":
+            w = W.model_b_1024(replicas=64, dealias=2)
+        elif args.workload == "model_b_1024_real_space_noise":
+            w = W.model_b_1024(replicas=64)
+            noise_space = 1
         elif args.workload == "cgl_2048":
             w = W.cgl_2048(replicas=4)
         else:
             w = W.model_a_128_3d(replicas=32)
-        g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, stream=stream.cuda_stream)
+        g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
+                        stream=stream.cuda_stream, noise_space=noise_space)
         g.init_random(max(w.sigma0, 0.1))
         if args.workload == "model_a_128_3d_tangent":
             seed = torch.zeros((w.replicas,) + w.shape, dtype=torch.float32, device="cuda")
@@ -512,7 +520,8 @@ def run_other(args):
         value = w.sites * w.replicas * K / (ms * 1e-3) / 1e9
         prof = sft.sft_profile(g.ctx, 10)
         g.close()
-        p1 = sft.Stepper(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, stream=stream.cuda_stream)
+        p1 = sft.Stepper(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
+                         stream=stream.cuda_stream, noise_space=noise_space)
         p1.init_random(0.1)
         p1.step_plain(2)
         msp = timed(lambda: p1.step_plain(K))
@@ -520,7 +529,9 @@ def run_other(args):
         p1.close()
         line.update({"value": value, "ms_per_step": ms / K,
                      "config": {"workload": args.workload, "lattice": "x".join(str(n) for n in w.n),
-                                "replicas": w.replicas, "scheme": scheme_name(w.scheme), "h": w.h},
+                                "replicas": w.replicas, "scheme": scheme_name(w.scheme), "h": w.h,
+                                "dealias": {0: "none", 1: "2/3 truncation", 2: "phase shifts"}[w.dealias],
+                                "noise": "real space + FFT" if noise_space else "Fourier space"},
                      "kernels_ms": list(map(float, prof)),
                      "plain": {"value": plain, "unit": UNIT, "replicas": 1, "graph": False,
                                "batched_speedup": value / plain}})

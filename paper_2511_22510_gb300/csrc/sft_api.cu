@@ -155,7 +155,10 @@ static StepArgs base_args(const sft_ctx* c) {
     a.rep0 = c->rep0;
     a.scale = (float)(1.0 / (double)c->sites);
     a.dk = (float)(2.0 * M_PI / (c->nx * c->cfg.dx[0]));
-    a.dealias = c->cfg.dealias;
+    a.dealias = c->cfg.dealias == 1;
+    a.pshift = c->cfg.dealias == 2;
+    a.tw_ps = a.pshift ? c->tw.get(2 * c->nx) : nullptr;
+    a.ps_off = (long long)c->R * c->nmodes;
     a.model = c->cfg.model;
     a.scheme = c->cfg.scheme;
     const double* p = c->cfg.p;
@@ -204,7 +207,7 @@ static cudaError_t launch_second(const sft_ctx* ctx, const StepArgs& a, int mode
 }
 
 static cudaError_t launch_cols_step(const sft_ctx* ctx, const StepArgs& a) {
-    if (ctx->pipe_cols && !a.rec_phi && !a.noise_in) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
+    if (ctx->pipe_cols && !a.rec_phi && !a.noise_in && !a.pshift) return launch_k2_cols_pipe(a, ctx->nl, ctx->stream);
     if (ctx->d == 2 && !ctx->cplx) return launch_k2_cols(a, MODE_STEP, ctx->nl, ctx->stream, ctx->col_shape);
     return launch_second(ctx, a, MODE_STEP);
 }
@@ -364,21 +367,10 @@ static sft_status enqueue_batch_step(sft_ctx* ctx, int k) {
     return SFT_OK;
 }
 
-// Enqueue the kernels of one step (k_in_chunk = k).
-static sft_status enqueue_step(sft_ctx* ctx, int k) {
-    if (ctx->is_batch) return enqueue_batch_step(ctx, k);
-    StepArgs a = base_args(ctx);
-    a.k_in_chunk = k;
-    if (ctx->d == 1) {
-        if (ctx->cplx) {
-            a.tw_a = ctx->tw.get(ctx->nx);
-        } else {
-            a.tw_a = ctx->tw.get(ctx->nx / 2);
-            a.tw_b = ctx->tw.get(ctx->nx);
-        }
-        CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
-        return SFT_OK;
-    }
+// The kernels of a 2-D step before its column pass (k_in_chunk = k): the
+// real-space noise and its transform where configured, and the row pass; a is
+// left set up for the column pass.
+static sft_status enqueue_front(sft_ctx* ctx, StepArgs& a, int k) {
     if (ctx->noise_spec) {
         // real-space noise (Sec. IV step 2): iid N(0, 1) per site into the real-space buffer, its
         // forward transform into noise_spec (Q as scratch, overwritten by the row pass below);
@@ -395,11 +387,39 @@ static sft_status enqueue_step(sft_ctx* ctx, int k) {
     a.qout = ctx->Q;
     a.tw_a = ctx->tw.get(ctx->nx / 2);
     a.tw_b = ctx->tw.get(ctx->nx);
-    CK(launch_rows(ctx, a, MODE_STEP));
+    if (a.pshift) {
+        // phase-shift dealiasing: the row pass runs over both copies of P (plain and shifted
+        // along y), 2R rows of blocks, each averaging its two x shifts
+        StepArgs r = a;
+        r.R = 2 * ctx->R;
+        CK(launch_rows(ctx, r, MODE_STEP_PS));
+    } else {
+        CK(launch_rows(ctx, a, MODE_STEP));
+    }
     a.qin = ctx->Q;
     a.pout = ctx->P;
     a.pyout = ctx->Py;
     a.tw_a = ctx->tw.get(ctx->ny);
+    return SFT_OK;
+}
+
+// Enqueue the kernels of one step (k_in_chunk = k).
+static sft_status enqueue_step(sft_ctx* ctx, int k) {
+    if (ctx->is_batch) return enqueue_batch_step(ctx, k);
+    StepArgs a = base_args(ctx);
+    a.k_in_chunk = k;
+    if (ctx->d == 1) {
+        if (ctx->cplx) {
+            a.tw_a = ctx->tw.get(ctx->nx);
+        } else {
+            a.tw_a = ctx->tw.get(ctx->nx / 2);
+            a.tw_b = ctx->tw.get(ctx->nx);
+        }
+        CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
+        return SFT_OK;
+    }
+    sft_status s = enqueue_front(ctx, a, k);
+    if (s != SFT_OK) return s;
     CK(launch_cols_step(ctx, a));
     return SFT_OK;
 }
@@ -467,7 +487,7 @@ static sft_status plan_step(sft_ctx* ctx) {
         return SFT_OK;
     }
     const char* env = getenv("SFT_AUTOTUNE");
-    if ((env && env[0] == '0') || ctx->cplx || ctx->d < 2) return SFT_OK;
+    if ((env && env[0] == '0') || ctx->cplx || ctx->d < 2 || ctx->cfg.dealias == 2) return SFT_OK;
     // SFT_PLAN="row,col,rpb,pipe" fixes the schedule (as sft_set_plan; e.g. to profile the one a timed run chose)
     if (const char* fixed = getenv("SFT_PLAN")) {
         int v[4];
@@ -633,12 +653,16 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
     if (cfg->precision != 0) return why = "only FP32 precision (0) is built", SFT_EUNSUPPORTED;
     if ((cfg->model == SFT_MODEL_A || cfg->model == SFT_MODEL_B) && cfg->p[4] != 0.0 && cfg->scheme == SFT_SETD2)
         return why = "r placed in F (p[4] != 0) is built for SETD-EM and SETD1", SFT_EUNSUPPORTED;
-    if (cfg->dealias != 0 && cfg->dealias != 1) return why = "dealias must be 0 or 1", SFT_EINVAL;
+    if (cfg->dealias < 0 || cfg->dealias > 2)
+        return why = "dealias must be 0 (none), 1 (2/3 truncation) or 2 (phase shifts)", SFT_EINVAL;
     int cplx = 0, nlk = 0;
     model_kind(cfg, &cplx, &nlk);
     if (cfg->noise_space != 0 && cfg->noise_space != 1) return why = "noise_space must be 0 or 1", SFT_EINVAL;
     if (cfg->noise_space == 1 && (cfg->d != 2 || cplx))
         return why = "real-space noise is built for 2-D real fields", SFT_EUNSUPPORTED;
+    if (cfg->dealias == 2 && (cfg->d != 2 || cplx || nlk != NL_CUBIC || cfg->noise_space != 0))
+        return why = "phase-shift dealiasing is built for 2-D real fields with the cubic term and Fourier-space noise",
+               SFT_EUNSUPPORTED;
     if (cfg->model == SFT_CUSTOM) {
         const int nl = cfg->custom_nl;
         if (nl < SFT_NL_NONE || nl > SFT_NL_CGL) return why = "unknown custom nonlinearity", SFT_EINVAL;
@@ -694,7 +718,8 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     for (int c = 0; c < ctx->hx; ++c) {
         // real fields: the first mx x-modes; complex fields: the mx x-modes with 3|a_x| < nx (compact order)
         const int cs = ctx->cplx && 2 * c >= ctx->nx ? ctx->nx - c : c;
-        if (!cfg->dealias || 3 * cs < ctx->nx) ctx->mx = ctx->cplx ? ctx->mx + 1 : c + 1;
+        if (!cfg->dealias || (cfg->dealias == 1 ? 3 * cs < ctx->nx : 2 * cs < ctx->nx))
+            ctx->mx = ctx->cplx ? ctx->mx + 1 : c + 1;
     }
     ctx->sites = (long long)ctx->nx * ctx->ny * ctx->nz;
     ctx->nmodes = (long long)ctx->hx * ctx->ny * ctx->nz;
@@ -713,8 +738,10 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     const size_t rs = (size_t)ctx->R * ctx->sites * (ctx->cplx ? sizeof(float2) : sizeof(float));
     auto dalloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
-    bool ok = dalloc((void**)&ctx->phi, ms) && dalloc((void**)&ctx->Q, ms);
-    if (ok && ctx->d >= 2) ok = dalloc((void**)&ctx->P, ms);
+    // phase-shift dealiasing keeps a second copy of P and Q (the grid shifted along y) behind the first
+    const size_t pq = cfg->dealias == 2 ? 2 * ms : ms;
+    bool ok = dalloc((void**)&ctx->phi, ms) && dalloc((void**)&ctx->Q, pq);
+    if (ok && ctx->d >= 2) ok = dalloc((void**)&ctx->P, pq);
     if (ok && ctx->d >= 2 && ctx->nl == NL_GRAD2) ok = dalloc((void**)&ctx->Py, ms);
     if (ok && cfg->scheme == SFT_SETD2) ok = dalloc((void**)&ctx->fprev, ms);
     if (ok && cfg->noise_space == 1) ok = dalloc((void**)&ctx->noise_spec, ms);
@@ -739,9 +766,9 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
         fprintf(stderr, "sft_create: device allocation failed\n");
         return cleanup(SFT_ENOMEM);
     }
-    if (cudaMemset(ctx->phi, 0, ms) != cudaSuccess || cudaMemset(ctx->Q, 0, ms) != cudaSuccess)
+    if (cudaMemset(ctx->phi, 0, ms) != cudaSuccess || cudaMemset(ctx->Q, 0, pq) != cudaSuccess)
         return cleanup(SFT_ECUDA);
-    if (ctx->P && cudaMemset(ctx->P, 0, ms) != cudaSuccess) return cleanup(SFT_ECUDA);
+    if (ctx->P && cudaMemset(ctx->P, 0, pq) != cudaSuccess) return cleanup(SFT_ECUDA);
     if (ctx->Py && cudaMemset(ctx->Py, 0, ms) != cudaSuccess) return cleanup(SFT_ECUDA);
     if (ctx->fprev && cudaMemset(ctx->fprev, 0, ms) != cudaSuccess) return cleanup(SFT_ECUDA);
     long long init[4] = {0, cfg->scheme == SFT_SETD2 ? 0 : -1, (long long)0x7fffffffffffffffLL, 0};
@@ -757,6 +784,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
         lens.push_back(ctx->nx);
     }
     if (ctx->d >= 2) lens.push_back(ctx->ny);
+    if (cfg->dealias == 2) lens.push_back(2 * ctx->nx);  // half-cell shift phases
     if (ctx->d == 1 && !ctx->cplx && k1_cluster_fft_len(ctx->nx))
         lens.push_back(k1_cluster_fft_len(ctx->nx));  // per-block FFT of the cluster kernel
     if (build_twiddles(ctx, lens) != SFT_OK) return cleanup(SFT_ECUDA);
@@ -852,8 +880,9 @@ sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
             fprintf(stderr, "sft_create_batch: member %d: %s\n", i, why.c_str());
             return vs;
         }
-        if (cfgs[i].noise_space != 0) {
-            fprintf(stderr, "sft_create_batch: member %d: real-space noise is built for single contexts\n", i);
+        if (cfgs[i].noise_space != 0 || cfgs[i].dealias == 2) {
+            fprintf(stderr, "sft_create_batch: member %d: real-space noise and phase-shift dealiasing are built for "
+                            "single contexts\n", i);
             return SFT_EUNSUPPORTED;
         }
         if (cfgs[i].model != cfgs[0].model || cfgs[i].scheme != cfgs[0].scheme ||
@@ -1083,7 +1112,9 @@ sft_status sft_dyn_start(sft_ctx* ctx, int M, int every) {
     if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     if (ctx->d != 2 || ctx->cplx)
         return fail(ctx, SFT_EUNSUPPORTED, "dynamic observables are built for 2-D real fields");
-    if (ctx->noise_spec) return fail(ctx, SFT_EUNSUPPORTED, "dynamic observables are built for the Fourier-space noise");
+    if (ctx->noise_spec || ctx->cfg.dealias == 2)
+        return fail(ctx, SFT_EUNSUPPORTED,
+                    "dynamic observables are built for the Fourier-space noise and 2/3 truncation (or none)");
     if (M < 16 || M > 16384 || (M & (M - 1)) || every < 1)
         return fail(ctx, SFT_EINVAL, "M must be a power of two in [16, 16384] and every >= 1");
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1504,10 +1535,11 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
 }
 
 static sft_status diff_supported(sft_ctx* ctx) {
-    if (ctx->cplx || ctx->nl != NL_CUBIC || ctx->cfg.scheme == SFT_SETD2 || (ctx->d == 1 && ctx->nx > 32768))
+    if (ctx->cplx || ctx->nl != NL_CUBIC || ctx->cfg.scheme == SFT_SETD2 || (ctx->d == 1 && ctx->nx > 32768) ||
+        ctx->cfg.dealias == 2)
         return fail(ctx, SFT_EUNSUPPORTED,
                     "tangent/adjoint are built for real fields with the cubic term (Model A/B), SETD-EM or SETD1 "
-                    "(1-D up to 32768 points)");
+                    "(1-D up to 32768 points), without phase-shift dealiasing");
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (!ctx->dphi) {
         CK(cudaMalloc(&ctx->dphi, ms));
@@ -1892,17 +1924,9 @@ sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, in
             CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
             CK(cudaEventRecord(e[1], ctx->stream));
         } else {
-            a.pin = ctx->P;
-            a.pyin = ctx->Py;
-            a.qout = ctx->Q;
-            a.tw_a = ctx->tw.get(ctx->nx / 2);
-            a.tw_b = ctx->tw.get(ctx->nx);
-            CK(launch_rows(ctx, a, MODE_STEP));
+            sft_status s = enqueue_front(ctx, a, 0);
+            if (s != SFT_OK) return s;
             CK(cudaEventRecord(e[1], ctx->stream));
-            a.qin = ctx->Q;
-            a.pout = ctx->P;
-            a.pyout = ctx->Py;
-            a.tw_a = ctx->tw.get(ctx->ny);
             CK(launch_cols_step(ctx, a));
             CK(cudaEventRecord(e[2], ctx->stream));
         }

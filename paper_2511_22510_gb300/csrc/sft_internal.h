@@ -16,7 +16,8 @@ enum KernelMode {
     MODE_PRIME = 5,
     MODE_ADJ_PRIME = 6,
     MODE_STEP_REC = 7,  // the step, also recording the state and the nonlinear force (dynamic observables)
-    MODE_STEP_RSN = 8   // the step with the noise read from a transformed real-space draw
+    MODE_STEP_RSN = 8,  // the step with the noise read from a transformed real-space draw
+    MODE_STEP_PS = 9    // the step with phase-shift dealiasing (grids shifted by half a cell)
 };
 
 // Everything a step kernel needs, passed by value.
@@ -30,6 +31,9 @@ struct StepArgs {
     float scale;   // 1 / (nx ny nz): folds the inverse-transform normalisation
     float dk;      // 2 pi / L
     int dealias;   // 1: 2/3 truncation
+    int pshift;    // 1: phase-shift dealiasing (the kernels' mask keeps all but the Nyquist modes)
+    const float2* tw_ps;  // e^{-i pi m / N}, m < 2N: half-cell shift phases (N = nx = ny)
+    long long ps_off;     // phase shift: offset of the shifted copies P1, Q1 behind P0, Q0 (R x modes)
     int model;     // sft_model
     int scheme;    // sft_scheme
     float s0, s0i; // nonlinear prefactor: A: -Gamma u; B: -Gamma u (times k^2); KPZ: lambda/2; CGL: -(1 + i beta)

@@ -175,6 +175,50 @@ __global__ void __launch_bounds__(RowCfg<M, SH>::THREADS, RowCfg<M, SH>::MINB) k
         if constexpr (MODE == MODE_TAN) store_tile<C>(tile, a.qout, rowbase, ncols, ny, y0);
         return;
     }
+    if constexpr (MODE == MODE_STEP_PS) {
+        // phase-shift dealiasing along x: q on the plain grid and on the grid shifted by half a
+        // cell along x (input phases e^{i pi k / N}, output phases e^{-i pi k / N}), averaged.
+        // The block's rows are those of one copy of P (plain or shifted along y: blockIdx.y runs
+        // over 2R copies).  Tile 0 holds the row for the plain grid, tile 1 a second copy for the
+        // shifted one (each team row is also its evaluation's exchange buffer).
+        static_assert(NL == NL_CUBIC, "phase-shift dealiasing: cubic term");
+        load_tile<C>(tile, a.pin, rowbase, ncols, ny, y0);
+        load_tile<C>(tile + ROWS * TS, a.pin, rowbase, ncols, ny, y0);
+        __syncthreads();
+        float2* r0 = tile + team * TS;
+        float2* r1 = tile + ROWS * TS + team * TS;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            z[e] = c2r_pre(r0[k], r0[M - k], __ldg(&twN[k]));
+        }
+        fft_line<M, true>(z, r0, t, twM);
+#pragma unroll
+        for (int e = 0; e < E; ++e) z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
+        fft_line<M, false>(z, r0, t, twM);
+        row_post<M>(z, r0, r0, ncols, t, twN);
+        const float2* __restrict__ tps = a.tw_ps;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            const float2 X = cmul(r1[k], cconj(__ldg(&tps[k]))), Xm = cmul(r1[M - k], cconj(__ldg(&tps[M - k])));
+            z[e] = c2r_pre(X, Xm, __ldg(&twN[k]));
+        }
+        fft_line<M, true>(z, r1, t, twM);
+#pragma unroll
+        for (int e = 0; e < E; ++e) z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
+        fft_line<M, false>(z, r1, t, twM);
+        row_post<M>(z, r1, r1, ncols, t, twN);
+        // each thread reads back the entries k = t + T e that it wrote itself
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            if (k < ncols) r0[k] = cscale(cadd(r0[k], cmul(r1[k], __ldg(&tps[k]))), 0.5f);
+        }
+        __syncthreads();
+        store_tile<C>(tile, a.qout, rowbase, ncols, ny, y0);
+        return;
+    }
     if constexpr (MODE == MODE_FWD) {
         const float* src = a.real_io + ((size_t)rep * ny + (yok ? y : 0)) * (2 * M);
 #pragma unroll
@@ -254,7 +298,8 @@ __global__ void __launch_bounds__(RowCfg<M, SH>::THREADS, RowCfg<M, SH>::MINB) k
 template <int M, int NL, int MODE, int SH = 0>
 static cudaError_t run_rows(const StepArgs& a, cudaStream_t s) {
     using C = RowCfg<M, SH>;
-    constexpr int NTILE = ((NL == NL_GRAD2 && MODE == MODE_STEP) || MODE == MODE_TAN || MODE == MODE_ADJ) ? 2 : 1;
+    constexpr int NTILE =
+        ((NL == NL_GRAD2 && MODE == MODE_STEP) || MODE == MODE_TAN || MODE == MODE_ADJ || MODE == MODE_STEP_PS) ? 2 : 1;
     const size_t sm = C::smem(NTILE);
     static bool attr = false;
     if (!attr) {
@@ -281,6 +326,7 @@ static cudaError_t rows_for(const StepArgs& a, int mode, int nl, cudaStream_t s,
     if (mode == MODE_INV) return run_rows<M, NL_CUBIC, MODE_INV>(a, s);
     if (mode == MODE_STEP && nl == NL_CUBIC) return rows_step<M, NL_CUBIC>(a, s, shape);
     if (mode == MODE_STEP && nl == NL_GRAD2) return rows_step<M, NL_GRAD2>(a, s, shape);
+    if (mode == MODE_STEP_PS && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_STEP_PS>(a, s);
     if (mode == MODE_TAN && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_TAN>(a, s);
     if (mode == MODE_ADJ && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_ADJ>(a, s);
     return cudaErrorInvalidValue;

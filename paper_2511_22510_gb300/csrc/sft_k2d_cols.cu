@@ -99,31 +99,50 @@ __device__ __forceinline__ void fixup_plane(float2 (&out)[FftPlan<NY, EM>::E], f
     }
 }
 
+// Dealiasing mask of mode (cc, a_y) on a 2-D real lattice: 2/3 truncation
+// (a.dealias), or, with phase-shift dealiasing (PS), every mode off the
+// Nyquist lines.
+template <bool PS>
+__device__ __forceinline__ bool keep_mode(const StepArgs& a, int cc, int ays, int ny) {
+    if constexpr (PS) return 2 * cc != a.nx && 2 * abs(ays) != ny;
+    return !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < ny);
+}
+
+// e^{-i pi s / N} for the signed index s, |s| < N (half-cell shift phase, conjugated)
+__device__ __forceinline__ float2 shift_phase_conj(const float2* __restrict__ tw_ps, int s) {
+    const float2 w = __ldg(&tw_ps[abs(s)]);
+    return s >= 0 ? w : cconj(w);
+}
+
 // P <- IFFT_y(M phi / N^2) for one column (and, for KPZ, P_y <- IFFT_y(i k_y M phi / N^2)):
-// the dealiased input of the next row pass.
-template <int NY, int NL, int EM>
+// the dealiased input of the next row pass.  Phase-shift dealiasing (PS) adds
+// the copy shifted by half a cell along y, P1 <- IFFT_y(M phi e^{i pi a_y / N} / N^2),
+// at a.ps_off behind P.
+template <int NY, int NL, int EM, bool PS = false>
 __device__ __forceinline__ void emit_p(const StepArgs& a, const float2 (&out)[FftPlan<NY, EM>::E], bool has_p, int cc,
                                        size_t colbase, float2* xb, int t) {
     using PL = FftPlan<NY, EM>;
     constexpr int T = PL::T, E = PL::E;
     if (!(has_p || T < 32)) return;
     float2 v[E];
-    float2 vy[NL == NL_GRAD2 ? E : 1];
+    float2 vy[(NL == NL_GRAD2 || PS) ? E : 1];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int ay = t + T * e;
         const int ays = signed_idx(ay, NY);
-        const bool inm = !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < NY);
+        const bool inm = keep_mode<PS>(a, cc, ays, NY);
         v[e] = (has_p && inm) ? cscale(out[e], a.scale) : czero();
         if constexpr (NL == NL_GRAD2) vy[e] = cscale(cmuli(v[e]), a.dk * (float)odd_idx(ay, NY));
+        if constexpr (PS) vy[e] = cmul(v[e], cconj(shift_phase_conj(a.tw_ps, ays)));
     }
     fft_line<NY, true, EM>(v, xb, t, a.tw_a);
-    if constexpr (NL == NL_GRAD2) fft_line<NY, true, EM>(vy, xb, t, a.tw_a);
+    if constexpr (NL == NL_GRAD2 || PS) fft_line<NY, true, EM>(vy, xb, t, a.tw_a);
     if (has_p) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             a.pout[colbase + t + T * e] = v[e];
             if constexpr (NL == NL_GRAD2) a.pyout[colbase + t + T * e] = vy[e];
+            if constexpr (PS) a.pout[a.ps_off + colbase + t + T * e] = vy[e];
         }
     }
 }
@@ -179,7 +198,9 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
 #pragma unroll
             for (int e = 0; e < E; ++e) a.pout[colbase + t + T * e] = v[e];
         }
-    } else if constexpr (MODE == MODE_STEP || MODE == MODE_STEP_REC || MODE == MODE_STEP_RSN) {
+    } else if constexpr (MODE == MODE_STEP || MODE == MODE_STEP_REC || MODE == MODE_STEP_RSN ||
+                         MODE == MODE_STEP_PS) {
+        constexpr bool PS = MODE == MODE_STEP_PS;
         if (!valid && T >= 32) return;
         const long long step = current_step(a);
         const bool first = (a.scheme == 2) && (step == *a.first_step);
@@ -197,6 +218,13 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = has_f ? a.qin[colbase + t + T * e] : czero();
         }
+        float2 v1[PS ? E : 1];  // phase shift: Q1, the row pass's result on the grid shifted along y
+        if constexpr (PS) {
+            if (has_f || T < 32) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) v1[e] = has_f ? a.qin[a.ps_off + colbase + t + T * e] : czero();
+            }
+        }
         // the noise depends on no loaded value: drawn while the loads of Q are in flight
         float2 out[E];
         if constexpr (MODE == MODE_STEP_RSN) {
@@ -209,6 +237,9 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
                                     out[e + 1]);
         }
         if (has_f || T < 32) fft_line<NY, false, EM>(v, xb, t, tw);
+        if constexpr (PS) {
+            if (has_f || T < 32) fft_line<NY, false, EM>(v1, xb, t, tw);
+        }
         cp_async_wait_all();
         team_sync<T>();
 #pragma unroll
@@ -216,9 +247,16 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
             const int ay = t + T * e;
             const int ays = signed_idx(ay, NY);
             const int q = cc * cc + ays * ays;
-            const bool inm = !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < NY);
+            const bool inm = keep_mode<PS>(a, cc, ays, NY);
             float2 F = czero();
-            if (has_f && inm) F = cscale(v[e], nl_prefactor(a, q).x);
+            if constexpr (PS) {
+                // mean over the grids shifted along y by 0 and half a cell (each already
+                // averaged over the two x shifts by the row pass)
+                if (has_f && inm)
+                    F = cscale(cadd(v[e], cmul(v1[e], shift_phase_conj(a.tw_ps, ays))), 0.5f * nl_prefactor(a, q).x);
+            } else {
+                if (has_f && inm) F = cscale(v[e], nl_prefactor(a, q).x);
+            }
             const Coefs co = load_coefs<false>(a.tab, cc * (NY / 2 + 1) + abs(ays), first);
             const float2 ph = sphi[ay];
             float2 Fp = czero();
@@ -261,7 +299,7 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
             }
             flag_nonfinite_acc(a, nf, step);
         }
-        emit_p<NY, NL, EM>(a, out, valid && cc < a.ncols, cc, colbase, xb, t);
+        emit_p<NY, NL, EM, PS>(a, out, valid && cc < a.ncols, cc, colbase, xb, t);
     } else if constexpr (MODE == MODE_TAN) {
         // primal step as in MODE_STEP, plus the tangent dphi <- f1 dphi + A M s DFT[q'] (no noise)
         if (!valid && T >= 32) return;
@@ -360,7 +398,10 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
         float2 out[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) out[e] = has_p ? a.phi[colbase + t + T * e] : czero();
-        emit_p<NY, NL, EM>(a, out, has_p, cc, colbase, xb, t);
+        if (a.pshift)
+            emit_p<NY, NL, EM, true>(a, out, has_p, cc, colbase, xb, t);
+        else
+            emit_p<NY, NL, EM>(a, out, has_p, cc, colbase, xb, t);
     }
     }  // replicas
 }
@@ -369,7 +410,9 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
 template <int NY, int NL, int MODE, int SH = 0>
 static cudaError_t run_cols(const StepArgs& a, cudaStream_t s) {
     using C = ColCfg<NY, SH>;
-    const size_t sm = (MODE == MODE_STEP || MODE == MODE_STEP_REC || MODE == MODE_STEP_RSN) ? C::smem_step() : C::smem();
+    const size_t sm = (MODE == MODE_STEP || MODE == MODE_STEP_REC || MODE == MODE_STEP_RSN || MODE == MODE_STEP_PS)
+                          ? C::smem_step()
+                          : C::smem();
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k2_cols_real<NY, NL, MODE, SH>,
@@ -388,6 +431,9 @@ template <int NY, int NL>
 static cudaError_t cols_step(const StepArgs& a, cudaStream_t s, int shape) {
     if (a.rec_phi) return run_cols<NY, NL, MODE_STEP_REC, 0>(a, s);  // recording: the default schedule
     if (a.noise_in) return run_cols<NY, NL, MODE_STEP_RSN, 0>(a, s);  // real-space noise: the default schedule
+    if constexpr (NL == NL_CUBIC) {
+        if (a.pshift) return run_cols<NY, NL, MODE_STEP_PS, 0>(a, s);  // phase-shift dealiasing
+    }
     if constexpr (ColCfg<NY>::WIDE) {
         if (shape == 1) return run_cols<NY, NL, MODE_STEP, 1>(a, s);
         if (shape == 2) return run_cols<NY, NL, MODE_STEP, 2>(a, s);

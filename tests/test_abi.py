@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 @pytest.mark.parametrize("bad", [
     dict(d=4), dict(n=[48, 48]), dict(replicas=0), dict(h=0.0), dict(h=float("nan")), dict(model=9),
-    dict(scheme=5), dict(dealias=2),
+    dict(scheme=5), dict(dealias=3), dict(dealias=-1),
 ])
 def test_invalid_configs_rejected_before_any_device_call(lib, bad):
     kw = dict(d=2, n=[64, 64], dx=[1.0, 1.0], replicas=1, model=0, p=[1, -0.5, 1, 0.5], scheme=1, h=0.01,
@@ -113,3 +113,17 @@ def test_real_space_noise_limits(lib, d, model, space, status):
     with pytest.raises(lib.SftError) as ei:
         lib.sft_create(cfg)
     assert ei.value.status == getattr(lib, status)
+
+
+@pytest.mark.parametrize("d,model,space", [
+    (1, 0, 0), (3, 0, 0),  # phase-shift dealiasing is built for 2-D lattices
+    (2, 2, 0),             # KPZ: quadratic gradient term
+    (2, 3, 0),             # complex field (CGL)
+    (2, 0, 1),             # with real-space noise
+])
+def test_phase_shift_dealiasing_limits(lib, d, model, space):
+    cfg = lib.make_config(d, [16] * d, [1.0] * d, 1, model, [1, -0.5, 1, 0.5], 1, 0.01, 1, dealias=2,
+                          noise_space=space)
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_create(cfg)
+    assert ei.value.status == lib.SFT_EUNSUPPORTED

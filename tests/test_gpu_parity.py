@@ -411,3 +411,48 @@ def test_real_space_noise_graph_and_plain_bit_identical(sft):
     assert rel_l2(c.field(), a.field()) > 1e-2
     for s in (a, b, c):
         s.close()
+
+
+# ------------------------------------------------------------------ phase-shift dealiasing
+PS_CASES = [
+    ("model_a_16_setd1", W.model_a_64(n=[16, 16], replicas=2, sigma0=0.3), 100),
+    ("model_a_64_em", W.model_a_64(replicas=2, scheme=0, sigma0=0.3), 100),
+    ("model_b_64_setd2", W.model_b_1024(n=[64, 64], scheme=2, h=0.025, sigma0=0.3), 100),
+    ("model_b_128_setd1_R3", W.model_b_1024(n=[128, 128], replicas=3, sigma0=0.3), 40),
+    ("model_a_512_setd1", W.model_a_64(n=[512, 512], replicas=1, sigma0=0.3), 10),
+    ("model_b_1024_setd1_R2", W.model_b_1024(replicas=2, h=0.05), 3),
+]
+
+
+@pytest.mark.parametrize("name,w,nsteps", PS_CASES, ids=[c[0] for c in PS_CASES])
+def test_phase_shift_dealiasing_step_parity(sft, oracle_mod, name, w, nsteps):
+    """Phase-shift dealiasing (dealias = 2): the row pass over both y copies of
+    P with its two x shifts, the column pass combining the y copies, against
+    the oracle's mean over the four half-cell-shifted grids."""
+    w = w.with_(dealias=2)
+    g, o = start_pair(sft, oracle_mod, w)
+    g.step(nsteps)
+    o.step(nsteps)
+    got = g.field()
+    for r in range(w.replicas):
+        assert rel_l2(got[r], o.field(r)) <= 1e-5, (name, r)
+    g.close()
+
+
+def test_phase_shift_graph_plain_and_checkpoint(sft):
+    w = W.model_b_1024(n=[64, 64], replicas=2, sigma0=0.3, scheme=2, dealias=2)
+    a, b = gpu_stepper(sft, w), gpu_stepper(sft, w)
+    f = W.initial_fields(w).astype(np.float32)
+    a.set_field(f)
+    b.set_field(f)
+    a.step(53)
+    b.step_plain(53)
+    assert np.array_equal(a.spectrum().view(np.uint64), b.spectrum().view(np.uint64))
+    # the Model B zero mode stays fixed bit for bit with the phase-shifted force too
+    s0 = gpu_stepper(sft, w)
+    s0.set_field(f)
+    z0 = s0.spectrum()[:, 0, 0].copy()
+    s0.step(40)
+    assert np.array_equal(s0.spectrum()[:, 0, 0].view(np.uint64), z0.view(np.uint64))
+    for s in (a, b, s0):
+        s.close()
