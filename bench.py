@@ -106,10 +106,18 @@ def algorithmic_bytes(w, scheme, ncols):
     return rows, cols
 
 
-def source_hash():
+# sources each recorded kernel is compiled from: its translation unit and the headers it includes
+KERNEL_SOURCES = {
+    "k2_cols_real": ["sft_k2d_cols.cu", "sft_step_common.cuh", "sft_device.cuh", "sft_async.cuh", "sft_internal.h"],
+    "k2_rows_real": ["sft_k2d.cu", "sft_step_common.cuh", "sft_device.cuh", "sft_async.cuh", "sft_internal.h"],
+}
+
+
+def source_hash(kernel):
+    """Hash of the sources a kernel is built from (a record taken on other sources is stale)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2511_22510_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(KERNEL_SOURCES[kernel]):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -127,7 +135,7 @@ def profile_traffic(kernel_tag):
     except Exception:
         return None
     ent = rec.get(kernel_tag)
-    if not ent or ent.get("source_hash") != source_hash():
+    if not ent or ent.get("source_hash") != source_hash(kernel_tag.split("_model")[0]):
         return None
     return ent.get("dram_bytes_per_launch")
 
