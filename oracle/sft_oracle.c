@@ -208,12 +208,49 @@ static void fft1d_radix2(cplx* x, int n, int sign) {
     }
 }
 
+/* Lengths that are not powers of two (3 x 2^k lattices): radix-2 decimation in
+ * time down to an odd length, whose DFT is taken from its definition (phase
+ * (k m mod n) / n of a turn). */
+static void fft1d_split(cplx* x, int n, int sign) {
+    if (n % 2) {
+        cplx* y = (cplx*)malloc(sizeof(cplx) * (size_t)n);
+        for (int k = 0; k < n; ++k) {
+            cplx acc = 0;
+            for (int m = 0; m < n; ++m) {
+                double ang = (double)sign * 2.0 * OR_PI * (double)((long)k * m % n) / (double)n;
+                acc += x[m] * (cos(ang) + I * sin(ang));
+            }
+            y[k] = acc;
+        }
+        memcpy(x, y, sizeof(cplx) * (size_t)n);
+        free(y);
+        return;
+    }
+    int h = n / 2;
+    cplx* ev = (cplx*)malloc(sizeof(cplx) * (size_t)h);
+    cplx* od = (cplx*)malloc(sizeof(cplx) * (size_t)h);
+    for (int i = 0; i < h; ++i) {
+        ev[i] = x[2 * i];
+        od[i] = x[2 * i + 1];
+    }
+    fft1d_split(ev, h, sign);
+    fft1d_split(od, h, sign);
+    for (int k = 0; k < h; ++k) {
+        double ang = (double)sign * 2.0 * OR_PI * (double)k / (double)n;
+        cplx w = (cos(ang) + I * sin(ang)) * od[k];
+        x[k] = ev[k] + w;
+        x[k + h] = ev[k] - w;
+    }
+    free(ev);
+    free(od);
+}
+
 /* In-place d-dimensional FFT of a row-major [n2][n1][n0] array (n0 fastest). */
 int or_fft_nd(int d, const int* n_in, double* data_ri, int sign) {
     int n[3] = {1, 1, 1};
     for (int i = 0; i < d; ++i) n[i] = n_in[i];
     for (int i = 0; i < 3; ++i)
-        if (!is_pow2(n[i])) return -1;
+        if (n[i] < 1) return -1;
     cplx* a = (cplx*)data_ri;
     int maxn = n[0] > n[1] ? n[0] : n[1];
     if (n[2] > maxn) maxn = n[2];
@@ -226,7 +263,10 @@ int or_fft_nd(int d, const int* n_in, double* data_ri, int sign) {
             for (int i2 = 0; i2 < n[o2]; ++i2) {
                 size_t base = i1 * stride[o1] + i2 * stride[o2];
                 for (int t = 0; t < n[ax]; ++t) line[t] = a[base + t * stride[ax]];
-                fft1d_radix2(line, n[ax], sign);
+                if (is_pow2(n[ax]))
+                    fft1d_radix2(line, n[ax], sign);
+                else
+                    fft1d_split(line, n[ax], sign);
                 for (int t = 0; t < n[ax]; ++t) a[base + t * stride[ax]] = line[t];
             }
     }
@@ -620,7 +660,7 @@ or_state* or_create(const or_config* cfg) {
     st->cfg = *cfg;
     st->n[0] = st->n[1] = st->n[2] = 1;
     for (int ax = 0; ax < cfg->d; ++ax) {
-        if (!is_pow2(cfg->n[ax]) || !(cfg->dx[ax] > 0)) {
+        if (cfg->n[ax] < 2 || cfg->n[ax] % 2 || !(cfg->dx[ax] > 0)) {
             free(st);
             return NULL;
         }

@@ -16,7 +16,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 # ---------------------------------------------------------------- transforms
-@pytest.mark.parametrize("shape", [(8,), (16,), (8, 16), (8, 8, 8), (2, 4, 8)])
+@pytest.mark.parametrize("shape", [(8,), (16,), (8, 16), (8, 8, 8), (2, 4, 8),
+                                   (12,), (24,), (48,), (6, 10), (24, 12), (3, 4, 6)])  # not powers of two
 def test_fft_matches_bruteforce_dft(oracle_mod, shape):
     rng = np.random.default_rng(1)
     x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
@@ -34,6 +35,17 @@ def test_bruteforce_dft_matches_numpy(oracle_mod, shape):
     assert np.abs(oracle_mod.dft_naive(x, -1) - ref).max() <= 1e-12 * np.abs(ref).max()
     refi = np.fft.ifftn(x) * x.size
     assert np.abs(oracle_mod.dft_naive(x, +1) - refi).max() <= 1e-12 * np.abs(refi).max()
+
+
+@pytest.mark.parametrize("shape", [(96,), (48, 48), (24, 96), (192, 12)])
+def test_fft_of_3x2k_lengths_matches_numpy(oracle_mod, shape):
+    """Lattices of 3 x 2^k points: the oracle's split-radix transform against numpy's FFT."""
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    ref = np.fft.fftn(x)
+    assert np.abs(oracle_mod.fft_nd(x, -1) - ref).max() <= 1e-12 * np.abs(ref).max()
+    refi = np.fft.ifftn(x) * x.size
+    assert np.abs(oracle_mod.fft_nd(x, +1) - refi).max() <= 1e-12 * np.abs(refi).max()
 
 
 def test_fft_parseval_and_roundtrip(oracle_mod):

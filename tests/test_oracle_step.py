@@ -598,3 +598,69 @@ def test_r_in_F_linear_closed_form(oracle_mod, model, scheme):
     want = np.fft.fft2(f0) * f ** n
     got = o.spectrum(0)
     assert np.allclose(got, want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
+
+
+# ------------------------------------------------------------ 3 x 2^k lattices
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_noise_free_linear_propagation_3x2k(oracle_mod, scheme):
+    """48 x 48 (a lattice of 3 x 2^k points): u = 0, D = 0 propagates every mode by
+    e^{c h} per step exactly, with numpy's wavenumbers."""
+    p = [1.0, 0.3, 0.0, 0.0]
+    w = W.model_a_64(n=[48, 48], dx=[0.7, 0.7], model=1, p=p, scheme=scheme, h=0.05)
+    o = make_oracle(oracle_mod, w)
+    rng = np.random.default_rng(5)
+    f0 = rng.standard_normal(w.shape)
+    o.set_field(0, f0)
+    S0 = np.fft.fft2(f0)
+    n = 30
+    o.step(n)
+    KY, KX = spectral_k(w.shape, 0.7)
+    k2 = KX ** 2 + KY ** 2
+    decay = np.exp(-k2 * (0.3 + k2) * n * w.h)
+    expect = S0 * decay
+    got = o.spectrum(0)
+    # each mode to rounding of the transforms, on the scale of its own decay
+    live = decay > 1e-200
+    err = np.abs(got - expect)[live] / (np.abs(S0).max() * decay[live])
+    # rounding of c h (relative eps) grows the error of e^{c h n} by |c h n| eps
+    cnh = (k2 * (0.3 + k2) * n * w.h)[live]
+    assert np.all(err <= 4 * 2.2e-16 * (n + cnh) + 1e-13)
+    assert np.abs(got[~live]).max() <= 1e-200 * np.abs(S0).max()
+
+
+def test_noise_structure_3x2k(oracle_mod):
+    """App. B on a 24 x 24 lattice: Hermitian noise, real self-conjugate modes,
+    unit mean |eta_a|^2."""
+    N = 24
+    o = make_oracle(oracle_mod, W.model_a_64(n=[N, N]))
+    acc = np.zeros((N, N))
+    for s in range(200):
+        eta = o.noise(0, s)
+        assert np.array_equal(eta, np.conj(np.roll(eta[::-1, ::-1], 1, axis=(0, 1))))
+        for iy in (0, N // 2):
+            for ix in (0, N // 2):
+                assert eta[iy, ix].imag == 0.0
+        acc += np.abs(eta) ** 2
+    assert abs(acc.mean() / 200 - 1.0) < 4 * math.sqrt(2 / (200 * N * N))
+
+
+def test_gaussian_model_a_structure_factor_3x2k(oracle_mod):
+    """Sec. V.A linear theory C_ET(k) = T / (r + k^2) on a 24 x 24 lattice."""
+    N, R = 24, 48
+    w = W.model_a_64(n=[N, N], dx=[0.5, 0.5], p=[1.0, 1.0, 0.0, 0.6], h=0.05)
+    o = make_oracle(oracle_mod, w, replicas=R)
+    o.step(200)
+    acc = None
+    S = 15
+    for _ in range(S):
+        o.step(20)
+        v, _ = o.shells(0)
+        acc = v if acc is None else acc + v
+    v = acc / S
+    dk = 2 * np.pi / (N * 0.5)
+    KY, KX = spectral_k(w.shape, 0.5)
+    kk = np.sqrt(KX ** 2 + KY ** 2)
+    for j in range(1, 6):
+        sel = (kk > (j - 1) * dk + 1e-9) & (kk <= j * dk + 1e-9)
+        ref = np.mean(0.6 / (1.0 + kk[sel] ** 2))
+        assert abs(v[j] - ref) < 5 * ref / math.sqrt(sel.sum() * R * S / 4), (j, v[j], ref)
