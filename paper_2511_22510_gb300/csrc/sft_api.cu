@@ -487,12 +487,12 @@ static sft_status plan_step(sft_ctx* ctx) {
         return SFT_OK;
     }
     const char* env = getenv("SFT_AUTOTUNE");
-    if ((env && env[0] == '0') || ctx->cplx || ctx->d < 2 || ctx->cfg.dealias == 2) return SFT_OK;
+    if ((env && env[0] == '0') || ctx->cplx || ctx->d < 2 || ctx->cfg.dealias == 2 || !is_pow2(ctx->nx)) return SFT_OK;
     // SFT_PLAN="row,col,rpb,pipe" fixes the schedule (as sft_set_plan; e.g. to profile the one a timed run chose)
     if (const char* fixed = getenv("SFT_PLAN")) {
         int v[4];
         if (sscanf(fixed, "%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3]) == 4) {
-            const bool ok = v[0] >= 0 && v[0] < k2_row_shapes() && v[1] >= 0 &&
+            const bool ok = v[0] >= 0 && v[0] < k2_row_shapes(ctx->nx) && v[1] >= 0 &&
                             v[1] < (ctx->d == 2 ? k2_col_shapes(ctx->ny) : 1) && v[2] >= 1 && v[2] <= 64 &&
                             (v[3] == 0 || (ctx->d == 2 && k2_pipe_supported(ctx->nx, ctx->ny, 0)));
             if (!ok) return fail(ctx, SFT_EINVAL, "SFT_PLAN names a schedule not built for this lattice");
@@ -527,7 +527,7 @@ static sft_status plan_step(sft_ctx* ctx) {
     a.tw_a = ctx->tw.get(ctx->nx / 2);
     a.tw_b = ctx->tw.get(ctx->nx);
     float best_ms = 1e30f;
-    for (int sh = 0; sh < k2_row_shapes(); ++sh) {
+    for (int sh = 0; sh < k2_row_shapes(ctx->nx); ++sh) {
         float ms = 0.f;
         CK(time_launch(ctx->stream, [&] { return launch_k2_rows(a, MODE_STEP, ctx->nl, ctx->stream, sh); }, &ms));
         if (ms < best_ms) best_ms = ms, best.row_shape = sh;
@@ -639,7 +639,8 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
     if (!cfg) return why = "null config", SFT_EINVAL;
     if (cfg->d < 1 || cfg->d > 3) return why = "d must be 1, 2 or 3", SFT_EINVAL;
     for (int i = 0; i < cfg->d; ++i) {
-        if (!is_pow2(cfg->n[i])) return why = "lattice sizes must be powers of two", SFT_EINVAL;
+        if (!is_pow2(cfg->n[i]) && !k2_mixed_size(cfg->n[i]))
+            return why = "lattice sizes must be powers of two (or 3 x 2^k, 48 .. 768, for 2-D real fields)", SFT_EINVAL;
         if (!(cfg->dx[i] > 0)) return why = "dx must be positive", SFT_EINVAL;
         if (cfg->n[i] != cfg->n[0] || cfg->dx[i] != cfg->dx[0])
             return why = "anisotropic lattices are not supported (coefficients are tabulated by |a|^2)",
@@ -660,6 +661,11 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
     if (cfg->noise_space != 0 && cfg->noise_space != 1) return why = "noise_space must be 0 or 1", SFT_EINVAL;
     if (cfg->noise_space == 1 && (cfg->d != 2 || cplx))
         return why = "real-space noise is built for 2-D real fields", SFT_EUNSUPPORTED;
+    if (!is_pow2(cfg->n[0]) &&
+        (cfg->d != 2 || cplx || cfg->dealias == 2 || cfg->noise_space != 0 || cfg->model == SFT_CUSTOM))
+        return why = "lattices of 3 x 2^k points are built for 2-D real fields (Model A/B, KPZ) with Fourier-space "
+                     "noise and 2/3 truncation (or none)",
+               SFT_EUNSUPPORTED;
     if (cfg->dealias == 2 && (cfg->d != 2 || cplx || nlk != NL_CUBIC || cfg->noise_space != 0))
         return why = "phase-shift dealiasing is built for 2-D real fields with the cubic term and Fourier-space noise",
                SFT_EUNSUPPORTED;
@@ -880,9 +886,9 @@ sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
             fprintf(stderr, "sft_create_batch: member %d: %s\n", i, why.c_str());
             return vs;
         }
-        if (cfgs[i].noise_space != 0 || cfgs[i].dealias == 2) {
-            fprintf(stderr, "sft_create_batch: member %d: real-space noise and phase-shift dealiasing are built for "
-                            "single contexts\n", i);
+        if (cfgs[i].noise_space != 0 || cfgs[i].dealias == 2 || !is_pow2(cfgs[i].n[0])) {
+            fprintf(stderr, "sft_create_batch: member %d: real-space noise, phase-shift dealiasing and 3 x 2^k "
+                            "lattices are built for single contexts\n", i);
             return SFT_EUNSUPPORTED;
         }
         if (cfgs[i].model != cfgs[0].model || cfgs[i].scheme != cfgs[0].scheme ||
@@ -1112,9 +1118,10 @@ sft_status sft_dyn_start(sft_ctx* ctx, int M, int every) {
     if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     if (ctx->d != 2 || ctx->cplx)
         return fail(ctx, SFT_EUNSUPPORTED, "dynamic observables are built for 2-D real fields");
-    if (ctx->noise_spec || ctx->cfg.dealias == 2)
+    if (ctx->noise_spec || ctx->cfg.dealias == 2 || !is_pow2(ctx->nx))
         return fail(ctx, SFT_EUNSUPPORTED,
-                    "dynamic observables are built for the Fourier-space noise and 2/3 truncation (or none)");
+                    "dynamic observables are built for power-of-two lattices with the Fourier-space noise and 2/3 "
+                    "truncation (or none)");
     if (M < 16 || M > 16384 || (M & (M - 1)) || every < 1)
         return fail(ctx, SFT_EINVAL, "M must be a power of two in [16, 16384] and every >= 1");
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1393,7 +1400,7 @@ sft_status sft_set_plan(sft_ctx* ctx, const int* plan, int n) {
     if (!ctx || !plan || n < 4) return SFT_EINVAL;
     if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     const bool real2 = ctx->d >= 2 && !ctx->cplx;
-    if (plan[0] < 0 || plan[0] >= (real2 ? k2_row_shapes() : 1) || plan[1] < 0 ||
+    if (plan[0] < 0 || plan[0] >= (real2 ? k2_row_shapes(ctx->nx) : 1) || plan[1] < 0 ||
         plan[1] >= (real2 && ctx->d == 2 ? k2_col_shapes(ctx->ny) : 1) || plan[2] < 1 || plan[2] > 64 ||
         (plan[3] != 0 && !(ctx->d == 2 && k2_pipe_supported(ctx->nx, ctx->ny, ctx->cplx))))
         return fail(ctx, SFT_EINVAL, "schedule outside the variants built for this lattice");
@@ -1536,10 +1543,10 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
 
 static sft_status diff_supported(sft_ctx* ctx) {
     if (ctx->cplx || ctx->nl != NL_CUBIC || ctx->cfg.scheme == SFT_SETD2 || (ctx->d == 1 && ctx->nx > 32768) ||
-        ctx->cfg.dealias == 2)
+        ctx->cfg.dealias == 2 || !is_pow2(ctx->nx))
         return fail(ctx, SFT_EUNSUPPORTED,
                     "tangent/adjoint are built for real fields with the cubic term (Model A/B), SETD-EM or SETD1 "
-                    "(1-D up to 32768 points), without phase-shift dealiasing");
+                    "(1-D up to 32768 points), power-of-two lattices without phase-shift dealiasing");
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (!ctx->dphi) {
         CK(cudaMalloc(&ctx->dphi, ms));

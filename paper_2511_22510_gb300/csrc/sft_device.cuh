@@ -120,20 +120,26 @@ __device__ __forceinline__ float2 normal_pair_for_index(uint64_t seed, uint64_t 
 #ifndef SFT_EMAX
 #define SFT_EMAX 16
 #endif
+//
+// Lines of N = 3 x 2^k points (MIXED) take 12 values per thread: one radix-3
+// pass, then radix-4 passes and a radix-2 remainder.
 template <int N, int EM = SFT_EMAX>
 struct FftPlan {
-    static_assert(N >= 2 && (N & (N - 1)) == 0, "power of two");
+    static constexpr bool MIXED = N % 3 == 0;
+    static_assert(N >= 2 && ((N & (N - 1)) == 0 || (MIXED && N >= 12 && ((N / 3) & (N / 3 - 1)) == 0)),
+                  "2^k or 3 x 2^k points");
     static constexpr int log2(int v) { return v <= 1 ? 0 : 1 + log2(v / 2); }
-    static constexpr int L = log2(N);
-    static constexpr int E = N <= 16 ? N : (N >= 512 ? EM : (N <= 32 && EM >= 32 ? N : 16));
+    static constexpr int L = log2(MIXED ? N / 3 : N);  // the power-of-two factor
+    static constexpr int E = MIXED ? 12 : (N <= 16 ? N : (N >= 512 ? EM : (N <= 32 && EM >= 32 ? N : 16)));
     static constexpr int T = N / E;
-    static constexpr int R0 = E;  // first radix
-    // remaining log2 after the first pass, split into radix-E passes and a remainder
-    static constexpr int LE = log2(E);
-    static constexpr int LR = L - log2(R0);
+    static constexpr int R0 = MIXED ? 3 : E;  // first radix
+    static constexpr int E2 = MIXED ? 4 : E;  // radix of the power-of-two passes
+    // remaining log2 after the first pass, split into radix-E2 passes and a remainder
+    static constexpr int LE = log2(E2);
+    static constexpr int LR = MIXED ? L : L - log2(R0);
     static constexpr int P = 1 + (LR + LE - 1) / LE;
     static constexpr int radix(int p) {
-        return p == 0 ? R0 : (p < P - 1 ? E : (LR % LE == 0 ? E : (1 << (LR % LE))));
+        return p == 0 ? R0 : (p < P - 1 ? E2 : (LR % LE == 0 ? E2 : (1 << (LR % LE))));
     }
     // padded exchange buffer: one pad element per R0 (first-pass radix) elements
     static constexpr int PAD = R0 >= 16 ? R0 : 16;
@@ -206,7 +212,16 @@ __device__ constexpr int bitrev(int k) {
 // frequency, then the bit-reversal permutation (resolved at compile time).
 template <int R, bool INV>
 __device__ __forceinline__ void dft_reg(float2* x) {
-    if constexpr (R > 1) {
+    if constexpr (R == 3) {
+        // y1 = a + w b + w^2 c, y2 = a + w^2 b + w c with w = e^{-+2 pi i / 3} = -1/2 -+ i sqrt(3)/2
+        const float2 a = x[0], s = cadd(x[1], x[2]), d = csub(x[1], x[2]);
+        const float2 t = make_float2(a.x - 0.5f * s.x, a.y - 0.5f * s.y);
+        const float h = 0.866025403784438647f;  // sin(2 pi / 3)
+        const float2 ihd = make_float2(-h * d.y, h * d.x);  // i h d
+        x[0] = cadd(a, s);
+        x[1] = INV ? cadd(t, ihd) : csub(t, ihd);
+        x[2] = INV ? csub(t, ihd) : cadd(t, ihd);
+    } else if constexpr (R > 1) {
 #pragma unroll
         for (int span = R / 2; span >= 1; span >>= 1) {
 #pragma unroll

@@ -28,6 +28,15 @@
 #endif
 namespace sft {
 
+// Index of the mirrored entry (M - k) mod M of an M-point line.
+template <int M>
+__device__ __forceinline__ int mirror_idx(int k) {
+    if constexpr ((M & (M - 1)) == 0)
+        return (M - k) & (M - 1);
+    else
+        return k == 0 ? 0 : M - k;
+}
+
 // R2C post-processing of one row held by a team (z = FFT_M of the packed real
 // line) into the spectral row trow[0..ncols); xb is the team's exchange buffer
 // (it may alias trow).
@@ -43,7 +52,7 @@ __device__ __forceinline__ void row_post(float2 (&z)[FftPlan<M>::E], float2* xb,
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int k = t + T * e;
-        z[e] = r2c_post(z[e], cconj(xb[xpos<M>((M - k) & (M - 1))]), __ldg(&twN[k]));
+        z[e] = r2c_post(z[e], cconj(xb[xpos<M>(mirror_idx<M>(k))]), __ldg(&twN[k]));
     }
     const float2 z0 = xb[0];
     team_sync<T>();
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(RowCfg<M, SH>::THREADS, RowCfg<M, SH>::MINB) k
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int k = t + T * e;
-            z[e] = r2c_post(z[e], cconj(xb[xpos<M>((M - k) & (M - 1))]), __ldg(&twN[k]));
+            z[e] = r2c_post(z[e], cconj(xb[xpos<M>(mirror_idx<M>(k))]), __ldg(&twN[k]));
         }
         const float2 z0 = xb[0];
         team_sync<T>();
@@ -332,10 +341,26 @@ static cudaError_t rows_for(const StepArgs& a, int mode, int nl, cudaStream_t s,
     return cudaErrorInvalidValue;
 }
 
-int k2_row_shapes() { return 3; }
+// Rows of M = 3 x 2^k points (lattices of 48 .. 768 points): transforms and the
+// step (default schedule).
+template <int M>
+static cudaError_t rows_for_mixed(const StepArgs& a, int mode, int nl, cudaStream_t s) {
+    if (mode == MODE_FWD) return run_rows<M, NL_CUBIC, MODE_FWD>(a, s);
+    if (mode == MODE_INV) return run_rows<M, NL_CUBIC, MODE_INV>(a, s);
+    if (mode == MODE_STEP && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_STEP>(a, s);
+    if (mode == MODE_STEP && nl == NL_GRAD2) return run_rows<M, NL_GRAD2, MODE_STEP>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+int k2_row_shapes(int nx) { return (nx & (nx - 1)) == 0 ? 3 : 1; }
 
 cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape) {
     switch (a.nx / 2) {
+        case 24: return rows_for_mixed<24>(a, mode, nl, s);
+        case 48: return rows_for_mixed<48>(a, mode, nl, s);
+        case 96: return rows_for_mixed<96>(a, mode, nl, s);
+        case 192: return rows_for_mixed<192>(a, mode, nl, s);
+        case 384: return rows_for_mixed<384>(a, mode, nl, s);
         case 8: return rows_for<8>(a, mode, nl, s, shape);
         case 16: return rows_for<16>(a, mode, nl, s, shape);
         case 32: return rows_for<32>(a, mode, nl, s, shape);

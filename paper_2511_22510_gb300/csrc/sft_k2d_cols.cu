@@ -455,16 +455,35 @@ static cudaError_t cols_for(const StepArgs& a, int mode, int nl, cudaStream_t s,
     return cudaErrorInvalidValue;
 }
 
+// Columns of NY = 3 x 2^k points (48 .. 768): transforms, the step and P (default schedule).
+template <int NY>
+static cudaError_t cols_for_mixed(const StepArgs& a, int mode, int nl, cudaStream_t s) {
+    if (mode == MODE_FWD) return run_cols<NY, NL_CUBIC, MODE_FWD>(a, s);
+    if (mode == MODE_INV) return run_cols<NY, NL_CUBIC, MODE_INV>(a, s);
+    if (mode == MODE_STEP && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_STEP>(a, s);
+    if (mode == MODE_STEP && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_STEP>(a, s);
+    if (mode == MODE_PRIME && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_PRIME>(a, s);
+    if (mode == MODE_PRIME && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_PRIME>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+bool k2_mixed_size(int n) { return n % 3 == 0 && n >= 48 && n <= 768 && ((n / 3) & (n / 3 - 1)) == 0; }
+
 bool k2_supported(int nx, int ny, int complex_field) {
     if (complex_field) return false;
-    auto ok = [](int n) { return n >= 16 && n <= 4096 && (n & (n - 1)) == 0; };
+    auto ok = [](int n) { return (n >= 16 && n <= 4096 && (n & (n - 1)) == 0) || k2_mixed_size(n); };
     return ok(nx) && ok(ny);
 }
 
-int k2_col_shapes(int ny) { return ny >= 512 ? 3 : 1; }
+int k2_col_shapes(int ny) { return (ny & (ny - 1)) == 0 && ny >= 512 ? 3 : 1; }
 
 cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape) {
     switch (a.ny) {
+        case 48: return cols_for_mixed<48>(a, mode, nl, s);
+        case 96: return cols_for_mixed<96>(a, mode, nl, s);
+        case 192: return cols_for_mixed<192>(a, mode, nl, s);
+        case 384: return cols_for_mixed<384>(a, mode, nl, s);
+        case 768: return cols_for_mixed<768>(a, mode, nl, s);
         case 16: return cols_for<16>(a, mode, nl, s, shape);
         case 32: return cols_for<32>(a, mode, nl, s, shape);
         case 64: return cols_for<64>(a, mode, nl, s, shape);

@@ -78,7 +78,8 @@ using namespace sft;
 extern "C" sft_status sft_step2d_noalloc(const sft_config* cfg, void* phi_dev, void* fprev_dev, int history_valid,
                                          int64_t step0, int64_t nsteps) {
     if (!cfg || !phi_dev || nsteps < 0 || step0 < 0) return SFT_EINVAL;
-    if (cfg->d != 2 || cfg->model == SFT_CGL || cfg->model == SFT_CUSTOM || cfg->noise_space != 0 || cfg->dealias == 2)
+    if (cfg->d != 2 || cfg->model == SFT_CGL || cfg->model == SFT_CUSTOM || cfg->noise_space != 0 || cfg->dealias == 2 ||
+        (cfg->n[0] & (cfg->n[0] - 1)) != 0)
         return SFT_EUNSUPPORTED;
     if (cfg->model != SFT_KPZ && cfg->p[4] != 0.0 && cfg->scheme == SFT_SETD2) return SFT_EUNSUPPORTED;
     const int nx = cfg->n[0], ny = cfg->n[1];

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(d=4), dict(n=[48, 48]), dict(replicas=0), dict(h=0.0), dict(h=float("nan")), dict(model=9),
+    dict(d=4), dict(n=[40, 40]), dict(n=[1536, 1536]), dict(replicas=0), dict(h=0.0), dict(h=float("nan")), dict(model=9),
     dict(scheme=5), dict(dealias=3), dict(dealias=-1),
 ])
 def test_invalid_configs_rejected_before_any_device_call(lib, bad):
@@ -124,6 +124,18 @@ def test_real_space_noise_limits(lib, d, model, space, status):
 def test_phase_shift_dealiasing_limits(lib, d, model, space):
     cfg = lib.make_config(d, [16] * d, [1.0] * d, 1, model, [1, -0.5, 1, 0.5], 1, 0.01, 1, dealias=2,
                           noise_space=space)
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_create(cfg)
+    assert ei.value.status == lib.SFT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("d,model,extra", [
+    (1, 0, {}), (3, 0, {}),                   # 3 x 2^k lattices are built for 2-D real fields
+    (2, 3, {}),                               # complex field (CGL)
+    (2, 0, dict(dealias=2)), (2, 0, dict(noise_space=1)),
+])
+def test_3x2k_lattice_limits(lib, d, model, extra):
+    cfg = lib.make_config(d, [48] * d, [1.0] * d, 1, model, [1, -0.5, 1, 0.5], 1, 0.01, 1, **extra)
     with pytest.raises(lib.SftError) as ei:
         lib.sft_create(cfg)
     assert ei.value.status == lib.SFT_EUNSUPPORTED

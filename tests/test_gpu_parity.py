@@ -456,3 +456,53 @@ def test_phase_shift_graph_plain_and_checkpoint(sft):
     assert np.array_equal(s0.spectrum()[:, 0, 0].view(np.uint64), z0.view(np.uint64))
     for s in (a, b, s0):
         s.close()
+
+
+# ------------------------------------------------------------------ lattices of 3 x 2^k points
+MIXED_CASES = [
+    ("model_a_48_setd1_R2", W.model_a_64(n=[48, 48], replicas=2, sigma0=0.3), 100),
+    ("model_b_96_setd2", W.model_b_1024(n=[96, 96], scheme=2, h=0.025, sigma0=0.3), 100),
+    ("kpz_2d_96_em_R2", W.kpz_2d(n=[96, 96], replicas=2, scheme=0), 100),
+    ("model_a_192_nodealias", W.model_a_64(n=[192, 192], dealias=0, sigma0=0.3), 40),
+    ("model_b_384_setd1_R3", W.model_b_1024(n=[384, 384], replicas=3, sigma0=0.3), 10),
+    ("model_b_768_setd1", W.model_b_1024(n=[768, 768], h=0.05), 3),
+]
+
+
+@pytest.mark.parametrize("name,w,nsteps", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
+def test_3x2k_lattice_step_parity(sft, oracle_mod, name, w, nsteps):
+    """Lattices of 3 x 2^k points: the radix-3 + radix-4/2 Stockham transforms of
+    the row and column passes against the oracle's split-radix transform."""
+    g, o = start_pair(sft, oracle_mod, w)
+    g.step(nsteps)
+    o.step(nsteps)
+    got = g.field()
+    spec = g.spectrum()
+    for r in range(w.replicas):
+        assert rel_l2(got[r], o.field(r)) <= 1e-5, (name, r)
+        assert rel_l2(spec[r], half_xmajor(o.spectrum(r), False)) <= 1e-5
+    g.close()
+
+
+def test_3x2k_graph_plain_and_observables(sft, oracle_mod):
+    w = W.model_a_64(n=[96, 96], replicas=2, sigma0=0.3)
+    a, b = gpu_stepper(sft, w), gpu_stepper(sft, w)
+    f = W.initial_fields(w).astype(np.float32)
+    a.set_field(f)
+    b.set_field(f)
+    a.step(53)
+    b.step_plain(53)
+    assert np.array_equal(a.spectrum().view(np.uint64), b.spectrum().view(np.uint64))
+    a.close()
+    b.close()
+    # S(k) shells, their mode counts and the roughness against the oracle
+    g, o = start_pair(sft, oracle_mod, w)
+    g.step(10)
+    o.step(10)
+    sk = g.observe(sft.SFT_OBS_SK)
+    ns = g.nshells()
+    ov, oc = o.shells(0)
+    assert np.array_equal(sk[ns:], oc)
+    assert np.allclose(sk[:ns], ov, rtol=2e-5, atol=1e-12 * np.abs(ov).max())
+    assert np.allclose(g.observe(sft.SFT_OBS_ROUGHNESS), o.roughness(), rtol=2e-5)
+    g.close()
