@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--workload", default="model_b_1024",
                     choices=["model_b_1024", "model_a_64", "kpz_ensemble", "cgl_2048", "model_a_128_3d",
                              "model_a_128_3d_tangent", "sde0d", "dynamics", "model_b_1024_phase_shift",
-                             "model_b_1024_real_space_noise"],
+                             "model_b_1024_real_space_noise", "model_b_768"],
                     help="model_b_1024 is the headline; the others print their own line for the other workloads")
     return ap.parse_args()
 
@@ -505,6 +505,8 @@ def run_other(args):
             w = W.model_a_64(replicas=1024)
         elif args.workload == "model_b_1024_phase_shift":
             w = W.model_b_1024(replicas=64, dealias=2)
+        elif args.workload == "model_b_768":
+            w = W.model_b_1024(n=[768, 768], replicas=64)
         elif args.workload == "model_b_1024_real_space_noise":
             w = W.model_b_1024(replicas=64)
             noise_space = 1
