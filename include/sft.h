@@ -96,8 +96,9 @@ typedef struct {
     int d;             /* 1, 2 or 3 */
     int n[3];          /* points per axis (x first), all equal (isotropic): powers of two, or, for
                         * 2-D real fields (Model A/B, KPZ) with Fourier-space noise and truncation
-                        * (or none), 3 x 2^k with 48 <= n <= 768 (a radix-3 pass ahead of the
-                        * radix-4/2 passes; no tangent/adjoint, dynamic recording or batches) */
+                        * (or none), p x 2^k with p in {3, 5, 7} and 16p <= n <= 768 (a radix-p
+                        * pass ahead of the radix-4/2 passes; no tangent/adjoint, dynamic recording
+                        * or batches) */
     double dx[3];      /* lattice spacing per axis; all equal */
     int replicas;      /* R >= 1 independent noise realisations */
     sft_model model;

@@ -121,18 +121,20 @@ __device__ __forceinline__ float2 normal_pair_for_index(uint64_t seed, uint64_t 
 #define SFT_EMAX 16
 #endif
 //
-// Lines of N = 3 x 2^k points (MIXED) take 12 values per thread: one radix-3
-// pass, then radix-4 passes and a radix-2 remainder.
+// Lines of N = p x 2^k points with an odd prime p in {3, 5, 7} (MIXED) take 4p
+// values per thread: one radix-p pass, then radix-4 passes and a radix-2
+// remainder.
 template <int N, int EM = SFT_EMAX>
 struct FftPlan {
-    static constexpr bool MIXED = N % 3 == 0;
-    static_assert(N >= 2 && ((N & (N - 1)) == 0 || (MIXED && N >= 12 && ((N / 3) & (N / 3 - 1)) == 0)),
-                  "2^k or 3 x 2^k points");
+    static constexpr int PR = N % 3 == 0 ? 3 : (N % 5 == 0 ? 5 : (N % 7 == 0 ? 7 : 1));  // odd factor
+    static constexpr bool MIXED = PR > 1;
+    static_assert(N >= 2 && ((N & (N - 1)) == 0 || (MIXED && N >= 4 * PR && ((N / PR) & (N / PR - 1)) == 0)),
+                  "2^k or p x 2^k points, p in {3, 5, 7}");
     static constexpr int log2(int v) { return v <= 1 ? 0 : 1 + log2(v / 2); }
-    static constexpr int L = log2(MIXED ? N / 3 : N);  // the power-of-two factor
-    static constexpr int E = MIXED ? 12 : (N <= 16 ? N : (N >= 512 ? EM : (N <= 32 && EM >= 32 ? N : 16)));
+    static constexpr int L = log2(MIXED ? N / PR : N);  // the power-of-two factor
+    static constexpr int E = MIXED ? 4 * PR : (N <= 16 ? N : (N >= 512 ? EM : (N <= 32 && EM >= 32 ? N : 16)));
     static constexpr int T = N / E;
-    static constexpr int R0 = MIXED ? 3 : E;  // first radix
+    static constexpr int R0 = MIXED ? PR : E;  // first radix
     static constexpr int E2 = MIXED ? 4 : E;  // radix of the power-of-two passes
     // remaining log2 after the first pass, split into radix-E2 passes and a remainder
     static constexpr int LE = log2(E2);
@@ -210,9 +212,64 @@ __device__ constexpr int bitrev(int k) {
 
 // In-register DFT of R values (R = 1, 2, 4, ..., 32): radix-2 decimation in
 // frequency, then the bit-reversal permutation (resolved at compile time).
+// cos and sin of 2 pi j / R for the radix-5 and radix-7 passes
+__device__ constexpr float kCos5[5] = {1.0f, 0.309016994374947451f, -0.809016994374947340f, -0.809016994374947562f,
+                                       0.309016994374947229f};
+__device__ constexpr float kSin5[5] = {0.0f, 0.951056516295153531f, 0.587785252292473248f, -0.587785252292473026f,
+                                       -0.951056516295153642f};
+__device__ constexpr float kCos7[7] = {1.0f, 0.623489801858733594f, -0.222520933956314337f, -0.900968867902419035f,
+                                       -0.900968867902419146f, -0.222520933956314587f, 0.623489801858733372f};
+__device__ constexpr float kSin7[7] = {0.0f, 0.781831482468029804f, 0.974927912181823619f, 0.433883739117558231f,
+                                       -0.433883739117558009f, -0.974927912181823619f, -0.781831482468029915f};
+
+// DFT of an odd number R of values from its definition, pairing m with R - m:
+// with s_m = x_m + x_{R-m}, d_m = x_m - x_{R-m} and theta = 2 pi k m / R,
+// A_k = x_0 + sum_m s_m cos(theta), B_k = sum_m d_m sin(theta), and
+// y_k = A_k -+ i B_k, y_{R-k} = A_k +- i B_k (forward / inverse).
+template <int R>
+__device__ __forceinline__ float odd_cos(int j) {
+    if constexpr (R == 5) return kCos5[j]; else return kCos7[j];
+}
+template <int R>
+__device__ __forceinline__ float odd_sin(int j) {
+    if constexpr (R == 5) return kSin5[j]; else return kSin7[j];
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_odd(float2* x) {
+    constexpr int H = (R - 1) / 2;
+    float2 s[H], d[H];
+    float2 y0 = x[0];
+#pragma unroll
+    for (int m = 1; m <= H; ++m) {
+        s[m - 1] = cadd(x[m], x[R - m]);
+        d[m - 1] = csub(x[m], x[R - m]);
+        y0 = cadd(y0, s[m - 1]);
+    }
+    float2 y[R];
+    y[0] = y0;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        float2 A = x[0], B = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 1; m <= H; ++m) {
+            const float c = odd_cos<R>((k * m) % R), sv = odd_sin<R>((k * m) % R);
+            A = make_float2(A.x + c * s[m - 1].x, A.y + c * s[m - 1].y);
+            B = make_float2(B.x + sv * d[m - 1].x, B.y + sv * d[m - 1].y);
+        }
+        const float2 iB = make_float2(-B.y, B.x);
+        y[k] = INV ? cadd(A, iB) : csub(A, iB);
+        y[R - k] = INV ? csub(A, iB) : cadd(A, iB);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = y[k];
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft_reg(float2* x) {
-    if constexpr (R == 3) {
+    if constexpr (R == 5 || R == 7) {
+        dft_odd<R, INV>(x);
+    } else if constexpr (R == 3) {
         // y1 = a + w b + w^2 c, y2 = a + w^2 b + w c with w = e^{-+2 pi i / 3} = -1/2 -+ i sqrt(3)/2
         const float2 a = x[0], s = cadd(x[1], x[2]), d = csub(x[1], x[2]);
         const float2 t = make_float2(a.x - 0.5f * s.x, a.y - 0.5f * s.y);

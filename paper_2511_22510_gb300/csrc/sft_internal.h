@@ -91,7 +91,9 @@ bool k1_use_cluster(int nx, int R, int mode);  // whether a 1-D launch of R repl
 cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape = 0);
 cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape = 0);
 int k2_row_shapes(int nx);  // schedule variants of the 2-D row pass for lattices of nx points
-bool k2_mixed_size(int n);   // 3 x 2^k points (48 .. 768): 2-D real fields, transforms and the step only
+cudaError_t launch_k2_rows_mixed(const StepArgs& a, int mode, int nl, cudaStream_t s);  // p x 2^k rows
+cudaError_t launch_k2_cols_mixed(const StepArgs& a, int mode, int nl, cudaStream_t s);  // p x 2^k columns
+bool k2_mixed_size(int n);   // p x 2^k points, p in {3, 5, 7}, 16p .. 768: 2-D real fields, transforms and step only
 int k2_col_shapes(int ny);  // schedule variants of the 2-D column pass for columns of ny points
 cudaError_t launch_k2_cols_pipe(const StepArgs& a, int nl, cudaStream_t s);
 cudaError_t launch_k3_planes(const StepArgs& a, int mode, int nl, cudaStream_t s);

@@ -466,6 +466,11 @@ MIXED_CASES = [
     ("model_a_192_nodealias", W.model_a_64(n=[192, 192], dealias=0, sigma0=0.3), 40),
     ("model_b_384_setd1_R3", W.model_b_1024(n=[384, 384], replicas=3, sigma0=0.3), 10),
     ("model_b_768_setd1", W.model_b_1024(n=[768, 768], h=0.05), 3),
+    ("model_a_80_setd1_R2", W.model_a_64(n=[80, 80], replicas=2, sigma0=0.3), 100),
+    ("kpz_2d_160_setd2", W.kpz_2d(n=[160, 160], scheme=2, h=0.005), 60),
+    ("model_b_640_setd1", W.model_b_1024(n=[640, 640], h=0.05), 3),
+    ("model_a_112_em_R2", W.model_a_64(n=[112, 112], replicas=2, scheme=0, sigma0=0.3), 100),
+    ("model_b_448_setd2", W.model_b_1024(n=[448, 448], scheme=2, h=0.025, sigma0=0.3), 5),
 ]
 
 

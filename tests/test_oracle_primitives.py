@@ -37,9 +37,10 @@ def test_bruteforce_dft_matches_numpy(oracle_mod, shape):
     assert np.abs(oracle_mod.dft_naive(x, +1) - refi).max() <= 1e-12 * np.abs(refi).max()
 
 
-@pytest.mark.parametrize("shape", [(96,), (48, 48), (24, 96), (192, 12)])
+@pytest.mark.parametrize("shape", [(96,), (48, 48), (24, 96), (192, 12), (80,), (160, 40), (112,), (56, 112)])
 def test_fft_of_3x2k_lengths_matches_numpy(oracle_mod, shape):
-    """Lattices of 3 x 2^k points: the oracle's split-radix transform against numpy's FFT."""
+    """Lattices of p x 2^k points (p = 3, 5, 7): the oracle's split-radix transform
+    against numpy's FFT."""
     rng = np.random.default_rng(4)
     x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
     ref = np.fft.fftn(x)
