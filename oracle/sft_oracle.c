@@ -660,7 +660,7 @@ or_state* or_create(const or_config* cfg) {
     st->cfg = *cfg;
     st->n[0] = st->n[1] = st->n[2] = 1;
     for (int ax = 0; ax < cfg->d; ++ax) {
-        if (cfg->n[ax] < 2 || cfg->n[ax] % 2 || !(cfg->dx[ax] > 0)) {
+        if (cfg->n[ax] < 1 || (cfg->n[ax] > 1 && cfg->n[ax] % 2) || !(cfg->dx[ax] > 0)) {  /* 1 or even */
             free(st);
             return NULL;
         }
