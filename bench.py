@@ -242,8 +242,11 @@ def run_reference(args):
     f0 = W.initial_fields(w, replicas=1)[0].astype(np.float32)
     o = oracle.Oracle(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
     o.set_field(0, f0.astype(np.float64))
-    if args.warmup > 0:
+    warm = 0
+    t_warm = time.perf_counter()
+    while warm < args.warmup and time.perf_counter() - t_warm < 30.0:  # warm-up steps, at most ~30 s
         o.step(1)
+        warm += 1
     times = []
     t_start = time.perf_counter()
     for _ in range(max(1, args.steps)):
@@ -256,7 +259,7 @@ def run_reference(args):
     value = w.sites * len(times) / el / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": len(times),
-        "warmup": 1 if args.warmup > 0 else 0, "ms_per_step": 1e3 * el / len(times), "higher_is_better": True,
+        "warmup": warm, "ms_per_step": 1e3 * el / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "model_b_1024_%s_h%g" % (scheme_name(args.scheme), args.h),
                    "lattice": "%dx%d" % (args.n, args.n), "replicas": 1},
