@@ -1939,7 +1939,7 @@ sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, in
             CK(cudaEventRecord(e[2], ctx->stream));
         }
         CK(launch_advance(ctx->dstep, 1, ctx->stream));
-        ctx->launches += nk + 1;
+        ctx->launches += ctx->launches_per_step + 1;  // the step's kernels (with any noise transform) + advance
     }
     ctx->step += nsteps;
     CK(cudaStreamSynchronize(ctx->stream));
