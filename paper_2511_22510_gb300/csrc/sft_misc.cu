@@ -1,6 +1,7 @@
 // sft_misc.cu -- per-context set-up and bookkeeping kernels: the FP64
 // coefficient tables, the Philox initial condition, the step counter, and the
 // shell-averaged observables.
+#include <type_traits>
 #include "sft_step_common.cuh"
 
 namespace sft {
@@ -221,15 +222,26 @@ cudaError_t launch_advance(long long* step_base, int by, cudaStream_t s) {
 // the stored half carries weight 2 off the planes a_x in {0, nx/2} (their
 // conjugate partners are not stored) and 1 on them.
 __device__ __forceinline__ int shell_of(long long q) {
-    long long j = (long long)sqrt((double)q);
+    // q < 2^31 on every built lattice: a single-precision root is within one of
+    // ceil(sqrt(q)); the integer steps make it exact
+    long long j = (long long)sqrtf((float)q);
     while (j * j < q) ++j;
     while (j > 0 && (j - 1) * (j - 1) >= q) --j;
     return (int)j;
 }
 
+// Modes per thread run: a thread takes kObsRun consecutive modes (along a_y) and
+// sums them per shell in registers, touching the shell accumulators once per
+// change of shell instead of once per mode.
+constexpr int kObsRun = 16;
+
 // Shell sums go through a per-block shared array when it fits (local = true),
-// else straight to the global accumulators.
+// else straight to the global accumulators.  A run's partial sum is FP32 for
+// the non-negative sums |phi|^2 and |ref|^2 (at most kObsRun terms) and FP64 for
+// the signed two-time products; every accumulation beyond a run is FP64.
+template <int KIND>
 __global__ void k_observe(const ObsArgs o, bool local) {
+    using Acc = typename std::conditional<KIND == 1, double, float>::type;
     extern __shared__ double acc[];
     const int r = blockIdx.y;
     if (local)
@@ -237,59 +249,91 @@ __global__ void k_observe(const ObsArgs o, bool local) {
     __shared__ double rough;
     if (threadIdx.x == 0) rough = 0.0;
     __syncthreads();
-    const long long nmodes = (long long)o.hx * o.nz * o.ny;
-    const long long chunk = (nmodes + gridDim.x - 1) / gridDim.x;
-    const long long m0 = blockIdx.x * chunk;
-    const long long m1 = min(nmodes, m0 + chunk);
+    const int nmodes = o.hx * o.nz * o.ny;  // per replica, < 2^31 on every built lattice
+    const int per = ((nmodes + gridDim.x - 1) / gridDim.x + kObsRun - 1) / kObsRun * kObsRun;
+    const int m0 = blockIdx.x * per;
+    const int m1 = min(nmodes, m0 + per);
+    const float2* phi = o.phi ? o.phi + (size_t)r * nmodes : nullptr;
+    const float2* ref = o.ref ? o.ref + (size_t)r * nmodes : nullptr;
+    double* gsum = o.shell_sum + (size_t)r * o.nshells;
     double my_rough = 0.0;
-    for (long long m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
-        const int ay = (int)(m % o.ny);
-        const int az = (int)((m / o.ny) % o.nz);
-        const int ax = (int)(m / ((long long)o.ny * o.nz));
-        const long long sx = o.complex_field ? signed_idx(ax, o.nx) : ax;
-        const long long sy = signed_idx(ay, o.ny), sz = signed_idx(az, o.nz);
-        const long long q = sx * sx + sy * sy + sz * sz;
-        const double w = (!o.complex_field && ax != 0 && 2 * ax != o.nx) ? 2.0 : 1.0;
-        const size_t idx = (size_t)r * nmodes + m;
-        const float2 v = o.phi ? o.phi[idx] : make_float2(0.f, 0.f);
-        double val;
-        if (o.kind == 0) {
-            val = (double)v.x * v.x + (double)v.y * v.y;
-            if (q != 0) my_rough += w * val;
-        } else if (o.kind == 1) {
-            const float2 u = o.ref[idx];
-            val = (double)v.x * u.x + (double)v.y * u.y;
-        } else {
-            const float2 u = o.ref[idx];
-            val = (double)u.x * u.x + (double)u.y * u.y;
+    for (int base = m0 + threadIdx.x * kObsRun; base < m1; base += blockDim.x * kObsRun) {
+        int cur_j = -1;
+        Acc cur = 0, run_rough = 0;
+        const int nrun = min(kObsRun, m1 - base);
+        for (int i = 0; i < nrun; ++i) {
+            const int m = base + i;
+            const int ay = m % o.ny;
+            const int rest = m / o.ny;
+            const int az = rest % o.nz;
+            const int ax = rest / o.nz;
+            const long long sx = o.complex_field ? signed_idx(ax, o.nx) : ax;
+            const long long sy = signed_idx(ay, o.ny), sz = signed_idx(az, o.nz);
+            const long long q = sx * sx + sy * sy + sz * sz;
+            const float w = (!o.complex_field && ax != 0 && 2 * ax != o.nx) ? 2.f : 1.f;
+            Acc val;
+            if constexpr (KIND == 0) {
+                const float2 v = phi ? phi[m] : make_float2(0.f, 0.f);
+                val = (Acc)(v.x * v.x + v.y * v.y);
+            } else if constexpr (KIND == 1) {
+                const float2 v = phi[m], u = ref[m];
+                val = (double)v.x * u.x + (double)v.y * u.y;
+            } else {
+                const float2 u = ref[m];
+                val = (Acc)(u.x * u.x + u.y * u.y);
+            }
+            const int j = shell_of(q);
+            if (j != cur_j) {
+                if (cur_j >= 0) {
+                    if (local)
+                        atomicAdd(&acc[cur_j], (double)cur * o.norm);
+                    else
+                        atomicAdd(&gsum[cur_j], (double)cur * o.norm);
+                }
+                cur_j = j;
+                cur = 0;
+            }
+            cur += w * val;
+            if (KIND == 0 && q != 0) run_rough += w * val;
         }
-        if (local)
-            atomicAdd(&acc[shell_of(q)], w * val * o.norm);
-        else
-            atomicAdd(&o.shell_sum[(size_t)r * o.nshells + shell_of(q)], w * val * o.norm);
+        if (cur_j >= 0) {
+            if (local)
+                atomicAdd(&acc[cur_j], (double)cur * o.norm);
+            else
+                atomicAdd(&gsum[cur_j], (double)cur * o.norm);
+        }
+        my_rough += (double)run_rough;
     }
-    if (o.rough) atomicAdd(&rough, my_rough);
+    if (KIND == 0 && o.rough) atomicAdd(&rough, my_rough);
     __syncthreads();
     if (local)
         for (int j = threadIdx.x; j < o.nshells; j += blockDim.x)
-            if (acc[j] != 0.0) atomicAdd(&o.shell_sum[(size_t)r * o.nshells + j], acc[j]);
-    if (threadIdx.x == 0 && o.rough) atomicAdd(&o.rough[r], rough);
+            if (acc[j] != 0.0) atomicAdd(&gsum[j], acc[j]);
+    if (threadIdx.x == 0 && KIND == 0 && o.rough) atomicAdd(&o.rough[r], rough);
 }
 
 cudaError_t launch_observe(const ObsArgs& o, cudaStream_t s) {
     const long long nmodes = (long long)o.hx * o.nz * o.ny;
-    long long nb = (nmodes + 1023) / 1024;
-    int blocks = (int)(nb < 1184 ? nb : 1184);
-    if (blocks < 1) blocks = 1;
-    dim3 grid(blocks, o.R);
+    // about four blocks per SM over all replicas, each over whole runs of modes
+    const long long runs = (nmodes + kObsRun - 1) / kObsRun;
+    long long nb = (608 + o.R - 1) / o.R;
+    const long long cap = (runs + 255) / 256;
+    if (nb > cap) nb = cap;
+    if (nb < 1) nb = 1;
+    dim3 grid((unsigned)nb, o.R);
     const bool local = sizeof(double) * (size_t)o.nshells <= 96 * 1024;
     const size_t sm = local ? sizeof(double) * (size_t)o.nshells : 0;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_observe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
-    k_observe<<<grid, 256, sm, s>>>(o, local);
-    return cudaGetLastError();
+    auto run = [&](auto kern) -> cudaError_t {
+        if (sm > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<grid, 256, sm, s>>>(o, local);
+        return cudaGetLastError();
+    };
+    if (o.kind == 1) return run(k_observe<1>);
+    if (o.kind == 2) return run(k_observe<2>);
+    return run(k_observe<0>);
 }
 
 }  // namespace sft
