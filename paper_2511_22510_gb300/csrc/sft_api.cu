@@ -372,13 +372,20 @@ static sft_status enqueue_batch_step(sft_ctx* ctx, int k) {
 // left set up for the column pass.
 static sft_status enqueue_front(sft_ctx* ctx, StepArgs& a, int k) {
     if (ctx->noise_spec) {
-        // real-space noise (Sec. IV step 2): iid N(0, 1) per site into the real-space buffer, its
-        // forward transform into noise_spec (Q as scratch, overwritten by the row pass below);
-        // the column pass reads eta_a = DFT[eta]_a / sqrt(N^d)
-        CK(launch_noise_real(ctx->real, ctx->sites, ctx->R, ctx->rep0, ctx->cfg.seed, ctx->dstep, k, ctx->stream));
-        sft_status s = forward_from_buffer(ctx, 0, ctx->R, ctx->noise_spec);
-        if (s != SFT_OK) return s;
-        ctx->launches -= 2;  // counted per step in launches_per_step
+        // real-space noise (Sec. IV step 2): iid N(0, 1) per site, drawn inside the forward row pass
+        // (Q as scratch, overwritten by the step's row pass below), then the column transform into
+        // noise_spec; the column pass reads eta_a = DFT[eta]_a / sqrt(N^d)
+        StepArgs f = a;
+        f.k_in_chunk = k;
+        f.ncols = ctx->hx;
+        f.qout = ctx->Q;
+        f.tw_a = ctx->tw.get(ctx->nx / 2);
+        f.tw_b = ctx->tw.get(ctx->nx);
+        CK(launch_rows(ctx, f, MODE_FWD_NOISE));
+        f.qin = ctx->Q;
+        f.phi = ctx->noise_spec;
+        f.tw_a = ctx->tw.get(ctx->ny);
+        CK(launch_second(ctx, f, MODE_FWD));
         a.noise_in = ctx->noise_spec;
         a.noise_scale = (float)(1.0 / std::sqrt((double)ctx->sites));
     }
@@ -860,7 +867,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
         }
     }
     ctx->launches_per_step = ctx->d == 1 ? 1 : 2;
-    if (cfg->noise_space == 1) ctx->launches_per_step += 3;  // draw + forward transform of the noise
+    if (cfg->noise_space == 1) ctx->launches_per_step += 2;  // forward transform of the noise (drawn in its row pass)
     {
         // column-pass variant: chosen by the plan autotuner unless SFT_COLUMN_PASS forces the
         // persistent bulk-copy pipelined kernel ("pipelined", where it is built) or the

@@ -17,7 +17,8 @@ enum KernelMode {
     MODE_ADJ_PRIME = 6,
     MODE_STEP_REC = 7,  // the step, also recording the state and the nonlinear force (dynamic observables)
     MODE_STEP_RSN = 8,  // the step with the noise read from a transformed real-space draw
-    MODE_STEP_PS = 9    // the step with phase-shift dealiasing (grids shifted by half a cell)
+    MODE_STEP_PS = 9,   // the step with phase-shift dealiasing (grids shifted by half a cell)
+    MODE_FWD_NOISE = 10 // row pass: forward transform of the step's real-space noise, drawn in registers
 };
 
 // Everything a step kernel needs, passed by value.
@@ -151,10 +152,6 @@ cudaError_t launch_init_random(float* real_out, float2* cplx_out, long long site
 // unit-variance Fourier noise of one step for every stored mode (diagnostics)
 cudaError_t launch_draw_noise(int nx, int ny, int nz, int hx, int cplx, int R, int rep0, uint64_t seed,
                               long long step, float2* out, cudaStream_t s);
-// real-space noise of one step: iid N(0,1) per site (Philox tag 3) into real_out;
-// the step is *step_base + k (graph replays) or, with step_base NULL, k
-cudaError_t launch_noise_real(float* real_out, long long sites, int R, int rep0, uint64_t seed,
-                              const long long* step_base, long long k, cudaStream_t s);
 // step counter advance (one thread)
 cudaError_t launch_advance(long long* step_base, int by, cudaStream_t s);
 

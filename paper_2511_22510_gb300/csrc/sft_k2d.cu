@@ -4,6 +4,7 @@
 
 namespace sft {
 
+// (the forward transform of the real-space noise is instantiated here, for power-of-two rows)
 int k2_row_shapes(int nx) { return (nx & (nx - 1)) == 0 ? 3 : 1; }
 
 cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape) {

@@ -238,6 +238,15 @@ __global__ void __launch_bounds__(RowCfg<M, SH>::THREADS, RowCfg<M, SH>::MINB) k
             const int m = t + T * e;
             z[e] = yok ? *reinterpret_cast<const float2*>(src + 2 * m) : czero();
         }
+    } else if constexpr (MODE == MODE_FWD_NOISE) {
+        // real-space noise of the step (Sec. IV step 2): site s = y nx + x takes normal s & 3 of
+        // Philox(ctr = (s >> 2, step, replica, 3)); the packed pair m of row y (sites 2m, 2m + 1) is
+        // normal pair y M + m, drawn here instead of being read from memory
+        const long long step = current_step(a);
+#pragma unroll
+        for (int e = 0; e < E; e += 2)
+            team_normal_pair<T>(a.seed, (uint64_t)(yok ? y : 0) * M, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep),
+                                z[e], z[e + 1], 3u);
     } else {
         load_tile<C>(tile, a.pin, rowbase, ncols, ny, y0);
         if constexpr (GRAD) load_tile<C>(tile + ROWS * TS, a.pyin, rowbase, ncols, ny, y0);
@@ -335,6 +344,7 @@ static cudaError_t rows_step(const StepArgs& a, cudaStream_t s, int shape) {
 template <int M>
 static cudaError_t rows_for(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape) {
     if (mode == MODE_FWD) return run_rows<M, NL_CUBIC, MODE_FWD>(a, s);
+    if (mode == MODE_FWD_NOISE) return run_rows<M, NL_CUBIC, MODE_FWD_NOISE>(a, s);
     if (mode == MODE_INV) return run_rows<M, NL_CUBIC, MODE_INV>(a, s);
     if (mode == MODE_STEP && nl == NL_CUBIC) return rows_step<M, NL_CUBIC>(a, s, shape);
     if (mode == MODE_STEP && nl == NL_GRAD2) return rows_step<M, NL_GRAD2>(a, s, shape);

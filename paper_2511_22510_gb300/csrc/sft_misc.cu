@@ -174,33 +174,6 @@ __global__ void k_init_random(float* real_out, float2* cplx_out, long long sites
     }
 }
 
-// Real-space noise of one step (Sec. IV step 2, the real-space alternative):
-// site s of replica r takes normal s & 3 of Philox(ctr = (s >> 2, step, r, 3)).
-__global__ void k_noise_real(float* real_out, long long sites, int rep0, uint64_t seed, const long long* step_base,
-                             long long k) {
-    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;
-    const long long s0 = 4 * g;
-    if (s0 >= sites) return;
-    const long long step = step_base ? *step_base + k : k;
-    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)step, (uint32_t)(rep0 + r), 3u), key);
-    const float2 a = recipe_bm_pair(w.x, w.y), b = recipe_bm_pair(w.z, w.w);
-    const float z[4] = {a.x, a.y, b.x, b.y};
-    for (int i = 0; i < 4 && s0 + i < sites; ++i) real_out[(size_t)r * sites + s0 + i] = z[i];
-}
-
-cudaError_t launch_noise_real(float* real_out, long long sites, int R, int rep0, uint64_t seed,
-                              const long long* step_base, long long k, cudaStream_t s) {
-    const long long threads = (sites + 3) / 4;
-    for (int r0 = 0; r0 < R; r0 += 65535) {  // grid.y holds at most 65535 replicas per launch
-        const int nr = R - r0 < 65535 ? R - r0 : 65535;
-        k_noise_real<<<dim3((unsigned)((threads + 255) / 256), nr), 256, 0, s>>>(real_out + (size_t)r0 * sites, sites,
-                                                                                 rep0 + r0, seed, step_base, k);
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t launch_init_random(float* real_out, float2* cplx_out, long long sites, int R, int rep0, uint64_t seed,
                                float sigma, cudaStream_t s) {
     const long long per = real_out ? 4 : 2;

@@ -73,17 +73,17 @@ __device__ __forceinline__ float2 fourier_noise(uint64_t seed, uint64_t j, uint3
 // call this (warp shuffles).
 template <int T>
 __device__ __forceinline__ void team_normal_pair(uint64_t seed, uint64_t jbase, int t, int e, uint32_t step,
-                                                 uint32_t replica, float2& z0, float2& z1) {
+                                                 uint32_t replica, float2& z0, float2& z1, uint32_t tag = 0u) {
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     if constexpr (T == 1) {
         const uint64_t j = jbase + e;
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 1), step, replica, 0u), key);
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 1), step, replica, tag), key);
         z0 = recipe_bm_pair(w.x, w.y);
         z1 = recipe_bm_pair(w.z, w.w);
     } else {
         const bool odd = (t & 1) != 0;
         const uint64_t j = jbase + t + (uint64_t)T * (e + (odd ? 1 : 0));
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 1), step, replica, 0u), key);
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 1), step, replica, tag), key);
         const float2 p0 = recipe_bm_pair(w.x, w.y), p1 = recipe_bm_pair(w.z, w.w);
         const float2 send = odd ? p0 : p1;
         float2 recv;

@@ -62,7 +62,7 @@ def test_schedule_profile_and_launch_count(sft, name, w, extra):
     prof = sft.sft_profile(g.ctx, 5)
     assert len(prof) == 3 and np.all(prof > 0) and abs(prof[0] + prof[1] - prof[2]) < 1e-6 * prof[2] + 1e-9
     per = sft.sft_launches_per_step(g.ctx)
-    assert per == (5 if extra.get("noise_space") else 2)
+    assert per == (4 if extra.get("noise_space") else 2)
     n0 = sft.sft_kernel_launches(g.ctx)
     g.step(40)  # graph chunks and plain steps
     g.sync()
