@@ -344,7 +344,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": warm,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded iid N(0, 0.01^2) fields, Philox noise)",
-        "config": {"workload": "model_b_1024_%s_h%g" % (scheme_name(w.scheme), w.h), "model": "Model B",
+        "config": {"workload": "model_b_1024_%s_h%g" % (scheme_name(w.scheme), w.h), "field": "Model B (conserved)",
                    "lattice": "%dx%d" % (w.n[0], w.n[1]), "replicas_per_gpu": R, "global_batch": R * ws,
                    "scheme": scheme_name(w.scheme), "h": w.h, "observe_every": OBS_EVERY,
                    "parallelism": "replicas x%d" % ws,
