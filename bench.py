@@ -229,6 +229,116 @@ def oracle_sample(w, nsteps, budget_s=25.0):
     return w.sites * done / el, done, f0, o.field(0)
 
 
+def _oracle_worker(job):
+    """One host process of the all-core oracle run: steps one replica of the
+    workload (replica offset `rep`), timed after a shared barrier."""
+    (cfg, rep, nsteps, barrier) = job
+    import oracle
+    w = W.model_b_1024(**cfg)
+    f0 = W.initial_fields(w, replicas=1, seed_offset=rep)[0].astype(np.float64)
+    o = oracle.Oracle(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias, replica0=rep)
+    o.set_field(0, f0)
+    barrier.wait()
+    t0 = time.perf_counter()
+    o.step(nsteps)
+    return time.perf_counter() - t0
+
+
+def host_cpu():
+    """Model name and logical core count of this host."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"model": model or "unknown", "logical_cores": os.cpu_count()}
+
+
+def oracle_all_cores(w, nsteps=2):
+    """The oracle as it stands on every host core: one spawned process per core,
+    each stepping its own replica of the workload (independent replicas, so the
+    cores share no work); throughput = all site-steps / the slowest process."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    n = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    cfg = dict(n=list(w.n), scheme=w.scheme, h=w.h)
+    with ctx.Manager() as man:
+        bar = man.Barrier(n)
+        with ctx.Pool(n) as pool:
+            times = pool.map(_oracle_worker, [(cfg, r, nsteps, bar) for r in range(n)])
+    el = max(times)
+    return {"value": w.sites * n * nsteps / el / 1e9, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": "FP64 oracle, %d processes (one per host core), each %d steps of its own %dx%d replica"
+                      % (n, nsteps, w.n[0], w.n[1]), "host": host_cpu()}
+
+
+def cufft_comparison(w, R, K, stream):
+    """Comparison column (not the product path): the same SETD1 step written
+    with torch.fft (cuFFT R2C/C2R) and elementwise torch ops, noise from
+    torch.randn without the Hermitian fix-up, on R replicas; Gsite-steps/s over K
+    steps with CUDA events."""
+    import torch
+    nx, ny = w.n
+    G, r, u, T = w.p[:4]
+    dev = "cuda"
+    kx = 2 * math.pi * torch.fft.rfftfreq(nx, d=w.dx[0], device=dev, dtype=torch.float64)
+    ky = 2 * math.pi * torch.fft.fftfreq(ny, d=w.dx[1], device=dev, dtype=torch.float64)
+    k2 = ky[:, None] ** 2 + kx[None, :] ** 2
+    ix = torch.arange(nx // 2 + 1, device=dev)[None, :]
+    iy = torch.fft.fftfreq(ny, d=1.0 / ny, device=dev).abs()[:, None]
+    mask = ((3 * ix < nx) & (3 * iy < ny)).to(torch.float32)
+    c = -G * k2 * (r + k2)
+    ch = c * w.h
+    f1 = torch.exp(ch)
+    A = torch.where(c != 0, torch.expm1(ch) / torch.where(c != 0, c, torch.ones_like(c)), torch.full_like(c, w.h))
+    D = G * T * k2
+    two = 2 * ch
+    phi1 = torch.where(two != 0, torch.expm1(two) / torch.where(two != 0, two, torch.ones_like(two)),
+                       torch.ones_like(two))
+    g = (nx * ny / (nx * w.dx[0])) ** 1.0 * torch.sqrt(2 * D * w.h * phi1)
+    s_nl = (-G * u * k2).to(torch.float32) * mask
+    f1, A, g = f1.to(torch.float32), A.to(torch.float32), (g / math.sqrt(2)).to(torch.float32)
+    with torch.cuda.stream(stream):
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(w.seed)
+        phi = torch.fft.rfft2(0.01 * torch.randn(R, ny, nx, device=dev, generator=gen))
+
+        def step(phi):
+            psi = torch.fft.irfft2(phi * mask, s=(ny, nx))
+            F = s_nl * torch.fft.rfft2(psi * psi * psi)
+            eta = torch.complex(torch.randn(phi.shape, device=dev, generator=gen),
+                                torch.randn(phi.shape, device=dev, generator=gen))
+            return f1 * phi + A * F + g * eta
+
+        for _ in range(5):
+            phi = step(phi)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(K):
+            phi = step(phi)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    return {"value": w.sites * R * K / (ms * 1e-3) / 1e9, "unit": UNIT, "replicas": R, "steps": K,
+            "form": "torch.fft (cuFFT R2C/C2R) + elementwise torch ops, torch.randn noise; comparison only"}
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores: each timed step is one FP64
     SETD step of one replica of the workload (a bounded sample), as many as fit
@@ -385,6 +495,26 @@ def run_gpu(args):
         line["cpu_baseline"] = {"value": ov / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "FP64 serial oracle, %d steps of one %dx%d replica" % (od, w.n[0], w.n[1])}
         line["error_vs_fp64"] = {"rel_l2_field": err, "steps": od, "tolerance": 1e-5}
+        line["cpu_baseline_all_cores"] = oracle_all_cores(w)
+        # the batched path at other replica counts (R = 1: the state fits in L2)
+        sweep = {}
+        for Rs in (1, 16):
+            gs = sft.Stepper(w.d, w.n, w.dx, Rs, w.model, w.p, w.scheme, w.h, w.seed, stream=stream.cuda_stream)
+            gs.set_field(f0[:Rs])
+            gs.step(64)
+            gs.sync()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            gs.step(400)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sweep[str(Rs)] = w.sites * Rs * 400 / (a.elapsed_time(b) * 1e-3) / 1e9
+            gs.close()
+        sweep[str(R)] = value
+        line["replica_sweep"] = {"unit": UNIT, "values": sweep,
+                                 "note": "batched graph path, 400 steps without S(k); R = 1 is L2-resident"}
+        line["cufft_comparison"] = cufft_comparison(w, R, 50, stream)
     # end to end through the public API with host buffers (every rank)
     pin = torch.from_numpy(f0).pin_memory()
     host_in = pin.numpy()
