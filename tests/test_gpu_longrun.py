@@ -1,0 +1,81 @@
+"""Long-run statistics of interacting models, GPU against the oracle.  After
+many steps the two sides are no longer comparable point by point (the
+dynamics amplify rounding), so each side runs its own independent ensemble
+(disjoint Philox replica counters and initial fields) and the ensemble means
+of the observables must agree within 4 combined standard errors:
+- Model B critical quench (the headline workload's parameters, 32^2): shell
+  averages of |phi_a|^2 (App. C) for the first shells after 400 steps;
+- KPZ in 1-D (the ensemble workload's parameters, 256 sites): the width w^2;
+- CGL (the 2-D workload's parameters, 32^2, SETD2): the mean |A|^2 and the
+  shell average of |A_a|^2 of the first shells."""
+import numpy as np
+import pytest
+
+import sft_inputs as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sft():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_22510_gb300 as m
+    m.load_library()
+    return m
+
+
+def shell_means(full, nshell):
+    """Per-replica shell averages of |F_a|^2 (F: (R, ny, nx) full spectra), shells j = ceil(|a|) = 1..nshell."""
+    R, ny, nx = full.shape
+    ay, ax = np.meshgrid(np.fft.fftfreq(ny, 1.0 / ny), np.fft.fftfreq(nx, 1.0 / nx), indexing="ij")
+    j = np.ceil(np.sqrt(ax ** 2 + ay ** 2) - 1e-12).astype(int)
+    p = np.abs(full) ** 2
+    return np.stack([p[:, j == s].mean(axis=1) for s in range(1, nshell + 1)], axis=1)
+
+
+def agree(x, y, z_max=4.0):
+    """Ensemble means of x and y (samples along axis 0) within z_max combined standard errors."""
+    se = np.sqrt(x.var(axis=0, ddof=1) / len(x) + y.var(axis=0, ddof=1) / len(y))
+    z = (x.mean(axis=0) - y.mean(axis=0)) / se
+    assert np.all(np.abs(z) < z_max), z
+    return z
+
+
+def run_pair(sft, oracle_mod, w, nsteps, R):
+    g = sft.Stepper(w.d, w.n, w.dx, R, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias, replica0=0)
+    f_gpu = W.initial_fields(w, replicas=R, seed_offset=0)
+    dt = np.complex64 if w.complex_field else np.float32
+    g.set_field(f_gpu.astype(dt))
+    g.step(nsteps)
+    a = g.field().astype(np.complex128 if w.complex_field else np.float64)
+    g.close()
+    o = oracle_mod.Oracle(w.d, w.n, w.dx, R, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias, replica0=R)
+    f_or = W.initial_fields(w, replicas=R, seed_offset=12345)
+    for r in range(R):
+        o.set_field(r, f_or[r].astype(dt).astype(np.complex128 if w.complex_field else np.float64))
+    o.step(nsteps)
+    b = np.stack([o.field(r) for r in range(R)])
+    return a, b
+
+
+def test_model_b_quench_structure_factor(sft, oracle_mod):
+    w = W.model_b_1024(n=[32, 32], h=0.05, sigma0=0.1)
+    a, b = run_pair(sft, oracle_mod, w, 400, 24)
+    agree(shell_means(np.fft.fft2(a), 6), shell_means(np.fft.fft2(b), 6))
+
+
+def test_kpz_1d_width(sft, oracle_mod):
+    w = W.kpz_1d(256, sigma0=0.0)
+    a, b = run_pair(sft, oracle_mod, w, 1000, 32)
+    wa = (a - a.mean(axis=1, keepdims=True)) ** 2
+    wb = (b - b.mean(axis=1, keepdims=True)) ** 2
+    agree(wa.mean(axis=1)[:, None], wb.mean(axis=1)[:, None])
+
+
+def test_cgl_amplitude_and_spectrum(sft, oracle_mod):
+    w = W.cgl_2048(n=[32, 32], sigma0=0.01)
+    a, b = run_pair(sft, oracle_mod, w, 300, 16)
+    agree((np.abs(a) ** 2).mean(axis=(1, 2))[:, None], (np.abs(b) ** 2).mean(axis=(1, 2))[:, None])
+    agree(shell_means(np.fft.fft2(a), 4), shell_means(np.fft.fft2(b), 4))
