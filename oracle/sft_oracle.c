@@ -208,7 +208,7 @@ static void fft1d_radix2(cplx* x, int n, int sign) {
     }
 }
 
-/* Lengths that are not powers of two (3 x 2^k lattices): radix-2 decimation in
+/* Lengths that are not powers of two (p x 2^k lattices, p odd): radix-2 decimation in
  * time down to an odd length, whose DFT is taken from its definition (phase
  * (k m mod n) / n of a turn). */
 static void fft1d_split(cplx* x, int n, int sign) {

@@ -458,7 +458,7 @@ def test_phase_shift_graph_plain_and_checkpoint(sft):
         s.close()
 
 
-# ------------------------------------------------------------------ lattices of 3 x 2^k points
+# ------------------------------------------------------------------ lattices of p x 2^k points (p = 3, 5, 7)
 MIXED_CASES = [
     ("model_a_48_setd1_R2", W.model_a_64(n=[48, 48], replicas=2, sigma0=0.3), 100),
     ("model_b_96_setd2", W.model_b_1024(n=[96, 96], scheme=2, h=0.025, sigma0=0.3), 100),
@@ -476,7 +476,7 @@ MIXED_CASES = [
 
 @pytest.mark.parametrize("name,w,nsteps", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
 def test_3x2k_lattice_step_parity(sft, oracle_mod, name, w, nsteps):
-    """Lattices of 3 x 2^k points: the radix-3 + radix-4/2 Stockham transforms of
+    """Lattices of p x 2^k points: the radix-p + radix-4/2 Stockham transforms of
     the row and column passes against the oracle's split-radix transform."""
     g, o = start_pair(sft, oracle_mod, w)
     g.step(nsteps)
