@@ -109,9 +109,9 @@ typedef struct {
     int dealias;       /* 1: 2/3-rule truncation (3|a_i| < n_i), 0: none, 2: phase-shift
                         * dealiasing (Sec. IV step 1): the nonlinear term is the mean over the
                         * 2^d grids shifted by half a cell along every subset of the axes, every
-                        * mode but the Nyquist ones kept (alias-free for the cubic term); built for
-                        * 2-D real fields with the cubic term and noise_space 0, at twice the P/Q
-                        * memory and about twice the transform work of a step */
+                        * mode but the Nyquist ones kept (alias-free for the cubic and the gradient-
+                        * squared terms); built for 2-D real fields (Model A/B, KPZ) with noise_space 0,
+                        * at twice the P/Q memory and two to four times the transform work of a step */
     int precision;     /* 0: FP32 state and transforms (only value supported) */
     void* stream;      /* cudaStream_t, or NULL for the default stream */
     int replica0;      /* global index of replica 0 (Philox counter word 2): ranks that shard one

@@ -674,8 +674,9 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
         return why = "lattices of p x 2^k points are built for 2-D real fields (Model A/B, KPZ) with Fourier-space "
                      "noise and 2/3 truncation (or none)",
                SFT_EUNSUPPORTED;
-    if (cfg->dealias == 2 && (cfg->d != 2 || cplx || nlk != NL_CUBIC || cfg->noise_space != 0))
-        return why = "phase-shift dealiasing is built for 2-D real fields with the cubic term and Fourier-space noise",
+    if (cfg->dealias == 2 && (cfg->d != 2 || cplx || (nlk != NL_CUBIC && nlk != NL_GRAD2) || cfg->noise_space != 0))
+        return why = "phase-shift dealiasing is built for 2-D real fields with the cubic or gradient-squared term and "
+                     "Fourier-space noise",
                SFT_EUNSUPPORTED;
     if (cfg->model == SFT_CUSTOM) {
         const int nl = cfg->custom_nl;
@@ -756,7 +757,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     const size_t pq = cfg->dealias == 2 ? 2 * ms : ms;
     bool ok = dalloc((void**)&ctx->phi, ms) && dalloc((void**)&ctx->Q, pq);
     if (ok && ctx->d >= 2) ok = dalloc((void**)&ctx->P, pq);
-    if (ok && ctx->d >= 2 && ctx->nl == NL_GRAD2) ok = dalloc((void**)&ctx->Py, ms);
+    if (ok && ctx->d >= 2 && ctx->nl == NL_GRAD2) ok = dalloc((void**)&ctx->Py, pq);
     if (ok && cfg->scheme == SFT_SETD2) ok = dalloc((void**)&ctx->fprev, ms);
     if (ok && cfg->noise_space == 1) ok = dalloc((void**)&ctx->noise_spec, ms);
     if (ok) {
@@ -783,7 +784,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     if (cudaMemset(ctx->phi, 0, ms) != cudaSuccess || cudaMemset(ctx->Q, 0, pq) != cudaSuccess)
         return cleanup(SFT_ECUDA);
     if (ctx->P && cudaMemset(ctx->P, 0, pq) != cudaSuccess) return cleanup(SFT_ECUDA);
-    if (ctx->Py && cudaMemset(ctx->Py, 0, ms) != cudaSuccess) return cleanup(SFT_ECUDA);
+    if (ctx->Py && cudaMemset(ctx->Py, 0, pq) != cudaSuccess) return cleanup(SFT_ECUDA);
     if (ctx->fprev && cudaMemset(ctx->fprev, 0, ms) != cudaSuccess) return cleanup(SFT_ECUDA);
     long long init[4] = {0, cfg->scheme == SFT_SETD2 ? 0 : -1, (long long)0x7fffffffffffffffLL, 0};
     ctx->first_step = init[1];

@@ -192,35 +192,54 @@ __global__ void __launch_bounds__(RowCfg<M, SH>::THREADS, RowCfg<M, SH>::MINB) k
         // cell along x (input phases e^{i pi k / N}, output phases e^{-i pi k / N}), averaged.
         // The block's rows are those of one copy of P (plain or shifted along y: blockIdx.y runs
         // over 2R copies).  Tile 0 holds the row for the plain grid, tile 1 a second copy for the
-        // shifted one (each team row is also its evaluation's exchange buffer).
-        static_assert(NL == NL_CUBIC, "phase-shift dealiasing: cubic term");
+        // shifted one (each team row is also its evaluation's exchange buffer); KPZ adds the
+        // matching rows of P_y in tiles 2 and 3.
+        constexpr bool G = NL == NL_GRAD2;
+        static_assert(NL == NL_CUBIC || G, "phase-shift dealiasing: cubic or gradient-squared term");
         load_tile<C>(tile, a.pin, rowbase, ncols, ny, y0);
         load_tile<C>(tile + ROWS * TS, a.pin, rowbase, ncols, ny, y0);
+        if constexpr (G) {
+            load_tile<C>(tile + 2 * ROWS * TS, a.pyin, rowbase, ncols, ny, y0);
+            load_tile<C>(tile + 3 * ROWS * TS, a.pyin, rowbase, ncols, ny, y0);
+        }
         __syncthreads();
         float2* r0 = tile + team * TS;
         float2* r1 = tile + ROWS * TS + team * TS;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int k = t + T * e;
-            z[e] = c2r_pre(r0[k], r0[M - k], __ldg(&twN[k]));
-        }
-        fft_line<M, true>(z, r0, t, twM);
-#pragma unroll
-        for (int e = 0; e < E; ++e) z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
-        fft_line<M, false>(z, r0, t, twM);
-        row_post<M>(z, r0, r0, ncols, t, twN);
         const float2* __restrict__ tps = a.tw_ps;
+        // q on one grid from the P row (and the P_y row), phase e^{i pi k / N} on the shifted one; xb: the P row
+        auto q_of = [&](const float2* prow, const float2* pyrow, bool shift, float2* xbuf) {
+            float2 zy[G ? E : 1];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int k = t + T * e;
-            const float2 X = cmul(r1[k], cconj(__ldg(&tps[k]))), Xm = cmul(r1[M - k], cconj(__ldg(&tps[M - k])));
-            z[e] = c2r_pre(X, Xm, __ldg(&twN[k]));
-        }
-        fft_line<M, true>(z, r1, t, twM);
+            for (int e = 0; e < E; ++e) {
+                const int k = t + T * e;
+                const float2 ph = shift ? cconj(__ldg(&tps[k])) : make_float2(1.f, 0.f);
+                const float2 phm = shift ? cconj(__ldg(&tps[M - k])) : make_float2(1.f, 0.f);
+                const float2 tw = __ldg(&twN[k]);
+                if constexpr (G) {
+                    // grad_x h from i k_x P (k_x = 0 at the Nyquist column), grad_y h from P_y
+                    const float kx = a.dk * (float)k, kxm = (k == 0) ? 0.f : a.dk * (float)(M - k);
+                    z[e] = c2r_pre(cmul(cscale(cmuli(prow[k]), kx), ph), cmul(cscale(cmuli(prow[M - k]), kxm), phm),
+                                   tw);
+                    zy[e] = c2r_pre(cmul(pyrow[k], ph), cmul(pyrow[M - k], phm), tw);
+                } else {
+                    z[e] = c2r_pre(cmul(prow[k], ph), cmul(prow[M - k], phm), tw);
+                }
+            }
+            fft_line<M, true>(z, xbuf, t, twM);
+            if constexpr (G) {
+                fft_line<M, true>(zy, xbuf, t, twM);
 #pragma unroll
-        for (int e = 0; e < E; ++e) z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
-        fft_line<M, false>(z, r1, t, twM);
-        row_post<M>(z, r1, r1, ncols, t, twN);
+                for (int e = 0; e < E; ++e)
+                    z[e] = make_float2(z[e].x * z[e].x + zy[e].x * zy[e].x, z[e].y * z[e].y + zy[e].y * zy[e].y);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
+            }
+            fft_line<M, false>(z, xbuf, t, twM);
+            row_post<M>(z, xbuf, xbuf, ncols, t, twN);
+        };
+        q_of(r0, G ? tile + 2 * ROWS * TS + team * TS : nullptr, false, r0);
+        q_of(r1, G ? tile + 3 * ROWS * TS + team * TS : nullptr, true, r1);
         // each thread reads back the entries k = t + T e that it wrote itself
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -320,7 +339,10 @@ template <int M, int NL, int MODE, int SH = 0>
 static cudaError_t run_rows(const StepArgs& a, cudaStream_t s) {
     using C = RowCfg<M, SH>;
     constexpr int NTILE =
-        ((NL == NL_GRAD2 && MODE == MODE_STEP) || MODE == MODE_TAN || MODE == MODE_ADJ || MODE == MODE_STEP_PS) ? 2 : 1;
+        (NL == NL_GRAD2 && MODE == MODE_STEP_PS)
+            ? 4
+            : (((NL == NL_GRAD2 && MODE == MODE_STEP) || MODE == MODE_TAN || MODE == MODE_ADJ || MODE == MODE_STEP_PS) ? 2
+                                                                                                                : 1);
     const size_t sm = C::smem(NTILE);
     static bool attr = false;
     if (!attr) {
@@ -349,6 +371,7 @@ static cudaError_t rows_for(const StepArgs& a, int mode, int nl, cudaStream_t s,
     if (mode == MODE_STEP && nl == NL_CUBIC) return rows_step<M, NL_CUBIC>(a, s, shape);
     if (mode == MODE_STEP && nl == NL_GRAD2) return rows_step<M, NL_GRAD2>(a, s, shape);
     if (mode == MODE_STEP_PS && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_STEP_PS>(a, s);
+    if (mode == MODE_STEP_PS && nl == NL_GRAD2) return run_rows<M, NL_GRAD2, MODE_STEP_PS>(a, s);
     if (mode == MODE_TAN && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_TAN>(a, s);
     if (mode == MODE_ADJ && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_ADJ>(a, s);
     return cudaErrorInvalidValue;

@@ -118,34 +118,60 @@ __device__ __forceinline__ float2 shift_phase_conj(const float2* __restrict__ tw
 
 // P <- IFFT_y(M phi / N^2) for one column (and, for KPZ, P_y <- IFFT_y(i k_y M phi / N^2)):
 // the dealiased input of the next row pass.  Phase-shift dealiasing (PS) adds
-// the copy shifted by half a cell along y, P1 <- IFFT_y(M phi e^{i pi a_y / N} / N^2),
-// at a.ps_off behind P.
+// the copies shifted by half a cell along y, P1 <- IFFT_y(M phi e^{i pi a_y / N} / N^2)
+// (and P_y1), at a.ps_off behind P (and P_y).  One transform at a time.
 template <int NY, int NL, int EM, bool PS = false>
 __device__ __forceinline__ void emit_p(const StepArgs& a, const float2 (&out)[FftPlan<NY, EM>::E], bool has_p, int cc,
                                        size_t colbase, float2* xb, int t) {
     using PL = FftPlan<NY, EM>;
     constexpr int T = PL::T, E = PL::E;
     if (!(has_p || T < 32)) return;
-    float2 v[E];
-    float2 vy[(NL == NL_GRAD2 || PS) ? E : 1];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int ay = t + T * e;
-        const int ays = signed_idx(ay, NY);
-        const bool inm = keep_mode<PS>(a, cc, ays, NY);
-        v[e] = (has_p && inm) ? cscale(out[e], a.scale) : czero();
-        if constexpr (NL == NL_GRAD2) vy[e] = cscale(cmuli(v[e]), a.dk * (float)odd_idx(ay, NY));
-        if constexpr (PS) vy[e] = cmul(v[e], cconj(shift_phase_conj(a.tw_ps, ays)));
-    }
-    fft_line<NY, true, EM>(v, xb, t, a.tw_a);
-    if constexpr (NL == NL_GRAD2 || PS) fft_line<NY, true, EM>(vy, xb, t, a.tw_a);
-    if (has_p) {
+    if constexpr (!PS) {
+        float2 v[E];
+        float2 vy[NL == NL_GRAD2 ? E : 1];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            a.pout[colbase + t + T * e] = v[e];
-            if constexpr (NL == NL_GRAD2) a.pyout[colbase + t + T * e] = vy[e];
-            if constexpr (PS) a.pout[a.ps_off + colbase + t + T * e] = vy[e];
+            const int ay = t + T * e;
+            const int ays = signed_idx(ay, NY);
+            const bool inm = keep_mode<false>(a, cc, ays, NY);
+            v[e] = (has_p && inm) ? cscale(out[e], a.scale) : czero();
+            if constexpr (NL == NL_GRAD2) vy[e] = cscale(cmuli(v[e]), a.dk * (float)odd_idx(ay, NY));
         }
+        fft_line<NY, true, EM>(v, xb, t, a.tw_a);
+        if constexpr (NL == NL_GRAD2) fft_line<NY, true, EM>(vy, xb, t, a.tw_a);
+        if (has_p) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                a.pout[colbase + t + T * e] = v[e];
+                if constexpr (NL == NL_GRAD2) a.pyout[colbase + t + T * e] = vy[e];
+            }
+        }
+        return;
+    }
+    // phase shift: kind bit 0 the y derivative i k_y, bit 1 the half-cell shift
+    auto one = [&](float2* dst, int kind) {
+        float2 v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int ay = t + T * e;
+            const int ays = signed_idx(ay, NY);
+            const bool inm = keep_mode<PS>(a, cc, ays, NY);
+            float2 x = (has_p && inm) ? cscale(out[e], a.scale) : czero();
+            if (kind & 1) x = cscale(cmuli(x), a.dk * (float)odd_idx(ay, NY));
+            if (kind & 2) x = cmul(x, cconj(shift_phase_conj(a.tw_ps, ays)));
+            v[e] = x;
+        }
+        fft_line<NY, true, EM>(v, xb, t, a.tw_a);
+        if (has_p) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) dst[colbase + t + T * e] = v[e];
+        }
+    };
+    one(a.pout, 0);
+    if constexpr (NL == NL_GRAD2) one(a.pyout, 1);
+    if constexpr (PS) {
+        one(a.pout + a.ps_off, 2);
+        if constexpr (NL == NL_GRAD2) one(a.pyout + a.ps_off, 3);
     }
 }
 
@@ -433,9 +459,7 @@ template <int NY, int NL>
 static cudaError_t cols_step(const StepArgs& a, cudaStream_t s, int shape) {
     if (a.rec_phi) return run_cols<NY, NL, MODE_STEP_REC, 0>(a, s);  // recording: the default schedule
     if (a.noise_in) return run_cols<NY, NL, MODE_STEP_RSN, 0>(a, s);  // real-space noise: the default schedule
-    if constexpr (NL == NL_CUBIC) {
-        if (a.pshift) return run_cols<NY, NL, MODE_STEP_PS, 0>(a, s);  // phase-shift dealiasing
-    }
+    if (a.pshift) return run_cols<NY, NL, MODE_STEP_PS, 0>(a, s);  // phase-shift dealiasing
     if constexpr (ColCfg<NY>::WIDE) {
         if (shape == 1) return run_cols<NY, NL, MODE_STEP, 1>(a, s);
         if (shape == 2) return run_cols<NY, NL, MODE_STEP, 2>(a, s);

@@ -117,7 +117,6 @@ def test_real_space_noise_limits(lib, d, model, space, status):
 
 @pytest.mark.parametrize("d,model,space", [
     (1, 0, 0), (3, 0, 0),  # phase-shift dealiasing is built for 2-D lattices
-    (2, 2, 0),             # KPZ: quadratic gradient term
     (2, 3, 0),             # complex field (CGL)
     (2, 0, 1),             # with real-space noise
 ])

@@ -421,6 +421,10 @@ PS_CASES = [
     ("model_b_128_setd1_R3", W.model_b_1024(n=[128, 128], replicas=3, sigma0=0.3), 40),
     ("model_a_512_setd1", W.model_a_64(n=[512, 512], replicas=1, sigma0=0.3), 10),
     ("model_b_1024_setd1_R2", W.model_b_1024(replicas=2, h=0.05), 3),
+    ("kpz_2d_32_setd1_R2", W.kpz_2d(n=[32, 32], replicas=2), 100),
+    ("kpz_2d_64_setd2", W.kpz_2d(n=[64, 64], scheme=2, h=0.005), 100),
+    ("kpz_2d_256_em_R3", W.kpz_2d(n=[256, 256], replicas=3, scheme=0, sigma0=0.5), 20),
+    ("kpz_2d_1024_setd1", W.kpz_2d(n=[1024, 1024], sigma0=0.5), 3),
 ]
 
 
