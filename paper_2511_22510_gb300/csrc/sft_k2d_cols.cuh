@@ -117,45 +117,51 @@ __device__ __forceinline__ float2 shift_phase_conj(const float2* __restrict__ tw
 }
 
 // P <- IFFT_y(M phi / N^2) for one column (and, for KPZ, P_y <- IFFT_y(i k_y M phi / N^2)):
-// the dealiased input of the next row pass.  Phase-shift dealiasing (PS) adds
-// the copies shifted by half a cell along y, P1 <- IFFT_y(M phi e^{i pi a_y / N} / N^2)
-// (and P_y1), at a.ps_off behind P (and P_y).  One transform at a time.
-template <int NY, int NL, int EM, bool PS = false>
+// the dealiased input of the next row pass.
+template <int NY, int NL, int EM>
 __device__ __forceinline__ void emit_p(const StepArgs& a, const float2 (&out)[FftPlan<NY, EM>::E], bool has_p, int cc,
                                        size_t colbase, float2* xb, int t) {
     using PL = FftPlan<NY, EM>;
     constexpr int T = PL::T, E = PL::E;
     if (!(has_p || T < 32)) return;
-    if constexpr (!PS) {
-        float2 v[E];
-        float2 vy[NL == NL_GRAD2 ? E : 1];
+    float2 v[E];
+    float2 vy[NL == NL_GRAD2 ? E : 1];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int ay = t + T * e;
+        const int ays = signed_idx(ay, NY);
+        const bool inm = keep_mode<false>(a, cc, ays, NY);
+        v[e] = (has_p && inm) ? cscale(out[e], a.scale) : czero();
+        if constexpr (NL == NL_GRAD2) vy[e] = cscale(cmuli(v[e]), a.dk * (float)odd_idx(ay, NY));
+    }
+    fft_line<NY, true, EM>(v, xb, t, a.tw_a);
+    if constexpr (NL == NL_GRAD2) fft_line<NY, true, EM>(vy, xb, t, a.tw_a);
+    if (has_p) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const int ay = t + T * e;
-            const int ays = signed_idx(ay, NY);
-            const bool inm = keep_mode<false>(a, cc, ays, NY);
-            v[e] = (has_p && inm) ? cscale(out[e], a.scale) : czero();
-            if constexpr (NL == NL_GRAD2) vy[e] = cscale(cmuli(v[e]), a.dk * (float)odd_idx(ay, NY));
+            a.pout[colbase + t + T * e] = v[e];
+            if constexpr (NL == NL_GRAD2) a.pyout[colbase + t + T * e] = vy[e];
         }
-        fft_line<NY, true, EM>(v, xb, t, a.tw_a);
-        if constexpr (NL == NL_GRAD2) fft_line<NY, true, EM>(vy, xb, t, a.tw_a);
-        if (has_p) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                a.pout[colbase + t + T * e] = v[e];
-                if constexpr (NL == NL_GRAD2) a.pyout[colbase + t + T * e] = vy[e];
-            }
-        }
-        return;
     }
-    // phase shift: kind bit 0 the y derivative i k_y, bit 1 the half-cell shift
+}
+
+// The same under phase-shift dealiasing: P0 and the copy shifted by half a cell
+// along y, P1 <- IFFT_y(M phi e^{i pi a_y / N} / N^2) at a.ps_off behind P (KPZ: P_y
+// and P_y1 as well), every mode off the Nyquist lines kept; one transform at a time.
+template <int NY, int NL, int EM>
+__device__ __forceinline__ void emit_p_ps(const StepArgs& a, const float2 (&out)[FftPlan<NY, EM>::E], bool has_p,
+                                          int cc, size_t colbase, float2* xb, int t) {
+    using PL = FftPlan<NY, EM>;
+    constexpr int T = PL::T, E = PL::E;
+    if (!(has_p || T < 32)) return;
+    // kind: bit 0 the y derivative i k_y, bit 1 the half-cell shift
     auto one = [&](float2* dst, int kind) {
         float2 v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int ay = t + T * e;
             const int ays = signed_idx(ay, NY);
-            const bool inm = keep_mode<PS>(a, cc, ays, NY);
+            const bool inm = keep_mode<true>(a, cc, ays, NY);
             float2 x = (has_p && inm) ? cscale(out[e], a.scale) : czero();
             if (kind & 1) x = cscale(cmuli(x), a.dk * (float)odd_idx(ay, NY));
             if (kind & 2) x = cmul(x, cconj(shift_phase_conj(a.tw_ps, ays)));
@@ -169,10 +175,8 @@ __device__ __forceinline__ void emit_p(const StepArgs& a, const float2 (&out)[Ff
     };
     one(a.pout, 0);
     if constexpr (NL == NL_GRAD2) one(a.pyout, 1);
-    if constexpr (PS) {
-        one(a.pout + a.ps_off, 2);
-        if constexpr (NL == NL_GRAD2) one(a.pyout + a.ps_off, 3);
-    }
+    one(a.pout + a.ps_off, 2);
+    if constexpr (NL == NL_GRAD2) one(a.pyout + a.ps_off, 3);
 }
 
 template <int NY, int NL, int MODE, int SH = 0>
@@ -327,7 +331,10 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
             }
             flag_nonfinite_acc(a, nf, step);
         }
-        emit_p<NY, NL, EM, PS>(a, out, valid && cc < a.ncols, cc, colbase, xb, t);
+        if constexpr (PS)
+            emit_p_ps<NY, NL, EM>(a, out, valid && cc < a.ncols, cc, colbase, xb, t);
+        else
+            emit_p<NY, NL, EM>(a, out, valid && cc < a.ncols, cc, colbase, xb, t);
     } else if constexpr (MODE == MODE_TAN) {
         // primal step as in MODE_STEP, plus the tangent dphi <- f1 dphi + A M s DFT[q'] (no noise)
         if (!valid && T >= 32) return;
@@ -427,7 +434,7 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
 #pragma unroll
         for (int e = 0; e < E; ++e) out[e] = has_p ? a.phi[colbase + t + T * e] : czero();
         if (a.pshift)
-            emit_p<NY, NL, EM, true>(a, out, has_p, cc, colbase, xb, t);
+            emit_p_ps<NY, NL, EM>(a, out, has_p, cc, colbase, xb, t);
         else
             emit_p<NY, NL, EM>(a, out, has_p, cc, colbase, xb, t);
     }
