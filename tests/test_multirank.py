@@ -52,6 +52,30 @@ def test_replica_offset_splits_an_ensemble(oracle_mod):
     assert not np.array_equal(o.field(0), want[2])
 
 
+@pytest.mark.parametrize("name,w,extra", [
+    ("real_space_noise", W.model_b_1024(n=[16, 16], sigma0=0.3), dict(noise_space=1)),
+    ("phase_shift", W.model_a_64(n=[16, 16], sigma0=0.3, dealias=2), {}),
+    ("lattice_24", W.model_a_64(n=[24, 24], sigma0=0.3), {}),
+], ids=["real_space_noise", "phase_shift", "lattice_24"])
+def test_replica_offset_splits_an_ensemble_for_the_variants(oracle_mod, name, w, extra):
+    """The variants shard the same way: their noise is keyed by the global replica index too."""
+    f0 = W.initial_fields(w, replicas=4)
+    ref = oracle_mod.Oracle(w.d, w.n, w.dx, 4, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias, **extra)
+    for r in range(4):
+        ref.set_field(r, f0[r])
+    ref.step(6)
+    want = np.stack([ref.field(r) for r in range(4)])
+    got = []
+    for r0 in (0, 2):
+        o = oracle_mod.Oracle(w.d, w.n, w.dx, 2, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
+                              replica0=r0, **extra)
+        for r in range(2):
+            o.set_field(r, f0[r0 + r])
+        o.step(6)
+        got += [o.field(r) for r in range(2)]
+    assert np.array_equal(np.stack(got), want)
+
+
 def test_two_gloo_ranks_reproduce_one_ensemble(oracle_mod, tmp_path):
     torch = pytest.importorskip("torch")
     import torch.multiprocessing as mp
