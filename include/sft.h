@@ -290,6 +290,8 @@ sft_status sft_draw_noise(sft_ctx* ctx, int64_t step, void* host_out, size_t byt
  * kernels per step + 1) receives the mean duration in milliseconds of each
  * kernel of the step in launch order (2-D: row pass, column pass; 1-D: the
  * line kernel) followed by the mean step duration; *nkernels the kernel count.
+ * With real-space noise the first entry also holds the noise's forward
+ * transform (the two kernels before the row pass).
  * The state advances exactly as with sft_step_plain.  Synchronises. */
 sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, int* nkernels);
 
