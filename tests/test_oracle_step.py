@@ -104,6 +104,19 @@ def test_real_space_noise_is_the_transformed_site_draw(oracle_mod):
                 assert eta[iy, ix].imag == 0.0
 
 
+@pytest.mark.parametrize("d,n", [(1, [64]), (3, [8, 4, 6])])
+def test_real_space_noise_other_dimensions(oracle_mod, d, n):
+    """The same site-by-site identity in 1-D and 3-D (site s = x + n_x (y + n_y z))."""
+    w = W.model_a_64(d=d, n=n, dx=[1.0] * d)
+    o = oracle_mod.Oracle(d, n, [1.0] * d, 1, w.model, w.p, w.scheme, w.h, 7, noise_space=1)
+    eta = o.noise(0, 4)
+    site = np.fft.ifftn(eta) * math.sqrt(np.prod(n))
+    assert np.abs(site.imag).max() < 1e-13
+    want = np.array([oracle_mod.normals4(7, s >> 2, 4, 0, 3)[s & 3] for s in range(int(np.prod(n)))],
+                    dtype=np.float64).reshape(tuple(reversed(n)))
+    assert np.abs(site.real - want).max() < 1e-12
+
+
 def test_gaussian_model_a_structure_factor_real_space_noise(oracle_mod):
     """Sec. IV step 2 / Sec. V.A: with the real-space draw the linear theory
     C_ET(k) = T / (r + k^2) holds as with the Fourier draw (the two noises have
