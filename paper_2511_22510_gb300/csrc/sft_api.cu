@@ -647,8 +647,8 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
     if (cfg->d < 1 || cfg->d > 3) return why = "d must be 1, 2 or 3", SFT_EINVAL;
     for (int i = 0; i < cfg->d; ++i) {
         if (!is_pow2(cfg->n[i]) && !k2_mixed_size(cfg->n[i]))
-            return why = "lattice sizes must be powers of two (or p x 2^k, p in {3, 5, 7}, 16p .. 768, for 2-D real "
-                         "fields)", SFT_EINVAL;
+            return why = "lattice sizes must be powers of two (or p x 2^k, p in {3, 5, 7}, 16p .. 768, for 1-D and 2-D "
+                         "real fields)", SFT_EINVAL;
         if (!(cfg->dx[i] > 0)) return why = "dx must be positive", SFT_EINVAL;
         if (cfg->n[i] != cfg->n[0] || cfg->dx[i] != cfg->dx[0])
             return why = "anisotropic lattices are not supported (coefficients are tabulated by |a|^2)",
@@ -670,9 +670,9 @@ static sft_status validate(const sft_config* cfg, std::string& why) {
     if (cfg->noise_space == 1 && (cfg->d != 2 || cplx))
         return why = "real-space noise is built for 2-D real fields", SFT_EUNSUPPORTED;
     if (!is_pow2(cfg->n[0]) &&
-        (cfg->d != 2 || cplx || cfg->dealias == 2 || cfg->noise_space != 0 || cfg->model == SFT_CUSTOM))
-        return why = "lattices of p x 2^k points are built for 2-D real fields (Model A/B, KPZ) with Fourier-space "
-                     "noise and 2/3 truncation (or none)",
+        (cfg->d == 3 || cplx || cfg->dealias == 2 || cfg->noise_space != 0 || cfg->model == SFT_CUSTOM))
+        return why = "lattices of p x 2^k points are built for 1-D and 2-D real fields (Model A/B, KPZ) with "
+                     "Fourier-space noise and 2/3 truncation (or none)",
                SFT_EUNSUPPORTED;
     if (cfg->dealias == 2 && (cfg->d != 2 || cplx || (nlk != NL_CUBIC && nlk != NL_GRAD2) || cfg->noise_space != 0))
         return why = "phase-shift dealiasing is built for 2-D real fields with the cubic or gradient-squared term and "

@@ -1,432 +1,11 @@
-// sft_k1d.cu -- whole-step 1-D kernels: one team of threads holds one replica's
-// spectrum in registers for the entire step (Sec. IV boxed algorithm), so the
-// only HBM traffic is one read and one write of the state (plus the SETD2
-// history).  Real fields keep the Hermitian half a in [0, N/2] and transform
-// through the N/2-point complex FFT; complex fields (CGL) use full C2C lines.
-#include "sft_step_common.cuh"
+// sft_k1d.cu -- whole-step 1-D kernels (in sft_k1d.cuh): the power-of-two
+// instantiations, the size dispatch and the persistent batch kernel.
+#include "sft_k1d.cuh"
 
 namespace sft {
 
-template <int M>
-struct LineCfg {
-    using PL = FftPlan<M>;
-    static constexpr int T = PL::T;
-    static constexpr int LINES = T >= 128 ? 1 : 128 / T;
-    static constexpr int THREADS = LINES * T;
-    static constexpr int XB = PL::BUF;
-    static constexpr size_t smem() { return sizeof(float2) * (size_t)LINES * XB; }
-};
-
-// R2C post-processing of a line held by a team: Xq[e] = X[t + T e] for the
-// N/2 = M lowest modes, XqM = the Nyquist mode (valid in every thread).
-template <int M>
-__device__ __forceinline__ void line_post(float2 (&z)[FftPlan<M>::E], float2* xb, int t,
-                                          const float2* __restrict__ twN, float2 (&Xq)[FftPlan<M>::E], float2& XqM) {
-    using PL = FftPlan<M>;
-    constexpr int T = PL::T, E = PL::E;
-    team_sync<T>();
-#pragma unroll
-    for (int e = 0; e < E; ++e) xb[xpos<M>(t + T * e)] = z[e];
-    team_sync<T>();
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int k = t + T * e;
-        Xq[e] = r2c_post(z[e], cconj(xb[xpos<M>((M - k) & (M - 1))]), __ldg(&twN[k]));
-    }
-    const float2 z0 = xb[0];
-    XqM = make_float2(z0.x - z0.y, 0.f);
-}
-
-// One SETD step of one real 1-D replica held by a team of T threads (Sec. IV
-// boxed algorithm): inverse transform of the masked state, nonlinearity,
-// forward transform, update with Philox noise.  r: replica (clamped when the
-// team is idle, valid = false); xb: the team's exchange buffer.
-template <int M, int NL>
-__device__ __forceinline__ void line_step(const StepArgs& a, int r, bool valid, int t, float2* xb) {
-    using PL = FftPlan<M>;
-    constexpr int T = PL::T, E = PL::E;
-    constexpr int NX = 2 * M;
-    const float2* __restrict__ twM = a.tw_a;
-    const float2* __restrict__ twN = a.tw_b;
-    float2* ph = a.phi + (size_t)r * (M + 1);
-    const float sc = a.scale;
-    float2 z[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int k = t + T * e;
-        float2 X = ph[k], Xm = ph[M - k];
-        X = (!a.dealias || 3 * k < NX) ? cscale(X, sc) : czero();
-        Xm = (!a.dealias || 3 * (M - k) < NX) ? cscale(Xm, sc) : czero();
-        if constexpr (NL == NL_GRAD2) {
-            X = cscale(cmuli(X), a.dk * (float)k);
-            Xm = cscale(cmuli(Xm), k == 0 ? 0.f : a.dk * (float)(M - k));
-        }
-        z[e] = c2r_pre(X, Xm, __ldg(&twN[k]));
-    }
-    fft_line<M, true>(z, xb, t, twM);
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        if constexpr (NL == NL_GRAD2)
-            z[e] = make_float2(z[e].x * z[e].x, z[e].y * z[e].y);
-        else
-            z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
-    }
-    fft_line<M, false>(z, xb, t, twM);
-    float2 Xq[E];
-    float2 XqM;
-    line_post<M>(z, xb, t, twN, Xq, XqM);
-    const long long step = current_step(a);
-    const bool first = (a.scheme == 2) && (step == *a.first_step);
-    float2* fp = a.fprev + (size_t)r * (M + 1);
-    const uint32_t rep = (uint32_t)(a.rep0 + r);
-    float2 zn0, zn1;
-    // modes k = t + T e, then (thread 0) the Nyquist mode k = M
-#pragma unroll
-    for (int e = 0; e <= E; ++e) {
-        if (e < E && (e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
-        if (e == E && t != 0) break;
-        const int k = (e < E) ? t + T * e : M;
-        const float2 xq = (e < E) ? Xq[e] : XqM;
-        const bool inm = !a.dealias || 3 * k < NX;
-        const float2 F = inm ? cscale(xq, nl_prefactor(a, k * k).x) : czero();
-        const Coefs co = load_coefs<false>(a.tab, k, first);
-        const float2 phv = ph[k];
-        const float2 Fp = (a.scheme == 2) ? fp[k] : czero();
-        const bool selfc = (k == 0 || k == M);
-        const float2 eta = (e < E) ? eta_of((e & 1) ? zn1 : zn0, selfc)
-                                   : fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
-        float2 o = setd_update<false>(co, phv, F, Fp, eta);
-        if (selfc) o.y = 0.f;
-        if (valid) {
-            ph[k] = o;
-            if (a.scheme == 2) fp[k] = F;
-            flag_nonfinite(a, o, step);
-        }
-    }
-}
-
-// Real field, N = 2M points.  Mode k of replica r sits at phi[r * (M + 1) + k].
-template <int M, int NL, int MODE>
-__global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a) {
-    using C = LineCfg<M>;
-    using PL = FftPlan<M>;
-    constexpr int T = PL::T, E = PL::E, LINES = C::LINES, XB = C::XB;
-    constexpr int NX = 2 * M;
-    extern __shared__ float2 sm[];
-    const int team = threadIdx.x / T, t = threadIdx.x % T;
-    const int r = blockIdx.x * LINES + team;
-    const bool valid = r < a.R;
-    const int rr = valid ? r : a.R - 1;
-    float2* xb = sm + team * XB;
-    const float2* __restrict__ twM = a.tw_a;
-    const float2* __restrict__ twN = a.tw_b;
-    float2* ph = a.phi + (size_t)rr * (M + 1);
-    float2 z[E];
-
-    if constexpr (MODE == MODE_TAN || MODE == MODE_ADJ) {
-        // TAN: primal step plus dphi <- f1 dphi + A M s DFT[3 psi^2 dpsi] (dpsi = IDFT(M dphi)).
-        // ADJ: lam <- f1 lam + M DFT[3 psi^2 w], w = IDFT(A s M lam), psi from the primal state phi.
-        static_assert(NL == NL_CUBIC, "tangent/adjoint: cubic term");
-        float2* dp = a.dphi + (size_t)rr * (M + 1);
-        const float sc = a.scale;
-        float2 zd[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int k = t + T * e;
-            const bool i1 = !a.dealias || 3 * k < NX, i2 = !a.dealias || 3 * (M - k) < NX;
-            const float2 tw = __ldg(&twN[k]);
-            z[e] = c2r_pre(i1 ? cscale(ph[k], sc) : czero(), i2 ? cscale(ph[M - k], sc) : czero(), tw);
-            float w1 = sc, w2 = sc;
-            if constexpr (MODE == MODE_ADJ) {
-                w1 *= __ldg(&a.tab[k]).y * nl_prefactor(a, k * k).x;
-                w2 *= __ldg(&a.tab[M - k]).y * nl_prefactor(a, (M - k) * (M - k)).x;
-            }
-            zd[e] = c2r_pre(i1 ? cscale(dp[k], w1) : czero(), i2 ? cscale(dp[M - k], w2) : czero(), tw);
-        }
-        fft_line<M, true>(z, xb, t, twM);
-        fft_line<M, true>(zd, xb, t, twM);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float2 p = z[e];
-            zd[e] = make_float2(3.f * p.x * p.x * zd[e].x, 3.f * p.y * p.y * zd[e].y);
-            z[e] = make_float2(p.x * p.x * p.x, p.y * p.y * p.y);
-        }
-        fft_line<M, false>(zd, xb, t, twM);
-        float2 dXq[E];
-        float2 dXqM;
-        line_post<M>(zd, xb, t, twN, dXq, dXqM);
-        if constexpr (MODE == MODE_ADJ) {
-#pragma unroll
-            for (int e = 0; e <= E; ++e) {
-                if (e == E && t != 0) break;
-                const int k = (e < E) ? t + T * e : M;
-                const bool inm = !a.dealias || 3 * k < NX;
-                const float2 v = inm ? ((e < E) ? dXq[e] : dXqM) : czero();
-                const float f1 = __ldg(&a.tab[k]).x;
-                float2 o = make_float2(f1 * dp[k].x + v.x, f1 * dp[k].y + v.y);
-                if (k == 0 || k == M) o.y = 0.f;
-                if (valid) dp[k] = o;
-            }
-            return;
-        } else {
-            fft_line<M, false>(z, xb, t, twM);
-            float2 Xq[E];
-            float2 XqM;
-            line_post<M>(z, xb, t, twN, Xq, XqM);
-            const long long step = current_step(a);
-            const uint32_t rep = (uint32_t)(a.rep0 + rr);
-            float2 zn0, zn1;
-#pragma unroll
-            for (int e = 0; e <= E; ++e) {
-                if (e < E && (e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
-                if (e == E && t != 0) break;
-                const int k = (e < E) ? t + T * e : M;
-                const bool inm = !a.dealias || 3 * k < NX;
-                const float sq = nl_prefactor(a, k * k).x;
-                const float2 F = inm ? cscale((e < E) ? Xq[e] : XqM, sq) : czero();
-                const float2 dF = inm ? cscale((e < E) ? dXq[e] : dXqM, sq) : czero();
-                const Coefs co = load_coefs<false>(a.tab, k, false);
-                const bool selfc = (k == 0 || k == M);
-                const float2 eta = (e < E) ? eta_of((e & 1) ? zn1 : zn0, selfc)
-                                           : fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
-                float2 o = setd_update<false>(co, ph[k], F, czero(), eta);
-                float2 d = setd_update<false>(co, dp[k], dF, czero(), czero());
-                if (selfc) {
-                    o.y = 0.f;
-                    d.y = 0.f;
-                }
-                if (valid) {
-                    ph[k] = o;
-                    dp[k] = d;
-                    flag_nonfinite(a, o, step);
-                }
-            }
-            return;
-        }
-    }
-
-    if constexpr (MODE == MODE_STEP) {
-        line_step<M, NL>(a, rr, valid, t, xb);
-        return;
-    }
-    if constexpr (MODE == MODE_FWD) {
-        const float* src = a.real_io + (size_t)rr * NX;
-#pragma unroll
-        for (int e = 0; e < E; ++e) z[e] = *reinterpret_cast<const float2*>(src + 2 * (t + T * e));
-    } else {
-        const float sc = a.scale;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int k = t + T * e;
-            float2 X = ph[k], Xm = ph[M - k];
-            if constexpr (MODE == MODE_STEP) {
-                X = (!a.dealias || 3 * k < NX) ? cscale(X, sc) : czero();
-                Xm = (!a.dealias || 3 * (M - k) < NX) ? cscale(Xm, sc) : czero();
-                if constexpr (NL == NL_GRAD2) {
-                    X = cscale(cmuli(X), a.dk * (float)k);
-                    Xm = cscale(cmuli(Xm), k == 0 ? 0.f : a.dk * (float)(M - k));
-                }
-            } else {
-                X = cscale(X, sc);
-                Xm = cscale(Xm, sc);
-            }
-            z[e] = c2r_pre(X, Xm, __ldg(&twN[k]));
-        }
-        fft_line<M, true>(z, xb, t, twM);
-        if constexpr (MODE == MODE_INV) {
-            if (valid) {
-                float* dst = a.real_io + (size_t)rr * NX;
-#pragma unroll
-                for (int e = 0; e < E; ++e) *reinterpret_cast<float2*>(dst + 2 * (t + T * e)) = z[e];
-            }
-            return;
-        } else {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if constexpr (NL == NL_GRAD2)
-                    z[e] = make_float2(z[e].x * z[e].x, z[e].y * z[e].y);
-                else
-                    z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
-            }
-        }
-    }
-    if constexpr (MODE != MODE_INV) {
-        fft_line<M, false>(z, xb, t, twM);
-        team_sync<T>();
-#pragma unroll
-        for (int e = 0; e < E; ++e) xb[xpos<M>(t + T * e)] = z[e];
-        team_sync<T>();
-        float2 Xq[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int k = t + T * e;
-            Xq[e] = r2c_post(z[e], cconj(xb[xpos<M>((M - k) & (M - 1))]), __ldg(&twN[k]));
-        }
-        const float2 z0 = xb[0];
-        const float2 XqM = make_float2(z0.x - z0.y, 0.f);
-        if constexpr (MODE == MODE_FWD) {
-            if (valid) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    float2 v = Xq[e];
-                    if (t + T * e == 0) v.y = 0.f;
-                    ph[t + T * e] = v;
-                }
-                if (t == 0) ph[M] = XqM;
-            }
-        } else {
-            const long long step = current_step(a);
-            const bool first = (a.scheme == 2) && (step == *a.first_step);
-            float2* fp = a.fprev + (size_t)rr * (M + 1);
-            const uint32_t rep = (uint32_t)(a.rep0 + rr);
-            float2 zn0, zn1;
-            // modes k = t + T e, then (thread 0) the Nyquist mode k = M
-#pragma unroll
-            for (int e = 0; e <= E; ++e) {
-                if (e < E && (e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
-                if (e == E && t != 0) break;
-                const int k = (e < E) ? t + T * e : M;
-                const float2 xq = (e < E) ? Xq[e] : XqM;
-                const bool inm = !a.dealias || 3 * k < NX;
-                const int q = k * k;
-                const float2 F = inm ? cscale(xq, nl_prefactor(a, q).x) : czero();
-                const Coefs co = load_coefs<false>(a.tab, k, first);
-                const float2 phv = ph[k];
-                const float2 Fp = (a.scheme == 2) ? fp[k] : czero();
-                const bool selfc = (k == 0 || k == M);
-                const float2 eta = (e < E) ? eta_of((e & 1) ? zn1 : zn0, selfc)
-                                           : fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
-                float2 o = setd_update<false>(co, phv, F, Fp, eta);
-                if (selfc) o.y = 0.f;
-                if (valid) {
-                    ph[k] = o;
-                    if (a.scheme == 2) fp[k] = F;
-                    flag_nonfinite(a, o, step);
-                }
-            }
-        }
-    }
-}
-
-// Complex field of N points (CGL).  Mode k of replica r at phi[r * N + k].
-template <int N, int MODE>
-__global__ void __launch_bounds__(LineCfg<N>::THREADS) k1_cplx(const StepArgs a) {
-    using C = LineCfg<N>;
-    using PL = FftPlan<N>;
-    constexpr int T = PL::T, E = PL::E, LINES = C::LINES, XB = C::XB;
-    extern __shared__ float2 sm[];
-    const int team = threadIdx.x / T, t = threadIdx.x % T;
-    const int r = blockIdx.x * LINES + team;
-    const bool valid = r < a.R;
-    const int rr = valid ? r : a.R - 1;
-    float2* xb = sm + team * XB;
-    const float2* __restrict__ tw = a.tw_a;
-    float2* ph = a.phi + (size_t)rr * N;
-    float2 z[E];
-    if constexpr (MODE == MODE_FWD) {
-        const float2* src = a.cplx_io + (size_t)rr * N;
-#pragma unroll
-        for (int e = 0; e < E; ++e) z[e] = src[t + T * e];
-        fft_line<N, false>(z, xb, t, tw);
-        if (valid) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) ph[t + T * e] = z[e];
-        }
-        return;
-    }
-    float2 raw[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int k = t + T * e;
-        raw[e] = ph[k];
-        const bool inm = !a.dealias || 3 * abs(signed_idx(k, N)) < N;
-        z[e] = (MODE == MODE_INV || inm) ? cscale(raw[e], a.scale) : czero();
-    }
-    fft_line<N, true>(z, xb, t, tw);
-    if constexpr (MODE == MODE_INV) {
-        if (valid) {
-            float2* dst = a.cplx_io + (size_t)rr * N;
-#pragma unroll
-            for (int e = 0; e < E; ++e) dst[t + T * e] = z[e];
-        }
-        return;
-    } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) z[e] = cscale(z[e], z[e].x * z[e].x + z[e].y * z[e].y);
-        fft_line<N, false>(z, xb, t, tw);
-        const long long step = current_step(a);
-        const bool first = (a.scheme == 2) && (step == *a.first_step);
-        float2* fp = a.fprev + (size_t)rr * N;
-        const uint32_t rep = (uint32_t)(a.rep0 + rr);
-        const float2 s = make_float2(a.s0, a.s0i);
-        float2 zn0, zn1;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            if ((e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
-            const int k = t + T * e;
-            const int ks = signed_idx(k, N);
-            const bool inm = !a.dealias || 3 * abs(ks) < N;
-            const float2 F = inm ? cmul(s, z[e]) : czero();
-            const Coefs co = load_coefs<true>(a.tab, abs(ks), first);
-            const float2 Fp = (a.scheme == 2) ? fp[k] : czero();
-            const float2 o = setd_update<true>(co, raw[e], F, Fp, eta_of((e & 1) ? zn1 : zn0, false));
-            if (valid) {
-                ph[k] = o;
-                if (a.scheme == 2) fp[k] = F;
-                flag_nonfinite(a, o, step);
-            }
-        }
-    }
-}
-
-template <int M, int NL, int MODE>
-static cudaError_t run_k1_real(const StepArgs& a, cudaStream_t s) {
-    using C = LineCfg<M>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k1_real<M, NL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::smem());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    k1_real<M, NL, MODE><<<(a.R + C::LINES - 1) / C::LINES, C::THREADS, C::smem(), s>>>(a);
-    return cudaGetLastError();
-}
-
-template <int N, int MODE>
-static cudaError_t run_k1_cplx(const StepArgs& a, cudaStream_t s) {
-    using C = LineCfg<N>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k1_cplx<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    k1_cplx<N, MODE><<<(a.R + C::LINES - 1) / C::LINES, C::THREADS, C::smem(), s>>>(a);
-    return cudaGetLastError();
-}
-
-template <int M>
-static cudaError_t k1r_for(const StepArgs& a, int mode, int nl, cudaStream_t s) {
-    if (mode == MODE_FWD) return run_k1_real<M, NL_CUBIC, MODE_FWD>(a, s);
-    if (mode == MODE_INV) return run_k1_real<M, NL_CUBIC, MODE_INV>(a, s);
-    if (mode == MODE_STEP && nl == NL_CUBIC) return run_k1_real<M, NL_CUBIC, MODE_STEP>(a, s);
-    if (mode == MODE_STEP && nl == NL_GRAD2) return run_k1_real<M, NL_GRAD2, MODE_STEP>(a, s);
-    if (mode == MODE_TAN && nl == NL_CUBIC) return run_k1_real<M, NL_CUBIC, MODE_TAN>(a, s);
-    if (mode == MODE_ADJ && nl == NL_CUBIC) return run_k1_real<M, NL_CUBIC, MODE_ADJ>(a, s);
-    return cudaErrorInvalidValue;
-}
-
-template <int N>
-static cudaError_t k1c_for(const StepArgs& a, int mode, cudaStream_t s) {
-    if (mode == MODE_FWD) return run_k1_cplx<N, MODE_FWD>(a, s);
-    if (mode == MODE_INV) return run_k1_cplx<N, MODE_INV>(a, s);
-    if (mode == MODE_STEP) return run_k1_cplx<N, MODE_STEP>(a, s);
-    return cudaErrorInvalidValue;
-}
-
 bool k1_supported(int nx, int complex_field) {
+    if (!complex_field && k2_mixed_size(nx)) return true;  // p x 2^k lines (sft_k1d_mixed.cu)
     if ((nx & (nx - 1)) != 0) return false;
     return complex_field ? (nx >= 16 && nx <= 16384) : (nx >= 32 && nx <= 65536);
 }
@@ -461,7 +40,7 @@ cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s) 
         case 4096: return k1r_for<4096>(a, mode, nl, s);
         case 8192: return k1r_for<8192>(a, mode, nl, s);
         case 16384: return k1r_for<16384>(a, mode, nl, s);
-        default: return cudaErrorInvalidValue;
+        default: return k2_mixed_size(a.nx) ? launch_k1_line_mixed(a, mode, nl, s) : cudaErrorInvalidValue;
     }
 }
 

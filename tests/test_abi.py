@@ -129,7 +129,7 @@ def test_phase_shift_dealiasing_limits(lib, d, model, space):
 
 
 @pytest.mark.parametrize("d,model,extra", [
-    (1, 0, {}), (3, 0, {}),                   # p x 2^k lattices are built for 2-D real fields
+    (3, 0, {}),                               # p x 2^k lattices are built for 1-D and 2-D real fields
     (2, 3, {}),                               # complex field (CGL)
     (2, 0, dict(dealias=2)), (2, 0, dict(noise_space=1)),
 ])

@@ -475,6 +475,11 @@ MIXED_CASES = [
     ("model_b_640_setd1", W.model_b_1024(n=[640, 640], h=0.05), 3),
     ("model_a_112_em_R2", W.model_a_64(n=[112, 112], replicas=2, scheme=0, sigma0=0.3), 100),
     ("model_b_448_setd2", W.model_b_1024(n=[448, 448], scheme=2, h=0.025, sigma0=0.3), 5),
+    ("kpz_1d_96_R3", W.kpz_1d(96, replicas=3), 100),
+    ("model_a_1d_48_setd2", W.model_a_64(d=1, n=[48], dx=[1.0], scheme=2, replicas=2, sigma0=0.3), 100),
+    ("kpz_1d_640_em", W.kpz_1d(640, replicas=2, scheme=0), 100),
+    ("model_b_1d_448", W.model_b_1024(d=1, n=[448], dx=[1.0], replicas=2, sigma0=0.3), 100),
+    ("kpz_1d_768_R200", W.kpz_1d(768, replicas=200, sigma0=0.2), 20),
 ]
 
 
