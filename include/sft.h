@@ -95,7 +95,7 @@ typedef enum { SFT_SETD_EM = 0, SFT_SETD1 = 1, SFT_SETD2 = 2 } sft_scheme;
 typedef struct {
     int d;             /* 1, 2 or 3 */
     int n[3];          /* points per axis (x first), all equal (isotropic): powers of two, or, for
-                        * 2-D real fields (Model A/B, KPZ) with Fourier-space noise and truncation
+                        * 1-D and 2-D real fields (Model A/B, KPZ) with Fourier-space noise and truncation
                         * (or none), p x 2^k with p in {3, 5, 7} and 16p <= n <= 768 (a radix-p
                         * pass ahead of the radix-4/2 passes; no tangent/adjoint, dynamic recording
                         * or batches) */
