@@ -10,8 +10,9 @@
  *
  * Everything is written for clarity, not speed: the spectrum is kept as a FULL
  * complex array (no half-spectrum tricks), transforms are a textbook radix-2
- * FFT (pinned against a brute-force DFT), and every mode is updated in a plain
- * loop.  Floating point is double precision except for the Gaussian-noise
+ * FFT (pinned against a brute-force DFT; lengths p x 2^k split by radix 2 down to
+ * the odd length, whose DFT is its definition), and every mode is updated in a
+ * plain loop.  Floating point is double precision except for the Gaussian-noise
  * recipe, which is specified in single precision so that both implementations
  * produce bit-identical normal deviates (they are widened to double here).
  *
@@ -27,6 +28,12 @@
  *   App. A: DFT conventions and the (N^2/L)^d noise variance in Fourier space.
  *   App. B: Hermitian structure of the noise for real fields.
  *   App. C: equal-time correlator C_ET(k) = (L/N^2)^d |phi_a|^2 and shell average.
+ *   Sec. III: 0-d SDE ensembles (SAO, GBM) under the five update rules of the
+ *     stability table.
+ *   Sec. IV step 1, alternative: phase-shift dealiasing (mean of the nonlinear
+ *     term over the 2^d half-cell-shifted grids).
+ *   Sec. IV step 2, alternative: noise drawn per real-space site and transformed.
+ *   Sec. V.A footnote: the r phi term placed in F (Model A/B, p[4] != 0).
  *
  * Readings where the paper is silent or inconsistent (each also listed in the
  * design notes of the repository):
@@ -40,6 +47,10 @@
  *   - Odd derivatives (KPZ gradient) use k = 0 at the Nyquist index.
  *   - Hermitian fix-up after every update: partner modes take the conjugate of
  *     their canonical mode and self-conjugate modes drop their imaginary part.
+ *   - Phase-shift dealiasing masks the Nyquist modes (their shifted copies are
+ *     not spectra of real fields) and keeps every other mode.
+ *   - Real-space noise: eta_a = DFT[eta]_a / sqrt(N^d), site s taking normal
+ *     s & 3 of Philox(s >> 2, step, replica, tag 3).
  */
 #include <complex.h>
 #include <math.h>
