@@ -150,8 +150,16 @@ typedef enum {
     SFT_OBS_ROUGHNESS = 4,   /* per replica w^2 = N^{-2d} sum_{a != 0} |phi_a|^2 (Sec. V.B, box = L) */
     SFT_OBS_RESPONSE = 5,    /* per shell sum Re(dphi_a(t) conj(dphi_a(t0))) / sum |dphi_a(t0)|^2 over
                                 replicas, dphi the tangent seeded at t0 by sft_tangent_step */
-    SFT_OBS_NSHELLS = 6      /* writes one value: the number of shells */
+    SFT_OBS_NSHELLS = 6,     /* writes one value: the number of shells */
+    SFT_OBS_SK_ACCUM = 7,    /* adds the current S(k) of every replica to a device time accumulator
+                                (compensated FP64 pairs); writes nothing, does not synchronise */
+    SFT_OBS_SK_TIME_MEAN = 8,/* nshells values: the time and replica mean of S(k) over the accumulated
+                                observations, then their count; synchronises */
+    SFT_OBS_SK_RESET = 9     /* clears the time accumulator; writes nothing */
 } sft_observable;
+/* Every shell sum is taken in a fixed order with compensated FP64 summation
+ * (the modes enumerated shell by shell), so repeated evaluations of the same
+ * state give the same bits. */
 
 /* Create a context (allocates all device memory, builds the FP64 coefficient
  * tables of Sec. II on the device, zero state).  *out receives the context or
@@ -192,6 +200,14 @@ sft_status sft_set_spectrum(sft_ctx* ctx, const void* host_in, size_t bytes);
  * (sft_sync, sft_observe, sft_get_field) as SFT_ENONFINITE. */
 sft_status sft_step(sft_ctx* ctx, int64_t nsteps);
 
+/* One-time preparation of sft_step, without advancing or touching the state:
+ * the schedule is chosen (as sft_get_plan) and the graph of a chunk of steps
+ * is captured and instantiated.  sft_step otherwise does this on its first
+ * call (running its first chunk as plain launches); calling sft_prepare first
+ * keeps that set-up out of a timed region.  Synchronises.  No counterpart in
+ * the paper. */
+sft_status sft_prepare(sft_ctx* ctx);
+
 /* Advance with the SAME kernels launched one by one from the host (no graph),
  * the plain unbatched form used for timing comparisons. */
 sft_status sft_step_plain(sft_ctx* ctx, int64_t nsteps);
@@ -202,10 +218,14 @@ sft_status sft_step_plain(sft_ctx* ctx, int64_t nsteps);
  * choice is cached per configuration for the process (SFT_AUTOTUNE=0 in the
  * environment keeps the defaults; SFT_PLAN="row,col,rpb,pipe" fixes the
  * schedule).  out[0]: row-pass shape (0: 128-thread blocks at 4 per SM, 1:
- * 256-thread blocks at 2 per SM, 2: 512-thread blocks at 1 per SM); out[1]: 2-D column
+ * 256-thread blocks at 2 per SM, 2: 512-thread blocks at 1 per SM; 3, rows of
+ * 1024 points with the cubic term: two rows per warp as one complex 1024-point
+ * transform in registers, tiles moved by TMA); out[1]: 2-D column
  * pass radix schedule and block shape (0: 8 values per thread, 256-thread
  * blocks, 3 per SM; 1: same, 4 per SM; 2: 16 values per thread, 128-thread
- * blocks, 4 per SM; columns shorter than 512 points have only 0); out[2]:
+ * blocks, 4 per SM; 3, columns of 1024 points with the cubic term: one warp
+ * per column, the column in registers through both transforms and the update;
+ * columns shorter than 512 points have only 0); out[2]:
  * replicas per column-pass block; out[3]: 1 when the pipelined bulk-copy
  * column pass runs.  cap >= 4.  The schedule changes no result beyond
  * rounding order: every variant computes the same step.  Not on batch
@@ -356,9 +376,12 @@ sft_status sft_sde0d(int kind, const double* p, int scheme, double h, int subste
  * lives in one fixed device array of about 7 MiB that every GPU loading this
  * library holds until exit; sizes beyond it (R * (n0/2 + 1) * n1 > 262144 modes,
  * or n > 512) return SFT_EINVAL.  The first call on a device looks that array
- * up and must come before any stream capture.  Calls share the array: calls
- * that overlap on the GPU race.  Synchronises cfg->stream; returns
- * SFT_ENONFINITE if the state became non-finite. */
+ * up and must come before any stream capture.  The address is kept for the
+ * process: do not call this entry point after a cudaDeviceReset (or anything
+ * else that destroys the device's primary context).  Calls share the array:
+ * calls that overlap on the GPU race.  The configuration passes the checks of
+ * sft_create first.  Synchronises cfg->stream; returns SFT_ENONFINITE if the
+ * state became non-finite. */
 sft_status sft_step2d_noalloc(const sft_config* cfg, void* phi_dev, void* fprev_dev, int history_valid,
                               int64_t step0, int64_t nsteps);
 

@@ -70,6 +70,10 @@ def lib():
             L.or_box_width.restype = C.c_int
             L.or_force.argtypes = [vp, C.c_int, dp]
             L.or_force.restype = C.c_int
+            L.or_mode_operators.argtypes = [vp, dp]
+            L.or_dyn_estimators.argtypes = [C.c_int, C.c_long, C.c_int, dp, dp, dp, dp, C.c_double, C.c_double, dp,
+                                            dp, dp]
+            L.or_dyn_estimators.restype = C.c_int
             L.or_sde0d.argtypes = [C.c_int, dp, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_int64, C.c_int64,
                                    C.c_int64, dp, dp]
             L.or_sde0d.restype = C.c_int
@@ -184,6 +188,31 @@ def phi12(z: complex):
 # --------------------------------------------------------------------------
 # Stepper
 # --------------------------------------------------------------------------
+def dyn_estimators(phi, F, c, D, T, norm):
+    """App. C estimators from an ensemble of recorded series.
+
+    phi, F: complex arrays (S, n, M) -- state and nonlinear term of n modes at M
+    sample times spanning T, for S replicas; c (complex) and D: (n,) linear
+    operator and noise strength; norm = (L/N^2)^d.  Returns (C, chi, Dbar) with
+    C, chi of shape (n, M) over the DFT frequency index b (omega_b = 2 pi b / T,
+    b signed) and Dbar the mean |2 Im chi - (omega / D) C| over modes with D > 0.
+    """
+    phi = np.ascontiguousarray(phi, dtype=np.complex128)
+    F = np.ascontiguousarray(F, dtype=np.complex128)
+    S, n, M = phi.shape
+    c = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.complex128), (n,)))
+    D = np.ascontiguousarray(np.broadcast_to(np.asarray(D, dtype=np.float64), (n,)))
+    Cout = np.zeros((n, M))
+    chi = np.zeros((n, M), dtype=np.complex128)
+    dbar = np.zeros(1)
+    rc = lib().or_dyn_estimators(S, n, M, _dptr(phi.view(np.float64)), _dptr(F.view(np.float64)),
+                                 _dptr(c.view(np.float64)), _dptr(D), float(T), float(norm), _dptr(Cout),
+                                 _dptr(chi.view(np.float64)), _dptr(dbar))
+    if rc != 0:
+        raise ValueError("dyn_estimators: bad arguments")
+    return Cout, chi, float(dbar[0])
+
+
 class Oracle:
     """One oracle context: R replicas of a d-dimensional periodic field.
 
@@ -337,6 +366,14 @@ class Oracle:
         out = np.zeros(self.ntot, dtype=np.complex128)
         lib().or_force(self._p, int(r), _dptr(out.view(np.float64)))
         return out.reshape(self.shape)
+
+    def mode_operators(self):
+        """(c_a, D_a) over the full spectrum (shape of a spectrum): the model's linear
+        operator and noise strength (Sec. V)."""
+        out = np.zeros(3 * self.ntot)
+        lib().or_mode_operators(self._p, _dptr(out))
+        out = out.reshape(self.ntot, 3)
+        return (out[:, 0] + 1j * out[:, 1]).reshape(self.shape), out[:, 2].reshape(self.shape)
 
     def box_width(self, ell):
         """w_ell^2 per replica: mean over boxes of ell^d sites of the in-box variance (Sec. V.B)."""

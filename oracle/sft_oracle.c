@@ -27,7 +27,9 @@
  *   Sec. V.C: complex Ginzburg-Landau.
  *   App. A: DFT conventions and the (N^2/L)^d noise variance in Fourier space.
  *   App. B: Hermitian structure of the noise for real fields.
- *   App. C: equal-time correlator C_ET(k) = (L/N^2)^d |phi_a|^2 and shell average.
+ *   App. C: equal-time correlator C_ET(k) = (L/N^2)^d |phi_a|^2 and shell average;
+ *     dynamic correlation C(k, omega), noise-inferred susceptibility chi(k, omega)
+ *     and the FDT deviation of Sec. V.A from recorded series (or_dyn_estimators).
  *   Sec. III: 0-d SDE ensembles (SAO, GBM) under the five update rules of the
  *     stability table.
  *   Sec. IV step 1, alternative: phase-shift dealiasing (mean of the nonlinear
@@ -1316,4 +1318,106 @@ int or_force(or_state* st, int replica, double* out_ri) {
     if (replica < 0 || replica >= st->cfg.replicas) return 1;
     nonlinear_term(st, st->phi + (size_t)replica * st->ntot, (cplx*)out_ri);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Dynamic observables of App. C from an ensemble of recorded time series.     */
+/*                                                                             */
+/* Input: S series (replicas) of n modes, each sampled at M times m = 0..M-1   */
+/* spanning the record duration T; phi[(s n + a) M + m] and F[...] complex     */
+/* (interleaved re, im): the state phi_a and the nonlinear term F_a at each    */
+/* sample; c[a] (complex, interleaved) the linear operator, D[a] the noise     */
+/* strength; norm = (L/N^2)^d.  The steps, in the paper's order:               */
+/*   1. time DFT of every series, phi_{a,b} = sum_m e^{+2 pi i b m / M}        */
+/*      phi_{a,m} (the printed exponent divides by T; read as M, the number    */
+/*      of samples, so that b indexes the M frequencies), and likewise K;      */
+/*   2. the deterministic force K = c phi + F (the Langevin drift K[phi] of    */
+/*      the Onsager-Machlup functional, in Fourier space);                     */
+/*   3. omega_b = 2 pi b / T with b the signed frequency index;                */
+/*   4. C_{a,b} = norm (T / M^2) <|phi_{a,b}|^2>_s;                            */
+/*   5. chi_{a,b} = norm (T / M^2) (1 / 2 D_a) <phi_{a,b} conj(-i omega_b       */
+/*      phi_{a,b} - K_{a,b})>_s;                                               */
+/*   6. Delta_{a,b} = 2 Im chi_{a,b} - (omega_b / D_a) C_{a,b} (Sec. V.A) and   */
+/*      Dbar = the mean of |Delta| over the frequencies and the modes.         */
+/* Readings: the ensemble sum over s is taken as the ensemble mean (1/S), as   */
+/* an estimator of the expectation; modes with D_a = 0 carry no noise, so      */
+/* chi is left zero there and they are left out of Dbar.  The DFT is the plain */
+/* O(M^2) sum of its definition.  C_out[a M + b] (real), chi_out[a M + b]      */
+/* (complex, interleaved), *dbar_out.                                          */
+/* ------------------------------------------------------------------------- */
+int or_dyn_estimators(int S, long n, int M, const double* phi_ri, const double* F_ri, const double* c_ri,
+                      const double* D, double T, double norm, double* C_out, double* chi_out, double* dbar_out) {
+    if (S < 1 || n < 1 || M < 1 || !(T > 0)) return 1;
+    const cplx* phi = (const cplx*)phi_ri;
+    const cplx* F = (const cplx*)F_ri;
+    const cplx* c = (const cplx*)c_ri;
+    cplx* chi = (cplx*)chi_out;
+    cplx* X = (cplx*)malloc(sizeof(cplx) * (size_t)M);
+    cplx* Y = (cplx*)malloc(sizeof(cplx) * (size_t)M);
+    if (!X || !Y) {
+        free(X);
+        free(Y);
+        return 2;
+    }
+    for (long i = 0; i < n * M; ++i) {
+        C_out[i] = 0.0;
+        chi[i] = 0.0;
+    }
+    const double pref = norm * T / ((double)M * M) / (double)S;
+    for (int s = 0; s < S; ++s) {
+        for (long a = 0; a < n; ++a) {
+            const cplx* ps = phi + ((size_t)s * n + a) * M;
+            const cplx* fs = F + ((size_t)s * n + a) * M;
+            /* step 1: time DFT with the + sign */
+            for (int b = 0; b < M; ++b) {
+                cplx xs = 0.0, ys = 0.0;
+                for (int m = 0; m < M; ++m) {
+                    const cplx e = cexp(2.0 * OR_PI * I * (double)(((long)b * m) % M) / (double)M);
+                    xs += e * ps[m];
+                    ys += e * fs[m];
+                }
+                X[b] = xs;
+                Y[b] = ys;
+            }
+            for (int b = 0; b < M; ++b) {
+                /* steps 2, 3 */
+                const cplx K = c[a] * X[b] + Y[b];
+                const int bs = 2 * b < M ? b : b - M;
+                const double om = 2.0 * OR_PI * (double)bs / T;
+                /* steps 4, 5 */
+                C_out[a * M + b] += pref * creal(X[b] * conj(X[b]));
+                if (D[a] > 0.0) chi[a * M + b] += pref / (2.0 * D[a]) * X[b] * conj(-I * om * X[b] - K);
+            }
+        }
+    }
+    /* step 6 */
+    double acc = 0.0;
+    long cnt = 0;
+    for (long a = 0; a < n; ++a) {
+        if (!(D[a] > 0.0)) continue;
+        for (int b = 0; b < M; ++b) {
+            const int bs = 2 * b < M ? b : b - M;
+            const double om = 2.0 * OR_PI * (double)bs / T;
+            acc += fabs(2.0 * cimag(chi[a * M + b]) - om / D[a] * C_out[a * M + b]);
+            ++cnt;
+        }
+    }
+    *dbar_out = cnt ? acc / (double)cnt : 0.0;
+    free(X);
+    free(Y);
+    return 0;
+}
+
+/* The linear operator c_a and the noise strength D_a of every mode of the full
+ * spectrum (Sec. V, per model), for the dynamic observables: out[3 idx] =
+ * Re c, out[3 idx + 1] = Im c, out[3 idx + 2] = D. */
+void or_mode_operators(const or_state* st, double* out) {
+    for (size_t idx = 0; idx < st->ntot; ++idx) {
+        cplx c, s;
+        double D;
+        mode_operator(st, idx, &c, &D, &s);
+        out[3 * idx] = creal(c);
+        out[3 * idx + 1] = cimag(c);
+        out[3 * idx + 2] = D;
+    }
 }

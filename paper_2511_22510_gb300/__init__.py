@@ -24,7 +24,7 @@ SFT_MODEL_A, SFT_MODEL_B, SFT_KPZ, SFT_CGL, SFT_CUSTOM = 0, 1, 2, 3, 4
 SFT_NL_NONE, SFT_NL_CUBIC, SFT_NL_GRAD2, SFT_NL_CGL = 0, 1, 2, 3
 SFT_SETD_EM, SFT_SETD1, SFT_SETD2 = 0, 1, 2
 (SFT_OBS_SK, SFT_OBS_SK_REPLICAS, SFT_OBS_MARK, SFT_OBS_CKT, SFT_OBS_ROUGHNESS, SFT_OBS_RESPONSE,
- SFT_OBS_NSHELLS) = range(7)
+ SFT_OBS_NSHELLS, SFT_OBS_SK_ACCUM, SFT_OBS_SK_TIME_MEAN, SFT_OBS_SK_RESET) = range(10)
 
 _STATUS_NAMES = {0: "SFT_OK", 1: "SFT_EINVAL", 2: "SFT_ENOMEM", 3: "SFT_ECUDA", 4: "SFT_ENONFINITE",
                  5: "SFT_ETIMEOUT", 6: "SFT_EUNSUPPORTED", 7: "SFT_ECHECKPOINT"}
@@ -32,7 +32,7 @@ _STATUS_NAMES = {0: "SFT_OK", 1: "SFT_EINVAL", 2: "SFT_ENOMEM", 3: "SFT_ECUDA", 
 # every function declared in include/sft.h
 ABI_FUNCTIONS = [
     "sft_create", "sft_create_batch", "sft_set_field", "sft_init_random", "sft_get_field", "sft_get_spectrum",
-    "sft_set_spectrum", "sft_step", "sft_step_plain", "sft_sync", "sft_observe", "sft_tangent_step",
+    "sft_set_spectrum", "sft_step", "sft_prepare", "sft_step_plain", "sft_sync", "sft_observe", "sft_tangent_step",
     "sft_adjoint", "sft_set_checkpoint_interval", "sft_checkpoint", "sft_restore", "sft_get_step",
     "sft_launches_per_step", "sft_kernel_launches", "sft_draw_noise", "sft_profile", "sft_step2d_noalloc",
     "sft_get_plan", "sft_set_plan", "sft_sde0d", "sft_box_width", "sft_dyn_start", "sft_dyn_result", "sft_last_error",
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
     L.sft_set_spectrum.argtypes = [vp, vp, sz]
     L.sft_step.argtypes = [vp, i64]
     L.sft_step_plain.argtypes = [vp, i64]
+    L.sft_prepare.argtypes = [vp]
     L.sft_sync.argtypes = [vp]
     L.sft_observe.argtypes = [vp, C.c_int, C.POINTER(C.c_double), sz, C.POINTER(sz)]
     L.sft_tangent_step.argtypes = [vp, vp, i64, vp]
@@ -188,6 +189,10 @@ def sft_step(ctx, nsteps: int):
 
 def sft_step_plain(ctx, nsteps: int):
     _check(ctx, load_library().sft_step_plain(ctx, int(nsteps)))
+
+
+def sft_prepare(ctx):
+    _check(ctx, load_library().sft_prepare(ctx))
 
 
 def sft_sync(ctx):
@@ -456,6 +461,9 @@ class Stepper:
     def step_plain(self, n: int = 1):
         sft_step_plain(self.ctx, n)
 
+    def prepare(self):
+        sft_prepare(self.ctx)
+
     def sync(self):
         sft_sync(self.ctx)
 
@@ -465,7 +473,8 @@ class Stepper:
     def observe(self, kind: int) -> np.ndarray:
         ns = self.nshells()
         cap = {SFT_OBS_SK: 2 * ns, SFT_OBS_SK_REPLICAS: self.R * ns, SFT_OBS_MARK: 0, SFT_OBS_CKT: 2 * ns,
-               SFT_OBS_ROUGHNESS: self.R, SFT_OBS_RESPONSE: ns}[kind]
+               SFT_OBS_ROUGHNESS: self.R, SFT_OBS_RESPONSE: ns, SFT_OBS_SK_ACCUM: 0, SFT_OBS_SK_TIME_MEAN: ns + 1,
+               SFT_OBS_SK_RESET: 0}[kind]
         return sft_observe(self.ctx, kind, cap)
 
     @property

@@ -55,7 +55,18 @@ struct sft_ctx {
     unsigned* dstatus = nullptr;
     double* dshell = nullptr;
     double* drough = nullptr;
+    // observation: the stored modes shell by shell, cut into chunks (ObsArgs), chunk partials, and the
+    // device time accumulator of S(k, t) (compensated pairs) with its sample count
+    int* d_order = nullptr;
+    int4* d_chunks = nullptr;
+    int* d_first_chunk = nullptr;
+    int nchunks = 0;
+    double2* d_part = nullptr;
+    double2* d_tacc = nullptr;
+    long long tacc_count = 0;
     Twiddles tw;
+    float2* tw32 = nullptr;  // W_1024^{t k1} for t, k1 < 32 (1024-point warp transforms)
+    int wait_limit = 0;      // StepArgs::wait_limit (SFT_WAIT_LIMIT; tests of the time-out path)
     // tangent / adjoint
     float2 *dphi = nullptr, *dseed = nullptr, *dP = nullptr, *dQ = nullptr;
     bool dp_valid = false;
@@ -178,6 +189,8 @@ static StepArgs base_args(const sft_ctx* c) {
     a.status = c->dstatus;
     a.bad_step = c->dstep + 2;
     a.rpb = c->rpb;
+    a.tw_32 = c->tw32;
+    a.wait_limit = c->wait_limit;
     a.tw_c = (c->d == 1 && !c->cplx && k1_cluster_fft_len(c->nx)) ? c->tw.get(k1_cluster_fft_len(c->nx)) : nullptr;
     a.rec_phi = c->rec_phi;
     a.rec_F = c->rec_F;
@@ -483,6 +496,20 @@ static void apply_plan(sft_ctx* ctx, const PlanChoice& p) {
 
 static sft_status prime(sft_ctx* ctx);
 
+// Whether row-pass schedule sh is built for the context's lattice and term.
+static bool row_shape_ok(const sft_ctx* ctx, int sh) {
+    if (sh < 0 || sh >= k2_row_shapes(ctx->nx)) return false;
+    if (sh == 3) return k2_pair_supported(ctx->nx, ctx->ny * ctx->nz, ctx->nl, ctx->cfg.dealias) && ctx->tw32;
+    return true;
+}
+
+// Whether column-pass schedule sh is built for the context's lattice and term.
+static bool col_shape_ok(const sft_ctx* ctx, int sh) {
+    if (sh < 0 || sh >= (ctx->d == 2 ? k2_col_shapes(ctx->ny) : 1)) return false;
+    if (sh == 3) return k2_colwarp_supported(ctx->nx, ctx->ny, ctx->nl, ctx->cfg.dealias) && ctx->tw32;
+    return true;
+}
+
 static sft_status plan_step(sft_ctx* ctx) {
     if (ctx->planned) return SFT_OK;
     ctx->planned = true;
@@ -499,8 +526,7 @@ static sft_status plan_step(sft_ctx* ctx) {
     if (const char* fixed = getenv("SFT_PLAN")) {
         int v[4];
         if (sscanf(fixed, "%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3]) == 4) {
-            const bool ok = v[0] >= 0 && v[0] < k2_row_shapes(ctx->nx) && v[1] >= 0 &&
-                            v[1] < (ctx->d == 2 ? k2_col_shapes(ctx->ny) : 1) && v[2] >= 1 && v[2] <= 64 &&
+            const bool ok = row_shape_ok(ctx, v[0]) && col_shape_ok(ctx, v[1]) && v[2] >= 1 && v[2] <= 64 &&
                             (v[3] == 0 || (ctx->d == 2 && k2_pipe_supported(ctx->nx, ctx->ny, 0)));
             if (!ok) return fail(ctx, SFT_EINVAL, "SFT_PLAN names a schedule not built for this lattice");
             apply_plan(ctx, PlanChoice{v[0], v[1], v[2], v[3]});
@@ -535,6 +561,7 @@ static sft_status plan_step(sft_ctx* ctx) {
     a.tw_b = ctx->tw.get(ctx->nx);
     float best_ms = 1e30f;
     for (int sh = 0; sh < k2_row_shapes(ctx->nx); ++sh) {
+        if (!row_shape_ok(ctx, sh)) continue;
         float ms = 0.f;
         CK(time_launch(ctx->stream, [&] { return launch_k2_rows(a, MODE_STEP, ctx->nl, ctx->stream, sh); }, &ms));
         if (ms < best_ms) best_ms = ms, best.row_shape = sh;
@@ -565,6 +592,7 @@ static sft_status plan_step(sft_ctx* ctx) {
             if (e == cudaSuccess && hist) e = cudaMemcpyAsync(tfp, ctx->fprev, sb, cudaMemcpyDeviceToDevice, ctx->stream);
             best_ms = 1e30f;
             for (int sh = 0; sh < k2_col_shapes(ctx->ny) && e == cudaSuccess; ++sh) {
+                if (!col_shape_ok(ctx, sh)) continue;
                 for (int rpb : kRpbChoices) {
                     c.rpb = rpb;
                     float ms = 0.f;
@@ -624,25 +652,29 @@ static sft_status capture_graph(sft_ctx* ctx) {
 }
 
 static sft_status build_twiddles(sft_ctx* ctx, const std::vector<int>& lens) {
-    std::vector<float2> host;
+    size_t total = 0;
     for (int L : lens) {
         bool dup = false;
         for (int x : ctx->tw.lens) dup |= (x == L);
         if (dup || L < 2) continue;
         ctx->tw.lens.push_back(L);
-        ctx->tw.offs.push_back(host.size());
-        for (int m = 0; m < L; ++m) {
-            const double ang = 2.0 * M_PI * (double)m / (double)L;
-            host.push_back(make_float2((float)std::cos(ang), (float)-std::sin(ang)));
-        }
+        ctx->tw.offs.push_back(total);
+        total += (size_t)L;
     }
-    if (host.empty()) host.push_back(make_float2(1.f, 0.f));
-    CK(cudaMalloc(&ctx->tw.dev, host.size() * sizeof(float2)));
-    CK(cudaMemcpy(ctx->tw.dev, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->tw.dev, std::max<size_t>(total, 1) * sizeof(float2)));
+    for (size_t i = 0; i < ctx->tw.lens.size(); ++i)
+        CK(launch_twiddles(ctx->tw.dev + ctx->tw.offs[i], ctx->tw.lens[i], ctx->stream));
     return SFT_OK;
 }
 
-static sft_status validate(const sft_config* cfg, std::string& why) {
+namespace sft {
+sft_status validate_config(const sft_config* cfg, std::string& why);
+}
+
+static sft_status validate(const sft_config* cfg, std::string& why) { return sft::validate_config(cfg, why); }
+
+// The checks every configuration passes before any device work (also used by the allocation-free entry point).
+sft_status sft::validate_config(const sft_config* cfg, std::string& why) {
     if (!cfg) return why = "null config", SFT_EINVAL;
     if (cfg->d < 1 || cfg->d > 3) return why = "d must be 1, 2 or 3", SFT_EINVAL;
     for (int i = 0; i < cfg->d; ++i) {
@@ -803,6 +835,12 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     if (ctx->d == 1 && !ctx->cplx && k1_cluster_fft_len(ctx->nx))
         lens.push_back(k1_cluster_fft_len(ctx->nx));  // per-block FFT of the cluster kernel
     if (build_twiddles(ctx, lens) != SFT_OK) return cleanup(SFT_ECUDA);
+    if (!ctx->cplx && ctx->d >= 2 && (ctx->nx == 1024 || ctx->ny == 1024)) {
+        // twiddles of the 1024-point warp transforms: entry k1 32 + t = W_1024^{t k1}
+        if (!dalloc((void**)&ctx->tw32, 1024 * sizeof(float2)) || launch_twiddles32(ctx->tw32, ctx->stream) != cudaSuccess)
+            return cleanup(SFT_ECUDA);
+    }
+    if (const char* wl = getenv("SFT_WAIT_LIMIT")) ctx->wait_limit = atoi(wl);
     // FP64 coefficient tables
     TableArgs t{};
     t.model = cfg->model;
@@ -866,6 +904,53 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
                 ctx->counts[isqrt_ceil(sx * sx + sy * sy + sz * sz)] += w;
             }
         }
+    }
+    {
+        // the stored modes shell by shell (index order inside a shell), cut into chunks of at most
+        // kObsChunkLen modes inside one shell: the fixed summation order of every observation
+        const long long nm = ctx->nmodes;
+        std::vector<int> shell_of_mode((size_t)nm), fill(ctx->nshells + 1, 0);
+        for (int ax = 0; ax < ctx->hx; ++ax) {
+            const long long sx = ctx->cplx ? (2 * ax < ctx->nx ? ax : ax - ctx->nx) : ax;
+            for (int az = 0; az < ctx->nz; ++az) {
+                const long long sz = 2 * az < ctx->nz ? az : az - ctx->nz;
+                for (int ay = 0; ay < ctx->ny; ++ay) {
+                    const long long sy = 2 * ay < ctx->ny ? ay : ay - ctx->ny;
+                    const long long m = ((long long)ax * ctx->nz + az) * ctx->ny + ay;
+                    shell_of_mode[(size_t)m] = (int)isqrt_ceil(sx * sx + sy * sy + sz * sz);
+                }
+            }
+        }
+        std::vector<int> start(ctx->nshells + 1, 0);
+        for (long long m = 0; m < nm; ++m) ++start[shell_of_mode[(size_t)m] + 1];
+        for (int j = 0; j < ctx->nshells; ++j) start[j + 1] += start[j];
+        std::vector<int> order((size_t)nm);
+        for (long long m = 0; m < nm; ++m) {
+            const int j = shell_of_mode[(size_t)m];
+            order[(size_t)(start[j] + fill[j]++)] = (int)m;
+        }
+        std::vector<int4> chunks;
+        std::vector<int> first(ctx->nshells + 1, 0);
+        for (int j = 0; j < ctx->nshells; ++j) {
+            first[j] = (int)chunks.size();
+            for (int b = start[j]; b < start[j + 1]; b += kObsChunkLen)
+                chunks.push_back(make_int4(j, b, std::min(kObsChunkLen, start[j + 1] - b), 0));
+        }
+        first[ctx->nshells] = (int)chunks.size();
+        ctx->nchunks = (int)chunks.size();
+        if (!dalloc((void**)&ctx->d_order, order.size() * sizeof(int)) ||
+            !dalloc((void**)&ctx->d_chunks, chunks.size() * sizeof(int4)) ||
+            !dalloc((void**)&ctx->d_first_chunk, first.size() * sizeof(int)) ||
+            !dalloc((void**)&ctx->d_part, (size_t)ctx->R * chunks.size() * sizeof(double2)) ||
+            !dalloc((void**)&ctx->d_tacc, (size_t)ctx->nshells * sizeof(double2)))
+            return cleanup(SFT_ENOMEM);
+        if (cudaMemcpy(ctx->d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ctx->d_chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(ctx->d_first_chunk, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemset(ctx->d_tacc, 0, (size_t)ctx->nshells * sizeof(double2)) != cudaSuccess)
+            return cleanup(SFT_ECUDA);
     }
     ctx->launches_per_step = ctx->d == 1 ? 1 : 2;
     if (cfg->noise_space == 1) ctx->launches_per_step += 2;  // forward transform of the noise (drawn in its row pass)
@@ -1389,6 +1474,26 @@ static sft_status step_impl(sft_ctx* ctx, int64_t nsteps, bool use_graph) {
 
 sft_status sft_step(sft_ctx* ctx, int64_t nsteps) { return step_impl(ctx, nsteps, true); }
 
+sft_status sft_prepare(sft_ctx* ctx) {
+    if (!ctx) return SFT_EINVAL;
+    if (!ctx->p_valid) {
+        sft_status s = prime(ctx);
+        if (s != SFT_OK) return s;
+    }
+    if (!ctx->planned) {
+        sft_status s = plan_step(ctx);
+        if (s != SFT_OK) return s;
+    }
+    if (!ctx->graph) {
+        // capture only: the graph is instantiated, nothing runs and the state is untouched
+        sft_status s = capture_graph(ctx);
+        if (s != SFT_OK) return s;
+    }
+    ctx->warmed = true;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SFT_OK;
+}
+
 sft_status sft_get_plan(sft_ctx* ctx, int* out, int cap) {
     if (!ctx || !out || cap < 4) return SFT_EINVAL;
     if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
@@ -1409,8 +1514,8 @@ sft_status sft_set_plan(sft_ctx* ctx, const int* plan, int n) {
     if (!ctx || !plan || n < 4) return SFT_EINVAL;
     if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
     const bool real2 = ctx->d >= 2 && !ctx->cplx;
-    if (plan[0] < 0 || plan[0] >= (real2 ? k2_row_shapes(ctx->nx) : 1) || plan[1] < 0 ||
-        plan[1] >= (real2 && ctx->d == 2 ? k2_col_shapes(ctx->ny) : 1) || plan[2] < 1 || plan[2] > 64 ||
+    if (plan[0] < 0 || (real2 ? !row_shape_ok(ctx, plan[0]) : plan[0] != 0) || plan[1] < 0 ||
+        (real2 && ctx->d == 2 ? !col_shape_ok(ctx, plan[1]) : plan[1] != 0) || plan[2] < 1 || plan[2] > 64 ||
         (plan[3] != 0 && !(ctx->d == 2 && k2_pipe_supported(ctx->nx, ctx->ny, ctx->cplx))))
         return fail(ctx, SFT_EINVAL, "schedule outside the variants built for this lattice");
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1459,8 +1564,26 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
                            cudaMemcpyDeviceToDevice, ctx->stream));
         return read_status(ctx);
     }
-    if (kind < 0 || kind > SFT_OBS_NSHELLS) return fail(ctx, SFT_EINVAL, "unknown observable");
-    if (!host_out) return SFT_EINVAL;
+    if (kind == SFT_OBS_SK_RESET) {
+        CK(cudaMemsetAsync(ctx->d_tacc, 0, (size_t)ns * sizeof(double2), ctx->stream));
+        ctx->tacc_count = 0;
+        return SFT_OK;
+    }
+    if (kind == SFT_OBS_SK_TIME_MEAN) {
+        if (!host_out || cap < (size_t)ns + 1) return fail(ctx, SFT_EINVAL, "output too small");
+        std::vector<double2> acc(ns);
+        CK(cudaMemcpyAsync(acc.data(), ctx->d_tacc, (size_t)ns * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+        sft_status s = read_status(ctx);
+        if (s != SFT_OK) return s;
+        const double samples = (double)ctx->tacc_count * ctx->R;
+        for (int j = 0; j < ns; ++j)
+            host_out[j] = (ctx->counts[j] > 0 && samples > 0) ? (acc[j].x + acc[j].y) / (ctx->counts[j] * samples) : 0.0;
+        host_out[ns] = (double)ctx->tacc_count;
+        if (written) *written = ns + 1;
+        return SFT_OK;
+    }
+    if (kind < 0 || kind > SFT_OBS_SK_RESET) return fail(ctx, SFT_EINVAL, "unknown observable");
+    if (!host_out && kind != SFT_OBS_SK_ACCUM) return SFT_EINVAL;
     if (kind == SFT_OBS_CKT && !ctx->snap) return fail(ctx, SFT_EINVAL, "two-time correlation needs SFT_OBS_MARK first");
     if (kind == SFT_OBS_RESPONSE && !ctx->dseed) return fail(ctx, SFT_EINVAL, "response needs a seeded tangent");
     ObsArgs o{};
@@ -1471,13 +1594,27 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
     o.R = ctx->R;
     o.complex_field = ctx->cplx;
     o.nshells = ns;
+    o.order = ctx->d_order;
+    o.chunks = ctx->d_chunks;
+    o.first_chunk = ctx->d_first_chunk;
+    o.nchunks = ctx->nchunks;
+    o.part = ctx->d_part;
     double norm = 1.0;
     for (int i = 0; i < ctx->d; ++i) norm *= ctx->cfg.dx[i] / ctx->cfg.n[i];
     const size_t nsum = (size_t)ctx->R * ns;
     std::vector<double> sums(nsum), sums2;
-    std::vector<double> rough(ctx->R);
-    CK(cudaMemsetAsync(ctx->dshell, 0, nsum * sizeof(double), ctx->stream));
-    CK(cudaMemsetAsync(ctx->drough, 0, ctx->R * sizeof(double), ctx->stream));
+    if (kind == SFT_OBS_SK_ACCUM) {
+        // S(k) of the current state added to the device time accumulator; nothing comes back
+        o.phi = ctx->phi;
+        o.norm = norm;
+        o.kind = 0;
+        o.shell_sum = ctx->dshell;
+        CK(launch_observe(o, ctx->stream));
+        CK(launch_obs_time_acc(ctx->dshell, ctx->R, ns, ctx->d_tacc, ctx->stream));
+        ctx->launches += 3;
+        ctx->tacc_count += 1;
+        return SFT_OK;
+    }
     if (kind == SFT_OBS_RESPONSE) {
         o.phi = ctx->dphi;
         o.ref = ctx->dseed;
@@ -1485,14 +1622,13 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
         o.kind = 1;
         o.shell_sum = ctx->dshell;
         CK(launch_observe(o, ctx->stream));
-        ctx->launches += 1;
+        ctx->launches += 2;
         CK(cudaMemcpyAsync(sums.data(), ctx->dshell, nsum * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         sums2.resize(nsum);
-        CK(cudaMemsetAsync(ctx->dshell, 0, nsum * sizeof(double), ctx->stream));
         o.kind = 2;
         CK(launch_observe(o, ctx->stream));
-        ctx->launches += 1;
+        ctx->launches += 2;
         CK(cudaMemcpyAsync(sums2.data(), ctx->dshell, nsum * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         sft_status s = read_status(ctx);
         if (s != SFT_OK) return s;
@@ -1513,17 +1649,25 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
     o.norm = norm;
     o.kind = kind == SFT_OBS_CKT ? 1 : 0;
     o.shell_sum = ctx->dshell;
-    o.rough = kind == SFT_OBS_ROUGHNESS ? ctx->drough : nullptr;
     CK(launch_observe(o, ctx->stream));
-    ctx->launches += 1;
+    ctx->launches += 2;
     CK(cudaMemcpyAsync(sums.data(), ctx->dshell, nsum * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(rough.data(), ctx->drough, ctx->R * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     sft_status s = read_status(ctx);
     if (s != SFT_OK) return s;
     if (kind == SFT_OBS_ROUGHNESS) {
+        // w^2 = N^{-2d} sum_{a != 0} |phi_a|^2: every shell but j = 0 (which holds a = 0 alone), summed
+        // in shell order with compensation
         if (cap < (size_t)ctx->R) return fail(ctx, SFT_EINVAL, "output too small");
         const double n2 = (double)ctx->sites * (double)ctx->sites;
-        for (int r = 0; r < ctx->R; ++r) host_out[r] = rough[r] / n2;
+        for (int r = 0; r < ctx->R; ++r) {
+            double acc = 0.0, c = 0.0;
+            for (int j = 1; j < ns; ++j) {
+                const double x = sums[(size_t)r * ns + j], t = acc + x;
+                c += std::fabs(acc) >= std::fabs(x) ? (acc - t) + x : (x - t) + acc;
+                acc = t;
+            }
+            host_out[r] = (acc + c) / norm / n2;
+        }
         if (written) *written = ctx->R;
         return SFT_OK;
     }
@@ -2011,7 +2155,8 @@ void sft_destroy(sft_ctx* ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     void* bufs[] = {ctx->phi,   ctx->fprev,  ctx->P,      ctx->Q,      ctx->Py,     ctx->snap, ctx->real,
                     ctx->cfield, ctx->tab,   ctx->dstep,  ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev,
-                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec};
+                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec, ctx->tw32,
+                    ctx->d_order, ctx->d_chunks, ctx->d_first_chunk, ctx->d_part, ctx->d_tacc};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -64,6 +64,7 @@ struct StepArgs {
     const float2* tw_a;  // table for the first transform length
     const float2* tw_b;  // table for the second transform length
     const float2* tw_c;  // 1-D lines of 65536 points: table of the 8192-point per-block FFT
+    const float2* tw_32; // 1024-point warp transforms: tw_32[k1 32 + t] = W_1024^{t k1} (t, k1 < 32)
     // step bookkeeping
     const long long* step_base;  // device: step index of k_in_chunk = 0
     int k_in_chunk;
@@ -71,6 +72,8 @@ struct StepArgs {
     unsigned* status;             // bit 0: non-finite state
     long long* bad_step;
     int rpb;                      // 2-D column pass: replicas per block (< 1: the default)
+    int wait_limit;               // iterations of a bounded device wait: 0 the default (2^22); < 0 none, so
+                                  // the first wait of a launch times out (exercises the time-out path)
     // recording for the dynamic observables (2-D real fields): at steps rec_start + m rec_every,
     // m < rec_M, mode j (state layout index, replicas included) writes phi_j and F_j to
     // rec_*[m rec_n + j] (step-major, coalesced), rec_n = R n_modes
@@ -97,6 +100,12 @@ cudaError_t launch_k2_cols_mixed(const StepArgs& a, int mode, int nl, cudaStream
 bool k2_mixed_size(int n);   // p x 2^k points, p in {3, 5, 7}, 16p .. 768: 2-D real fields, transforms and step only
 int k2_col_shapes(int ny);  // schedule variants of the 2-D column pass for columns of ny points
 cudaError_t launch_k2_cols_pipe(const StepArgs& a, int nl, cudaStream_t s);
+// row pass of the step on rows of 1024 points, two rows per warp, TMA tiles (cubic term)
+bool k2_pair_supported(int nx, int ny, int nl, int dealias);
+cudaError_t launch_k2_rows_pair(const StepArgs& a, int nl, cudaStream_t s);
+// column pass of the step on columns of 1024 points, one warp per column (cubic term)
+bool k2_colwarp_supported(int nx, int ny, int nl, int dealias);
+cudaError_t launch_k2_cols_warp(const StepArgs& a, int nl, cudaStream_t s);
 cudaError_t launch_k3_planes(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2c_rows(const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_k2c_cols(const StepArgs& a, int mode, cudaStream_t s);
@@ -145,6 +154,10 @@ __host__ __device__ inline long long table_k2_index(int d, int hy, long long ent
     return entry;
 }
 cudaError_t launch_build_table(const TableArgs& t, cudaStream_t s);
+// tw[m] = e^{-2 pi i m / L} for m < L (every twiddle table of the step kernels)
+cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
+// tw[k1 32 + t] = W_1024^{t k1} for t, k1 < 32 (1024-point warp transforms)
+cudaError_t launch_twiddles32(float2* tw, cudaStream_t s);
 
 // initial condition (Philox tag 1) into a real-space buffer
 cudaError_t launch_init_random(float* real_out, float2* cplx_out, long long sites, int R, int rep0, uint64_t seed,
@@ -162,10 +175,21 @@ struct ObsArgs {
     const float2* ref;  // snapshot for two-time, tangent seed for response
     double norm;        // (L/N^2)^d
     int kind;           // 0: |phi|^2, 1: Re(phi conj(ref)), 2: |ref|^2 (response denominator)
-    double* shell_sum;  // [R][nshells] accumulators (zeroed by caller)
-    double* rough;      // [R] sum over a != 0 of |phi_a|^2 (full-spectrum weights)
+    double* shell_sum;  // [R][nshells] out: norm times the weighted shell sums
+    // the stored modes of one replica shell by shell (built once per lattice): order[] lists the
+    // mode indices of shell 0, then shell 1, ...; chunks[c] = {shell, start, length, 0} cuts it into
+    // runs of at most kObsChunkLen modes inside one shell; the chunks of shell j are
+    // first_chunk[j] .. first_chunk[j + 1] - 1
+    const int* order;
+    const int4* chunks;
+    const int* first_chunk;
+    int nchunks;
+    double2* part;      // [R][nchunks] scratch: compensated chunk sums (sum, correction)
 };
+constexpr int kObsChunkLen = 1024;
 cudaError_t launch_observe(const ObsArgs& o, cudaStream_t s);
+// acc[j] += sum_r shell_sum[r][j] (compensated pairs): the device time accumulator of S(k, t)
+cudaError_t launch_obs_time_acc(const double* shell_sum, int R, int nshells, double2* acc, cudaStream_t s);
 // per replica: sum over the boxes of ell^d sites of the height variance in the box (out zeroed by the caller)
 cudaError_t launch_box_width(const float* real, int nx, int ny, int nz, int d, int ell, int R, double* out,
                              cudaStream_t s);

@@ -5,9 +5,12 @@
 namespace sft {
 
 // (the forward transform of the real-space noise is instantiated here, for power-of-two rows)
-int k2_row_shapes(int nx) { return (nx & (nx - 1)) == 0 ? 3 : 1; }
+// shapes 0-2: the block shapes of k2_rows_real; 3 (rows of 1024 points): the two-rows-per-warp kernel of
+// sft_k2d_pair.cu (cubic term, see k2_pair_supported)
+int k2_row_shapes(int nx) { return (nx & (nx - 1)) == 0 ? (nx == 1024 ? 4 : 3) : 1; }
 
 cudaError_t launch_k2_rows(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape) {
+    if (shape == 3) return mode == MODE_STEP ? launch_k2_rows_pair(a, nl, s) : cudaErrorInvalidValue;
     switch (a.nx / 2) {
         case 8: return rows_for<8>(a, mode, nl, s, shape);
         case 16: return rows_for<16>(a, mode, nl, s, shape);

@@ -16,9 +16,12 @@ bool k2_supported(int nx, int ny, int complex_field) {
     return ok(nx) && ok(ny);
 }
 
-int k2_col_shapes(int ny) { return (ny & (ny - 1)) == 0 && ny >= 512 ? 3 : 1; }
+// shapes 0-2: the radix schedules and block shapes of k2_cols_real; 3 (columns of 1024 points): one warp
+// per column, sft_k2d_colwarp.cu (cubic term, see k2_colwarp_supported)
+int k2_col_shapes(int ny) { return (ny & (ny - 1)) == 0 && ny >= 512 ? (ny == 1024 ? 4 : 3) : 1; }
 
 cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape) {
+    if (shape == 3 && mode == MODE_STEP && !a.rec_phi && !a.noise_in && !a.pshift) return launch_k2_cols_warp(a, nl, s);
     switch (a.ny) {
         case 16: return cols_for<16>(a, mode, nl, s, shape);
         case 32: return cols_for<32>(a, mode, nl, s, shape);

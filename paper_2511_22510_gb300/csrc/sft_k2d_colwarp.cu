@@ -1,0 +1,139 @@
+// sft_k2d_colwarp.cu -- column pass of the 2-D real-field step on columns of
+// 1024 points, one warp per column (cubic term).
+//
+// Same step as the column pass of sft_k2d_cols.cuh (Sec. IV boxed algorithm,
+// the y half of steps 3-5): Q --FFT along y--> DFT[q]; F = M s DFT[q];
+// phi <- f1 phi + A F + B F_prev + g eta with the Philox noise of App. B;
+// Hermitian fix-up on the self-conjugate columns; P <- IFFT_y(M phi / N^2).
+// The column's 1024 values stay in the warp's registers (32 per lane, index
+// lane + 32 e) through both transforms and the update, so the only shared
+// memory traffic is one transpose per transform; the global loads and stores
+// of a slot are whole 256-byte lines of the column.  The noise of every mode
+// is drawn exactly as in the other column passes (the same counters, the same
+// words and the same Box-Muller recipe), so the result is the same step.
+#include "sft_step_common.cuh"
+#include "sft_warpfft.cuh"
+
+namespace sft {
+
+namespace {
+
+constexpr int kCwNY = 1024;
+constexpr int kCwWarps = 4;  // columns per block
+
+template <bool DEAL>
+__global__ void __launch_bounds__(kCwWarps * 32, 4) k2_cols_warp(const StepArgs a) {
+    constexpr int NY = kCwNY;
+    // slots e (index lane + 32 e) outside the 2/3 band |a_y| < 342 in every lane: e = 11 .. 20
+    constexpr uint32_t ZMASK = DEAL ? 0x001FF800u : 0u;
+    __shared__ __align__(16) float2 xbuf[kCwWarps][NY];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cc = blockIdx.x * kCwWarps + warp;
+    if (cc >= a.hx) return;  // whole warp
+    float2* xb = xbuf[warp];
+    const float2* __restrict__ tw32 = a.tw_32;
+    const long long step = current_step(a);
+    const bool first = (a.scheme == 2) && (step == *a.first_step);
+    const bool has_f = cc < a.ncols;
+    const bool plane = (cc == 0 || 2 * cc == a.nx);
+    const bool keep_x = !DEAL || 3 * cc < a.nx;
+    const float sB = a.model == 1 ? a.s0 * a.dk * a.dk : a.s0;  // Model B: s = -Gamma u k^2
+    const float4* __restrict__ trow = a.tab + (size_t)cc * (NY / 2 + 1);
+    for (int ri = 0; ri < a.rpb; ++ri) {
+        const int rep = blockIdx.y * a.rpb + ri;
+        if (rep >= a.R) break;
+        const size_t colbase = ((size_t)rep * a.hx + cc) * NY;
+        float2 v[32];
+        if (has_f) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = a.qin[colbase + lane + 32 * e];
+            fft1024_warp<false, 0u>(v, xb, lane, tw32);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = czero();
+        }
+        float nf = 0.f;
+#pragma unroll
+        for (int e = 0; e < 32; e += 2) {
+            float2 z0, z1;
+            team_normal_pair<32>(a.seed, (uint64_t)cc * NY, lane, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), z0, z1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int s = e + h;
+                const int ay = lane + 32 * s;
+                const int ays = ay < NY / 2 ? ay : ay - NY;  // signed index (ay = 512 -> -512)
+                const int aya = ays < 0 ? -ays : ays;
+                const bool inm = keep_x && (!DEAL || 3 * aya < NY);
+                float2 F = czero();
+                if (has_f && inm) {
+                    const float sq = a.model == 1 ? sB * (float)(cc * cc + ays * ays) : sB;
+                    F = cscale(v[s], sq);
+                }
+                const Coefs co = load_coefs<false>(reinterpret_cast<const float4*>(trow), aya, first);
+                const float2 ph = a.phi[colbase + ay];
+                float2 Fp = czero();
+                if (a.scheme == 2 && has_f) Fp = a.fprev[colbase + ay];
+                const bool selfc = plane && (ay == 0 || ay == NY / 2);
+                const float2 out = setd_update<false>(co, ph, F, Fp, eta_of(h ? z1 : z0, selfc));
+                if (a.scheme == 2 && has_f) a.fprev[colbase + ay] = F;
+                v[s] = out;
+            }
+        }
+        if (plane) {
+            // partners a_y > 512 take the conjugate of 1024 - a_y; self-conjugate modes are real
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) xb[lane + 32 * e] = v[e];
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int ay = lane + 32 * e;
+                if (2 * ay > NY) v[e] = cconj(xb[NY - ay]);
+                if (ay == 0 || 2 * ay == NY) v[e].y = 0.f;
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            a.phi[colbase + lane + 32 * e] = v[e];
+            nf = nonfinite_acc(nf, v[e]);
+        }
+        flag_nonfinite_acc(a, nf, step);
+        if (has_f) {
+            // P <- IFFT_y(M phi / N^2): the masked slots are zero in every lane
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int ay = lane + 32 * e;
+                const int aya = ay <= NY / 2 ? ay : NY - ay;
+                v[e] = ((ZMASK >> e) & 1u) ? czero() : ((!DEAL || 3 * aya < NY) ? cscale(v[e], a.scale) : czero());
+            }
+            fft1024_warp<true, ZMASK>(v, xb, lane, tw32);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) a.pout[colbase + lane + 32 * e] = v[e];
+        }
+    }
+}
+
+template <bool DEAL>
+cudaError_t run_cw(const StepArgs& a, cudaStream_t s) {
+    StepArgs b = a;
+    if (b.rpb < 1) b.rpb = 4;
+    dim3 grid((a.hx + kCwWarps - 1) / kCwWarps, (a.R + b.rpb - 1) / b.rpb);
+    k2_cols_warp<DEAL><<<grid, kCwWarps * 32, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool k2_colwarp_supported(int nx, int ny, int nl, int dealias) {
+    (void)nx;
+    return ny == kCwNY && nl == NL_CUBIC && (dealias == 0 || dealias == 1);
+}
+
+cudaError_t launch_k2_cols_warp(const StepArgs& a, int nl, cudaStream_t s) {
+    if (!k2_colwarp_supported(a.nx, a.ny, nl, a.pshift ? 2 : a.dealias) || !a.tw_32 || a.rec_phi || a.noise_in)
+        return cudaErrorInvalidValue;
+    return a.dealias ? run_cw<true>(a, s) : run_cw<false>(a, s);
+}
+
+}  // namespace sft

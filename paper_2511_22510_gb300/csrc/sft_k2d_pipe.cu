@@ -7,8 +7,9 @@
 // team of T threads walks a strided list of (column, replica) items and keeps
 // two shared-memory stages; while it computes item k, the next item's row-pass
 // column and state column stream in with cp.async.bulk, completing on a
-// per-stage mbarrier.  Waits are bounded: a wait that runs out sets status
-// bit 1 (time-out), drains its in-flight copy (bounded) and stops.
+// per-stage mbarrier.  Waits are bounded (StepArgs::wait_limit): a wait that
+// runs out sets status bit 1 (time-out), lets its copies in flight land
+// (bounded) and stops.
 #include "sft_async.cuh"
 #include "sft_step_common.cuh"
 
@@ -73,11 +74,13 @@ __global__ void __launch_bounds__(ColPipeCfg<NY>::THREADS, 1) k2_cols_pipe(const
         fence_proxy_async_smem();
         team_sync<T>();  // the team is done with the other stage
         if (t == 0 && i + G < total) issue(i + G, 1 - s);
-        if (!mbar_wait_bounded(&bar[s], (uint32_t)((k >> 1) & 1))) atomicOr(&team_abort[team], 1u);
+        if (!mbar_wait_bounded(&bar[s], (uint32_t)((k >> 1) & 1), wait_iters(a))) atomicOr(&team_abort[team], 1u);
         team_sync<T>();
         if (team_abort[team]) {
+            // report the time-out, let both stages' copies in flight land (bounded waits) and stop
             if (t == 0) {
                 atomicOr(a.status, 2u);
+                mbar_wait_bounded(&bar[s], (uint32_t)((k >> 1) & 1));
                 if (i + G < total) mbar_wait_bounded(&bar[1 - s], (uint32_t)(((k + 1) >> 1) & 1));
             }
             return;

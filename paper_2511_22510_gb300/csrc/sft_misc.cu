@@ -148,6 +148,37 @@ cudaError_t launch_build_table(const TableArgs& t, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- twiddle tables
+// tw[m] = W_L^m = e^{-2 pi i m / L}, m < L: sin and cos of pi (2m / L) in FP64
+// (exact zeros at the quarter turns), rounded to float.
+__global__ void k_twiddles(float2* tw, int L) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= L) return;
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)L, &sn, &cs);
+    tw[m] = make_float2((float)cs, (float)-sn);
+}
+
+cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s) {
+    if (L < 1) return cudaSuccess;
+    k_twiddles<<<(L + 127) / 128, 128, 0, s>>>(tw, L);
+    return cudaGetLastError();
+}
+
+// tw[k1 32 + t] = W_1024^{t k1} for t, k1 < 32 (the 1024-point warp transforms)
+__global__ void k_twiddles32(float2* tw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 1024) return;
+    double sn, cs;
+    sincospi(2.0 * (double)((i >> 5) * (i & 31)) / 1024.0, &sn, &cs);
+    tw[i] = make_float2((float)cs, (float)-sn);
+}
+
+cudaError_t launch_twiddles32(float2* tw, cudaStream_t s) {
+    k_twiddles32<<<8, 128, 0, s>>>(tw);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------- initial condition
 // Real fields: site s of replica r is sigma * z[s & 3] of the four normals of
 // Philox(ctr = (s >> 2, 0, r, 1)); complex fields: sigma (z_a + i z_b) of the
@@ -191,122 +222,104 @@ cudaError_t launch_advance(long long* step_base, int by, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- observables
-// Shell j = ceil(|a|) (App. C: the shell (k_j - dk, k_j]).  For real fields
-// the stored half carries weight 2 off the planes a_x in {0, nx/2} (their
-// conjugate partners are not stored) and 1 on them.
-__device__ __forceinline__ int shell_of(long long q) {
-    // q < 2^31 on every built lattice: a single-precision root is within one of
-    // ceil(sqrt(q)); the integer steps make it exact
-    long long j = (long long)sqrtf((float)q);
-    while (j * j < q) ++j;
-    while (j > 0 && (j - 1) * (j - 1) >= q) --j;
-    return (int)j;
+// Shell sums in a fixed order with compensation, so that repeated evaluations
+// give the same bits and long sums keep FP64 accuracy (App. C estimators):
+// the stored modes are enumerated shell by shell (ObsArgs::order, built once
+// per lattice on the host) and cut into chunks of at most kObsChunkLen modes
+// inside one shell.  One warp per chunk and replica sums its modes with
+// Neumaier's compensated summation (each lane a fixed stride of the chunk,
+// then a fixed shuffle tree combining (sum, correction) pairs by Knuth's
+// two-sum); a second pass combines the chunks of every shell in order.  For
+// real fields the stored half carries weight 2 off the planes a_x in {0, nx/2}
+// and 1 on them.
+
+// s + x with its rounding error carried in c (Neumaier)
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
+    const double t = s + x;
+    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
 }
 
-// Modes per thread run: a thread takes kObsRun consecutive modes (along a_y) and
-// sums them per shell in registers, touching the shell accumulators once per
-// change of shell instead of once per mode.
-constexpr int kObsRun = 16;
-
-// Shell sums go through a per-block shared array when it fits (local = true),
-// else straight to the global accumulators.  A run's partial sum is FP32 for
-// the non-negative sums |phi|^2 and |ref|^2 (at most kObsRun terms) and FP64 for
-// the signed two-time products; every accumulation beyond a run is FP64.
 template <int KIND>
-__global__ void k_observe(const ObsArgs o, bool local) {
-    using Acc = typename std::conditional<KIND == 1, double, float>::type;
-    extern __shared__ double acc[];
+__global__ void k_obs_chunks(const ObsArgs o) {
+    const int chunk = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     const int r = blockIdx.y;
-    if (local)
-        for (int j = threadIdx.x; j < o.nshells; j += blockDim.x) acc[j] = 0.0;
-    __shared__ double rough;
-    if (threadIdx.x == 0) rough = 0.0;
-    __syncthreads();
-    const int nmodes = o.hx * o.nz * o.ny;  // per replica, < 2^31 on every built lattice
-    const int per = ((nmodes + gridDim.x - 1) / gridDim.x + kObsRun - 1) / kObsRun * kObsRun;
-    const int m0 = blockIdx.x * per;
-    const int m1 = min(nmodes, m0 + per);
-    const float2* phi = o.phi ? o.phi + (size_t)r * nmodes : nullptr;
-    const float2* ref = o.ref ? o.ref + (size_t)r * nmodes : nullptr;
-    double* gsum = o.shell_sum + (size_t)r * o.nshells;
-    double my_rough = 0.0;
-    for (int base = m0 + threadIdx.x * kObsRun; base < m1; base += blockDim.x * kObsRun) {
-        int cur_j = -1;
-        Acc cur = 0, run_rough = 0;
-        const int nrun = min(kObsRun, m1 - base);
-        for (int i = 0; i < nrun; ++i) {
-            const int m = base + i;
-            const int ay = m % o.ny;
-            const int rest = m / o.ny;
-            const int az = rest % o.nz;
-            const int ax = rest / o.nz;
-            const long long sx = o.complex_field ? signed_idx(ax, o.nx) : ax;
-            const long long sy = signed_idx(ay, o.ny), sz = signed_idx(az, o.nz);
-            const long long q = sx * sx + sy * sy + sz * sz;
-            const float w = (!o.complex_field && ax != 0 && 2 * ax != o.nx) ? 2.f : 1.f;
-            Acc val;
-            if constexpr (KIND == 0) {
-                const float2 v = phi ? phi[m] : make_float2(0.f, 0.f);
-                val = (Acc)(v.x * v.x + v.y * v.y);
-            } else if constexpr (KIND == 1) {
-                const float2 v = phi[m], u = ref[m];
-                val = (double)v.x * u.x + (double)v.y * u.y;
-            } else {
-                const float2 u = ref[m];
-                val = (Acc)(u.x * u.x + u.y * u.y);
-            }
-            const int j = shell_of(q);
-            if (j != cur_j) {
-                if (cur_j >= 0) {
-                    if (local)
-                        atomicAdd(&acc[cur_j], (double)cur * o.norm);
-                    else
-                        atomicAdd(&gsum[cur_j], (double)cur * o.norm);
-                }
-                cur_j = j;
-                cur = 0;
-            }
-            cur += w * val;
-            if (KIND == 0 && q != 0) run_rough += w * val;
+    if (chunk >= o.nchunks) return;  // whole warp
+    const int4 ch = o.chunks[chunk];
+    const size_t nm = (size_t)o.hx * o.nz * o.ny;
+    const float2* phi = o.phi ? o.phi + (size_t)r * nm : nullptr;
+    const float2* ref = o.ref ? o.ref + (size_t)r * nm : nullptr;
+    const int plane = o.nz * o.ny;
+    double s = 0.0, c = 0.0;
+    for (int i = lane; i < ch.z; i += 32) {
+        const int m = o.order[ch.y + i];
+        const int ax = m / plane;
+        const double w = (!o.complex_field && ax != 0 && 2 * ax != o.nx) ? 2.0 : 1.0;
+        double val;
+        if constexpr (KIND == 0) {
+            const float2 v = phi[m];
+            val = (double)v.x * v.x + (double)v.y * v.y;
+        } else if constexpr (KIND == 1) {
+            const float2 v = phi[m], u = ref[m];
+            val = (double)v.x * u.x + (double)v.y * u.y;
+        } else {
+            const float2 u = ref[m];
+            val = (double)u.x * u.x + (double)u.y * u.y;
         }
-        if (cur_j >= 0) {
-            if (local)
-                atomicAdd(&acc[cur_j], (double)cur * o.norm);
-            else
-                atomicAdd(&gsum[cur_j], (double)cur * o.norm);
-        }
-        my_rough += (double)run_rough;
+        neumaier_add(s, c, w * val);
     }
-    if (KIND == 0 && o.rough) atomicAdd(&rough, my_rough);
-    __syncthreads();
-    if (local)
-        for (int j = threadIdx.x; j < o.nshells; j += blockDim.x)
-            if (acc[j] != 0.0) atomicAdd(&gsum[j], acc[j]);
-    if (threadIdx.x == 0 && KIND == 0 && o.rough) atomicAdd(&o.rough[r], rough);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double s2 = __shfl_down_sync(0xffffffffu, s, off), c2 = __shfl_down_sync(0xffffffffu, c, off);
+        neumaier_add(s, c, s2);
+        c += c2;
+    }
+    if (lane == 0) o.part[(size_t)r * o.nchunks + chunk] = make_double2(s, c);
+}
+
+// shell_sum[r][j] = norm * (the chunks of shell j combined in order)
+__global__ void k_obs_shells(const ObsArgs o) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)o.R * o.nshells) return;
+    const int r = (int)(i / o.nshells), j = (int)(i % o.nshells);
+    const double2* p = o.part + (size_t)r * o.nchunks;
+    double s = 0.0, c = 0.0;
+    for (int k = o.first_chunk[j]; k < o.first_chunk[j + 1]; ++k) {
+        neumaier_add(s, c, p[k].x);
+        c += p[k].y;
+    }
+    o.shell_sum[i] = (s + c) * o.norm;
 }
 
 cudaError_t launch_observe(const ObsArgs& o, cudaStream_t s) {
-    const long long nmodes = (long long)o.hx * o.nz * o.ny;
-    // about four blocks per SM over all replicas, each over whole runs of modes
-    const long long runs = (nmodes + kObsRun - 1) / kObsRun;
-    long long nb = (608 + o.R - 1) / o.R;
-    const long long cap = (runs + 255) / 256;
-    if (nb > cap) nb = cap;
-    if (nb < 1) nb = 1;
-    dim3 grid((unsigned)nb, o.R);
-    const bool local = sizeof(double) * (size_t)o.nshells <= 96 * 1024;
-    const size_t sm = local ? sizeof(double) * (size_t)o.nshells : 0;
-    auto run = [&](auto kern) -> cudaError_t {
-        if (sm > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-        }
-        kern<<<grid, 256, sm, s>>>(o, local);
-        return cudaGetLastError();
-    };
-    if (o.kind == 1) return run(k_observe<1>);
-    if (o.kind == 2) return run(k_observe<2>);
-    return run(k_observe<0>);
+    if (o.nchunks < 1) return cudaErrorInvalidValue;
+    dim3 g1((unsigned)((o.nchunks + 7) / 8), o.R);
+    if (o.kind == 1)
+        k_obs_chunks<1><<<g1, 256, 0, s>>>(o);
+    else if (o.kind == 2)
+        k_obs_chunks<2><<<g1, 256, 0, s>>>(o);
+    else
+        k_obs_chunks<0><<<g1, 256, 0, s>>>(o);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)o.R * o.nshells;
+    k_obs_shells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o);
+    return cudaGetLastError();
+}
+
+// Time accumulator of S(k, t): acc[j] += sum over replicas r (in order) of shell_sum[r][j], as a
+// compensated (sum, correction) pair.
+__global__ void k_obs_time_acc(const double* shell_sum, int R, int nshells, double2* acc) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nshells) return;
+    double s = acc[j].x, c = acc[j].y;
+    for (int r = 0; r < R; ++r) neumaier_add(s, c, shell_sum[(size_t)r * nshells + j]);
+    acc[j] = make_double2(s, c);
+}
+
+cudaError_t launch_obs_time_acc(const double* shell_sum, int R, int nshells, double2* acc, cudaStream_t s) {
+    k_obs_time_acc<<<(nshells + 127) / 128, 128, 0, s>>>(shell_sum, R, nshells, acc);
+    return cudaGetLastError();
 }
 
 }  // namespace sft

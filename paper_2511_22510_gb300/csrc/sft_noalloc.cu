@@ -12,14 +12,22 @@
 // That array exists once per GPU that loads this library and stays allocated
 // until the process exits.  Its address is looked up once per device, with the
 // device current, on that device's first call (cudaGetSymbolAddress); make
-// that first call before any stream capture.  Every call shares the array and
-// it keeps the previous call's contents, so calls whose work overlaps on the
-// GPU (different streams, or different host threads on one stream without
-// ordering) race on it: order them.
+// that first call before any stream capture.  The address is kept for the rest
+// of the process, so the entry point must not be called after anything that
+// destroys the device's primary context (cudaDeviceReset): the module is then
+// loaded again elsewhere and the kept address is stale.  Every call shares the
+// array and it keeps the previous call's contents, so calls whose work
+// overlaps on the GPU (different streams, or different host threads on one
+// stream without ordering) race on it: order them.
+//
+// A configuration passes the same checks as sft_create (validate_config) and
+// then the limits of the scratch below.
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <mutex>
+#include <string>
 
 #include "../../include/sft.h"
 #include "sft_internal.h"
@@ -47,21 +55,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 std::mutex g_mu;
 unsigned char* g_addr[64] = {nullptr};
 
-// twiddle tables W_L^m = e^{-2 pi i m / L} for the three lengths, FP64 -> float
-__global__ void k_noalloc_twiddles(float2* tw, int l0, int l1, int l2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lens[3] = {l0, l1, l2};
-    int off = 0;
-    for (int k = 0; k < 3; ++k) {
-        if (i >= off && i < off + lens[k]) {
-            double sn, cs;
-            sincospi(2.0 * (double)(i - off) / (double)lens[k], &sn, &cs);
-            tw[i] = make_float2((float)cs, (float)-sn);
-        }
-        off += lens[k];
-    }
-}
-
 // counters: [0] step base, [1] SETD2 first step, [2] bad step; status word after them
 __global__ void k_noalloc_counters(long long* cnt, unsigned* status, long long step0, long long first) {
     cnt[0] = step0;
@@ -71,6 +64,7 @@ __global__ void k_noalloc_counters(long long* cnt, unsigned* status, long long s
 }
 
 }  // namespace
+sft_status validate_config(const sft_config* cfg, std::string& why);  // sft_api.cu: the checks of sft_create
 }  // namespace sft
 
 using namespace sft;
@@ -78,14 +72,19 @@ using namespace sft;
 extern "C" sft_status sft_step2d_noalloc(const sft_config* cfg, void* phi_dev, void* fprev_dev, int history_valid,
                                          int64_t step0, int64_t nsteps) {
     if (!cfg || !phi_dev || nsteps < 0 || step0 < 0) return SFT_EINVAL;
+    std::string why;
+    const sft_status vs = validate_config(cfg, why);
+    if (vs != SFT_OK) {
+        fprintf(stderr, "sft_step2d_noalloc: %s\n", why.c_str());
+        return vs;
+    }
+    // the variants this entry point carries: 2-D real fields (Model A/B, KPZ), power-of-two sizes,
+    // Fourier-space noise, 2/3 truncation or none
     if (cfg->d != 2 || cfg->model == SFT_CGL || cfg->model == SFT_CUSTOM || cfg->noise_space != 0 || cfg->dealias == 2 ||
         (cfg->n[0] & (cfg->n[0] - 1)) != 0)
         return SFT_EUNSUPPORTED;
-    if (cfg->model != SFT_KPZ && cfg->p[4] != 0.0 && cfg->scheme == SFT_SETD2) return SFT_EUNSUPPORTED;
     const int nx = cfg->n[0], ny = cfg->n[1];
-    if (nx != ny || cfg->dx[0] != cfg->dx[1] || !k2_supported(nx, ny, 0)) return SFT_EUNSUPPORTED;
     if (nx > kNoAllocMaxN) return SFT_EINVAL;
-    if (cfg->replicas < 1 || !(cfg->h > 0) || cfg->scheme < SFT_SETD_EM || cfg->scheme > SFT_SETD2) return SFT_EINVAL;
     if (cfg->scheme == SFT_SETD2 && !fprev_dev) return SFT_EINVAL;
     const int hx = nx / 2 + 1;
     const long long modes = (long long)cfg->replicas * hx * ny;
@@ -116,8 +115,10 @@ extern "C" sft_status sft_step2d_noalloc(const sft_config* cfg, void* phi_dev, v
 
     // per-call set-up inside the scratch (it keeps the last call's contents)
     const int nl = cfg->model == SFT_KPZ ? NL_GRAD2 : NL_CUBIC;
-    const int lw = nx / 2 + nx + ny;
-    k_noalloc_twiddles<<<(lw + 127) / 128, 128, 0, st>>>(tw, nx / 2, nx, ny);
+    // twiddle tables of the three transform lengths, by the builder sft_create uses
+    if (launch_twiddles(tw, nx / 2, st) != cudaSuccess || launch_twiddles(tw + nx / 2, nx, st) != cudaSuccess ||
+        launch_twiddles(tw + nx / 2 + nx, ny, st) != cudaSuccess)
+        return SFT_ECUDA;
     const float2* twM = tw;
     const float2* twN = tw + nx / 2;
     const float2* twY = tw + nx / 2 + nx;

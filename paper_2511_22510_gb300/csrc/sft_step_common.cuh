@@ -128,6 +128,11 @@ __device__ __forceinline__ void block_copy(int n, Load&& load, Store&& store) {
 
 __device__ __forceinline__ long long current_step(const StepArgs& a) { return *a.step_base + a.k_in_chunk; }
 
+// Iteration limit of the launch's bounded waits (StepArgs::wait_limit).
+__device__ __forceinline__ uint32_t wait_iters(const StepArgs& a) {
+    return a.wait_limit == 0 ? (1u << 22) : (a.wait_limit < 0 ? 0u : (uint32_t)a.wait_limit);
+}
+
 __device__ __forceinline__ void flag_nonfinite(const StepArgs& a, float2 v, long long step) {
     if (!isfinite(v.x) || !isfinite(v.y)) {
         atomicOr(a.status, 1u);

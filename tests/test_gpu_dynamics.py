@@ -1,9 +1,10 @@
 """Dynamic correlation C(k, omega), noise-inferred susceptibility chi(k, omega)
 and the deviation from the FDT (App. C, Sec. V.A) on the GPU.
 
-* Parity: the GPU's C_ab and chi_ab equal the same estimators evaluated with
-  numpy on series recorded from the oracle (its state and its nonlinear force
-  F at every sampled step).
+* Parity: the GPU's C_ab, chi_ab and Dbar equal the oracle's App. C
+  estimators (oracle.dyn_estimators, pinned in test_oracle_dynamics.py) on the
+  series recorded from the oracle (its state and its nonlinear force F at every
+  sampled step), with the oracle's own c_a and D_a.
 * For a linear model (u = 0) the deterministic force is K = c phi, so every
   sample gives phi conj(-i omega phi - c phi) = (i omega - c) |phi|^2 and the
   estimator obeys 2 Im chi = (omega / D) C exactly: a check of the whole sign
@@ -46,20 +47,6 @@ def half_layout(full):
     return full[:, : nx // 2 + 1].T.ravel()
 
 
-def estimators(phi, F, c, D, T, norm):
-    """phi, F: (R, nmodes, M) series; returns C, chi (nmodes, M), b at index b mod M."""
-    M = phi.shape[-1]
-    X = np.fft.ifft(phi, axis=-1) * M  # sum_m e^{+2 pi i b m / M}
-    Y = np.fft.ifft(F, axis=-1) * M
-    b = np.fft.fftfreq(M, 1.0 / M)
-    w = 2 * np.pi * b / T
-    K = c[None, :, None] * X + Y
-    Z = -1j * w[None, None, :] * X - K
-    C = norm * np.sum(np.abs(X) ** 2, axis=0)
-    chi = norm / (2 * D[:, None]) * np.sum(X * np.conj(Z), axis=0)
-    return C, chi, w
-
-
 def test_dynamics_against_oracle(sft, oracle_mod):
     w = W.model_a_64(n=[16, 16], replicas=4, sigma0=0.3, h=0.02)
     M, every = 32, 2
@@ -84,12 +71,16 @@ def test_dynamics_against_oracle(sft, oracle_mod):
             phi[r, :, m] = half_layout(o.spectrum(r))
             F[r, :, m] = half_layout(o.force(r))
         o.step(every)
-    c, D = model_a_c_D(w)
+    c_full, D_full = o.mode_operators()
+    c, D = half_layout(c_full), half_layout(D_full)
     T = M * every * w.h
-    norm = (w.dx[0] / w.n[0]) ** 2 * T / M ** 2 / w.replicas
-    Co, chio, om = estimators(phi, F, c, D, T, norm)
+    norm = (w.dx[0] / w.n[0]) ** 2
+    Co, chio, dbar_o = oracle_mod.dyn_estimators(phi, F, c, D, T, norm)
     assert np.linalg.norm(C - Co) <= 1e-4 * np.linalg.norm(Co)
     assert np.linalg.norm(chi - chio) <= 1e-4 * np.linalg.norm(chio)
+    assert abs(dbar - dbar_o) <= 1e-3 * dbar_o
+    # the GPU's Dbar is its own C and chi summarised the same way
+    om = 2 * np.pi * np.fft.fftfreq(M, 1.0 / M) / T
     dev = np.abs(2 * chi.imag - om[None, :] / D[:, None] * C)
     assert abs(dbar - dev.mean()) <= 1e-9 * (1 + dev.mean())
 
