@@ -69,6 +69,7 @@ struct sft_ctx {
     int wait_limit = 0;      // StepArgs::wait_limit (SFT_WAIT_LIMIT; tests of the time-out path)
     // tangent / adjoint
     float2 *dphi = nullptr, *dseed = nullptr, *dP = nullptr, *dQ = nullptr;
+    float2* dfprev = nullptr;  // SETD2: the tangent's history dF of the previous step
     bool dp_valid = false;
     // host mirrors
     long long step = 0;
@@ -181,6 +182,7 @@ static StepArgs base_args(const sft_ctx* c) {
         default: a.s0 = -1.f; a.s0i = (float)(-p[1]); break;
     }
     a.seed = c->cfg.seed;
+    philox_key_schedule(a.seed, a.ks);
     a.tab = c->tab;
     a.phi = c->phi;
     a.fprev = c->fprev;
@@ -1694,16 +1696,22 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
     return SFT_OK;
 }
 
-static sft_status diff_supported(sft_ctx* ctx) {
-    if (ctx->cplx || ctx->nl != NL_CUBIC || ctx->cfg.scheme == SFT_SETD2 || (ctx->d == 1 && ctx->nx > 32768) ||
-        ctx->cfg.dealias == 2 || !is_pow2(ctx->nx))
+// adjoint: whether the adjoint (not only the tangent) is asked for
+static sft_status diff_supported(sft_ctx* ctx, bool adjoint) {
+    if (ctx->cplx || ctx->nl != NL_CUBIC || (adjoint && ctx->cfg.scheme == SFT_SETD2) ||
+        (ctx->d == 1 && ctx->nx > 32768) || ctx->cfg.dealias == 2 || !is_pow2(ctx->nx))
         return fail(ctx, SFT_EUNSUPPORTED,
-                    "tangent/adjoint are built for real fields with the cubic term (Model A/B), SETD-EM or SETD1 "
-                    "(1-D up to 32768 points), power-of-two lattices without phase-shift dealiasing");
+                    "tangent/adjoint are built for real fields with the cubic term (Model A/B), the tangent for "
+                    "every scheme and the adjoint for SETD-EM and SETD1 (1-D up to 32768 points), power-of-two "
+                    "lattices without phase-shift dealiasing");
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (!ctx->dphi) {
         CK(cudaMalloc(&ctx->dphi, ms));
         CK(cudaMemsetAsync(ctx->dphi, 0, ms, ctx->stream));
+    }
+    if (ctx->cfg.scheme == SFT_SETD2 && !ctx->dfprev) {
+        CK(cudaMalloc(&ctx->dfprev, ms));
+        CK(cudaMemsetAsync(ctx->dfprev, 0, ms, ctx->stream));
     }
     if (!ctx->dseed) CK(cudaMalloc(&ctx->dseed, ms));
     if (ctx->d >= 2 && !ctx->dP) {
@@ -1743,13 +1751,15 @@ static sft_status device_field_from_spectrum(sft_ctx* ctx, const float2* src, vo
 sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps, void* dphi_out_dev) {
     if (!ctx || nsteps < 0) return SFT_EINVAL;
     if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
-    sft_status s = diff_supported(ctx);
+    sft_status s = diff_supported(ctx, false);
     if (s != SFT_OK) return s;
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (dphi0_dev) {
         s = spectrum_from_device_field(ctx, dphi0_dev, ctx->dphi);
         if (s != SFT_OK) return s;
         CK(cudaMemcpyAsync(ctx->dseed, ctx->dphi, ms, cudaMemcpyDeviceToDevice, ctx->stream));
+        // a perturbation seeded now leaves the nonlinear term of the previous step unchanged
+        if (ctx->dfprev) CK(cudaMemsetAsync(ctx->dfprev, 0, ms, ctx->stream));
         ctx->dp_valid = false;
     }
     if (!ctx->p_valid) {
@@ -1768,6 +1778,7 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
     for (int64_t i = 0; i < nsteps; ++i) {
         StepArgs a = base_args(ctx);
         a.dphi = ctx->dphi;
+        a.dfprev = ctx->dfprev;
         if (ctx->d == 1) {
             a.tw_a = ctx->tw.get(ctx->nx / 2);
             a.tw_b = ctx->tw.get(ctx->nx);
@@ -1810,7 +1821,7 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
 sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* grad_dev) {
     if (!ctx || !cot_dev || !grad_dev || nsteps < 1) return SFT_EINVAL;
     if (ctx->is_batch) return fail(ctx, SFT_EUNSUPPORTED, "not available on a batch context; use its members' configurations individually");
-    sft_status s = diff_supported(ctx);
+    sft_status s = diff_supported(ctx, true);
     if (s != SFT_OK) return s;
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     const int64_t K = ctx->ckpt_segment;
@@ -2155,7 +2166,7 @@ void sft_destroy(sft_ctx* ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     void* bufs[] = {ctx->phi,   ctx->fprev,  ctx->P,      ctx->Q,      ctx->Py,     ctx->snap, ctx->real,
                     ctx->cfield, ctx->tab,   ctx->dstep,  ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev,
-                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec, ctx->tw32,
+                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec, ctx->tw32, ctx->dfprev,
                     ctx->d_order, ctx->d_chunks, ctx->d_first_chunk, ctx->d_part, ctx->d_tacc};
     for (void* p : bufs)
         if (p) cudaFree(p);

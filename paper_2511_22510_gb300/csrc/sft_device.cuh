@@ -39,6 +39,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
+// The same generator with the ten round keys given (ks[2i], ks[2i + 1] = key +
+// i Weyl constants): kernels pass the schedule of their seed as a kernel
+// parameter, so no key additions are issued per call.
+__device__ __forceinline__ uint4 philox4x32_10_ks(uint4 c, const uint32_t (&ks)[20]) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ ks[2 * i], lo1, hi0 ^ c.w ^ ks[2 * i + 1], lo0);
+    }
+    return c;
+}
+
 // --------------------------------------------------------- Box-Muller recipe
 // ln x for x in [2^-24, 1]: x = 2^e m, m in (1/sqrt2, sqrt2]; ln m = 2 atanh(s),
 // s = (m-1)/(m+1), odd Taylor series of atanh through s^11; ln 2 split in a

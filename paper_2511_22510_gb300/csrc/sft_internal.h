@@ -39,6 +39,7 @@ struct StepArgs {
     int scheme;    // sft_scheme
     float s0, s0i; // nonlinear prefactor: A: -Gamma u; B: -Gamma u (times k^2); KPZ: lambda/2; CGL: -(1 + i beta)
     uint64_t seed;
+    uint32_t ks[20];    // Philox round keys of the seed: ks[2i], ks[2i + 1] = seed words + i Weyl constants
     const float4* tab;  // per |a|^2 coefficients {f1, A, B, g} (complex: 2 float4 per entry)
     // buffers (x-major layouts, replica-major)
     float2* phi;        // state
@@ -84,6 +85,18 @@ struct StepArgs {
     const float2* noise_in;  // real-space noise: DFT of the draw (state layout); eta = noise_scale * noise_in
     float noise_scale;
 };
+
+// Round keys of Philox4x32-10 for a seed: the key, then bumped by the Weyl constants 0x9E3779B9 / 0xBB67AE85
+// before each further round (StepArgs::ks).
+inline void philox_key_schedule(uint64_t seed, uint32_t (&ks)[20]) {
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        ks[2 * i] = k0;
+        ks[2 * i + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
 
 // launchers (return cudaGetLastError of the launch); each picks the template
 // instance for the lattice size and returns cudaErrorInvalidValue if none.

@@ -189,7 +189,10 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
             float2 XqM;
             line_post<M>(z, xb, t, twN, Xq, XqM);
             const long long step = current_step(a);
+            const bool first = (a.scheme == 2) && (step == *a.first_step);
             const uint32_t rep = (uint32_t)(a.rep0 + rr);
+            float2* fp = a.fprev + (size_t)rr * (M + 1);
+            float2* dfp = a.dfprev + (size_t)rr * (M + 1);
             float2 zn0, zn1;
 #pragma unroll
             for (int e = 0; e <= E; ++e) {
@@ -200,12 +203,15 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
                 const float sq = nl_prefactor(a, k * k).x;
                 const float2 F = inm ? cscale((e < E) ? Xq[e] : XqM, sq) : czero();
                 const float2 dF = inm ? cscale((e < E) ? dXq[e] : dXqM, sq) : czero();
-                const Coefs co = load_coefs<false>(a.tab, k, false);
+                const Coefs co = load_coefs<false>(a.tab, k, first);
                 const bool selfc = (k == 0 || k == M);
                 const float2 eta = (e < E) ? eta_of((e & 1) ? zn1 : zn0, selfc)
                                            : fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
-                float2 o = setd_update<false>(co, ph[k], F, czero(), eta);
-                float2 d = setd_update<false>(co, dp[k], dF, czero(), czero());
+                // SETD2: B F_prev for the primal, B dF_prev with the tangent's own history (zero at the seed)
+                const float2 Fp = (a.scheme == 2) ? fp[k] : czero();
+                const float2 dFp = (a.scheme == 2) ? dfp[k] : czero();
+                float2 o = setd_update<false>(co, ph[k], F, Fp, eta);
+                float2 d = setd_update<false>(co, dp[k], dF, dFp, czero());
                 if (selfc) {
                     o.y = 0.f;
                     d.y = 0.f;
@@ -213,6 +219,10 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
                 if (valid) {
                     ph[k] = o;
                     dp[k] = d;
+                    if (a.scheme == 2) {
+                        fp[k] = F;
+                        dfp[k] = dF;
+                    }
                     flag_nonfinite(a, o, step);
                 }
             }

@@ -339,6 +339,7 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
         // primal step as in MODE_STEP, plus the tangent dphi <- f1 dphi + A M s DFT[q'] (no noise)
         if (!valid && T >= 32) return;
         const long long step = current_step(a);
+        const bool first = (a.scheme == 2) && (step == *a.first_step);
         const bool has_f = valid && cc < a.ncols;
         float2 dv[E];
         if (has_f || T < 32) {
@@ -363,10 +364,20 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
             const float sq = nl_prefactor(a, q).x;
             const float2 F = (has_f && inm) ? cscale(v[e], sq) : czero();
             const float2 dF = (has_f && inm) ? cscale(dv[e], sq) : czero();
-            const Coefs co = load_coefs<false>(a.tab, cc * (NY / 2 + 1) + abs(ays), false);
+            const Coefs co = load_coefs<false>(a.tab, cc * (NY / 2 + 1) + abs(ays), first);
             const bool selfc = plane && (ay == 0 || 2 * ay == NY);
-            out[e] = setd_update<false>(co, a.phi[colbase + ay], F, czero(), eta_of(out[e], selfc));
-            dv[e] = setd_update<false>(co, a.dphi[colbase + ay], dF, czero(), czero());
+            // SETD2: B F_prev for the primal, B dF_prev with the tangent's own history (zero at the seed)
+            float2 Fp = czero(), dFp = czero();
+            if (a.scheme == 2 && has_f) {
+                Fp = a.fprev[colbase + ay];
+                dFp = a.dfprev[colbase + ay];
+            }
+            out[e] = setd_update<false>(co, a.phi[colbase + ay], F, Fp, eta_of(out[e], selfc));
+            dv[e] = setd_update<false>(co, a.dphi[colbase + ay], dF, dFp, czero());
+            if (a.scheme == 2 && has_f) {
+                a.fprev[colbase + ay] = F;
+                a.dfprev[colbase + ay] = dF;
+            }
         }
         fixup_plane<NY, EM>(out, xb, t, plane);
         fixup_plane<NY, EM>(dv, xb, t, plane);

@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(kCwWarps * 32, 4) k2_cols_warp(const StepArgs 
 #pragma unroll
         for (int e = 0; e < 32; e += 2) {
             float2 z0, z1;
-            team_normal_pair<32>(a.seed, (uint64_t)cc * NY, lane, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), z0, z1);
+            team_normal_pair_ks<32>(a.ks, (uint64_t)cc * NY, lane, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), z0,
+                                    z1);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int s = e + h;

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
 
     if constexpr (MODE == MODE_STEP || MODE == MODE_TAN || MODE == MODE_ADJ) {
         const long long step = current_step(a);
-        const bool first = (MODE == MODE_STEP) && (a.scheme == 2) && (step == *a.first_step);
+        const bool first = (MODE == MODE_STEP || MODE == MODE_TAN) && (a.scheme == 2) && (step == *a.first_step);
         const bool has_f = c < a.ncols;
         for (int it = 0; it < C::ITERS; ++it) {
             const int line = team + it * C::TEAMS;
@@ -127,7 +127,12 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
                         o = setd_update<false>(co, state[idx], F, Fp, eta_of(zz[h], selfc));
                         if (line < N && a.scheme == 2 && has_f) a.fprev[idx] = F;
                     } else if constexpr (MODE == MODE_TAN) {
-                        o = setd_update<false>(co, state[idx], cscale(Fh, nl_prefactor(a, q).x), czero(), czero());
+                        // SETD2: B dF_prev with the tangent's own history (zero at the seed)
+                        const float2 dF = cscale(Fh, nl_prefactor(a, q).x);
+                        float2 dFp = czero();
+                        if (a.scheme == 2 && has_f) dFp = a.dfprev[idx];
+                        o = setd_update<false>(co, state[idx], dF, dFp, czero());
+                        if (line < N && a.scheme == 2 && has_f) a.dfprev[idx] = dF;
                     } else {
                         const float2 l = state[idx];
                         o = make_float2(co.f1.x * l.x + Fh.x, co.f1.x * l.y + Fh.y);

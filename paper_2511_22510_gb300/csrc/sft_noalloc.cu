@@ -157,6 +157,7 @@ extern "C" sft_status sft_step2d_noalloc(const sft_config* cfg, void* phi_dev, v
     a.s0 = cfg->model == SFT_KPZ ? (float)(0.5 * cfg->p[1]) : (float)(-cfg->p[0] * cfg->p[2]);
     a.s0i = 0.f;
     a.seed = cfg->seed;
+    philox_key_schedule(a.seed, a.ks);
     a.tab = tab;
     a.phi = (float2*)phi_dev;
     a.fprev = (float2*)fprev_dev;

@@ -43,7 +43,15 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("name,w", CASES, ids=[c[0] for c in CASES])
+# SETD2 (Eq. SETD2): the tangent carries its own history dF_prev, zero at the seed
+TAN_CASES = CASES + [
+    ("model_a_64_setd2", W.model_a_64(n=[64, 64], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
+    ("model_b_1d_128_setd2", W.model_b_1024(d=1, n=[128], dx=[1.0], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
+    ("model_a_3d_16_setd2", W.model_a_128_3d(n=[16, 16, 16], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
+]
+
+
+@pytest.mark.parametrize("name,w", TAN_CASES, ids=[c[0] for c in TAN_CASES])
 def test_tangent_parity(env, oracle_mod, name, w):
     m, torch = env
     f0 = W.initial_fields(w)
