@@ -387,7 +387,7 @@ class Oracle:
         out = np.zeros(self.R * self.ntot)
         rc = lib().or_adjoint(self._p, _dptr(a), int(nsteps), _dptr(out))
         if rc != 0:
-            raise ValueError("adjoint needs a real field and SETD-EM or SETD1")
+            raise ValueError("adjoint needs a real field (and truncation or no dealiasing)")
         return out.reshape((self.R,) + self.shape)
 
 

@@ -1102,38 +1102,52 @@ int or_observe_response(const or_state* st, double* out) {
 
 /* ------------------------------------------------------------------------- */
 /* Adjoint (transpose of the tangent with respect to the real-space inner    */
-/* product sum_x u(x) v(x)), real fields, SETD-EM and SETD1.  With C(m) the  */
-/* real-space Fourier multiplier by m (symmetric when m is real and even),   */
-/* the tangent of one step is C(f1) + C(a M s) D(q') C(M); its transpose is  */
-/* C(f1) + C(M) D(q') C(a M s).  For KPZ the gradient multiplier i k is odd, */
-/* so its transpose is -i k.                                                  */
+/* product sum_x u(x) v(x)), real fields.  With C(m) the real-space Fourier  */
+/* multiplier by m (symmetric when m is real and even) and L_n = C(M s) D(q'_n) */
+/* C(M) the linearised nonlinear term of step n, the tangent of Eq. SETD2 is  */
+/*   dF_n = L_n dphi_n,  dphi_{n+1} = f1 dphi_n + a_n dF_n + b_n dF_{n-1}     */
+/* (dF_{-1} = 0 at the seed; SETD-EM and SETD1 have b = 0).  Its transpose    */
+/* runs backward from the cotangent lam_N of dphi_N with mu_{N-1} = 0:        */
+/*   nu_n = a_n lam_{n+1} + mu_n          (the cotangent of dF_n),            */
+/*   lam_n = f1 lam_{n+1} + L_n^T nu_n,   L_n^T = C(M) D(q'_n) C(M s),        */
+/*   mu_{n-1} = b_n lam_{n+1},                                                */
+/* with the SETD1 pair at the step that starts SETD2 (no F_{-1} exists).  For */
+/* KPZ the gradient multiplier i k is odd, so its transpose is -i k.          */
 /* ------------------------------------------------------------------------- */
 int or_adjoint(or_state* st, const double* lam_in, int64_t nsteps, double* grad_out) {
-    if (st->cplx_field || st->cfg.scheme == OR_SETD2 || st->cfg.dealias == 2) return -1;
+    if (st->cplx_field || st->cfg.dealias == 2) return -1;
     size_t nt = st->ntot;
     int R = st->cfg.replicas;
     cplx* traj = (cplx*)malloc(nt * (size_t)R * (size_t)(nsteps > 0 ? nsteps : 1) * sizeof(cplx));
+    /* step t of the recorded trajectory used the SETD1 pair if it started the SETD2 history */
+    int* first_of = (int*)calloc((size_t)(nsteps > 0 ? nsteps : 1), sizeof(int));
     for (int64_t t = 0; t < nsteps; ++t) {
         memcpy(traj + (size_t)t * nt * R, st->phi, nt * (size_t)R * sizeof(cplx));
+        first_of[t] = (st->cfg.scheme == OR_SETD2) && !st->have_fprev;
         or_step(st, 1);
     }
     cplx* lam = (cplx*)malloc(nt * sizeof(cplx));
+    cplx* mu = (cplx*)malloc(nt * sizeof(cplx));
     cplx* w = (cplx*)malloc(nt * sizeof(cplx));
     cplx* g = (cplx*)malloc(nt * sizeof(cplx));
     cplx* acc = (cplx*)malloc(nt * sizeof(cplx));
     for (int r = 0; r < R; ++r) {
-        for (size_t i = 0; i < nt; ++i) lam[i] = lam_in[(size_t)r * nt + i];
+        for (size_t i = 0; i < nt; ++i) {
+            lam[i] = lam_in[(size_t)r * nt + i];
+            mu[i] = 0.0;
+        }
         fft_full(st, lam, -1);
         hermitian_fixup(st, lam);
         for (int64_t t = nsteps - 1; t >= 0; --t) {
             const cplx* phi = traj + (size_t)t * nt * R + (size_t)r * nt;
-            /* W = IDFT(a M s Lam) */
+            /* W = IDFT(M s nu), nu = a lam + mu; then mu <- b lam (lam of step t + 1) */
             for (size_t i = 0; i < nt; ++i) {
                 cplx f1, a, b, gg, c, s;
                 double D;
-                mode_coefs(st, i, 0, &f1, &a, &b, &gg);
+                mode_coefs(st, i, first_of[t], &f1, &a, &b, &gg);
                 mode_operator(st, i, &c, &D, &s);
-                w[i] = a * mode_mask(st, i) * s * lam[i];
+                w[i] = mode_mask(st, i) * s * (a * lam[i] + mu[i]);
+                mu[i] = b * lam[i];
             }
             fft_full(st, w, +1);
             for (size_t i = 0; i < nt; ++i) w[i] = creal(w[i]) / (double)nt;
@@ -1168,16 +1182,19 @@ int or_adjoint(or_state* st, const double* lam_in, int64_t nsteps, double* grad_
             }
             for (size_t i = 0; i < nt; ++i) {
                 cplx f1, a, b, gg;
-                mode_coefs(st, i, 0, &f1, &a, &b, &gg);
+                mode_coefs(st, i, first_of[t], &f1, &a, &b, &gg);
                 lam[i] = f1 * lam[i] + acc[i];
             }
             hermitian_fixup(st, lam);
+            hermitian_fixup(st, mu);
         }
         memcpy(w, lam, nt * sizeof(cplx));
         fft_full(st, w, +1);
         for (size_t i = 0; i < nt; ++i) grad_out[(size_t)r * nt + i] = creal(w[i]) / (double)nt;
     }
     free(traj);
+    free(first_of);
+    free(mu);
     free(lam);
     free(w);
     free(g);

@@ -70,6 +70,7 @@ struct sft_ctx {
     // tangent / adjoint
     float2 *dphi = nullptr, *dseed = nullptr, *dP = nullptr, *dQ = nullptr;
     float2* dfprev = nullptr;  // SETD2: the tangent's history dF of the previous step
+    float2* dmu = nullptr;     // SETD2 adjoint: the cotangent of the history term
     bool dp_valid = false;
     // host mirrors
     long long step = 0;
@@ -1698,12 +1699,15 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
 
 // adjoint: whether the adjoint (not only the tangent) is asked for
 static sft_status diff_supported(sft_ctx* ctx, bool adjoint) {
-    if (ctx->cplx || ctx->nl != NL_CUBIC || (adjoint && ctx->cfg.scheme == SFT_SETD2) ||
-        (ctx->d == 1 && ctx->nx > 32768) || ctx->cfg.dealias == 2 || !is_pow2(ctx->nx))
+    // the cubic term in 1-D, 2-D and 3-D; the KPZ term and the complex |A|^2 A term (CGL) in 1-D; the adjoint
+    // for real fields
+    const bool term = ctx->nl == NL_CUBIC || (ctx->d == 1 && (ctx->nl == NL_GRAD2 || ctx->nl == NL_CGL));
+    if (!term || (adjoint && ctx->cplx) || (ctx->d == 1 && ctx->nx > 32768) || ctx->cfg.dealias == 2 ||
+        !is_pow2(ctx->nx) || ctx->cfg.noise_space != 0)
         return fail(ctx, SFT_EUNSUPPORTED,
-                    "tangent/adjoint are built for real fields with the cubic term (Model A/B), the tangent for "
-                    "every scheme and the adjoint for SETD-EM and SETD1 (1-D up to 32768 points), power-of-two "
-                    "lattices without phase-shift dealiasing");
+                    "the tangent is built for the cubic term (Model A/B, d = 1..3) and, in 1-D, the KPZ and CGL "
+                    "terms; the adjoint for the real fields among them; every scheme; 1-D lines up to 32768 "
+                    "points, power-of-two lattices, 2/3 truncation or none, Fourier-space noise");
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (!ctx->dphi) {
         CK(cudaMalloc(&ctx->dphi, ms));
@@ -1713,6 +1717,7 @@ static sft_status diff_supported(sft_ctx* ctx, bool adjoint) {
         CK(cudaMalloc(&ctx->dfprev, ms));
         CK(cudaMemsetAsync(ctx->dfprev, 0, ms, ctx->stream));
     }
+    if (adjoint && ctx->cfg.scheme == SFT_SETD2 && !ctx->dmu) CK(cudaMalloc(&ctx->dmu, ms));
     if (!ctx->dseed) CK(cudaMalloc(&ctx->dseed, ms));
     if (ctx->d >= 2 && !ctx->dP) {
         CK(cudaMalloc(&ctx->dP, ms));
@@ -1731,8 +1736,9 @@ static sft_status set_step_counter(sft_ctx* ctx, long long step) {
 
 // dst spectrum <- forward transform of R real-space fields at a device pointer
 static sft_status spectrum_from_device_field(sft_ctx* ctx, const void* dev_field, float2* dst) {
-    const size_t rs = (size_t)ctx->R * ctx->sites * sizeof(float);
-    CK(cudaMemcpyAsync(ctx->real, dev_field, rs, cudaMemcpyDeviceToDevice, ctx->stream));
+    const size_t rs = (size_t)ctx->R * ctx->sites * (ctx->cplx ? sizeof(float2) : sizeof(float));
+    CK(cudaMemcpyAsync(ctx->cplx ? (void*)ctx->cfield : (void*)ctx->real, dev_field, rs, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
     sft_status s = forward_from_buffer(ctx, 0, ctx->R, dst);
     if (s != SFT_OK) return s;
     ctx->launches += ctx->d == 1 ? 1 : 2;
@@ -1743,8 +1749,9 @@ static sft_status device_field_from_spectrum(sft_ctx* ctx, const float2* src, vo
     sft_status s = inverse_to_buffer(ctx, src, 0, ctx->R);
     if (s != SFT_OK) return s;
     ctx->launches += ctx->d == 1 ? 1 : 2;
-    CK(cudaMemcpyAsync(dev_field, ctx->real, (size_t)ctx->R * ctx->sites * sizeof(float), cudaMemcpyDeviceToDevice,
-                       ctx->stream));
+    CK(cudaMemcpyAsync(dev_field, ctx->cplx ? (const void*)ctx->cfield : (const void*)ctx->real,
+                       (size_t)ctx->R * ctx->sites * (ctx->cplx ? sizeof(float2) : sizeof(float)),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
     return SFT_OK;
 }
 
@@ -1780,8 +1787,10 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
         a.dphi = ctx->dphi;
         a.dfprev = ctx->dfprev;
         if (ctx->d == 1) {
-            a.tw_a = ctx->tw.get(ctx->nx / 2);
-            a.tw_b = ctx->tw.get(ctx->nx);
+            // complex lines: one C2C length; real lines: the half length and the full length
+            a.tw_a = ctx->cplx ? ctx->tw.get(ctx->nx) : ctx->tw.get(ctx->nx / 2);
+            a.tw_b = ctx->cplx ? nullptr : ctx->tw.get(ctx->nx);
+            if (!a.tw_a || (!ctx->cplx && !a.tw_b)) return fail(ctx, SFT_EINVAL, "twiddle table missing");
             CK(launch_k1_line(a, MODE_TAN, ctx->nl, ctx->stream));
             ctx->launches += 1;
         } else {
@@ -1849,26 +1858,40 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
             return s_;              \
         }                           \
     } while (0)
-    if (cudaMalloc(&ckpt, ms * (size_t)nseg) != cudaSuccess || cudaMalloc(&traj, ms * (size_t)(K + 1)) != cudaSuccess ||
-        cudaMalloc(&phiN, ms) != cudaSuccess) {
+    // a checkpoint holds the state and, for SETD2, the history F_prev that the next step reads
+    const bool hist = ctx->cfg.scheme == SFT_SETD2;
+    const size_t cs = hist ? 2 * ms : ms;
+    const size_t cm = hist ? 2 * (size_t)ctx->R * ctx->nmodes : (size_t)ctx->R * ctx->nmodes;  // in float2
+    if (cudaMalloc(&ckpt, cs * (size_t)nseg) != cudaSuccess || cudaMalloc(&traj, ms * (size_t)(K + 1)) != cudaSuccess ||
+        cudaMalloc(&phiN, cs) != cudaSuccess) {
         release();
         return fail(ctx, SFT_ENOMEM, "adjoint checkpoint buffers");
     }
     // forward sweep: state at the start of every segment
     for (int64_t sg = 0; sg < nseg; ++sg) {
-        CKA(cudaMemcpyAsync(ckpt + (size_t)sg * ctx->R * ctx->nmodes, ctx->phi, ms, cudaMemcpyDeviceToDevice,
-                            ctx->stream));
+        CKA(cudaMemcpyAsync(ckpt + (size_t)sg * cm, ctx->phi, ms, cudaMemcpyDeviceToDevice, ctx->stream));
+        if (hist)
+            CKA(cudaMemcpyAsync(ckpt + (size_t)sg * cm + cm / 2, ctx->fprev, ms, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
         SKA(step_impl(ctx, std::min<int64_t>(K, nsteps - sg * K), true));
     }
     CKA(cudaMemcpyAsync(phiN, ctx->phi, ms, cudaMemcpyDeviceToDevice, ctx->stream));
-    // lambda_N
+    if (hist) CKA(cudaMemcpyAsync(phiN + cm / 2, ctx->fprev, ms, cudaMemcpyDeviceToDevice, ctx->stream));
+    // lambda_N; the SETD2 history cotangent mu_{N-1} = 0
     SKA(spectrum_from_device_field(ctx, cot_dev, ctx->dphi));
+    if (ctx->dmu) CKA(cudaMemsetAsync(ctx->dmu, 0, ms, ctx->stream));
+    // whether step n of the sweep (global index step0 + n) took the SETD1 pair that starts SETD2
+    auto starts_setd2 = [&](int64_t n) {
+        return ctx->cfg.scheme == SFT_SETD2 && n >= 0 && step0 + n == ctx->first_step ? 1 : 0;
+    };
     bool w_valid = false;
     for (int64_t sg = nseg - 1; sg >= 0; --sg) {
         const int64_t n0 = sg * K, len = std::min<int64_t>(K, nsteps - n0);
         // recompute the segment, keeping each step's primal input
-        CKA(cudaMemcpyAsync(ctx->phi, ckpt + (size_t)sg * ctx->R * ctx->nmodes, ms, cudaMemcpyDeviceToDevice,
-                            ctx->stream));
+        CKA(cudaMemcpyAsync(ctx->phi, ckpt + (size_t)sg * cm, ms, cudaMemcpyDeviceToDevice, ctx->stream));
+        if (hist)
+            CKA(cudaMemcpyAsync(ctx->fprev, ckpt + (size_t)sg * cm + cm / 2, ms, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
         SKA(set_step_counter(ctx, step0 + n0));
         if (ctx->d >= 2) {
             StepArgs a = base_args(ctx);
@@ -1890,6 +1913,9 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
             float2* slot = traj + (size_t)i * ctx->R * ctx->nmodes;
             StepArgs a = base_args(ctx);
             a.dphi = ctx->dphi;
+            a.dmu = ctx->dmu;
+            a.adj_first_n = starts_setd2(n0 + i);
+            a.adj_first_prev = starts_setd2(n0 + i - 1);
             if (ctx->d == 1) {
                 a.phi = slot;
                 a.tw_a = ctx->tw.get(ctx->nx / 2);
@@ -1898,9 +1924,12 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
                 ctx->launches += 1;
             } else {
                 if (!w_valid) {
-                    a.dpout = ctx->dP;
-                    a.tw_a = ctx->tw.get(ctx->ny);
-                    CKA(launch_second(ctx, a, MODE_ADJ_PRIME));
+                    // W_{N-1} = IDFT(M s A_{N-1} lam_N)
+                    StepArgs b = a;
+                    b.dpout = ctx->dP;
+                    b.tw_a = ctx->tw.get(ctx->ny);
+                    b.adj_first_prev = starts_setd2(n0 + i);
+                    CKA(launch_second(ctx, b, MODE_ADJ_PRIME));
                     w_valid = true;
                 }
                 a.pin = slot;
@@ -1920,6 +1949,7 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
     SKA(device_field_from_spectrum(ctx, ctx->dphi, grad_dev));
     // the primal ends at step0 + nsteps, as after nsteps of sft_step
     CKA(cudaMemcpyAsync(ctx->phi, phiN, ms, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (hist) CKA(cudaMemcpyAsync(ctx->fprev, phiN + cm / 2, ms, cudaMemcpyDeviceToDevice, ctx->stream));
     SKA(set_step_counter(ctx, step0 + nsteps));
     ctx->p_valid = false;
     ctx->dp_valid = false;
@@ -2166,7 +2196,7 @@ void sft_destroy(sft_ctx* ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     void* bufs[] = {ctx->phi,   ctx->fprev,  ctx->P,      ctx->Q,      ctx->Py,     ctx->snap, ctx->real,
                     ctx->cfield, ctx->tab,   ctx->dstep,  ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev,
-                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec, ctx->tw32, ctx->dfprev,
+                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec, ctx->tw32, ctx->dfprev, ctx->dmu,
                     ctx->d_order, ctx->d_chunks, ctx->d_first_chunk, ctx->d_part, ctx->d_tacc};
     for (void* p : bufs)
         if (p) cudaFree(p);

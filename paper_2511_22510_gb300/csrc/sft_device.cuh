@@ -114,6 +114,77 @@ __device__ __forceinline__ float2 recipe_bm_pair(uint32_t wa, uint32_t wb) {
     return make_float2(__fmul_rn(rad, cs), __fmul_rn(rad, sn));
 }
 
+// The recipe for two pairs at once, (wa0, wb0) and (wa1, wb1), with the paired
+// single-precision instructions of sm_100 and later (__fadd2_rn, __fmul2_rn,
+// __ffma2_rn: per component the same correctly rounded operation as the
+// scalar one): every floating-point step of recipe_log, recipe_sincos_turn
+// and recipe_bm_pair, in the same order, so each pair has exactly the bits of
+// recipe_bm_pair.  Returns (z0, z1) of the first pair in .x, .y and of the
+// second in .z, .w.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ float2 recipe_log2(float2 x) {
+    const uint32_t b0 = __float_as_uint(x.x), b1 = __float_as_uint(x.y);
+    int e0 = (int)(b0 >> 23) - 127, e1 = (int)(b1 >> 23) - 127;
+    float2 m = make_float2(__uint_as_float((b0 & 0x007FFFFFu) | 0x3F800000u),
+                           __uint_as_float((b1 & 0x007FFFFFu) | 0x3F800000u));
+    // m > sqrt2: halve it (an exact product) and bump the exponent
+    const bool h0 = m.x > 0x1.6a09e6p+0f, h1 = m.y > 0x1.6a09e6p+0f;
+    m = __fmul2_rn(m, make_float2(h0 ? 0.5f : 1.0f, h1 ? 0.5f : 1.0f));
+    e0 += h0 ? 1 : 0;
+    e1 += h1 ? 1 : 0;
+    const float2 num = __fadd2_rn(m, f2(-1.0f)), den = __fadd2_rn(m, f2(1.0f));
+    const float2 s = make_float2(__fdiv_rn(num.x, den.x), __fdiv_rn(num.y, den.y));
+    const float2 s2 = __fmul2_rn(s, s);
+    float2 p = __ffma2_rn(s2, f2(0x1.745d18p-4f), f2(0x1.c71c72p-4f));
+    p = __ffma2_rn(s2, p, f2(0x1.24924ap-3f));
+    p = __ffma2_rn(s2, p, f2(0x1.99999ap-3f));
+    p = __ffma2_rn(s2, p, f2(0x1.555556p-2f));
+    const float2 t = __fmul2_rn(s2, p);
+    const float2 two_s = __fadd2_rn(s, s);
+    const float2 lnm = __ffma2_rn(two_s, t, two_s);
+    const float2 ef = make_float2(__int2float_rn(e0), __int2float_rn(e1));
+    return __ffma2_rn(ef, f2(0x1.62e4p-1f), __ffma2_rn(ef, f2(0x1.7f7d1cp-20f), lnm));
+}
+
+__device__ __forceinline__ void recipe_sincos_turn2(uint32_t k0, uint32_t k1, float2& sn, float2& cs) {
+    const uint32_t qq0 = (k0 + 0x200000u) >> 22, qq1 = (k1 + 0x200000u) >> 22;
+    const int32_t r0 = (int32_t)k0 - (int32_t)(qq0 << 22), r1 = (int32_t)k1 - (int32_t)(qq1 << 22);
+    const float2 x = __fmul2_rn(make_float2(__int2float_rn(r0), __int2float_rn(r1)), f2(0x1.921fb6p-22f));
+    const float2 x2 = __fmul2_rn(x, x);
+    float2 ps = __ffma2_rn(x2, f2(-0x1.ae6456p-26f), f2(0x1.71de3ap-19f));
+    ps = __ffma2_rn(x2, ps, f2(-0x1.a01a02p-13f));
+    ps = __ffma2_rn(x2, ps, f2(0x1.111112p-7f));
+    ps = __ffma2_rn(x2, ps, f2(-0x1.555556p-3f));
+    const float2 sx = __ffma2_rn(__fmul2_rn(x, x2), ps, x);
+    float2 pc = __ffma2_rn(x2, f2(-0x1.27e4fcp-22f), f2(0x1.a01a02p-16f));
+    pc = __ffma2_rn(x2, pc, f2(-0x1.6c16c2p-10f));
+    pc = __ffma2_rn(x2, pc, f2(0x1.555556p-5f));
+    pc = __ffma2_rn(x2, pc, f2(-0.5f));
+    const float2 cx = __ffma2_rn(x2, pc, f2(1.0f));
+    auto quad = [](uint32_t q, float s, float c, float& so, float& co) {
+        switch (q & 3u) {
+            case 0: so = s; co = c; break;
+            case 1: so = c; co = -s; break;
+            case 2: so = -s; co = -c; break;
+            default: so = -c; co = s; break;
+        }
+    };
+    quad(qq0, sx.x, cx.x, sn.x, cs.x);
+    quad(qq1, sx.y, cx.y, sn.y, cs.y);
+}
+
+__device__ __forceinline__ float4 recipe_bm_pair2(uint32_t wa0, uint32_t wb0, uint32_t wa1, uint32_t wb1) {
+    const float2 u1 = __fmul2_rn(make_float2(__uint2float_rn((wa0 >> 8) + 1u), __uint2float_rn((wa1 >> 8) + 1u)),
+                                 f2(0x1p-24f));
+    const float2 l = __fmul2_rn(f2(-2.0f), recipe_log2(u1));
+    const float2 rad = make_float2(__fsqrt_rn(l.x), __fsqrt_rn(l.y));
+    float2 sn, cs;
+    recipe_sincos_turn2(wb0 >> 8, wb1 >> 8, sn, cs);
+    const float2 z0 = __fmul2_rn(rad, cs), z1 = __fmul2_rn(rad, sn);
+    return make_float4(z0.x, z1.x, z0.y, z1.y);
+}
+
 // The normal pair belonging to counter index j (x-major mode enumeration):
 // Philox(ctr = (j >> 1, step, replica, tag), key = seed) -> words w0..w3;
 // even j takes the pair of (w0, w1), odd j the pair of (w2, w3).

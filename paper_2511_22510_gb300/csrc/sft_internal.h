@@ -61,6 +61,11 @@ struct StepArgs {
     const float2* dpin;
     const float2* dpyin;
     float2* dpyout;
+    // SETD2 adjoint (Eq. SETD2 transposed): the history cotangent mu (1-D lines keep it between steps) and
+    // whether step n (adj_first_n) or step n - 1 (adj_first_prev) of the backward sweep is the step that
+    // starts the SETD2 history (SETD1 pair: A + B and B = 0)
+    float2* dmu;
+    int adj_first_n, adj_first_prev;
     // twiddle tables for the transform lengths used by the kernel
     const float2* tw_a;  // table for the first transform length
     const float2* tw_b;  // table for the second transform length

@@ -98,7 +98,7 @@ __device__ __forceinline__ void line_step(const StepArgs& a, int r, bool valid, 
     // modes k = t + T e, then (thread 0) the Nyquist mode k = M
 #pragma unroll
     for (int e = 0; e <= E; ++e) {
-        if (e < E && (e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
+        if (e < E && (e & 1) == 0) team_normal_pair_ks<T>(a.ks, 0, t, e, (uint32_t)step, rep, zn0, zn1);
         if (e == E && t != 0) break;
         const int k = (e < E) ? t + T * e : M;
         const float2 xq = (e < E) ? Xq[e] : XqM;
@@ -139,9 +139,12 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
     float2 z[E];
 
     if constexpr (MODE == MODE_TAN || MODE == MODE_ADJ) {
-        // TAN: primal step plus dphi <- f1 dphi + A M s DFT[3 psi^2 dpsi] (dpsi = IDFT(M dphi)).
-        // ADJ: lam <- f1 lam + M DFT[3 psi^2 w], w = IDFT(A s M lam), psi from the primal state phi.
-        static_assert(NL == NL_CUBIC, "tangent/adjoint: cubic term");
+        // TAN: primal step plus dphi <- f1 dphi + A M s DFT[q'] with q' = 3 psi^2 dpsi (cubic,
+        // dpsi = IDFT(M dphi)) or 2 g dg (KPZ, g = IDFT(i k M phi), dg = IDFT(i k M dphi)).
+        // ADJ: lam <- f1 lam + M DFT[3 psi^2 w] (cubic) or (-i k) M DFT[2 g w] (KPZ: the transpose of the
+        // odd multiplier i k), w = IDFT(A s M lam), psi and g from the primal state phi.
+        static_assert(NL == NL_CUBIC || NL == NL_GRAD2, "tangent/adjoint: cubic or gradient-squared term");
+        constexpr bool G = NL == NL_GRAD2;
         float2* dp = a.dphi + (size_t)rr * (M + 1);
         const float sc = a.scale;
         float2 zd[E];
@@ -150,21 +153,48 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
             const int k = t + T * e;
             const bool i1 = !a.dealias || 3 * k < NX, i2 = !a.dealias || 3 * (M - k) < NX;
             const float2 tw = __ldg(&twN[k]);
-            z[e] = c2r_pre(i1 ? cscale(ph[k], sc) : czero(), i2 ? cscale(ph[M - k], sc) : czero(), tw);
-            float w1 = sc, w2 = sc;
-            if constexpr (MODE == MODE_ADJ) {
-                w1 *= __ldg(&a.tab[k]).y * nl_prefactor(a, k * k).x;
-                w2 *= __ldg(&a.tab[M - k]).y * nl_prefactor(a, (M - k) * (M - k)).x;
+            // KPZ: i k on the primal (and on the tangent), k = 0 at the Nyquist mode M - 0
+            const float k1 = a.dk * (float)k, k2 = k == 0 ? 0.f : a.dk * (float)(M - k);
+            float2 X1 = i1 ? cscale(ph[k], sc) : czero(), X2 = i2 ? cscale(ph[M - k], sc) : czero();
+            if constexpr (G) {
+                X1 = cscale(cmuli(X1), k1);
+                X2 = cscale(cmuli(X2), k2);
             }
-            zd[e] = c2r_pre(i1 ? cscale(dp[k], w1) : czero(), i2 ? cscale(dp[M - k], w2) : czero(), tw);
+            z[e] = c2r_pre(X1, X2, tw);
+            float w1 = sc, w2 = sc;
+            float2 L1 = dp[k], L2 = dp[M - k];
+            if constexpr (MODE == MODE_ADJ) {
+                // nu_n = A_n lam_{n+1} + mu_n (SETD2 history cotangent, kept between the steps in dmu)
+                const bool fa = a.adj_first_n != 0;
+                L1 = cscale(L1, load_coefs<false>(a.tab, k, fa).A.x);
+                L2 = cscale(L2, load_coefs<false>(a.tab, M - k, fa).A.x);
+                if (a.scheme == 2) {
+                    const float2* mu = a.dmu + (size_t)rr * (M + 1);
+                    L1 = cadd(L1, mu[k]);
+                    L2 = cadd(L2, mu[M - k]);
+                }
+                w1 *= nl_prefactor(a, k * k).x;
+                w2 *= nl_prefactor(a, (M - k) * (M - k)).x;
+            }
+            float2 D1 = i1 ? cscale(L1, w1) : czero(), D2 = i2 ? cscale(L2, w2) : czero();
+            if constexpr (G && MODE == MODE_TAN) {
+                D1 = cscale(cmuli(D1), k1);
+                D2 = cscale(cmuli(D2), k2);
+            }
+            zd[e] = c2r_pre(D1, D2, tw);
         }
         fft_line<M, true>(z, xb, t, twM);
         fft_line<M, true>(zd, xb, t, twM);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const float2 p = z[e];
-            zd[e] = make_float2(3.f * p.x * p.x * zd[e].x, 3.f * p.y * p.y * zd[e].y);
-            z[e] = make_float2(p.x * p.x * p.x, p.y * p.y * p.y);
+            if constexpr (G) {
+                zd[e] = make_float2(2.f * p.x * zd[e].x, 2.f * p.y * zd[e].y);
+                z[e] = make_float2(p.x * p.x, p.y * p.y);
+            } else {
+                zd[e] = make_float2(3.f * p.x * p.x * zd[e].x, 3.f * p.y * p.y * zd[e].y);
+                z[e] = make_float2(p.x * p.x * p.x, p.y * p.y * p.y);
+            }
         }
         fft_line<M, false>(zd, xb, t, twM);
         float2 dXq[E];
@@ -176,11 +206,17 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
                 if (e == E && t != 0) break;
                 const int k = (e < E) ? t + T * e : M;
                 const bool inm = !a.dealias || 3 * k < NX;
-                const float2 v = inm ? ((e < E) ? dXq[e] : dXqM) : czero();
-                const float f1 = __ldg(&a.tab[k]).x;
-                float2 o = make_float2(f1 * dp[k].x + v.x, f1 * dp[k].y + v.y);
+                float2 v = inm ? ((e < E) ? dXq[e] : dXqM) : czero();
+                if constexpr (G) v = cscale(cmuli(v), k == M ? 0.f : -a.dk * (float)k);  // (-i k), odd: 0 at Nyquist
+                const float4 tk = __ldg(&a.tab[k]);
+                const float2 lk = dp[k];
+                float2 o = make_float2(tk.x * lk.x + v.x, tk.x * lk.y + v.y);
                 if (k == 0 || k == M) o.y = 0.f;
-                if (valid) dp[k] = o;
+                if (valid) {
+                    dp[k] = o;
+                    // SETD2: mu_{n-1} = B_n lam_{n+1}
+                    if (a.scheme == 2) a.dmu[(size_t)rr * (M + 1) + k] = a.adj_first_n ? czero() : cscale(lk, tk.z);
+                }
             }
             return;
         } else {
@@ -196,7 +232,7 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
             float2 zn0, zn1;
 #pragma unroll
             for (int e = 0; e <= E; ++e) {
-                if (e < E && (e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
+                if (e < E && (e & 1) == 0) team_normal_pair_ks<T>(a.ks, 0, t, e, (uint32_t)step, rep, zn0, zn1);
                 if (e == E && t != 0) break;
                 const int k = (e < E) ? t + T * e : M;
                 const bool inm = !a.dealias || 3 * k < NX;
@@ -308,7 +344,7 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
             // modes k = t + T e, then (thread 0) the Nyquist mode k = M
 #pragma unroll
             for (int e = 0; e <= E; ++e) {
-                if (e < E && (e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
+                if (e < E && (e & 1) == 0) team_normal_pair_ks<T>(a.ks, 0, t, e, (uint32_t)step, rep, zn0, zn1);
                 if (e == E && t != 0) break;
                 const int k = (e < E) ? t + T * e : M;
                 const float2 xq = (e < E) ? Xq[e] : XqM;
@@ -376,18 +412,40 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k1_cplx(const StepArgs a)
         }
         return;
     } else {
+        // tangent (MODE_TAN): dq = 2 |A|^2 dA + A^2 conj(dA), the linearisation of |A|^2 A, with
+        // dA = IDFT(M dphi); the tangent update has no noise and its own SETD2 history
+        constexpr bool TAN = MODE == MODE_TAN;
+        float2* dp = TAN ? a.dphi + (size_t)rr * N : nullptr;
+        float2 draw[TAN ? E : 1], zd[TAN ? E : 1];
+        if constexpr (TAN) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int k = t + T * e;
+                draw[e] = dp[k];
+                const bool inm = !a.dealias || 3 * abs(signed_idx(k, N)) < N;
+                zd[e] = inm ? cscale(draw[e], a.scale) : czero();
+            }
+            fft_line<N, true>(zd, xb, t, tw);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const float2 A = z[e], dA = zd[e];
+                zd[e] = cadd(cscale(dA, 2.f * (A.x * A.x + A.y * A.y)), cmul(cmul(A, A), cconj(dA)));
+            }
+            fft_line<N, false>(zd, xb, t, tw);
+        }
 #pragma unroll
         for (int e = 0; e < E; ++e) z[e] = cscale(z[e], z[e].x * z[e].x + z[e].y * z[e].y);
         fft_line<N, false>(z, xb, t, tw);
         const long long step = current_step(a);
         const bool first = (a.scheme == 2) && (step == *a.first_step);
         float2* fp = a.fprev + (size_t)rr * N;
+        float2* dfp = TAN ? a.dfprev + (size_t)rr * N : nullptr;
         const uint32_t rep = (uint32_t)(a.rep0 + rr);
         const float2 s = make_float2(a.s0, a.s0i);
         float2 zn0, zn1;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            if ((e & 1) == 0) team_normal_pair<T>(a.seed, 0, t, e, (uint32_t)step, rep, zn0, zn1);
+            if ((e & 1) == 0) team_normal_pair_ks<T>(a.ks, 0, t, e, (uint32_t)step, rep, zn0, zn1);
             const int k = t + T * e;
             const int ks = signed_idx(k, N);
             const bool inm = !a.dealias || 3 * abs(ks) < N;
@@ -399,6 +457,15 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k1_cplx(const StepArgs a)
                 ph[k] = o;
                 if (a.scheme == 2) fp[k] = F;
                 flag_nonfinite(a, o, step);
+            }
+            if constexpr (TAN) {
+                const float2 dF = inm ? cmul(s, zd[e]) : czero();
+                const float2 dFp = (a.scheme == 2) ? dfp[k] : czero();
+                const float2 d = setd_update<true>(co, draw[e], dF, dFp, czero());
+                if (valid) {
+                    dp[k] = d;
+                    if (a.scheme == 2) dfp[k] = dF;
+                }
             }
         }
     }
@@ -440,6 +507,8 @@ static cudaError_t k1r_for(const StepArgs& a, int mode, int nl, cudaStream_t s) 
     if (mode == MODE_STEP && nl == NL_GRAD2) return run_k1_real<M, NL_GRAD2, MODE_STEP>(a, s);
     if (mode == MODE_TAN && nl == NL_CUBIC) return run_k1_real<M, NL_CUBIC, MODE_TAN>(a, s);
     if (mode == MODE_ADJ && nl == NL_CUBIC) return run_k1_real<M, NL_CUBIC, MODE_ADJ>(a, s);
+    if (mode == MODE_TAN && nl == NL_GRAD2) return run_k1_real<M, NL_GRAD2, MODE_TAN>(a, s);
+    if (mode == MODE_ADJ && nl == NL_GRAD2) return run_k1_real<M, NL_GRAD2, MODE_ADJ>(a, s);
     return cudaErrorInvalidValue;
 }
 
@@ -448,6 +517,7 @@ static cudaError_t k1c_for(const StepArgs& a, int mode, cudaStream_t s) {
     if (mode == MODE_FWD) return run_k1_cplx<N, MODE_FWD>(a, s);
     if (mode == MODE_INV) return run_k1_cplx<N, MODE_INV>(a, s);
     if (mode == MODE_STEP) return run_k1_cplx<N, MODE_STEP>(a, s);
+    if (mode == MODE_TAN) return run_k1_cplx<N, MODE_TAN>(a, s);
     return cudaErrorInvalidValue;
 }
 

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(ClPlan<L>::T, 1024 / ClPlan<L>::T) k1_cluster(
 #pragma unroll
             for (int e = 0; e <= E; ++e) {
                 if (e < E && (e & 1) == 0)
-                    team_normal_pair<T>(a.seed, (uint64_t)q * L, t, e, (uint32_t)step, rep, zn0, zn1);
+                    team_normal_pair_ks<T>(a.ks, (uint64_t)q * L, t, e, (uint32_t)step, rep, zn0, zn1);
                 if (e == E && !last_owner) break;
                 const int k = (e < E) ? q * L + t + T * e : M;
                 const float2 xq = (e < E) ? Xq[e] : XqM;

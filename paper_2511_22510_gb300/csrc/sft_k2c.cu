@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(CColCfg<NY>::THREADS, 512 / CColCfg<NY>::THREA
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     if ((e & 1) == 0)
-                        team_normal_pair<T>(a.seed, (uint64_t)ax * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep),
+                        team_normal_pair_ks<T>(a.ks, (uint64_t)ax * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep),
                                             out[e], out[e + 1]);
                     const int ay = t + T * e;
                     const int ays = signed_idx(ay, NY);

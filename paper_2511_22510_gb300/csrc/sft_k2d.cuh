@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(RowCfg<M, SH>::THREADS, RowCfg<M, SH>::MINB) k
         const long long step = current_step(a);
 #pragma unroll
         for (int e = 0; e < E; e += 2)
-            team_normal_pair<T>(a.seed, (uint64_t)(yok ? y : 0) * M, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep),
+            team_normal_pair_ks<T>(a.ks, (uint64_t)(yok ? y : 0) * M, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep),
                                 z[e], z[e + 1], 3u);
     } else {
         load_tile<C>(tile, a.pin, rowbase, ncols, ny, y0);

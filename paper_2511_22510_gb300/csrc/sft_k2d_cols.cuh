@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
         } else {
 #pragma unroll
             for (int e = 0; e < E; e += 2)
-                team_normal_pair<T>(a.seed, (uint64_t)cc * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
+                team_normal_pair_ks<T>(a.ks, (uint64_t)cc * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
                                     out[e + 1]);
         }
         if (has_f || T < 32) fft_line<NY, false, EM>(v, xb, t, tw);
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             if ((e & 1) == 0)
-                team_normal_pair<T>(a.seed, (uint64_t)cc * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
+                team_normal_pair_ks<T>(a.ks, (uint64_t)cc * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
                                     out[e + 1]);
             const int ay = t + T * e;
             const int ays = signed_idx(ay, NY);
@@ -394,12 +394,18 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
         b.pout = a.dpout;
         emit_p<NY, NL, EM>(b, dv, valid && cc < a.ncols, cc, colbase, xb, t);
     } else if constexpr (MODE == MODE_ADJ || MODE == MODE_ADJ_PRIME) {
-        // adjoint: lam <- f1 lam + M DFT[v] (v from the row pass), then W = IDFT_y(A s M lam / N^2)
+        // adjoint of step n: lam_n = f1 lam_{n+1} + M DFT[v] (v from the row pass), mu_{n-1} = B_n lam_{n+1}
+        // (SETD2), then W = IDFT_y(M s (A_{n-1} lam_n + mu_{n-1}) / N^2) for step n - 1.  ADJ_PRIME: W from
+        // lam_N alone (mu = 0).
         if (!valid && T >= 32) return;
         const bool has_f = valid && cc < a.ncols;
         float2 lam[E];
+        float2 mu[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) lam[e] = a.dphi[colbase + t + T * e];
+        for (int e = 0; e < E; ++e) {
+            lam[e] = a.dphi[colbase + t + T * e];
+            mu[e] = czero();
+        }
         if constexpr (MODE == MODE_ADJ) {
             if (has_f || T < 32) {
 #pragma unroll
@@ -413,6 +419,10 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
                 const bool inm = !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < NY);
                 const float f1 = __ldg(&a.tab[cc * (NY / 2 + 1) + abs(ays)]).x;
                 const float2 dv = (has_f && inm) ? v[e] : czero();
+                if (a.scheme == 2 && !a.adj_first_n) {
+                    const float b = __ldg(&a.tab[cc * (NY / 2 + 1) + abs(ays)]).z;
+                    mu[e] = cscale(lam[e], b);
+                }
                 lam[e] = make_float2(f1 * lam[e].x + dv.x, f1 * lam[e].y + dv.y);
             }
             fixup_plane<NY, EM>(lam, xb, t, plane);
@@ -429,8 +439,9 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
                 const int ays = signed_idx(ay, NY);
                 const int q = cc * cc + ays * ays;
                 const bool inm = !a.dealias || (3 * cc < a.nx && 3 * abs(ays) < NY);
-                const Coefs co = load_coefs<false>(a.tab, cc * (NY / 2 + 1) + abs(ays), false);
-                v[e] = (has_p && inm) ? cscale(lam[e], co.A.x * nl_prefactor(a, q).x * a.scale) : czero();
+                const Coefs co = load_coefs<false>(a.tab, cc * (NY / 2 + 1) + abs(ays), a.adj_first_prev != 0);
+                const float2 nu = make_float2(co.A.x * lam[e].x + mu[e].x, co.A.x * lam[e].y + mu[e].y);
+                v[e] = (has_p && inm) ? cscale(nu, nl_prefactor(a, q).x * a.scale) : czero();
             }
             fft_line<NY, true, EM>(v, xb, t, tw);
             if (has_p) {

@@ -5,10 +5,13 @@
 // the y half of steps 3-5): Q --FFT along y--> DFT[q]; F = M s DFT[q];
 // phi <- f1 phi + A F + B F_prev + g eta with the Philox noise of App. B;
 // Hermitian fix-up on the self-conjugate columns; P <- IFFT_y(M phi / N^2).
-// The column's 1024 values stay in the warp's registers (32 per lane, index
-// lane + 32 e) through both transforms and the update, so the only shared
-// memory traffic is one transpose per transform; the global loads and stores
-// of a slot are whole 256-byte lines of the column.  The noise of every mode
+// The column's 1024 values are held by the warp in registers (32 per lane,
+// index lane + 32 e) through each transform, with one transpose per transform
+// through the warp's 8 KB shared buffer; between the transforms the column
+// waits in that buffer in natural order while a loop that is not unrolled (so
+// the kernel's code stays small enough for the instruction cache) updates two
+// slots per trip, loading the state one trip ahead.  The global loads and
+// stores of a slot are whole 256-byte lines of the column.  The noise of every mode
 // is drawn exactly as in the other column passes (the same counters, the same
 // words and the same Box-Muller recipe), so the result is the same step.
 #include "sft_step_common.cuh"
@@ -43,75 +46,93 @@ __global__ void __launch_bounds__(kCwWarps * 32, 4) k2_cols_warp(const StepArgs 
         const int rep = blockIdx.y * a.rpb + ri;
         if (rep >= a.R) break;
         const size_t colbase = ((size_t)rep * a.hx + cc) * NY;
-        float2 v[32];
+        const float2* __restrict__ phin = a.phi + colbase;
+        // DFT_y[q] of the column into xb in natural order (zero outside the carried columns)
         if (has_f) {
+            float2 v[32];
 #pragma unroll
             for (int e = 0; e < 32; ++e) v[e] = a.qin[colbase + lane + 32 * e];
             fft1024_warp<false, 0u>(v, xb, lane, tw32);
-        } else {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] = czero();
+            for (int e = 0; e < 32; ++e) xb[lane + 32 * e] = v[e];
         }
+        __syncwarp();
+        // the update, two slots (one Philox call) per trip of a loop that is not unrolled: the column stays
+        // in xb, the state of the next pair of slots is loaded one trip ahead
         float nf = 0.f;
-#pragma unroll
+        float2 ph0 = phin[lane], ph1 = phin[lane + 32];
+#pragma unroll 1
         for (int e = 0; e < 32; e += 2) {
+            float2 nx0 = czero(), nx1 = czero();
+            if (e + 2 < 32) {
+                nx0 = phin[lane + 32 * (e + 2)];
+                nx1 = phin[lane + 32 * (e + 3)];
+            }
             float2 z0, z1;
             team_normal_pair_ks<32>(a.ks, (uint64_t)cc * NY, lane, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), z0,
                                     z1);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int s = e + h;
-                const int ay = lane + 32 * s;
+                const int ay = lane + 32 * (e + h);
                 const int ays = ay < NY / 2 ? ay : ay - NY;  // signed index (ay = 512 -> -512)
                 const int aya = ays < 0 ? -ays : ays;
                 const bool inm = keep_x && (!DEAL || 3 * aya < NY);
                 float2 F = czero();
                 if (has_f && inm) {
                     const float sq = a.model == 1 ? sB * (float)(cc * cc + ays * ays) : sB;
-                    F = cscale(v[s], sq);
+                    F = cscale(xb[ay], sq);
                 }
-                const Coefs co = load_coefs<false>(reinterpret_cast<const float4*>(trow), aya, first);
-                const float2 ph = a.phi[colbase + ay];
+                const Coefs co = load_coefs<false>(trow, aya, first);
                 float2 Fp = czero();
                 if (a.scheme == 2 && has_f) Fp = a.fprev[colbase + ay];
                 const bool selfc = plane && (ay == 0 || ay == NY / 2);
-                const float2 out = setd_update<false>(co, ph, F, Fp, eta_of(h ? z1 : z0, selfc));
+                const float2 out = setd_update<false>(co, h ? ph1 : ph0, F, Fp, eta_of(h ? z1 : z0, selfc));
                 if (a.scheme == 2 && has_f) a.fprev[colbase + ay] = F;
-                v[s] = out;
+                if (plane) {
+                    xb[ay] = out;  // stored after the fix-up below
+                } else {
+                    a.phi[colbase + ay] = out;
+                    nf = nonfinite_acc(nf, out);
+                    xb[ay] = (has_f && inm) ? cscale(out, a.scale) : czero();
+                }
             }
+            ph0 = nx0;
+            ph1 = nx1;
         }
+        __syncwarp();
         if (plane) {
-            // partners a_y > 512 take the conjugate of 1024 - a_y; self-conjugate modes are real
-            __syncwarp();
-#pragma unroll
-            for (int e = 0; e < 32; ++e) xb[lane + 32 * e] = v[e];
-            __syncwarp();
+            // partners a_y > 512 take the conjugate of 1024 - a_y, self-conjugate modes are real; then the
+            // state is stored and the masked, scaled column is left in xb
+            float2 w[32];
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
                 const int ay = lane + 32 * e;
-                if (2 * ay > NY) v[e] = cconj(xb[NY - ay]);
-                if (ay == 0 || 2 * ay == NY) v[e].y = 0.f;
+                w[e] = (2 * ay > NY) ? cconj(xb[NY - ay]) : xb[ay];
+                if (ay == 0 || 2 * ay == NY) w[e].y = 0.f;
             }
             __syncwarp();
-        }
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            a.phi[colbase + lane + 32 * e] = v[e];
-            nf = nonfinite_acc(nf, v[e]);
-        }
-        flag_nonfinite_acc(a, nf, step);
-        if (has_f) {
-            // P <- IFFT_y(M phi / N^2): the masked slots are zero in every lane
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
                 const int ay = lane + 32 * e;
                 const int aya = ay <= NY / 2 ? ay : NY - ay;
-                v[e] = ((ZMASK >> e) & 1u) ? czero() : ((!DEAL || 3 * aya < NY) ? cscale(v[e], a.scale) : czero());
+                a.phi[colbase + ay] = w[e];
+                nf = nonfinite_acc(nf, w[e]);
+                xb[ay] = (has_f && (!DEAL || 3 * aya < NY)) ? cscale(w[e], a.scale) : czero();
             }
+            __syncwarp();
+        }
+        flag_nonfinite_acc(a, nf, step);
+        if (has_f) {
+            // P <- IFFT_y(M phi / N^2): the masked slots are zero in every lane
+            float2 v[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = ((ZMASK >> e) & 1u) ? czero() : xb[lane + 32 * e];
+            __syncwarp();
             fft1024_warp<true, ZMASK>(v, xb, lane, tw32);
 #pragma unroll
             for (int e = 0; e < 32; ++e) a.pout[colbase + lane + 32 * e] = v[e];
         }
+        __syncwarp();
     }
 }
 

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
 
     fft1024_warp<true, C::ZIN>(v, xb, lane, tw32);
 #pragma unroll
-    for (int e = 0; e < 32; ++e) v[e] = make_float2(v[e].x * v[e].x * v[e].x, v[e].y * v[e].y * v[e].y);
+    for (int e = 0; e < 32; ++e) v[e] = __fmul2_rn(__fmul2_rn(v[e], v[e]), v[e]);
     fft1024_warp<false, 0u>(v, xb, lane, tw32);
 
     // Q_y[k], Q_{y+1}[k] for the carried columns k = lane + 32 e < NC; W[1024 - k] comes from lane
@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
         const int k = lane + 32 * e;
         if (32 * e + 31 < C::NC || k < C::NC) {
             const float2 w = v[e];
-            const float4 q = make_float4(0.5f * (w.x + wm.x), 0.5f * (w.y - wm.y), 0.5f * (w.y + wm.y),
-                                         0.5f * (wm.x - w.x));
+            const float2 qa = __fmul2_rn(f2(0.5f), __fadd2_rn(w, make_float2(wm.x, -wm.y)));
+            const float2 qb = __fmul2_rn(f2(0.5f), __fadd2_rn(make_float2(w.y, wm.x), make_float2(wm.y, -w.x)));
+            const float4 q = make_float4(qa.x, qa.y, qb.x, qb.y);
             *reinterpret_cast<float4*>(tile + tile_pos(k, warp)) = q;
         }
     }

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(ColPipeCfg<NY>::THREADS, 1) k2_cols_pipe(const
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             if ((e & 1) == 0)
-                team_normal_pair<T>(a.seed, (uint64_t)c * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
+                team_normal_pair_ks<T>(a.ks, (uint64_t)c * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep), out[e],
                                     out[e + 1]);
             const int ay = t + T * e;
             const int ays = signed_idx(ay, NY);

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
             for (int e = 0; e < E; e += 2) {
                 float2 zz[2] = {czero(), czero()};
                 if constexpr (MODE == MODE_STEP)
-                    team_normal_pair<T>(a.seed, ((uint64_t)c * N + az) * N, t, e, (uint32_t)step,
+                    team_normal_pair_ks<T>(a.ks, ((uint64_t)c * N + az) * N, t, e, (uint32_t)step,
                                         (uint32_t)(a.rep0 + rep), zz[0], zz[1]);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -134,8 +134,11 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
                         o = setd_update<false>(co, state[idx], dF, dFp, czero());
                         if (line < N && a.scheme == 2 && has_f) a.dfprev[idx] = dF;
                     } else {
+                        // adjoint of step n: lam_n = f1 lam_{n+1} + M DFT[v]; SETD2: mu_{n-1} = B_n lam_{n+1}
                         const float2 l = state[idx];
                         o = make_float2(co.f1.x * l.x + Fh.x, co.f1.x * l.y + Fh.y);
+                        if (a.scheme == 2 && line < N)
+                            a.dmu[idx] = a.adj_first_n ? czero() : cscale(l, __ldg(&a.tab[q]).z);
                     }
                     if (selfc) o.y = 0.f;
                     if (line < N) S[az * RS + ay] = o;
@@ -182,11 +185,15 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
             const int ays = signed_idx(ay, N), azs = signed_idx(az, N);
             const bool inm = (MODE == MODE_INV) || !a.dealias || (3 * c < a.nx && 3 * abs(ays) < N && 3 * abs(azs) < N);
             float w = a.scale;
+            float2 o = S[az * RS + ay];
             if constexpr (MODE == MODE_ADJ || MODE == MODE_ADJ_PRIME) {
+                // W = IDFT(M s (A_{n-1} lam_n + mu_{n-1}) / N^3); ADJ_PRIME: mu = 0
                 const int q = c * c + ays * ays + azs * azs;
-                w *= __ldg(&a.tab[q]).y * nl_prefactor(a, q).x;
+                const Coefs co = load_coefs<false>(a.tab, q, a.adj_first_prev != 0);
+                o = cscale(o, co.A.x);
+                if (MODE == MODE_ADJ && a.scheme == 2) o = cadd(o, a.dmu[base + f]);
+                w *= nl_prefactor(a, q).x;
             }
-            const float2 o = S[az * RS + ay];
             S[az * RS + ay] = inm ? cscale(o, w) : czero();
         }
         __syncthreads();

@@ -99,17 +99,25 @@ template <int T>
 __device__ __forceinline__ void team_normal_pair_ks(const uint32_t (&ks)[20], uint64_t jbase, int t, int e,
                                                     uint32_t step, uint32_t replica, float2& z0, float2& z1,
                                                     uint32_t tag = 0u) {
-    static_assert(T > 1 && T % 2 == 0, "lane pairs");
-    const bool odd = (t & 1) != 0;
-    const uint64_t j = jbase + t + (uint64_t)T * (e + (odd ? 1 : 0));
-    const uint4 w = philox4x32_10_ks(make_uint4((uint32_t)(j >> 1), step, replica, tag), ks);
-    const float2 p0 = recipe_bm_pair(w.x, w.y), p1 = recipe_bm_pair(w.z, w.w);
-    const float2 send = odd ? p0 : p1;
-    float2 recv;
-    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
-    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
-    z0 = odd ? recv : p0;
-    z1 = odd ? p1 : recv;
+    if constexpr (T == 1) {
+        const uint64_t j = jbase + e;
+        const uint4 w = philox4x32_10_ks(make_uint4((uint32_t)(j >> 1), step, replica, tag), ks);
+        const float4 pp = recipe_bm_pair2(w.x, w.y, w.z, w.w);
+        z0 = make_float2(pp.x, pp.y);
+        z1 = make_float2(pp.z, pp.w);
+    } else {
+        const bool odd = (t & 1) != 0;
+        const uint64_t j = jbase + t + (uint64_t)T * (e + (odd ? 1 : 0));
+        const uint4 w = philox4x32_10_ks(make_uint4((uint32_t)(j >> 1), step, replica, tag), ks);
+        const float4 pp = recipe_bm_pair2(w.x, w.y, w.z, w.w);
+        const float2 p0 = make_float2(pp.x, pp.y), p1 = make_float2(pp.z, pp.w);
+        const float2 send = odd ? p0 : p1;
+        float2 recv;
+        recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+        recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+        z0 = odd ? recv : p0;
+        z1 = odd ? p1 : recv;
+    }
 }
 
 // eta from a normal pair: self-conjugate modes real N(0,1), others (z0 + i z1)/sqrt2.

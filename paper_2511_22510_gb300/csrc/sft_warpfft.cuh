@@ -18,6 +18,11 @@
 
 namespace sft {
 
+// Complex sum and difference with the paired single-precision instructions of
+// sm_100 and later (one instruction for both components).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
 // 32-point DFT in registers (radix-2 decimation in frequency, then the
 // bit-reversal permutation resolved at compile time).  ZIN marks inputs known
 // to be zero: the first stage skips the additions they would take part in.
@@ -37,8 +42,8 @@ __device__ __forceinline__ void dft32(float2 (&x)[32]) {
             x[i] = a;
             x[i + 16] = twiddle_const<INV>(a, i, 32);
         } else {
-            x[i] = cadd(a, b);
-            x[i + 16] = twiddle_const<INV>(csub(a, b), i, 32);
+            x[i] = padd(a, b);
+            x[i + 16] = twiddle_const<INV>(psub(a, b), i, 32);
         }
     }
 #pragma unroll
@@ -48,8 +53,8 @@ __device__ __forceinline__ void dft32(float2 (&x)[32]) {
 #pragma unroll
             for (int i = 0; i < span; ++i) {
                 const float2 a = x[blk + i], b = x[blk + i + span];
-                x[blk + i] = cadd(a, b);
-                x[blk + i + span] = twiddle_const<INV>(csub(a, b), i * (16 / span), 32);
+                x[blk + i] = padd(a, b);
+                x[blk + i + span] = twiddle_const<INV>(psub(a, b), i * (16 / span), 32);
             }
         }
     }

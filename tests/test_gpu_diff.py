@@ -22,10 +22,11 @@ def env():
 
 def make_pair(m, oracle_mod, w, f0):
     g = m.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
-    g.set_field(f0.astype(np.float32))
+    dt, dt64 = (np.complex64, np.complex128) if w.complex_field else (np.float32, np.float64)
+    g.set_field(f0.astype(dt))
     o = oracle_mod.Oracle(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
     for r in range(w.replicas):
-        o.set_field(r, f0[r].astype(np.float32).astype(np.float64))
+        o.set_field(r, f0[r].astype(dt).astype(dt64))
     return g, o
 
 
@@ -43,11 +44,16 @@ CASES = [
 ]
 
 
-# SETD2 (Eq. SETD2): the tangent carries its own history dF_prev, zero at the seed
+# SETD2 (Eq. SETD2): the tangent carries its own history dF_prev, zero at the seed; KPZ (Sec. V.B):
+# dq = 2 grad h . grad dh; CGL (Sec. V.C): dq = 2 |A|^2 dA + A^2 conj(dA), complex seeds
 TAN_CASES = CASES + [
     ("model_a_64_setd2", W.model_a_64(n=[64, 64], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
     ("model_b_1d_128_setd2", W.model_b_1024(d=1, n=[128], dx=[1.0], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
     ("model_a_3d_16_setd2", W.model_a_128_3d(n=[16, 16, 16], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
+    ("kpz_1d_256_setd1", W.kpz_1d(256, replicas=3, sigma0=0.5)),
+    ("kpz_1d_512_setd2", W.kpz_1d(512, replicas=2, sigma0=0.5, scheme=2)),
+    ("cgl_1d_128_setd2", W.cgl_2048(d=1, n=[128], dx=[0.5], replicas=2, p=[2.0, -0.5, 1e-3])),
+    ("cgl_1d_256_setd1", W.cgl_2048(d=1, n=[256], dx=[0.5], replicas=2, scheme=1, p=[0.5, 0.3, 1e-2])),
 ]
 
 
@@ -58,7 +64,7 @@ def test_tangent_parity(env, oracle_mod, name, w):
     d0 = W.initial_fields(w.with_(sigma0=1.0), seed_offset=9)
     g, o = make_pair(m, oracle_mod, w, f0)
     nst = 20
-    dev_in = torch.from_numpy(d0.astype(np.float32)).cuda()
+    dev_in = torch.from_numpy(d0.astype(np.complex64 if w.complex_field else np.float32)).cuda()
     dev_out = torch.zeros_like(dev_in)
     torch.cuda.synchronize()
     m.sft_tangent_step(g.ctx, dev_in.data_ptr(), nst, dev_out.data_ptr())
@@ -104,7 +110,16 @@ def test_tangent_matches_gpu_finite_differences(env):
     g.close()
 
 
-@pytest.mark.parametrize("name,w", CASES, ids=[c[0] for c in CASES])
+ADJ_CASES = CASES + [
+    ("kpz_1d_256_setd1", W.kpz_1d(256, replicas=3, sigma0=0.5)),
+    ("model_a_64_setd2", W.model_a_64(n=[64, 64], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
+    ("model_b_1d_128_setd2", W.model_b_1024(d=1, n=[128], dx=[1.0], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
+    ("model_a_3d_16_setd2", W.model_a_128_3d(n=[16, 16, 16], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
+    ("kpz_1d_512_setd2", W.kpz_1d(512, replicas=2, sigma0=0.5, scheme=2)),
+]
+
+
+@pytest.mark.parametrize("name,w", ADJ_CASES, ids=[c[0] for c in ADJ_CASES])
 def test_adjoint_dot_product_and_parity(env, oracle_mod, name, w):
     """<lambda, T delta> = <A lambda, delta> on the GPU, and the GPU gradient
     against the oracle's; checkpoint segments of 7 steps over a 20-step horizon
