@@ -68,7 +68,7 @@ struct sft_ctx {
     float2* tw32 = nullptr;  // W_1024^{t k1} for t, k1 < 32 (1024-point warp transforms)
     int wait_limit = 0;      // StepArgs::wait_limit (SFT_WAIT_LIMIT; tests of the time-out path)
     // tangent / adjoint
-    float2 *dphi = nullptr, *dseed = nullptr, *dP = nullptr, *dQ = nullptr;
+    float2 *dphi = nullptr, *dseed = nullptr, *dP = nullptr, *dQ = nullptr, *dPy = nullptr;
     float2* dfprev = nullptr;  // SETD2: the tangent's history dF of the previous step
     float2* dmu = nullptr;     // SETD2 adjoint: the cotangent of the history term
     bool dp_valid = false;
@@ -467,7 +467,7 @@ struct PlanChoice {
 };
 std::mutex g_plan_mu;
 std::map<PlanKey, PlanChoice> g_plans;
-constexpr int kRpbChoices[] = {2, 4, 8};
+constexpr int kRpbChoices[] = {1, 2, 4, 8};
 constexpr int kPlanReps = 4;
 }  // namespace
 
@@ -1699,15 +1699,19 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
 
 // adjoint: whether the adjoint (not only the tangent) is asked for
 static sft_status diff_supported(sft_ctx* ctx, bool adjoint) {
-    // the cubic term in 1-D, 2-D and 3-D; the KPZ term and the complex |A|^2 A term (CGL) in 1-D; the adjoint
-    // for real fields
-    const bool term = ctx->nl == NL_CUBIC || (ctx->d == 1 && (ctx->nl == NL_GRAD2 || ctx->nl == NL_CGL));
-    if (!term || (adjoint && ctx->cplx) || (ctx->d == 1 && ctx->nx > 32768) || ctx->cfg.dealias == 2 ||
+    // tangent: the cubic term in 1-D, 2-D and 3-D; the KPZ term and the complex |A|^2 A term (CGL) in 1-D and
+    // 2-D (complex rows up to 2048 points); adjoint: the cubic term, and the KPZ term in 1-D
+    const bool tan_term = ctx->nl == NL_CUBIC ||
+                          (ctx->d <= 2 && ctx->nl == NL_GRAD2) ||
+                          (ctx->nl == NL_CGL && (ctx->d == 1 || (ctx->d == 2 && ctx->nx <= 2048)));
+    const bool adj_term = ctx->nl == NL_CUBIC || (ctx->d == 1 && ctx->nl == NL_GRAD2);
+    if (!(adjoint ? adj_term : tan_term) || (ctx->d == 1 && ctx->nx > 32768) || ctx->cfg.dealias == 2 ||
         !is_pow2(ctx->nx) || ctx->cfg.noise_space != 0)
         return fail(ctx, SFT_EUNSUPPORTED,
-                    "the tangent is built for the cubic term (Model A/B, d = 1..3) and, in 1-D, the KPZ and CGL "
-                    "terms; the adjoint for the real fields among them; every scheme; 1-D lines up to 32768 "
-                    "points, power-of-two lattices, 2/3 truncation or none, Fourier-space noise");
+                    "the tangent is built for the cubic term (Model A/B, d = 1..3) and the KPZ and CGL terms "
+                    "(d = 1, 2; complex rows up to 2048 points); the adjoint for the cubic term and the 1-D KPZ "
+                    "term; every scheme; 1-D lines up to 32768 points, power-of-two lattices, 2/3 truncation or "
+                    "none, Fourier-space noise");
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (!ctx->dphi) {
         CK(cudaMalloc(&ctx->dphi, ms));
@@ -1724,6 +1728,10 @@ static sft_status diff_supported(sft_ctx* ctx, bool adjoint) {
         CK(cudaMalloc(&ctx->dQ, ms));
         CK(cudaMemsetAsync(ctx->dP, 0, ms, ctx->stream));
         CK(cudaMemsetAsync(ctx->dQ, 0, ms, ctx->stream));
+    }
+    if (ctx->d >= 2 && ctx->nl == NL_GRAD2 && !ctx->dPy) {
+        CK(cudaMalloc(&ctx->dPy, ms));
+        CK(cudaMemsetAsync(ctx->dPy, 0, ms, ctx->stream));
     }
     return SFT_OK;
 }
@@ -1777,6 +1785,7 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
         StepArgs a = base_args(ctx);
         a.phi = ctx->dphi;
         a.pout = ctx->dP;
+        a.pyout = ctx->dPy;
         a.tw_a = ctx->tw.get(ctx->ny);
         CK(launch_second(ctx, a, MODE_PRIME));
         ctx->launches += 1;
@@ -1796,6 +1805,8 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
         } else {
             a.pin = ctx->P;
             a.dpin = ctx->dP;
+            a.pyin = ctx->Py;
+            a.dpyin = ctx->dPy;
             a.qout = ctx->Q;
             a.dqout = ctx->dQ;
             a.tw_a = ctx->tw.get(ctx->nx / 2);
@@ -1805,6 +1816,8 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
             a.dqin = ctx->dQ;
             a.pout = ctx->P;
             a.dpout = ctx->dP;
+            a.pyout = ctx->Py;
+            a.dpyout = ctx->dPy;
             a.tw_a = ctx->tw.get(ctx->ny);
             if (ctx->d == 3) {
                 // the plane pass runs the primal step, then the (noise-free) tangent update
@@ -1812,7 +1825,7 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
                 CK(launch_second(ctx, a, MODE_TAN));
                 ctx->launches += 1;
             } else {
-                CK(launch_k2_cols(a, MODE_TAN, ctx->nl, ctx->stream));
+                CK(launch_second(ctx, a, MODE_TAN));
             }
             ctx->launches += 2;
         }
@@ -2196,7 +2209,7 @@ void sft_destroy(sft_ctx* ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     void* bufs[] = {ctx->phi,   ctx->fprev,  ctx->P,      ctx->Q,      ctx->Py,     ctx->snap, ctx->real,
                     ctx->cfield, ctx->tab,   ctx->dstep,  ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev,
-                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec, ctx->tw32, ctx->dfprev, ctx->dmu,
+                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec, ctx->tw32, ctx->dfprev, ctx->dmu, ctx->dPy,
                     ctx->d_order, ctx->d_chunks, ctx->d_first_chunk, ctx->d_part, ctx->d_tacc};
     for (void* p : bufs)
         if (p) cudaFree(p);

@@ -48,6 +48,64 @@ __global__ void __launch_bounds__(CRowCfg<N>::THREADS) k2_rows_cplx(const StepAr
     float2* trow = sm + team * TS;
     const float2* __restrict__ tw = a.tw_a;
     float2 z[E];
+    if constexpr (MODE == MODE_TAN) {
+        // tangent: A = IDFT_x(P), dA = IDFT_x(dP); Q = DFT_x(|A|^2 A) and dQ = DFT_x(2 |A|^2 dA + A^2 conj(dA)),
+        // the linearisation of |A|^2 A.  Tile 0: P (then Q), tile 1: dP (then dQ); each team row is also its
+        // transform's exchange buffer.
+        float2* drow = sm + (ROWS + team) * TS;
+        auto load = [&](const float2* src, float2* dst) {
+            block_copy<C::THREADS, ROWS * N>(
+                ROWS * ncols,
+                [&](int f) {
+                    const int c = f / ROWS, yy = f % ROWS;
+                    return (y0 + yy < ny) ? src[((size_t)rep * hx + c) * ny + y0 + yy] : czero();
+                },
+                [&](int f, float2 v) { dst[(f % ROWS) * TS + f / ROWS] = v; });
+        };
+        load(a.pin, sm);
+        load(a.dpin, sm + ROWS * TS);
+        __syncthreads();
+        float2 zd[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int ax = t + T * e;
+            const bool in = cmask_x(ax, nx, ncols);
+            z[e] = in ? trow[ccomp_x(ax, nx, ncols)] : czero();
+            zd[e] = in ? drow[ccomp_x(ax, nx, ncols)] : czero();
+        }
+        fft_line<N, true>(z, trow, t, tw);
+        fft_line<N, true>(zd, drow, t, tw);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float2 A = z[e], dA = zd[e];
+            const float a2 = A.x * A.x + A.y * A.y;
+            zd[e] = cadd(cscale(dA, 2.f * a2), cmul(cmul(A, A), cconj(dA)));
+            z[e] = cscale(A, a2);
+        }
+        fft_line<N, false>(z, trow, t, tw);
+        fft_line<N, false>(zd, drow, t, tw);
+        team_sync<T>();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int ax = t + T * e;
+            if (cmask_x(ax, nx, ncols)) {
+                trow[ccomp_x(ax, nx, ncols)] = z[e];
+                drow[ccomp_x(ax, nx, ncols)] = zd[e];
+            }
+        }
+        __syncthreads();
+        auto store = [&](const float2* src, float2* dst) {
+            block_copy<C::THREADS, ROWS * N>(
+                ROWS * ncols, [&](int f) { return src[(f % ROWS) * TS + f / ROWS]; },
+                [&](int f, float2 v) {
+                    const int c = f / ROWS, yy = f % ROWS;
+                    if (y0 + yy < ny) dst[((size_t)rep * hx + c) * ny + y0 + yy] = v;
+                });
+        };
+        store(sm, a.qout);
+        store(sm + ROWS * TS, a.dqout);
+        return;
+    }
     if constexpr (MODE == MODE_FWD) {
         const float2* src = a.cplx_io + ((size_t)rep * ny + (yok ? y : 0)) * N;
 #pragma unroll
@@ -204,6 +262,69 @@ __global__ void __launch_bounds__(CColCfg<NY>::THREADS, 512 / CColCfg<NY>::THREA
                         flag_nonfinite(a, out[e], step);
                     }
                 }
+            } else if constexpr (MODE == MODE_TAN) {
+                // the primal step (as MODE_STEP, without staging) and the tangent update of Eq. SETD1/SETD2
+                // linearised: dphi <- f1 dphi + A M s DFT[dq] + B dF_prev, no noise; P and dP emitted below
+                const long long step = current_step(a);
+                const bool first = (a.scheme == 2) && (step == *a.first_step);
+                const bool has_f = valid && inx;
+                float2 dv[E];
+                if (has_f || T < 32) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        v[e] = has_f ? a.qin[cbase + t + T * e] : czero();
+                        dv[e] = has_f ? a.dqin[cbase + t + T * e] : czero();
+                    }
+                    fft_line<NY, false>(v, xb, t, tw);
+                    fft_line<NY, false>(dv, xb, t, tw);
+                }
+                const float2 s = make_float2(a.s0, a.s0i);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & 1) == 0)
+                        team_normal_pair_ks<T>(a.ks, (uint64_t)ax * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep),
+                                               out[e], out[e + 1]);
+                    const int ay = t + T * e;
+                    const int ays = signed_idx(ay, NY);
+                    const bool inm = has_f && (!a.dealias || 3 * abs(ays) < NY);
+                    const float2 F = inm ? cmul(s, v[e]) : czero();
+                    const float2 dF = inm ? cmul(s, dv[e]) : czero();
+                    const Coefs co = load_coefs<true>(a.tab, abs(axs) * (NY / 2 + 1) + abs(ays), first);
+                    float2 Fp = czero(), dFp = czero();
+                    if (a.scheme == 2 && has_f) {
+                        Fp = a.fprev[colbase + ay];
+                        dFp = a.dfprev[colbase + ay];
+                    }
+                    out[e] = setd_update<true>(co, a.phi[colbase + ay], F, Fp, eta_of(out[e], false));
+                    dv[e] = setd_update<true>(co, a.dphi[colbase + ay], dF, dFp, czero());
+                    if (a.scheme == 2 && has_f && valid) {
+                        a.fprev[colbase + ay] = F;
+                        a.dfprev[colbase + ay] = dF;
+                    }
+                }
+                if (valid) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        a.phi[colbase + t + T * e] = out[e];
+                        a.dphi[colbase + t + T * e] = dv[e];
+                        flag_nonfinite(a, out[e], step);
+                    }
+                }
+                // dP <- IFFT_y(M dphi / N^2)
+                const bool has_dp = valid && inx;
+                if (has_dp || T < 32) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int ay = t + T * e;
+                        const bool inm = has_dp && (!a.dealias || 3 * abs(signed_idx(ay, NY)) < NY);
+                        dv[e] = inm ? cscale(dv[e], a.scale) : czero();
+                    }
+                    fft_line<NY, true>(dv, xb, t, tw);
+                    if (has_dp) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) a.dpout[cbase + t + T * e] = dv[e];
+                    }
+                }
             } else {  // MODE_PRIME
 #pragma unroll
                 for (int e = 0; e < E; ++e) out[e] = a.phi[colbase + t + T * e];
@@ -229,14 +350,15 @@ __global__ void __launch_bounds__(CColCfg<NY>::THREADS, 512 / CColCfg<NY>::THREA
 template <int N, int MODE>
 static cudaError_t run_crows(const StepArgs& a, cudaStream_t s) {
     using C = CRowCfg<N>;
+    const size_t sm = (MODE == MODE_TAN ? 2 : 1) * C::smem();
     static bool attr = false;
     if (!attr) {
         cudaError_t e =
-            cudaFuncSetAttribute(k2_rows_cplx<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem());
+            cudaFuncSetAttribute(k2_rows_cplx<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k2_rows_cplx<N, MODE><<<dim3((a.ny + C::ROWS - 1) / C::ROWS, a.R), C::THREADS, C::smem(), s>>>(a);
+    k2_rows_cplx<N, MODE><<<dim3((a.ny + C::ROWS - 1) / C::ROWS, a.R), C::THREADS, sm, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -260,6 +382,7 @@ static cudaError_t crows_for(const StepArgs& a, int mode, cudaStream_t s) {
         case MODE_STEP: return run_crows<N, MODE_STEP>(a, s);
         case MODE_FWD: return run_crows<N, MODE_FWD>(a, s);
         case MODE_INV: return run_crows<N, MODE_INV>(a, s);
+        case MODE_TAN: return run_crows<N, MODE_TAN>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -271,6 +394,7 @@ static cudaError_t ccols_for(const StepArgs& a, int mode, cudaStream_t s) {
         case MODE_FWD: return run_ccols<NY, MODE_FWD>(a, s);
         case MODE_INV: return run_ccols<NY, MODE_INV>(a, s);
         case MODE_PRIME: return run_ccols<NY, MODE_PRIME>(a, s);
+        case MODE_TAN: return run_ccols<NY, MODE_TAN>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(RowCfg<M, SH>::THREADS, RowCfg<M, SH>::MINB) k
     using PL = FftPlan<M>;
     constexpr int T = PL::T, E = PL::E, ROWS = C::ROWS, TS = C::TS;
     constexpr bool GRAD = (NL == NL_GRAD2) && (MODE == MODE_STEP);
-    static_assert(!((MODE == MODE_TAN || MODE == MODE_ADJ) && NL != NL_CUBIC), "tangent/adjoint: cubic term");
+    static_assert(!(MODE == MODE_ADJ && NL != NL_CUBIC), "adjoint: cubic term");
     extern __shared__ float2 sm[];
     float2* tile = sm;
     const int team = threadIdx.x / T, t = threadIdx.x % T;
@@ -151,6 +151,57 @@ __global__ void __launch_bounds__(RowCfg<M, SH>::THREADS, RowCfg<M, SH>::MINB) k
     const float2* __restrict__ twN = a.tw_b;
     float2 z[E];
 
+    if constexpr (MODE == MODE_TAN && NL == NL_GRAD2) {
+        // KPZ tangent: q = g_x^2 + g_y^2 and q' = 2 (g_x dg_x + g_y dg_y), g_x = IDFT_x(i k_x P), g_y = IDFT_x(P_y),
+        // dg likewise from dP, dP_y (Sec. V.B linearised).  Tiles: 0 P (then Q), 1 P_y, 2 dP (then dQ), 3 dP_y;
+        // tile rows 0 and then 1 serve as the team's exchange buffer once read.
+        load_tile<C>(tile, a.pin, rowbase, ncols, ny, y0);
+        load_tile<C>(tile + ROWS * TS, a.pyin, rowbase, ncols, ny, y0);
+        load_tile<C>(tile + 2 * ROWS * TS, a.dpin, rowbase, ncols, ny, y0);
+        load_tile<C>(tile + 3 * ROWS * TS, a.dpyin, rowbase, ncols, ny, y0);
+        __syncthreads();
+        float2* r0 = tile + team * TS;
+        float2* r1 = tile + ROWS * TS + team * TS;
+        float2* r2 = tile + 2 * ROWS * TS + team * TS;
+        float2* r3 = tile + 3 * ROWS * TS + team * TS;
+        float2 zd[E], zy[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            const float2 tw = __ldg(&twN[k]);
+            const float kx = a.dk * (float)k, kxm = (k == 0) ? 0.f : a.dk * (float)(M - k);
+            z[e] = c2r_pre(cscale(cmuli(r0[k]), kx), cscale(cmuli(r0[M - k]), kxm), tw);
+            zd[e] = c2r_pre(cscale(cmuli(r2[k]), kx), cscale(cmuli(r2[M - k]), kxm), tw);
+            zy[e] = c2r_pre(r1[k], r1[M - k], tw);
+        }
+        fft_line<M, true>(z, r0, t, twM);
+        fft_line<M, true>(zd, r0, t, twM);
+        fft_line<M, true>(zy, r0, t, twM);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            zd[e] = make_float2(2.f * z[e].x * zd[e].x, 2.f * z[e].y * zd[e].y);
+            z[e] = make_float2(z[e].x * z[e].x + zy[e].x * zy[e].x, z[e].y * z[e].y + zy[e].y * zy[e].y);
+        }
+        fft_line<M, false>(z, r0, t, twM);
+        row_post<M>(z, r0, r0, ncols, t, twN);  // Q in tile 0
+        // dg_y from dP_y (tile 3), exchanging through tile 1
+        team_sync<T>();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            z[e] = c2r_pre(r3[k], r3[M - k], __ldg(&twN[k]));
+        }
+        fft_line<M, true>(z, r1, t, twM);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            zd[e] = make_float2(zd[e].x + 2.f * zy[e].x * z[e].x, zd[e].y + 2.f * zy[e].y * z[e].y);
+        fft_line<M, false>(zd, r1, t, twM);
+        row_post<M>(zd, r1, r2, ncols, t, twN);  // dQ in tile 2
+        __syncthreads();
+        store_tile<C>(tile, a.qout, rowbase, ncols, ny, y0);
+        store_tile<C>(tile + 2 * ROWS * TS, a.dqout, rowbase, ncols, ny, y0);
+        return;
+    }
     if constexpr (MODE == MODE_TAN || MODE == MODE_ADJ) {
         // tangent: q' = 3 psi^2 dpsi next to q = psi^3; adjoint: v = 3 psi^2 w.
         // tile 0: primal P (psi), tile 1: tangent dP (dpsi) or adjoint W.
@@ -339,7 +390,7 @@ template <int M, int NL, int MODE, int SH = 0>
 static cudaError_t run_rows(const StepArgs& a, cudaStream_t s) {
     using C = RowCfg<M, SH>;
     constexpr int NTILE =
-        (NL == NL_GRAD2 && MODE == MODE_STEP_PS)
+        (NL == NL_GRAD2 && (MODE == MODE_STEP_PS || MODE == MODE_TAN))
             ? 4
             : (((NL == NL_GRAD2 && MODE == MODE_STEP) || MODE == MODE_TAN || MODE == MODE_ADJ || MODE == MODE_STEP_PS) ? 2
                                                                                                                 : 1);
@@ -373,6 +424,7 @@ static cudaError_t rows_for(const StepArgs& a, int mode, int nl, cudaStream_t s,
     if (mode == MODE_STEP_PS && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_STEP_PS>(a, s);
     if (mode == MODE_STEP_PS && nl == NL_GRAD2) return run_rows<M, NL_GRAD2, MODE_STEP_PS>(a, s);
     if (mode == MODE_TAN && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_TAN>(a, s);
+    if (mode == MODE_TAN && nl == NL_GRAD2) return run_rows<M, NL_GRAD2, MODE_TAN>(a, s);
     if (mode == MODE_ADJ && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_ADJ>(a, s);
     return cudaErrorInvalidValue;
 }

@@ -392,6 +392,7 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
         emit_p<NY, NL, EM>(a, out, valid && cc < a.ncols, cc, colbase, xb, t);
         StepArgs b = a;
         b.pout = a.dpout;
+        b.pyout = a.dpyout;
         emit_p<NY, NL, EM>(b, dv, valid && cc < a.ncols, cc, colbase, xb, t);
     } else if constexpr (MODE == MODE_ADJ || MODE == MODE_ADJ_PRIME) {
         // adjoint of step n: lam_n = f1 lam_{n+1} + M DFT[v] (v from the row pass), mu_{n-1} = B_n lam_{n+1}
@@ -505,6 +506,7 @@ static cudaError_t cols_for(const StepArgs& a, int mode, int nl, cudaStream_t s,
     if (mode == MODE_PRIME && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_PRIME>(a, s);
     if (mode == MODE_PRIME && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_PRIME>(a, s);
     if (mode == MODE_TAN && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_TAN>(a, s);
+    if (mode == MODE_TAN && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_TAN>(a, s);
     if (mode == MODE_ADJ && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_ADJ>(a, s);
     if (mode == MODE_ADJ_PRIME && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_ADJ_PRIME>(a, s);
     return cudaErrorInvalidValue;

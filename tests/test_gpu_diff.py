@@ -54,6 +54,10 @@ TAN_CASES = CASES + [
     ("kpz_1d_512_setd2", W.kpz_1d(512, replicas=2, sigma0=0.5, scheme=2)),
     ("cgl_1d_128_setd2", W.cgl_2048(d=1, n=[128], dx=[0.5], replicas=2, p=[2.0, -0.5, 1e-3])),
     ("cgl_1d_256_setd1", W.cgl_2048(d=1, n=[256], dx=[0.5], replicas=2, scheme=1, p=[0.5, 0.3, 1e-2])),
+    ("kpz_2d_32_setd1", W.kpz_2d(n=[32, 32], replicas=2, sigma0=0.5)),
+    ("kpz_2d_64_setd2", W.kpz_2d(n=[64, 64], replicas=2, sigma0=0.5, scheme=2)),
+    ("cgl_2d_32_setd2", W.cgl_2048(n=[32, 32], replicas=2, p=[2.0, -0.5, 1e-3])),
+    ("cgl_2d_64_setd1", W.cgl_2048(n=[64, 64], replicas=2, scheme=1, p=[0.5, 0.3, 1e-2])),
 ]
 
 

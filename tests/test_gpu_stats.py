@@ -4,10 +4,11 @@ Gaussian Model A and Model B (u = 0) are Ornstein-Uhlenbeck processes per
 Fourier mode.  SETD1 (Sec. II) integrates each exactly in distribution, so the
 stationary equal-time structure factor is S(k) = T / (r + k^2) for every mode
 (Sec. V.A; Model B's conserved noise and k^2 mobility cancel), at any h.  The
-test runs an ensemble of replicas to equilibrium, samples the per-replica shell
-averages (App. C) at well separated times and requires every shell to agree
-with the exact shell average within 4 standard errors (estimated from the
-samples), and the mean squared z-score to be that of a unit normal.
+test runs 8 independent ensembles (8 seeds, 8 replicas each) to equilibrium,
+samples the per-replica shell averages (App. C) at well separated times and
+requires every shell to agree with the exact shell average within 3 standard
+errors (estimated from the samples), and the mean squared z-score to be that
+of a unit normal.
 """
 import numpy as np
 import pytest
@@ -42,26 +43,29 @@ def exact_shells(n, L, r, T):
     return sums / np.maximum(counts, 1), counts
 
 
+SEEDS = [11, 12, 13, 14, 15, 16, 17, 18]
+
 CASES = [
     # relaxation time of the slowest mode: 20 steps (Model A, 1 / (Gamma r h));
     # 20 steps (Model B 16^2, 1 / (Gamma k1^2 (r + k1^2) h)); samples 5 of them apart
-    ("model_a", W.model_a_64(p=[1.0, 0.5, 0.0, 0.5], h=0.1, replicas=64, sigma0=0.0), 1000, 100),
-    ("model_b", W.model_b_1024(n=[16, 16], p=[1.0, 0.5, 0.0, 0.5], h=0.5, replicas=64, sigma0=0.0), 2000, 100),
+    ("model_a", W.model_a_64(p=[1.0, 0.5, 0.0, 0.5], h=0.1, replicas=8, sigma0=0.0), 1000, 100),
+    ("model_b", W.model_b_1024(n=[16, 16], p=[1.0, 0.5, 0.0, 0.5], h=0.5, replicas=8, sigma0=0.0), 2000, 100),
 ]
 
 
 @pytest.mark.parametrize("name,w,n_eq,gap", CASES, ids=[c[0] for c in CASES])
 def test_gaussian_structure_factor(sft, name, w, n_eq, gap):
-    g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
-    g.set_field(np.zeros((w.replicas,) + w.shape, dtype=np.float32))
-    g.step(n_eq)
-    ns = g.nshells()
     samples = []
-    for _ in range(20):
-        g.step(gap)
-        samples.append(g.observe(sft.SFT_OBS_SK_REPLICAS).reshape(w.replicas, ns))
-    counts = g.observe(sft.SFT_OBS_SK)[ns:]
-    g.close()
+    for seed in SEEDS:
+        g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, seed, dealias=w.dealias)
+        g.set_field(np.zeros((w.replicas,) + w.shape, dtype=np.float32))
+        g.step(n_eq)
+        ns = g.nshells()
+        for _ in range(20):
+            g.step(gap)
+            samples.append(g.observe(sft.SFT_OBS_SK_REPLICAS).reshape(w.replicas, ns))
+        counts = g.observe(sft.SFT_OBS_SK)[ns:]
+        g.close()
     S = np.concatenate(samples)
     exp, exp_counts = exact_shells(w.n[0], w.n[0] * w.dx[0], w.p[1], w.p[3])
     assert len(exp) == ns and np.array_equal(counts, exp_counts)
@@ -71,5 +75,5 @@ def test_gaussian_structure_factor(sft, name, w, n_eq, gap):
     mean = S.mean(axis=0)[first:]
     se = S.std(axis=0, ddof=1)[first:] / np.sqrt(S.shape[0])
     z = (mean - exp[first:]) / se
-    assert np.all(np.abs(z) < 4.0), (name, np.argmax(np.abs(z)) + first, z[np.argmax(np.abs(z))])
+    assert np.all(np.abs(z) < 3.0), (name, np.argmax(np.abs(z)) + first, z[np.argmax(np.abs(z))])
     assert 0.5 < float(np.mean(z ** 2)) < 1.6, (name, float(np.mean(z ** 2)))
