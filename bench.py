@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--h", type=float, default=0.05)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--precision", type=int, default=0,
+                    help="cgl_2048: 1 runs the split-BF16x3 tensor-core transforms of the precision study")
     ap.add_argument("--workload", default="model_b_1024",
                     choices=["model_b_1024", "model_a_64", "kpz_ensemble", "cgl_2048", "model_a_128_3d",
                              "model_a_128_3d_tangent", "sde0d", "dynamics", "model_b_1024_phase_shift",
@@ -677,8 +679,9 @@ def run_other(args):
             w = W.cgl_2048(replicas=4)
         else:
             w = W.model_a_128_3d(replicas=32)
+        prec = args.precision if args.workload == "cgl_2048" else 0
         g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
-                        stream=stream.cuda_stream, noise_space=noise_space)
+                        stream=stream.cuda_stream, noise_space=noise_space, precision=prec)
         g.init_random(max(w.sigma0, 0.1))
         if args.workload == "model_a_128_3d_tangent":
             seed = torch.zeros((w.replicas,) + w.shape, dtype=torch.float32, device="cuda")
@@ -694,7 +697,7 @@ def run_other(args):
         prof = sft.sft_profile(g.ctx, 10)
         g.close()
         p1 = sft.Stepper(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
-                         stream=stream.cuda_stream, noise_space=noise_space)
+                         stream=stream.cuda_stream, noise_space=noise_space, precision=prec)
         p1.init_random(0.1)
         p1.step_plain(2)
         msp = timed(lambda: p1.step_plain(K))
@@ -704,7 +707,8 @@ def run_other(args):
                      "config": {"workload": args.workload, "lattice": "x".join(str(n) for n in w.n),
                                 "replicas": w.replicas, "scheme": scheme_name(w.scheme), "h": w.h,
                                 "dealias": {0: "none", 1: "2/3 truncation", 2: "phase shifts"}[w.dealias],
-                                "noise": "real space + FFT" if noise_space else "Fourier space"},
+                                "noise": "real space + FFT" if noise_space else "Fourier space",
+                                "transforms": "split-BF16x3 tensor cores (precision study)" if prec else "FP32"},
                      "kernels_ms": list(map(float, prof)),
                      "plain": {"value": plain, "unit": UNIT, "replicas": 1, "graph": False,
                                "batched_speedup": value / plain}})

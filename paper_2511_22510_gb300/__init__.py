@@ -121,7 +121,8 @@ def _check(ctx, status: int):
 # ---------------------------------------------------------------- thin wrappers
 def make_config(d: int, n: Sequence[int], dx: Sequence[float], replicas: int, model: int, p: Sequence[float],
                 scheme: int, h: float, seed: int, dealias: int = 1, stream: Optional[int] = None,
-                replica0: int = 0, custom: Optional[dict] = None, noise_space: int = 0) -> sft_config:
+                replica0: int = 0, custom: Optional[dict] = None, noise_space: int = 0,
+                precision: int = 0) -> sft_config:
     """custom (SFT_CUSTOM): {"nl": SFT_NL_*, "complex_field": 0/1, "c": c(|a|^2), "D": D(|a|^2),
     "s": s(|a|^2) or None}, arrays over q = 0 .. sum_i (n_i/2)^2 (complex c or s for complex fields)."""
     cfg = sft_config()
@@ -137,7 +138,7 @@ def make_config(d: int, n: Sequence[int], dx: Sequence[float], replicas: int, mo
     cfg.h = float(h)
     cfg.seed = int(seed)
     cfg.dealias = dealias
-    cfg.precision = 0
+    cfg.precision = int(precision)
     cfg.stream = stream
     cfg.replica0 = replica0
     cfg.noise_space = int(noise_space)
@@ -403,9 +404,9 @@ class Stepper:
     """
 
     def __init__(self, d, n, dx, replicas, model, p, scheme, h, seed, dealias=1, stream=None, replica0=0,
-                 custom=None, noise_space=0):
+                 custom=None, noise_space=0, precision=0):
         self.cfg = make_config(d, n, dx, replicas, model, p, scheme, h, seed, dealias, stream, replica0, custom,
-                               noise_space)
+                               noise_space, precision)
         self.ctx = sft_create(self.cfg)
         self.d, self.R = d, replicas
         self.n = [int(n[i]) for i in range(d)]

@@ -71,6 +71,7 @@ struct sft_ctx {
     float2 *dphi = nullptr, *dseed = nullptr, *dP = nullptr, *dQ = nullptr, *dPy = nullptr;
     float2* dfprev = nullptr;  // SETD2: the tangent's history dF of the previous step
     float2* dmu = nullptr;     // SETD2 adjoint: the cotangent of the history term
+    float2 *tcb1 = nullptr, *tcb2 = nullptr;  // precision study: scratch of the tensor-core step
     bool dp_valid = false;
     // host mirrors
     long long step = 0;
@@ -441,6 +442,11 @@ static sft_status enqueue_step(sft_ctx* ctx, int k) {
         CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
         return SFT_OK;
     }
+    if (ctx->cfg.precision == 1) {
+        // precision study: the step through the split-BF16x3 tensor-core transforms
+        CK(launch_tc_step(a, ctx->tcb1, ctx->tcb2, ctx->tw.get(ctx->nx), ctx->stream));
+        return SFT_OK;
+    }
     sft_status s = enqueue_front(ctx, a, k);
     if (s != SFT_OK) return s;
     CK(launch_cols_step(ctx, a));
@@ -694,7 +700,17 @@ sft_status sft::validate_config(const sft_config* cfg, std::string& why) {
     if (!(cfg->h > 0) || !std::isfinite(cfg->h)) return why = "h must be positive and finite", SFT_EINVAL;
     if (cfg->model < SFT_MODEL_A || cfg->model > SFT_CUSTOM) return why = "unknown model", SFT_EINVAL;
     if (cfg->scheme < SFT_SETD_EM || cfg->scheme > SFT_SETD2) return why = "unknown scheme", SFT_EINVAL;
-    if (cfg->precision != 0) return why = "only FP32 precision (0) is built", SFT_EUNSUPPORTED;
+    if (cfg->precision != 0) {
+        // 1: the split-BF16x3 tensor-core transforms of the precision study, complex 2-D fields of 1024^2
+        // or 2048^2 points with Fourier-space noise
+        int cp = 0, nl1 = 0;
+        model_kind(cfg, &cp, &nl1);
+        if (cfg->precision != 1) return why = "precision must be 0 (FP32) or 1 (split-BF16x3 study)", SFT_EINVAL;
+        if (!cp || cfg->d != 2 || !tc_supported(cfg->n[0], cfg->n[1]) || cfg->noise_space != 0 || cfg->dealias == 2)
+            return why = "the split-BF16x3 tensor-core path is built for complex 2-D fields of 1024^2 or 2048^2 "
+                         "points, Fourier-space noise, 2/3 truncation or none",
+                   SFT_EUNSUPPORTED;
+    }
     if ((cfg->model == SFT_MODEL_A || cfg->model == SFT_MODEL_B) && cfg->p[4] != 0.0 && cfg->scheme == SFT_SETD2)
         return why = "r placed in F (p[4] != 0) is built for SETD-EM and SETD1", SFT_EUNSUPPORTED;
     if (cfg->dealias < 0 || cfg->dealias > 2)
@@ -795,6 +811,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     if (ok && ctx->d >= 2 && ctx->nl == NL_GRAD2) ok = dalloc((void**)&ctx->Py, pq);
     if (ok && cfg->scheme == SFT_SETD2) ok = dalloc((void**)&ctx->fprev, ms);
     if (ok && cfg->noise_space == 1) ok = dalloc((void**)&ctx->noise_spec, ms);
+    if (ok && cfg->precision == 1) ok = dalloc((void**)&ctx->tcb1, ms) && dalloc((void**)&ctx->tcb2, ms);
     if (ok) {
         if (ctx->cplx)
             ok = dalloc((void**)&ctx->cfield, rs);
@@ -957,6 +974,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     }
     ctx->launches_per_step = ctx->d == 1 ? 1 : 2;
     if (cfg->noise_space == 1) ctx->launches_per_step += 2;  // forward transform of the noise (drawn in its row pass)
+    if (cfg->precision == 1) ctx->launches_per_step = 9;     // prep, 4 transforms, 2 transposes, |A|^2 A, update
     {
         // column-pass variant: chosen by the plan autotuner unless SFT_COLUMN_PASS forces the
         // persistent bulk-copy pipelined kernel ("pipelined", where it is built) or the
@@ -2137,6 +2155,11 @@ sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, in
             }
             CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
             CK(cudaEventRecord(e[1], ctx->stream));
+        } else if (ctx->cfg.precision == 1) {
+            // precision study: the whole tensor-core step, reported as the first entry (the second is empty)
+            CK(launch_tc_step(a, ctx->tcb1, ctx->tcb2, ctx->tw.get(ctx->nx), ctx->stream));
+            CK(cudaEventRecord(e[1], ctx->stream));
+            CK(cudaEventRecord(e[2], ctx->stream));
         } else {
             sft_status s = enqueue_front(ctx, a, 0);
             if (s != SFT_OK) return s;
@@ -2209,7 +2232,7 @@ void sft_destroy(sft_ctx* ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     void* bufs[] = {ctx->phi,   ctx->fprev,  ctx->P,      ctx->Q,      ctx->Py,     ctx->snap, ctx->real,
                     ctx->cfield, ctx->tab,   ctx->dstep,  ctx->dstatus, ctx->dshell, ctx->drough, ctx->tw.dev,
-                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec, ctx->tw32, ctx->dfprev, ctx->dmu, ctx->dPy,
+                    ctx->dphi,  ctx->dseed, ctx->dP,     ctx->dQ,      ctx->noise_spec, ctx->tw32, ctx->dfprev, ctx->dmu, ctx->dPy, ctx->tcb1, ctx->tcb2,
                     ctx->d_order, ctx->d_chunks, ctx->d_first_chunk, ctx->d_part, ctx->d_tacc};
     for (void* p : bufs)
         if (p) cudaFree(p);

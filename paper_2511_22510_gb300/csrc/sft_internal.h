@@ -124,6 +124,10 @@ cudaError_t launch_k2_rows_pair(const StepArgs& a, int nl, cudaStream_t s);
 // column pass of the step on columns of 1024 points, one warp per column (cubic term)
 bool k2_colwarp_supported(int nx, int ny, int nl, int dealias);
 cudaError_t launch_k2_cols_warp(const StepArgs& a, int nl, cudaStream_t s);
+// precision study (sft_config.precision = 1): complex 2-D step through split-BF16x3 tensor-core transforms
+bool tc_supported(int nx, int ny);
+cudaError_t launch_tc_step(const StepArgs& a, float2* b1, float2* b2, const float2* twN, cudaStream_t s);
+cudaError_t launch_tc_fft(int n, int inverse, float2* data, long long nlines, const float2* twN, cudaStream_t s);
 cudaError_t launch_k3_planes(const StepArgs& a, int mode, int nl, cudaStream_t s);
 cudaError_t launch_k2c_rows(const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_k2c_cols(const StepArgs& a, int mode, cudaStream_t s);
