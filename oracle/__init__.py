@@ -383,11 +383,19 @@ class Oracle:
         return out
 
     def adjoint(self, lam, nsteps):
-        a = np.ascontiguousarray(lam, dtype=np.float64).reshape(-1)
-        out = np.zeros(self.R * self.ntot)
+        """Gradient of <lam, field after nsteps> with respect to the field now (the transpose of the
+        tangent for the real inner product; complex fields: Re sum conj(u) v).  Advances the state."""
+        cf = np.iscomplexobj(lam) or self.complex_field
+        if cf:
+            a = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128)).view(np.float64).reshape(-1)
+        else:
+            a = np.ascontiguousarray(lam, dtype=np.float64).reshape(-1)
+        out = np.zeros(self.R * self.ntot * (2 if cf else 1))
         rc = lib().or_adjoint(self._p, _dptr(a), int(nsteps), _dptr(out))
         if rc != 0:
-            raise ValueError("adjoint needs a real field (and truncation or no dealiasing)")
+            raise ValueError("adjoint: truncation or no dealiasing; complex fields with the |A|^2 A term only")
+        if cf:
+            return out.view(np.complex128).reshape((self.R,) + self.shape)
         return out.reshape((self.R,) + self.shape)
 
 

@@ -1113,9 +1113,16 @@ int or_observe_response(const or_state* st, double* out) {
 /*   mu_{n-1} = b_n lam_{n+1},                                                */
 /* with the SETD1 pair at the step that starts SETD2 (no F_{-1} exists).  For */
 /* KPZ the gradient multiplier i k is odd, so its transpose is -i k.          */
+/* Complex fields (CGL, Sec. V.C) take the real inner product                 */
+/* Re sum_x conj(u(x)) v(x); every Fourier multiplier m then transposes to    */
+/* conj(m) (f1, a, b and the prefactor s are complex), and the pointwise      */
+/* linearisation dA -> 2 |A|^2 dA + A^2 conj(dA) of |A|^2 A is its own        */
+/* transpose, so L_n^T = C(M) D(q'_n) C(conj(M s)).                           */
 /* ------------------------------------------------------------------------- */
 int or_adjoint(or_state* st, const double* lam_in, int64_t nsteps, double* grad_out) {
-    if (st->cplx_field || st->cfg.dealias == 2) return -1;
+    if (st->cfg.dealias == 2) return -1;
+    if (st->cplx_field && st->nl != OR_NL_CGL && st->nl != OR_NL_NONE) return -1;
+    const int cf = st->cplx_field;
     size_t nt = st->ntot;
     int R = st->cfg.replicas;
     cplx* traj = (cplx*)malloc(nt * (size_t)R * (size_t)(nsteps > 0 ? nsteps : 1) * sizeof(cplx));
@@ -1133,7 +1140,8 @@ int or_adjoint(or_state* st, const double* lam_in, int64_t nsteps, double* grad_
     cplx* acc = (cplx*)malloc(nt * sizeof(cplx));
     for (int r = 0; r < R; ++r) {
         for (size_t i = 0; i < nt; ++i) {
-            lam[i] = lam_in[(size_t)r * nt + i];
+            lam[i] = cf ? lam_in[2 * ((size_t)r * nt + i)] + I * lam_in[2 * ((size_t)r * nt + i) + 1]
+                        : lam_in[(size_t)r * nt + i];
             mu[i] = 0.0;
         }
         fft_full(st, lam, -1);
@@ -1146,13 +1154,23 @@ int or_adjoint(or_state* st, const double* lam_in, int64_t nsteps, double* grad_
                 double D;
                 mode_coefs(st, i, first_of[t], &f1, &a, &b, &gg);
                 mode_operator(st, i, &c, &D, &s);
-                w[i] = mode_mask(st, i) * s * (a * lam[i] + mu[i]);
-                mu[i] = b * lam[i];
+                w[i] = mode_mask(st, i) * conj(s) * (conj(a) * lam[i] + mu[i]);
+                mu[i] = conj(b) * lam[i];
             }
             fft_full(st, w, +1);
-            for (size_t i = 0; i < nt; ++i) w[i] = creal(w[i]) / (double)nt;
+            for (size_t i = 0; i < nt; ++i) w[i] = (cf ? w[i] : creal(w[i])) / (double)nt;
             for (size_t i = 0; i < nt; ++i) acc[i] = 0.0;
-            if (st->nl == OR_NL_CUBIC) {
+            if (st->nl == OR_NL_CGL) {
+                /* q' = 2 |A|^2 w + A^2 conj(w), A = IDFT(M phi) */
+                for (size_t i = 0; i < nt; ++i) g[i] = mode_mask(st, i) * phi[i];
+                fft_full(st, g, +1);
+                for (size_t i = 0; i < nt; ++i) {
+                    const cplx A = g[i] / (double)nt;
+                    g[i] = 2.0 * (creal(A) * creal(A) + cimag(A) * cimag(A)) * w[i] + A * A * conj(w[i]);
+                }
+                fft_full(st, g, -1);
+                for (size_t i = 0; i < nt; ++i) acc[i] = mode_mask(st, i) * g[i];
+            } else if (st->nl == OR_NL_CUBIC) {
                 for (size_t i = 0; i < nt; ++i) g[i] = mode_mask(st, i) * phi[i];
                 fft_full(st, g, +1);
                 for (size_t i = 0; i < nt; ++i) {
@@ -1183,14 +1201,22 @@ int or_adjoint(or_state* st, const double* lam_in, int64_t nsteps, double* grad_
             for (size_t i = 0; i < nt; ++i) {
                 cplx f1, a, b, gg;
                 mode_coefs(st, i, first_of[t], &f1, &a, &b, &gg);
-                lam[i] = f1 * lam[i] + acc[i];
+                lam[i] = conj(f1) * lam[i] + acc[i];
             }
             hermitian_fixup(st, lam);
             hermitian_fixup(st, mu);
         }
         memcpy(w, lam, nt * sizeof(cplx));
         fft_full(st, w, +1);
-        for (size_t i = 0; i < nt; ++i) grad_out[(size_t)r * nt + i] = creal(w[i]) / (double)nt;
+        for (size_t i = 0; i < nt; ++i) {
+            const cplx v = w[i] / (double)nt;
+            if (cf) {
+                grad_out[2 * ((size_t)r * nt + i)] = creal(v);
+                grad_out[2 * ((size_t)r * nt + i) + 1] = cimag(v);
+            } else {
+                grad_out[(size_t)r * nt + i] = creal(v);
+            }
+        }
     }
     free(traj);
     free(first_of);

@@ -594,6 +594,66 @@ def test_adjoint_dot_product_identity(oracle_mod, model, scheme, pre):
         assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + 1e-300), (lhs, rhs)
 
 
+@pytest.mark.parametrize("d,scheme,pre", [(2, 1, 0), (2, 2, 0), (2, 2, 3), (2, 0, 0), (1, 2, 0), (1, 1, 2)])
+def test_adjoint_dot_product_identity_complex(oracle_mod, d, scheme, pre):
+    """CGL (Sec. V.C, complex field): with the real inner product
+    Re sum_x conj(u) v, <lambda_N, T delta_0> = <A lambda_N, delta_0> to
+    rounding, T the tangent (pinned by finite differences above, model 3)."""
+    n = [16, 16] if d == 2 else [32]
+    w = W.model_a_64(d=d, n=n, dx=[1.0] * d, model=3, p=[2.0, -0.5, 1e-3], scheme=scheme, h=0.02, sigma0=0.3)
+    assert w.complex_field
+    f0 = W.initial_fields(w, replicas=2)
+    d0 = W.initial_fields(w.with_(sigma0=1.0), replicas=2, seed_offset=3)
+    lam = W.initial_fields(w.with_(sigma0=1.0), replicas=2, seed_offset=4)
+    nst = 12
+    o = make_oracle(oracle_mod, w, replicas=2)
+    for r in range(2):
+        o.set_field(r, f0[r])
+    o.step(pre)
+    tan = o.tangent_step(d0, nst)
+    o2 = make_oracle(oracle_mod, w, replicas=2)
+    for r in range(2):
+        o2.set_field(r, f0[r])
+    o2.step(pre)
+    grad = o2.adjoint(lam, nst)
+    for r in range(2):
+        lhs = np.sum(np.conj(lam[r]) * tan[r]).real
+        rhs = np.sum(np.conj(grad[r]) * d0[r]).real
+        assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + 1e-300), (lhs, rhs)
+    # the primal ends where plain steps end
+    o3 = make_oracle(oracle_mod, w, replicas=2)
+    for r in range(2):
+        o3.set_field(r, f0[r])
+    o3.step(pre + nst)
+    assert np.allclose(o2.field(1), o3.field(1), rtol=0, atol=1e-13)
+
+
+def test_adjoint_complex_gradient_by_finite_differences(oracle_mod):
+    """CGL adjoint against a directional derivative of the scalar
+    J(phi_0) = Re <lambda, phi_N(phi_0)>: Re <grad J, delta> equals the central
+    difference of J along delta (O(e^2)), for a real and an imaginary delta."""
+    w = W.model_a_64(n=[16, 16], model=3, p=[2.0, -0.5, 1e-3], scheme=2, h=0.02, sigma0=0.3)
+    f0 = W.initial_fields(w)[0]
+    lam = W.initial_fields(w.with_(sigma0=1.0), seed_offset=4)
+    base = W.initial_fields(w.with_(sigma0=1.0), seed_offset=6)[0]
+    nst = 10
+    o = make_oracle(oracle_mod, w)
+    o.set_field(0, f0)
+    grad = o.adjoint(lam, nst)[0]
+
+    def J(x):
+        q = make_oracle(oracle_mod, w)
+        q.set_field(0, x)
+        q.step(nst)
+        return np.sum(np.conj(lam[0]) * q.field(0)).real
+
+    for delta in (base.real + 0j, 1j * base.imag):
+        eps = 1e-4
+        fd = (J(f0 + eps * delta) - J(f0 - eps * delta)) / (2 * eps)
+        ad = np.sum(np.conj(grad) * delta).real
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
 @pytest.mark.parametrize("model,scheme", [(0, 1), (1, 1), (0, 0), (1, 0)])
 def test_r_in_F_linear_closed_form(oracle_mod, model, scheme):
     """Model A/B with r placed in F (p[4] = 1, the variant of the Sec. V.A
