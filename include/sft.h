@@ -271,22 +271,32 @@ sft_status sft_dyn_result(sft_ctx* ctx, double* C_out, double* chi_out, size_t c
  * fields, not on batch contexts.  Synchronises. */
 sft_status sft_box_width(sft_ctx* ctx, int ell, double* host_out, size_t cap, size_t* written);
 
-/* Linear response by forward-mode differentiation of the step (tangent map),
- * advanced together with the primal on the same noise path:
- *   dphi <- f1 dphi + A dF + B dF(t-h),  dF = M s DFT[q'(psi) IDFT(M dphi)].
+/* Linear response by forward-mode differentiation of the step (tangent map,
+ * Sec. II schemes linearised; the response of Sec. V.A), advanced together
+ * with the primal on the same noise path:
+ *   dphi <- f1 dphi + A dF + B dF(t-h),  dF = M s DFT[q'(psi) IDFT(M dphi)],
+ * with the tangent's own history dF(t-h) under SETD2 (zero at the seed).
  * dphi0_dev: DEVICE pointer to R real-space fields (layout as set_field) that
  * seed the tangent, or NULL to continue the current tangent.  dphi_out_dev:
  * DEVICE pointer receiving the R real-space tangent fields after nsteps, or
- * NULL.  Advances the primal by nsteps.  Real fields, SETD-EM or SETD1. */
+ * NULL.  Advances the primal by nsteps.  Built for the cubic term (d = 1..3),
+ * the KPZ term (d = 1, 2) and the CGL term (d = 1, 2; rows up to 2048 points),
+ * every scheme, power-of-two lattices, truncation or no dealiasing,
+ * Fourier-space noise, 1-D lines up to 32768 points; otherwise
+ * SFT_EUNSUPPORTED before any device work. */
 sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps, void* dphi_out_dev);
 
-/* Reverse-mode differentiation: given a cotangent lambda on the real-space
- * fields after nsteps (DEVICE pointer, R fields), writes into grad_out_dev
- * (DEVICE, R fields) the gradient of sum_x lambda(x) phi_{t+n}(x) with respect
- * to phi_t(x), the real-space state at the call.  The primal is advanced by
- * nsteps; the backward sweep recomputes it from device checkpoints taken every
- * `segment` steps (sft_set_checkpoint_interval, default 100), regenerating the
- * noise from its Philox counters.  Real fields, SETD-EM or SETD1. */
+/* Reverse-mode differentiation (the transpose of the tangent above): given a
+ * cotangent lambda on the real-space fields after nsteps (DEVICE pointer, R
+ * fields), writes into grad_out_dev (DEVICE, R fields) the gradient of
+ * sum_x lambda(x) phi_{t+n}(x) (complex fields: Re sum_x conj(lambda(x))
+ * phi_{t+n}(x)) with respect to phi_t(x), the real-space state at the call.
+ * SETD2 is transposed with a history cotangent.  The primal is advanced by
+ * nsteps; the backward sweep recomputes it from device checkpoints (state and
+ * SETD2 history) taken every `segment` steps (sft_set_checkpoint_interval,
+ * default 100), regenerating the noise from its Philox counters.  Same
+ * coverage as sft_tangent_step; SFT_ENOMEM if the checkpoint buffers cannot be
+ * allocated. */
 sft_status sft_adjoint(sft_ctx* ctx, const void* cotangent_dev, int64_t nsteps, void* grad_out_dev);
 sft_status sft_set_checkpoint_interval(sft_ctx* ctx, int segment);
 

@@ -229,6 +229,19 @@ static cudaError_t launch_cols_step(const sft_ctx* ctx, const StepArgs& a) {
     return launch_second(ctx, a, MODE_STEP);
 }
 
+// Twiddle tables of a 1-D line launch: complex fields transform N-point lines (tw_a); real fields N/2-point
+// lines with the N-point table of the real-to-complex post-processing (tw_b).  False if one is missing.
+static bool set_line_twiddles(const sft_ctx* ctx, StepArgs& a) {
+    if (ctx->cplx) {
+        a.tw_a = ctx->tw.get(ctx->nx);
+        a.tw_b = nullptr;
+        return a.tw_a != nullptr;
+    }
+    a.tw_a = ctx->tw.get(ctx->nx / 2);
+    a.tw_b = ctx->tw.get(ctx->nx);
+    return a.tw_a != nullptr && a.tw_b != nullptr;
+}
+
 // ------------------------------------------------------------ transforms
 // state <- forward transform of the real-space buffer (c->real / c->cfield),
 // for R replicas starting at replica r0.
@@ -239,12 +252,7 @@ static sft_status forward_from_buffer(sft_ctx* ctx, int r0, int R, float2* dst =
     a.real_io = ctx->real + (size_t)r0 * ctx->sites;
     a.cplx_io = ctx->cfield ? ctx->cfield + (size_t)r0 * ctx->sites : nullptr;
     if (ctx->d == 1) {
-        if (ctx->cplx) {
-            a.tw_a = ctx->tw.get(ctx->nx);
-        } else {
-            a.tw_a = ctx->tw.get(ctx->nx / 2);
-            a.tw_b = ctx->tw.get(ctx->nx);
-        }
+        if (!set_line_twiddles(ctx, a)) return fail(ctx, SFT_EINVAL, "twiddle table missing");
         CK(launch_k1_line(a, MODE_FWD, ctx->nl, ctx->stream));
         ctx->launches += 1;
     } else {
@@ -270,12 +278,7 @@ static sft_status inverse_to_buffer(sft_ctx* ctx, const float2* src, int r0, int
     a.real_io = ctx->real + (size_t)r0 * ctx->sites;
     a.cplx_io = ctx->cfield ? ctx->cfield + (size_t)r0 * ctx->sites : nullptr;
     if (ctx->d == 1) {
-        if (ctx->cplx) {
-            a.tw_a = ctx->tw.get(ctx->nx);
-        } else {
-            a.tw_a = ctx->tw.get(ctx->nx / 2);
-            a.tw_b = ctx->tw.get(ctx->nx);
-        }
+        if (!set_line_twiddles(ctx, a)) return fail(ctx, SFT_EINVAL, "twiddle table missing");
         CK(launch_k1_line(a, MODE_INV, ctx->nl, ctx->stream));
         ctx->launches += 1;
     } else {
@@ -331,14 +334,16 @@ static sft_status prime(sft_ctx* ctx) {
 
 // One primal step with explicit intermediates: reads P from pin, leaves the
 // next step's P in pout (2-D); used by the adjoint's segment recompute.
-static sft_status enqueue_step_io(sft_ctx* ctx, const float2* pin, float2* pout) {
+static sft_status enqueue_step_io(sft_ctx* ctx, const float2* pin, float2* pout, const float2* pyin = nullptr,
+                                  float2* pyout = nullptr) {
     StepArgs a = base_args(ctx);
     if (ctx->d == 1) {
-        a.tw_a = ctx->tw.get(ctx->nx / 2);
-        a.tw_b = ctx->tw.get(ctx->nx);
+        if (!set_line_twiddles(ctx, a)) return fail(ctx, SFT_EINVAL, "twiddle table missing");
         CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
     } else {
         a.pin = pin;
+        a.pyin = pyin ? pyin : ctx->Py;
+        a.pyout = pyout ? pyout : ctx->Py;
         a.qout = ctx->Q;
         a.tw_a = ctx->tw.get(ctx->nx / 2);
         a.tw_b = ctx->tw.get(ctx->nx);
@@ -433,12 +438,7 @@ static sft_status enqueue_step(sft_ctx* ctx, int k) {
     StepArgs a = base_args(ctx);
     a.k_in_chunk = k;
     if (ctx->d == 1) {
-        if (ctx->cplx) {
-            a.tw_a = ctx->tw.get(ctx->nx);
-        } else {
-            a.tw_a = ctx->tw.get(ctx->nx / 2);
-            a.tw_b = ctx->tw.get(ctx->nx);
-        }
+        if (!set_line_twiddles(ctx, a)) return fail(ctx, SFT_EINVAL, "twiddle table missing");
         CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
         return SFT_OK;
     }
@@ -1718,17 +1718,18 @@ sft_status sft_observe(sft_ctx* ctx, int kind, double* host_out, size_t cap, siz
 // adjoint: whether the adjoint (not only the tangent) is asked for
 static sft_status diff_supported(sft_ctx* ctx, bool adjoint) {
     // tangent: the cubic term in 1-D, 2-D and 3-D; the KPZ term and the complex |A|^2 A term (CGL) in 1-D and
-    // 2-D (complex rows up to 2048 points); adjoint: the cubic term, and the KPZ term in 1-D
+    // 2-D (complex rows up to 2048 points); adjoint: the cubic term and the KPZ and CGL terms in 1-D and 2-D
     const bool tan_term = ctx->nl == NL_CUBIC ||
                           (ctx->d <= 2 && ctx->nl == NL_GRAD2) ||
                           (ctx->nl == NL_CGL && (ctx->d == 1 || (ctx->d == 2 && ctx->nx <= 2048)));
-    const bool adj_term = ctx->nl == NL_CUBIC || (ctx->d == 1 && ctx->nl == NL_GRAD2);
+    const bool adj_term = ctx->nl == NL_CUBIC || (ctx->d <= 2 && ctx->nl == NL_GRAD2) ||
+                          (ctx->nl == NL_CGL && (ctx->d == 1 || (ctx->d == 2 && ctx->nx <= 2048)));
     if (!(adjoint ? adj_term : tan_term) || (ctx->d == 1 && ctx->nx > 32768) || ctx->cfg.dealias == 2 ||
         !is_pow2(ctx->nx) || ctx->cfg.noise_space != 0)
         return fail(ctx, SFT_EUNSUPPORTED,
                     "the tangent is built for the cubic term (Model A/B, d = 1..3) and the KPZ and CGL terms "
-                    "(d = 1, 2; complex rows up to 2048 points); the adjoint for the cubic term and the 1-D KPZ "
-                    "term; every scheme; 1-D lines up to 32768 points, power-of-two lattices, 2/3 truncation or "
+                    "(d = 1, 2; complex rows up to 2048 points); the adjoint likewise; "
+                    "every scheme; 1-D lines up to 32768 points, power-of-two lattices, 2/3 truncation or "
                     "none, Fourier-space noise");
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     if (!ctx->dphi) {
@@ -1815,9 +1816,7 @@ sft_status sft_tangent_step(sft_ctx* ctx, const void* dphi0_dev, int64_t nsteps,
         a.dfprev = ctx->dfprev;
         if (ctx->d == 1) {
             // complex lines: one C2C length; real lines: the half length and the full length
-            a.tw_a = ctx->cplx ? ctx->tw.get(ctx->nx) : ctx->tw.get(ctx->nx / 2);
-            a.tw_b = ctx->cplx ? nullptr : ctx->tw.get(ctx->nx);
-            if (!a.tw_a || (!ctx->cplx && !a.tw_b)) return fail(ctx, SFT_EINVAL, "twiddle table missing");
+            if (!set_line_twiddles(ctx, a)) return fail(ctx, SFT_EINVAL, "twiddle table missing");
             CK(launch_k1_line(a, MODE_TAN, ctx->nl, ctx->stream));
             ctx->launches += 1;
         } else {
@@ -1867,10 +1866,11 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
     const int64_t K = ctx->ckpt_segment;
     const int64_t nseg = (nsteps + K - 1) / K;
     const long long step0 = ctx->step;
-    float2 *ckpt = nullptr, *traj = nullptr, *phiN = nullptr;
+    float2 *ckpt = nullptr, *traj = nullptr, *trajy = nullptr, *phiN = nullptr;
     auto release = [&]() {
         if (ckpt) cudaFree(ckpt);
         if (traj) cudaFree(traj);
+        if (trajy) cudaFree(trajy);
         if (phiN) cudaFree(phiN);
     };
 #define CKA(call)                                                                                     \
@@ -1895,6 +1895,12 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
     const size_t cm = hist ? 2 * (size_t)ctx->R * ctx->nmodes : (size_t)ctx->R * ctx->nmodes;  // in float2
     if (cudaMalloc(&ckpt, cs * (size_t)nseg) != cudaSuccess || cudaMalloc(&traj, ms * (size_t)(K + 1)) != cudaSuccess ||
         cudaMalloc(&phiN, cs) != cudaSuccess) {
+        release();
+        return fail(ctx, SFT_ENOMEM, "adjoint checkpoint buffers");
+    }
+    // the KPZ term in 2-D also keeps each step's second intermediate P_y = IDFT_y(i k_y M phi)
+    const bool grad2d = ctx->d >= 2 && ctx->nl == NL_GRAD2;
+    if (grad2d && cudaMalloc(&trajy, ms * (size_t)(K + 1)) != cudaSuccess) {
         release();
         return fail(ctx, SFT_ENOMEM, "adjoint checkpoint buffers");
     }
@@ -1924,19 +1930,24 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
             CKA(cudaMemcpyAsync(ctx->fprev, ckpt + (size_t)sg * cm + cm / 2, ms, cudaMemcpyDeviceToDevice,
                                 ctx->stream));
         SKA(set_step_counter(ctx, step0 + n0));
+        const size_t sl = (size_t)ctx->R * ctx->nmodes;  // one trajectory slot, in float2
         if (ctx->d >= 2) {
             StepArgs a = base_args(ctx);
             a.pout = traj;
+            a.pyout = grad2d ? trajy : ctx->Py;
             a.tw_a = ctx->tw.get(ctx->ny);
             CKA(launch_second(ctx, a, MODE_PRIME));
         }
         for (int64_t i = 0; i < len; ++i) {
-            float2* slot = traj + (size_t)i * ctx->R * ctx->nmodes;
+            float2* slot = traj + (size_t)i * sl;
             if (ctx->d == 1) {
                 CKA(cudaMemcpyAsync(slot, ctx->phi, ms, cudaMemcpyDeviceToDevice, ctx->stream));
                 SKA(enqueue_step_io(ctx, nullptr, nullptr));
+            } else if (grad2d) {
+                float2* sloty = trajy + (size_t)i * sl;
+                SKA(enqueue_step_io(ctx, slot, slot + sl, sloty, sloty + sl));
             } else {
-                SKA(enqueue_step_io(ctx, slot, slot + (size_t)ctx->R * ctx->nmodes));
+                SKA(enqueue_step_io(ctx, slot, slot + sl));
             }
         }
         // reverse sweep over the segment
@@ -1949,8 +1960,10 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
             a.adj_first_prev = starts_setd2(n0 + i - 1);
             if (ctx->d == 1) {
                 a.phi = slot;
-                a.tw_a = ctx->tw.get(ctx->nx / 2);
-                a.tw_b = ctx->tw.get(ctx->nx);
+                if (!set_line_twiddles(ctx, a)) {
+                    release();
+                    return fail(ctx, SFT_EINVAL, "twiddle table missing");
+                }
                 CKA(launch_k1_line(a, MODE_ADJ, ctx->nl, ctx->stream));
                 ctx->launches += 1;
             } else {
@@ -1966,10 +1979,16 @@ sft_status sft_adjoint(sft_ctx* ctx, const void* cot_dev, int64_t nsteps, void* 
                 a.pin = slot;
                 a.dpin = ctx->dP;
                 a.dqout = ctx->dQ;
+                if (grad2d) {
+                    // KPZ: P_y of the step in, DFT_x(v_y) out through Q (free during the backward sweep)
+                    a.pyin = trajy + (size_t)i * ctx->R * ctx->nmodes;
+                    a.qout = ctx->Q;
+                }
                 a.tw_a = ctx->tw.get(ctx->nx / 2);
                 a.tw_b = ctx->tw.get(ctx->nx);
                 CKA(launch_rows(ctx, a, MODE_ADJ));
                 a.dqin = ctx->dQ;
+                a.qin = ctx->Q;
                 a.dpout = ctx->dP;
                 a.tw_a = ctx->tw.get(ctx->ny);
                 CKA(launch_second(ctx, a, MODE_ADJ));
@@ -2147,12 +2166,7 @@ sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, in
         StepArgs a = base_args(ctx);
         CK(cudaEventRecord(e[0], ctx->stream));
         if (ctx->d == 1) {
-            if (ctx->cplx) {
-                a.tw_a = ctx->tw.get(ctx->nx);
-            } else {
-                a.tw_a = ctx->tw.get(ctx->nx / 2);
-                a.tw_b = ctx->tw.get(ctx->nx);
-            }
+            if (!set_line_twiddles(ctx, a)) return fail(ctx, SFT_EINVAL, "twiddle table missing");
             CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
             CK(cudaEventRecord(e[1], ctx->stream));
         } else if (ctx->cfg.precision == 1) {

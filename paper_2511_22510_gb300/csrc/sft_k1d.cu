@@ -11,6 +11,8 @@ bool k1_supported(int nx, int complex_field) {
 }
 
 cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s) {
+    // complex lines read the N-point table tw_a; real lines the N/2-point table tw_a and the N-point table tw_b
+    if (!a.tw_a || (nl != NL_CGL && !a.tw_b)) return cudaErrorInvalidValue;
     if (nl != NL_CGL && k1_use_cluster(a.nx, a.R, mode)) return launch_k1_cluster(a, mode, nl, s);
     if (nl == NL_CGL) {
         switch (a.nx) {

@@ -411,6 +411,47 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k1_cplx(const StepArgs a)
             for (int e = 0; e < E; ++e) dst[t + T * e] = z[e];
         }
         return;
+    } else if constexpr (MODE == MODE_ADJ) {
+        // adjoint for the real inner product Re sum conj(u) v: every Fourier multiplier transposes to its
+        // conjugate and the pointwise 2 |A|^2 dA + A^2 conj(dA) is its own transpose (Sec. V.C linearised):
+        //   nu = conj(a_n) lam + mu,  w = IDFT(M conj(s) nu),  lam <- conj(f1) lam + M DFT[2 |A|^2 w + A^2 conj(w)],
+        //   mu <- conj(b_n) lam (SETD2 history cotangent; zero at the step that starts SETD2)
+        float2* dp = a.dphi + (size_t)rr * N;
+        float2* mu = a.scheme == 2 ? a.dmu + (size_t)rr * N : nullptr;
+        const bool fa = a.adj_first_n != 0;
+        const float2 sw = make_float2(a.s0 * a.scale, -a.s0i * a.scale);  // conj(s) / N
+        float2 lam[E], zw[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            const int ks = signed_idx(k, N);
+            const bool inm = !a.dealias || 3 * abs(ks) < N;
+            lam[e] = dp[k];
+            const Coefs co = load_coefs<true>(a.tab, abs(ks), fa);
+            float2 nu = cmul(cconj(co.A), lam[e]);
+            if (mu) nu = cadd(nu, mu[k]);
+            zw[e] = inm ? cmul(sw, nu) : czero();
+        }
+        fft_line<N, true>(zw, xb, t, tw);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float2 A = z[e], w = zw[e];
+            zw[e] = cadd(cscale(w, 2.f * (A.x * A.x + A.y * A.y)), cmul(cmul(A, A), cconj(w)));
+        }
+        fft_line<N, false>(zw, xb, t, tw);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            const int ks = signed_idx(k, N);
+            const bool inm = !a.dealias || 3 * abs(ks) < N;
+            const Coefs co = load_coefs<true>(a.tab, abs(ks), fa);
+            const float2 o = cadd(cmul(cconj(co.f1), lam[e]), inm ? zw[e] : czero());
+            if (valid) {
+                dp[k] = o;
+                if (mu) mu[k] = fa ? czero() : cmul(cconj(co.B), lam[e]);
+            }
+        }
+        return;
     } else {
         // tangent (MODE_TAN): dq = 2 |A|^2 dA + A^2 conj(dA), the linearisation of |A|^2 A, with
         // dA = IDFT(M dphi); the tangent update has no noise and its own SETD2 history
@@ -518,6 +559,7 @@ static cudaError_t k1c_for(const StepArgs& a, int mode, cudaStream_t s) {
     if (mode == MODE_INV) return run_k1_cplx<N, MODE_INV>(a, s);
     if (mode == MODE_STEP) return run_k1_cplx<N, MODE_STEP>(a, s);
     if (mode == MODE_TAN) return run_k1_cplx<N, MODE_TAN>(a, s);
+    if (mode == MODE_ADJ) return run_k1_cplx<N, MODE_ADJ>(a, s);
     return cudaErrorInvalidValue;
 }
 

@@ -48,10 +48,12 @@ __global__ void __launch_bounds__(CRowCfg<N>::THREADS) k2_rows_cplx(const StepAr
     float2* trow = sm + team * TS;
     const float2* __restrict__ tw = a.tw_a;
     float2 z[E];
-    if constexpr (MODE == MODE_TAN) {
+    if constexpr (MODE == MODE_TAN || MODE == MODE_ADJ) {
         // tangent: A = IDFT_x(P), dA = IDFT_x(dP); Q = DFT_x(|A|^2 A) and dQ = DFT_x(2 |A|^2 dA + A^2 conj(dA)),
         // the linearisation of |A|^2 A.  Tile 0: P (then Q), tile 1: dP (then dQ); each team row is also its
-        // transform's exchange buffer.
+        // transform's exchange buffer.  Adjoint: the same map applied to W = IDFT(M conj(s) nu) (dP) is its own
+        // transpose for the real inner product Re sum conj(u) v, and Q is not needed.
+        constexpr bool TAN = MODE == MODE_TAN;
         float2* drow = sm + (ROWS + team) * TS;
         auto load = [&](const float2* src, float2* dst) {
             block_copy<C::THREADS, ROWS * N>(
@@ -82,14 +84,14 @@ __global__ void __launch_bounds__(CRowCfg<N>::THREADS) k2_rows_cplx(const StepAr
             zd[e] = cadd(cscale(dA, 2.f * a2), cmul(cmul(A, A), cconj(dA)));
             z[e] = cscale(A, a2);
         }
-        fft_line<N, false>(z, trow, t, tw);
+        if constexpr (TAN) fft_line<N, false>(z, trow, t, tw);
         fft_line<N, false>(zd, drow, t, tw);
         team_sync<T>();
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int ax = t + T * e;
             if (cmask_x(ax, nx, ncols)) {
-                trow[ccomp_x(ax, nx, ncols)] = z[e];
+                if constexpr (TAN) trow[ccomp_x(ax, nx, ncols)] = z[e];
                 drow[ccomp_x(ax, nx, ncols)] = zd[e];
             }
         }
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(CRowCfg<N>::THREADS) k2_rows_cplx(const StepAr
                     if (y0 + yy < ny) dst[((size_t)rep * hx + c) * ny + y0 + yy] = v;
                 });
         };
-        store(sm, a.qout);
+        if constexpr (TAN) store(sm, a.qout);
         store(sm + ROWS * TS, a.dqout);
         return;
     }
@@ -325,6 +327,57 @@ __global__ void __launch_bounds__(CColCfg<NY>::THREADS, 512 / CColCfg<NY>::THREA
                         for (int e = 0; e < E; ++e) a.dpout[cbase + t + T * e] = dv[e];
                     }
                 }
+            } else if constexpr (MODE == MODE_ADJ || MODE == MODE_ADJ_PRIME) {
+                // adjoint of step n for the real inner product Re sum conj(u) v (multipliers conjugated):
+                // lam_n = conj(f1) lam_{n+1} + M DFT_y[dQ] (dQ from the row pass), mu_{n-1} = conj(B_n) lam_{n+1}
+                // (SETD2), then W = IDFT_y(M conj(s) (conj(A_{n-1}) lam_n + mu_{n-1}) / N^2) for step n - 1.
+                // ADJ_PRIME: W from lam_N alone (mu = 0).
+                const bool has_f = valid && inx;
+                float2 lam[E], mu[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    lam[e] = a.dphi[colbase + t + T * e];
+                    mu[e] = czero();
+                }
+                if constexpr (MODE == MODE_ADJ) {
+                    if (has_f || T < 32) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) v[e] = has_f ? a.dqin[cbase + t + T * e] : czero();
+                        fft_line<NY, false>(v, xb, t, tw);
+                    }
+                    const bool fa = a.adj_first_n != 0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int ays = signed_idx(t + T * e, NY);
+                        const bool inm = has_f && (!a.dealias || 3 * abs(ays) < NY);
+                        const Coefs co = load_coefs<true>(a.tab, abs(axs) * (NY / 2 + 1) + abs(ays), fa);
+                        if (a.scheme == 2 && !fa) mu[e] = cmul(cconj(co.B), lam[e]);
+                        lam[e] = cadd(cmul(cconj(co.f1), lam[e]), inm ? v[e] : czero());
+                    }
+                    if (valid) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) a.dphi[colbase + t + T * e] = lam[e];
+                    }
+                }
+                const bool has_p = valid && inx;
+                if (has_p || T < 32) {
+                    const float2 sw = make_float2(a.s0 * a.scale, -a.s0i * a.scale);  // conj(s) / N^2
+                    const bool fp = a.adj_first_prev != 0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int ays = signed_idx(t + T * e, NY);
+                        const bool inm = has_p && (!a.dealias || 3 * abs(ays) < NY);
+                        const Coefs co = load_coefs<true>(a.tab, abs(axs) * (NY / 2 + 1) + abs(ays), fp);
+                        const float2 nu = cadd(cmul(cconj(co.A), lam[e]), mu[e]);
+                        v[e] = inm ? cmul(sw, nu) : czero();
+                    }
+                    fft_line<NY, true>(v, xb, t, tw);
+                    if (has_p) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) a.dpout[cbase + t + T * e] = v[e];
+                    }
+                }
+                continue;
             } else {  // MODE_PRIME
 #pragma unroll
                 for (int e = 0; e < E; ++e) out[e] = a.phi[colbase + t + T * e];
@@ -350,7 +403,7 @@ __global__ void __launch_bounds__(CColCfg<NY>::THREADS, 512 / CColCfg<NY>::THREA
 template <int N, int MODE>
 static cudaError_t run_crows(const StepArgs& a, cudaStream_t s) {
     using C = CRowCfg<N>;
-    const size_t sm = (MODE == MODE_TAN ? 2 : 1) * C::smem();
+    const size_t sm = (MODE == MODE_TAN || MODE == MODE_ADJ ? 2 : 1) * C::smem();
     static bool attr = false;
     if (!attr) {
         cudaError_t e =
@@ -383,6 +436,7 @@ static cudaError_t crows_for(const StepArgs& a, int mode, cudaStream_t s) {
         case MODE_FWD: return run_crows<N, MODE_FWD>(a, s);
         case MODE_INV: return run_crows<N, MODE_INV>(a, s);
         case MODE_TAN: return run_crows<N, MODE_TAN>(a, s);
+        case MODE_ADJ: return run_crows<N, MODE_ADJ>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -395,6 +449,8 @@ static cudaError_t ccols_for(const StepArgs& a, int mode, cudaStream_t s) {
         case MODE_INV: return run_ccols<NY, MODE_INV>(a, s);
         case MODE_PRIME: return run_ccols<NY, MODE_PRIME>(a, s);
         case MODE_TAN: return run_ccols<NY, MODE_TAN>(a, s);
+        case MODE_ADJ: return run_ccols<NY, MODE_ADJ>(a, s);
+        case MODE_ADJ_PRIME: return run_ccols<NY, MODE_ADJ_PRIME>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(RowCfg<M, SH>::THREADS, RowCfg<M, SH>::MINB) k
     using PL = FftPlan<M>;
     constexpr int T = PL::T, E = PL::E, ROWS = C::ROWS, TS = C::TS;
     constexpr bool GRAD = (NL == NL_GRAD2) && (MODE == MODE_STEP);
-    static_assert(!(MODE == MODE_ADJ && NL != NL_CUBIC), "adjoint: cubic term");
+    static_assert(!(MODE == MODE_ADJ && NL != NL_CUBIC && NL != NL_GRAD2), "adjoint: cubic or KPZ term");
     extern __shared__ float2 sm[];
     float2* tile = sm;
     const int team = threadIdx.x / T, t = threadIdx.x % T;
@@ -200,6 +200,46 @@ __global__ void __launch_bounds__(RowCfg<M, SH>::THREADS, RowCfg<M, SH>::MINB) k
         __syncthreads();
         store_tile<C>(tile, a.qout, rowbase, ncols, ny, y0);
         store_tile<C>(tile + 2 * ROWS * TS, a.dqout, rowbase, ncols, ny, y0);
+        return;
+    }
+    if constexpr (MODE == MODE_ADJ && NL == NL_GRAD2) {
+        // KPZ adjoint (the transpose of q' = 2 (g_x dg_x + g_y dg_y), Sec. V.B linearised): with w the row of
+        // W = IDFT(M s nu), v_x = 2 g_x w and v_y = 2 g_y w; the row pass returns DFT_x(v_x) and DFT_x(v_y),
+        // and the column pass applies the transposed gradient multipliers -i k_x, -i k_y.  Tiles: 0 P (then
+        // DFT_x(v_x)), 1 P_y (then DFT_x(v_y)), 2 W; tile rows 0 and 1 serve as the team's exchange buffers.
+        load_tile<C>(tile, a.pin, rowbase, ncols, ny, y0);
+        load_tile<C>(tile + ROWS * TS, a.pyin, rowbase, ncols, ny, y0);
+        load_tile<C>(tile + 2 * ROWS * TS, a.dpin, rowbase, ncols, ny, y0);
+        __syncthreads();
+        float2* r0 = tile + team * TS;
+        float2* r1 = tile + ROWS * TS + team * TS;
+        const float2* r2 = tile + 2 * ROWS * TS + team * TS;
+        float2 zw[E], zy[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            const float2 tw = __ldg(&twN[k]);
+            const float kx = a.dk * (float)k, kxm = (k == 0) ? 0.f : a.dk * (float)(M - k);
+            z[e] = c2r_pre(cscale(cmuli(r0[k]), kx), cscale(cmuli(r0[M - k]), kxm), tw);
+            zy[e] = c2r_pre(r1[k], r1[M - k], tw);
+            zw[e] = c2r_pre(r2[k], r2[M - k], tw);
+        }
+        fft_line<M, true>(z, r0, t, twM);
+        fft_line<M, true>(zy, r0, t, twM);
+        fft_line<M, true>(zw, r0, t, twM);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            z[e] = make_float2(2.f * z[e].x * zw[e].x, 2.f * z[e].y * zw[e].y);
+            zy[e] = make_float2(2.f * zy[e].x * zw[e].x, 2.f * zy[e].y * zw[e].y);
+        }
+        fft_line<M, false>(z, r0, t, twM);
+        row_post<M>(z, r0, r0, ncols, t, twN);
+        team_sync<T>();
+        fft_line<M, false>(zy, r1, t, twM);
+        row_post<M>(zy, r1, r1, ncols, t, twN);
+        __syncthreads();
+        store_tile<C>(tile, a.dqout, rowbase, ncols, ny, y0);
+        store_tile<C>(tile + ROWS * TS, a.qout, rowbase, ncols, ny, y0);
         return;
     }
     if constexpr (MODE == MODE_TAN || MODE == MODE_ADJ) {
@@ -392,8 +432,12 @@ static cudaError_t run_rows(const StepArgs& a, cudaStream_t s) {
     constexpr int NTILE =
         (NL == NL_GRAD2 && (MODE == MODE_STEP_PS || MODE == MODE_TAN))
             ? 4
-            : (((NL == NL_GRAD2 && MODE == MODE_STEP) || MODE == MODE_TAN || MODE == MODE_ADJ || MODE == MODE_STEP_PS) ? 2
-                                                                                                                : 1);
+            : ((NL == NL_GRAD2 && MODE == MODE_ADJ)
+                   ? 3
+                   : (((NL == NL_GRAD2 && MODE == MODE_STEP) || MODE == MODE_TAN || MODE == MODE_ADJ ||
+                       MODE == MODE_STEP_PS)
+                          ? 2
+                          : 1));
     const size_t sm = C::smem(NTILE);
     static bool attr = false;
     if (!attr) {
@@ -426,6 +470,7 @@ static cudaError_t rows_for(const StepArgs& a, int mode, int nl, cudaStream_t s,
     if (mode == MODE_TAN && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_TAN>(a, s);
     if (mode == MODE_TAN && nl == NL_GRAD2) return run_rows<M, NL_GRAD2, MODE_TAN>(a, s);
     if (mode == MODE_ADJ && nl == NL_CUBIC) return run_rows<M, NL_CUBIC, MODE_ADJ>(a, s);
+    if (mode == MODE_ADJ && nl == NL_GRAD2) return run_rows<M, NL_GRAD2, MODE_ADJ>(a, s);
     return cudaErrorInvalidValue;
 }
 

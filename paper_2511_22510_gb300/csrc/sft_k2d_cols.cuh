@@ -412,6 +412,21 @@ __global__ void __launch_bounds__(ColCfg<NY, SH>::THREADS, ColCfg<NY, SH>::MINB)
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[e] = has_f ? a.dqin[colbase + t + T * e] : czero();
                 fft_line<NY, false, EM>(v, xb, t, tw);
+                if constexpr (NL == NL_GRAD2) {
+                    // KPZ: dqin = DFT_x(v_x), qin = DFT_x(v_y); the transposed gradients give
+                    // -i (k_x DFT[v_x] + k_y DFT[v_y]) (odd multipliers: zero at the Nyquist indices)
+                    float2 vy[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) vy[e] = has_f ? a.qin[colbase + t + T * e] : czero();
+                    fft_line<NY, false, EM>(vy, xb, t, tw);
+                    const float kx = a.dk * (float)odd_idx(cc, a.nx);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const float ky = a.dk * (float)odd_idx(t + T * e, NY);
+                        const float2 w = make_float2(kx * v[e].x + ky * vy[e].x, kx * v[e].y + ky * vy[e].y);
+                        v[e] = make_float2(w.y, -w.x);
+                    }
+                }
             }
 #pragma unroll
             for (int e = 0; e < E; ++e) {
@@ -509,6 +524,8 @@ static cudaError_t cols_for(const StepArgs& a, int mode, int nl, cudaStream_t s,
     if (mode == MODE_TAN && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_TAN>(a, s);
     if (mode == MODE_ADJ && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_ADJ>(a, s);
     if (mode == MODE_ADJ_PRIME && nl == NL_CUBIC) return run_cols<NY, NL_CUBIC, MODE_ADJ_PRIME>(a, s);
+    if (mode == MODE_ADJ && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_ADJ>(a, s);
+    if (mode == MODE_ADJ_PRIME && nl == NL_GRAD2) return run_cols<NY, NL_GRAD2, MODE_ADJ_PRIME>(a, s);
     return cudaErrorInvalidValue;
 }
 

@@ -24,8 +24,10 @@ namespace {
 constexpr int kCwNY = 1024;
 constexpr int kCwWarps = 4;  // columns per block
 
+// 5 blocks (20 warps) per SM caps the kernel at 96 registers (no spill with 2/3 truncation, 8 bytes without);
+// the latency-bound update loop gains more from the extra warps than the transforms lose to the tighter budget
 template <bool DEAL>
-__global__ void __launch_bounds__(kCwWarps * 32, 4) k2_cols_warp(const StepArgs a) {
+__global__ void __launch_bounds__(kCwWarps * 32, 5) k2_cols_warp(const StepArgs a) {
     constexpr int NY = kCwNY;
     // slots e (index lane + 32 e) outside the 2/3 band |a_y| < 342 in every lane: e = 11 .. 20
     constexpr uint32_t ZMASK = DEAL ? 0x001FF800u : 0u;

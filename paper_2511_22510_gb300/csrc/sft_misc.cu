@@ -250,8 +250,7 @@ __global__ void k_obs_chunks(const ObsArgs o) {
     const float2* phi = o.phi ? o.phi + (size_t)r * nm : nullptr;
     const float2* ref = o.ref ? o.ref + (size_t)r * nm : nullptr;
     const int plane = o.nz * o.ny;
-    double s = 0.0, c = 0.0;
-    for (int i = lane; i < ch.z; i += 32) {
+    auto term = [&](int i) -> double {
         const int m = o.order[ch.y + i];
         const int ax = m / plane;
         const double w = (!o.complex_field && ax != 0 && 2 * ax != o.nx) ? 2.0 : 1.0;
@@ -266,7 +265,27 @@ __global__ void k_obs_chunks(const ObsArgs o) {
             const float2 u = ref[m];
             val = (double)u.x * u.x + (double)u.y * u.y;
         }
-        neumaier_add(s, c, w * val);
+        return w * val;
+    };
+    // four independent compensated sums per lane (entries lane + 32 (4 u + k) go to sum k), so four gathers
+    // are in flight; they are combined in the order k = 0..3
+    double s4[4] = {0.0, 0.0, 0.0, 0.0}, c4[4] = {0.0, 0.0, 0.0, 0.0};
+    int i = lane;
+    for (; i + 96 < ch.z; i += 128) {
+        const double t0 = term(i), t1 = term(i + 32), t2 = term(i + 64), t3 = term(i + 96);
+        neumaier_add(s4[0], c4[0], t0);
+        neumaier_add(s4[1], c4[1], t1);
+        neumaier_add(s4[2], c4[2], t2);
+        neumaier_add(s4[3], c4[3], t3);
+    }
+    if (i < ch.z) neumaier_add(s4[0], c4[0], term(i));
+    if (i + 32 < ch.z) neumaier_add(s4[1], c4[1], term(i + 32));
+    if (i + 64 < ch.z) neumaier_add(s4[2], c4[2], term(i + 64));
+    double s = s4[0], c = c4[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+        neumaier_add(s, c, s4[k]);
+        c += c4[k];
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

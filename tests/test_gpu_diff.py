@@ -120,6 +120,15 @@ ADJ_CASES = CASES + [
     ("model_b_1d_128_setd2", W.model_b_1024(d=1, n=[128], dx=[1.0], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
     ("model_a_3d_16_setd2", W.model_a_128_3d(n=[16, 16, 16], replicas=2, sigma0=0.3, h=0.02, scheme=2)),
     ("kpz_1d_512_setd2", W.kpz_1d(512, replicas=2, sigma0=0.5, scheme=2)),
+    ("kpz_2d_32_setd1", W.kpz_2d(n=[32, 32], replicas=2, sigma0=0.5)),
+    ("kpz_2d_64_setd2", W.kpz_2d(n=[64, 64], replicas=2, sigma0=0.5, scheme=2)),
+    ("kpz_2d_128_em_nodeal", W.kpz_2d(n=[128, 128], replicas=2, sigma0=0.5, scheme=0, dealias=0)),
+    # CGL (Sec. V.C): the transpose for the real inner product Re sum conj(u) v, complex cotangents
+    ("cgl_1d_128_setd2", W.cgl_2048(d=1, n=[128], dx=[0.5], replicas=2, p=[2.0, -0.5, 1e-3])),
+    ("cgl_1d_256_setd1", W.cgl_2048(d=1, n=[256], dx=[0.5], replicas=2, scheme=1, p=[0.5, 0.3, 1e-2])),
+    ("cgl_2d_32_setd2", W.cgl_2048(n=[32, 32], replicas=2, p=[2.0, -0.5, 1e-3])),
+    ("cgl_2d_64_setd1", W.cgl_2048(n=[64, 64], replicas=2, scheme=1, p=[0.5, 0.3, 1e-2])),
+    ("cgl_2d_64_em_nodeal", W.cgl_2048(n=[64, 64], replicas=2, scheme=0, dealias=0, p=[0.5, 0.3, 1e-2])),
 ]
 
 
@@ -129,9 +138,10 @@ def test_adjoint_dot_product_and_parity(env, oracle_mod, name, w):
     against the oracle's; checkpoint segments of 7 steps over a 20-step horizon
     force the recompute of the primal from checkpoints."""
     m, torch = env
+    dt = np.complex64 if w.complex_field else np.float32
     f0 = W.initial_fields(w)
-    d0 = W.initial_fields(w.with_(sigma0=1.0), seed_offset=3).astype(np.float32)
-    lam = W.initial_fields(w.with_(sigma0=1.0), seed_offset=4).astype(np.float32)
+    d0 = W.initial_fields(w.with_(sigma0=1.0), seed_offset=3).astype(dt)
+    lam = W.initial_fields(w.with_(sigma0=1.0), seed_offset=4).astype(dt)
     nst = 20
     g1, o = make_pair(m, oracle_mod, w, f0)
     din = torch.from_numpy(d0).cuda()
@@ -145,13 +155,15 @@ def test_adjoint_dot_product_and_parity(env, oracle_mod, name, w):
     torch.cuda.synchronize()
     m.sft_adjoint(g2.ctx, lin.data_ptr(), nst, grad.data_ptr())
     torch.cuda.synchronize()
-    tan = dout.cpu().numpy().astype(np.float64)
-    gr = grad.cpu().numpy().astype(np.float64)
+    dt64 = np.complex128 if w.complex_field else np.float64
+    tan = dout.cpu().numpy().astype(dt64)
+    gr = grad.cpu().numpy().astype(dt64)
     for r in range(w.replicas):
-        lhs = float(np.sum(lam[r].astype(np.float64) * tan[r]))
-        rhs = float(np.sum(gr[r] * d0[r].astype(np.float64)))
+        # the real inner product (complex fields: Re sum conj(u) v)
+        lhs = float(np.vdot(lam[r].astype(dt64), tan[r]).real)
+        rhs = float(np.vdot(gr[r], d0[r].astype(dt64)).real)
         assert abs(lhs - rhs) <= 2e-5 * (abs(lhs) + abs(rhs)), (name, lhs, rhs)
-    go = o.adjoint(lam.astype(np.float64), nst)
+    go = o.adjoint(lam.astype(dt64), nst)
     for r in range(w.replicas):
         assert rel(gr[r], go[r]) <= 1e-5, (name, r, rel(gr[r], go[r]))
     # the primal ends where nsteps of plain stepping end
