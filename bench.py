@@ -117,6 +117,9 @@ KERNEL_SOURCES = {
                      "sft_internal.h"],
     "k2_rows_pair": ["sft_k2d_pair.cu", "sft_warpfft.cuh", "sft_step_common.cuh", "sft_device.cuh", "sft_async.cuh",
                      "sft_internal.h"],
+    "k2_cols_warp": ["sft_k2d_colwarp.cu", "sft_warpfft.cuh", "sft_step_common.cuh", "sft_device.cuh",
+                     "sft_async.cuh", "sft_internal.h"],
+    "k2_cols_pipe": ["sft_k2d_pipe.cu", "sft_step_common.cuh", "sft_device.cuh", "sft_async.cuh", "sft_internal.h"],
 }
 
 
@@ -459,7 +462,8 @@ def run_gpu(args):
     prof = sft.sft_profile(g.ctx, 50)
     plan = sft.sft_get_plan(g.ctx)
     row_kernel = "k2_rows_pair" if plan[0] == 3 else "k2_rows_real"
-    kern = [(row_kernel, prof[0], rows_b * R), ("k2_cols_real", prof[1], cols_b * R)]
+    col_kernel = "k2_cols_pipe" if plan[3] else ("k2_cols_warp" if plan[1] == 3 else "k2_cols_real")
+    kern = [(row_kernel, prof[0], rows_b * R), (col_kernel, prof[1], cols_b * R)]
     dom = max(kern, key=lambda k: k[1])
     peak, peak_kind = measured_peak()
     achieved = dom[2] / (dom[1] * 1e-3) / 1e9

@@ -157,9 +157,11 @@ typedef enum {
                                 observations, then their count; synchronises */
     SFT_OBS_SK_RESET = 9     /* clears the time accumulator; writes nothing */
 } sft_observable;
-/* Every shell sum is taken in a fixed order with compensated FP64 summation
- * (the modes enumerated shell by shell), so repeated evaluations of the same
- * state give the same bits. */
+/* Every shell sum is taken in a fixed order (the modes enumerated shell by
+ * shell), so repeated evaluations of the same state give the same bits: runs
+ * of at most 32 modes in single-precision pairs built from error-free
+ * transformations (exact products by fused multiply-add, two-sum), the runs
+ * combined with compensated FP64 summation. */
 
 /* Create a context (allocates all device memory, builds the FP64 coefficient
  * tables of Sec. II on the device, zero state).  *out receives the context or

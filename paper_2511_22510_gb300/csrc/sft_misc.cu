@@ -226,18 +226,38 @@ cudaError_t launch_advance(long long* step_base, int by, cudaStream_t s) {
 // give the same bits and long sums keep FP64 accuracy (App. C estimators):
 // the stored modes are enumerated shell by shell (ObsArgs::order, built once
 // per lattice on the host) and cut into chunks of at most kObsChunkLen modes
-// inside one shell.  One warp per chunk and replica sums its modes with
-// Neumaier's compensated summation (each lane a fixed stride of the chunk,
-// then a fixed shuffle tree combining (sum, correction) pairs by Knuth's
-// two-sum); a second pass combines the chunks of every shell in order.  For
-// real fields the stored half carries weight 2 off the planes a_x in {0, nx/2}
-// and 1 on them.
+// inside one shell.  One warp per chunk and replica: each lane sums a fixed
+// stride of the chunk (at most 32 modes) in single-precision pairs made of
+// error-free transformations -- products split exactly by a fused
+// multiply-add (x x = p + e, Dekker), sums by Knuth's two-sum -- so that no
+// bit of a term is lost, then converts its pair to FP64; lanes are combined by
+// a fixed shuffle tree and chunks in order, both with Neumaier's compensated
+// FP64 summation.  (This GPU's FP64 rate is a small fraction of its FP32 rate:
+// two FP64 operations per mode would cost more than the gather.)  For real
+// fields the stored half carries weight 2 off the planes a_x in {0, nx/2} and
+// 1 on them (exact in FP32).
 
 // s + x with its rounding error carried in c (Neumaier)
 __device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
     const double t = s + x;
     c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
     s = t;
+}
+
+// (hi, lo) += x exactly up to the rounding of lo: Knuth's two-sum of hi and x, the error into lo
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+    const float s = hi + x, bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+}
+
+// (hi, lo) += w (a b + c d), each product split exactly (a b = p + fma(a, b, -p)); w in {1, 2}
+__device__ __forceinline__ void ff_add_dot2(float& hi, float& lo, float w, float a, float b, float c, float d) {
+    const float p1 = a * b, p2 = c * d;
+    const float e1 = fmaf(a, b, -p1), e2 = fmaf(c, d, -p2);
+    ff_add(hi, lo, w * p1);
+    ff_add(hi, lo, w * p2);
+    lo += w * (e1 + e2);
 }
 
 template <int KIND>
@@ -250,43 +270,32 @@ __global__ void k_obs_chunks(const ObsArgs o) {
     const float2* phi = o.phi ? o.phi + (size_t)r * nm : nullptr;
     const float2* ref = o.ref ? o.ref + (size_t)r * nm : nullptr;
     const int plane = o.nz * o.ny;
-    auto term = [&](int i) -> double {
+    // two independent pairs per lane (entries lane + 64 u and lane + 64 u + 32), so two gathers are in flight
+    float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
+    auto term = [&](int i, int k) {
         const int m = o.order[ch.y + i];
         const int ax = m / plane;
-        const double w = (!o.complex_field && ax != 0 && 2 * ax != o.nx) ? 2.0 : 1.0;
-        double val;
+        const float w = (!o.complex_field && ax != 0 && 2 * ax != o.nx) ? 2.f : 1.f;
         if constexpr (KIND == 0) {
             const float2 v = phi[m];
-            val = (double)v.x * v.x + (double)v.y * v.y;
+            ff_add_dot2(hi[k], lo[k], w, v.x, v.x, v.y, v.y);
         } else if constexpr (KIND == 1) {
             const float2 v = phi[m], u = ref[m];
-            val = (double)v.x * u.x + (double)v.y * u.y;
+            ff_add_dot2(hi[k], lo[k], w, v.x, u.x, v.y, u.y);
         } else {
             const float2 u = ref[m];
-            val = (double)u.x * u.x + (double)u.y * u.y;
+            ff_add_dot2(hi[k], lo[k], w, u.x, u.x, u.y, u.y);
         }
-        return w * val;
     };
-    // four independent compensated sums per lane (entries lane + 32 (4 u + k) go to sum k), so four gathers
-    // are in flight; they are combined in the order k = 0..3
-    double s4[4] = {0.0, 0.0, 0.0, 0.0}, c4[4] = {0.0, 0.0, 0.0, 0.0};
     int i = lane;
-    for (; i + 96 < ch.z; i += 128) {
-        const double t0 = term(i), t1 = term(i + 32), t2 = term(i + 64), t3 = term(i + 96);
-        neumaier_add(s4[0], c4[0], t0);
-        neumaier_add(s4[1], c4[1], t1);
-        neumaier_add(s4[2], c4[2], t2);
-        neumaier_add(s4[3], c4[3], t3);
+    for (; i + 32 < ch.z; i += 64) {
+        term(i, 0);
+        term(i + 32, 1);
     }
-    if (i < ch.z) neumaier_add(s4[0], c4[0], term(i));
-    if (i + 32 < ch.z) neumaier_add(s4[1], c4[1], term(i + 32));
-    if (i + 64 < ch.z) neumaier_add(s4[2], c4[2], term(i + 64));
-    double s = s4[0], c = c4[0];
-#pragma unroll
-    for (int k = 1; k < 4; ++k) {
-        neumaier_add(s, c, s4[k]);
-        c += c4[k];
-    }
+    if (i < ch.z) term(i, 0);
+    double s = (double)hi[0], c = (double)lo[0];
+    neumaier_add(s, c, (double)hi[1]);
+    c += (double)lo[1];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const double s2 = __shfl_down_sync(0xffffffffu, s, off), c2 = __shfl_down_sync(0xffffffffu, c, off);

@@ -11,8 +11,12 @@ is a linear map J (the noise enters additively and drops out of it).
   backward(g)     = J^T g          (adjoint, ``sft_adjoint``, checkpointed with
                                     Philox noise regeneration)
 Both run in the library's CUDA kernels; this module only marshals tensors.
-Real fields, SETD-EM or SETD1, Model A/B (the cases the library
-differentiates).
+Every case the library differentiates: the cubic term (d = 1..3), the KPZ and
+CGL terms (d = 1, 2), every scheme.  Complex fields (CGL) take complex64
+tensors; J is then only real-linear (the linearised |A|^2 A term holds
+conj(dA)), and backward returns its transpose for the real inner product
+Re sum conj(u) v, which is the vector-Jacobian product of torch's convention
+for a real loss (grad = dL/dRe + i dL/dIm).
 """
 from __future__ import annotations
 
@@ -27,7 +31,7 @@ def _device_fields(x: torch.Tensor, stepper: Stepper, what: str) -> torch.Tensor
     shape = (stepper.R,) + tuple(stepper.shape)
     if tuple(x.shape) != shape:
         raise ValueError("%s must have shape %s (replicas, lattice), got %s" % (what, shape, tuple(x.shape)))
-    return x.detach().to(torch.float32).contiguous()
+    return x.detach().to(torch.complex64 if stepper.complex_field else torch.float32).contiguous()
 
 
 class SETDPropagate(torch.autograd.Function):

@@ -227,6 +227,8 @@ AUTOGRAD_CASES = [
     ("model_a_32", W.model_a_64(n=[32, 32], replicas=2, sigma0=0.3, h=0.02)),
     ("model_b_3d_16_em", W.model_a_128_3d(n=[16, 16, 16], model=1, p=[1.0, -0.5, 1.0, 0.2], scheme=0, h=0.02,
                                           sigma0=0.3)),
+    ("kpz_2d_32_setd2", W.kpz_2d(n=[32, 32], replicas=2, sigma0=0.5, scheme=2)),
+    ("cgl_2d_32_setd2", W.cgl_2048(n=[32, 32], replicas=2, p=[2.0, -0.5, 1e-3])),
 ]
 
 
@@ -237,9 +239,10 @@ def test_autograd_function(env, oracle_mod, name, w):
     the backward pass leaves the stepper where the forward left it."""
     m, torch = env
     from paper_2511_22510_gb300.response import propagate
+    dt, dt64 = (np.complex64, np.complex128) if w.complex_field else (np.float32, np.float64)
     f0 = W.initial_fields(w)
-    v0 = W.initial_fields(w.with_(sigma0=1.0), seed_offset=5).astype(np.float32)
-    gw = W.initial_fields(w.with_(sigma0=1.0), seed_offset=6).astype(np.float32)
+    v0 = W.initial_fields(w.with_(sigma0=1.0), seed_offset=5).astype(dt)
+    gw = W.initial_fields(w.with_(sigma0=1.0), seed_offset=6).astype(dt)
     nst = 15
     g, o = make_pair(m, oracle_mod, w, f0)
     m.sft_set_checkpoint_interval(g.ctx, 6)
@@ -247,24 +250,26 @@ def test_autograd_function(env, oracle_mod, name, w):
     out = propagate(v, g, nst)
     after_forward = g.spectrum()
     gt = torch.from_numpy(gw).cuda()
-    (out * gt).sum().backward()
+    # a real loss: Re sum conj(g) J v (complex fields), sum g J v (real fields)
+    loss = (out * gt.conj()).sum()
+    (loss.real if w.complex_field else loss).backward()
     assert np.array_equal(g.spectrum(), after_forward)
     assert g.step_count == nst
-    jv = out.detach().cpu().numpy().astype(np.float64)
-    jtg = v.grad.cpu().numpy().astype(np.float64)
-    tan_o = o.tangent_step(v0.astype(np.float64), nst)
+    jv = out.detach().cpu().numpy().astype(dt64)
+    jtg = v.grad.cpu().numpy().astype(dt64)
+    tan_o = o.tangent_step(v0.astype(dt64), nst)
     o2 = make_pair(m, oracle_mod, w, f0)[1]
-    adj_o = o2.adjoint(gw.astype(np.float64), nst)
+    adj_o = o2.adjoint(gw.astype(dt64), nst)
     for r in range(w.replicas):
         assert rel(jv[r], tan_o[r]) <= 1e-5, (name, r)
         assert rel(jtg[r], adj_o[r]) <= 1e-5, (name, r)
-        lhs = float(np.sum(jv[r] * gw[r]))
-        rhs = float(np.sum(v0[r] * jtg[r]))
+        lhs = float(np.vdot(gw[r].astype(dt64), jv[r]).real)
+        rhs = float(np.vdot(jtg[r], v0[r].astype(dt64)).real)
         assert abs(lhs - rhs) <= 2e-5 * (abs(lhs) + abs(rhs)), (name, lhs, rhs)
     # linear in v, same noise path: a second propagation from the same start doubles with 2 v
     g2, _ = make_pair(m, oracle_mod, w, f0)
     out2 = propagate(2.0 * v.detach(), g2, nst)
-    assert rel(out2.cpu().numpy().astype(np.float64), 2.0 * jv) <= 1e-6
+    assert rel(out2.cpu().numpy().astype(dt64), 2.0 * jv) <= 1e-6
     for x in (g, g2):
         x.close()
 
