@@ -110,9 +110,11 @@ typedef struct {
                         * dealiasing (Sec. IV step 1): the nonlinear term is the mean over the
                         * 2^d grids shifted by half a cell along every subset of the axes, every
                         * mode but the Nyquist ones kept (alias-free for the cubic and the gradient-
-                        * squared terms); built for 2-D real fields (Model A/B, KPZ) with noise_space 0,
-                        * at twice the P/Q memory and two to four times the transform work of a step */
-    int precision;     /* 0: FP32 state and transforms (only value supported) */
+                        * squared terms); built for 2-D real fields and power-of-two 1-D real lines of up
+                        * to 16384 points (Model A/B, KPZ) with noise_space 0, at twice the P/Q memory
+                        * and two to four times the transform work of a step */
+    int precision;     /* 0: FP32 state and transforms; 1: the split-BF16x3 tensor-core transforms of
+                        * the precision study (complex 2-D fields of 1024^2 or 2048^2 points) */
     void* stream;      /* cudaStream_t, or NULL for the default stream */
     int replica0;      /* global index of replica 0 (Philox counter word 2): ranks that shard one
                           ensemble pass disjoint offsets; 0 for a stand-alone context */
@@ -135,7 +137,8 @@ typedef struct {
      * structure of App. B; 1 draws iid N(0,1) per real-space site (Philox
      * ctr = (site >> 2, step, replica, 3), normal site & 3) and takes
      * eta_a = DFT[eta]_a / sqrt(N^d): one extra forward transform per step.
-     * 1 is built for 2-D real fields. */
+     * 1 is built for 2-D real fields and power-of-two 1-D real lines of up to
+     * 16384 points (cubic or gradient-squared term). */
     int noise_space;
 } sft_config;
 

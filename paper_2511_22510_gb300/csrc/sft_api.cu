@@ -17,6 +17,12 @@
 #include "../../include/sft.h"
 #include "sft_internal.h"
 
+namespace sft {
+// complex 2-D step on columns of 1024 or 2048 points, one warp per 1024 points (sft_k2c_colwarp.cu)
+bool k2c_colwarp_supported(int ny);
+cudaError_t launch_k2c_cols_warp(const StepArgs& a, cudaStream_t s);
+}  // namespace sft
+
 using namespace sft;
 
 namespace {
@@ -219,7 +225,12 @@ static cudaError_t launch_rows(const sft_ctx* ctx, StepArgs a, int mode) {
 // Second pass: columns (2-D) or a_x planes (3-D).
 static cudaError_t launch_second(const sft_ctx* ctx, const StepArgs& a, int mode) {
     if (ctx->d == 3) return launch_k3_planes(a, mode, ctx->nl, ctx->stream);
-    if (ctx->cplx) return launch_k2c_cols(a, mode, ctx->stream);
+    if (ctx->cplx) {
+        // the step on complex columns of 1024 or 2048 points: warp-resident transforms
+        if (mode == MODE_STEP && k2c_colwarp_supported(ctx->ny) && a.tw_32 && !a.rec_phi && !a.noise_in && !a.pshift)
+            return launch_k2c_cols_warp(a, ctx->stream);
+        return launch_k2c_cols(a, mode, ctx->stream);
+    }
     return launch_k2_cols(a, mode, ctx->nl, ctx->stream);
 }
 
@@ -231,6 +242,17 @@ static cudaError_t launch_cols_step(const sft_ctx* ctx, const StepArgs& a) {
 
 // Twiddle tables of a 1-D line launch: complex fields transform N-point lines (tw_a); real fields N/2-point
 // lines with the N-point table of the real-to-complex post-processing (tw_b).  False if one is missing.
+// Mode of the 1-D step kernel: the plain step or one of its variants (phase shifts, real-space noise); the
+// variants keep the plain evaluation of the nonlinear term in Q (one line of M + 1 entries per replica).
+static int line_step_mode(const sft_ctx* ctx, StepArgs& a) {
+    a.qout = ctx->Q;
+    if (ctx->cfg.noise_space == 1) {
+        a.noise_scale = (float)(1.0 / std::sqrt((double)ctx->sites));
+        return MODE_STEP_RSN;
+    }
+    return ctx->cfg.dealias == 2 ? MODE_STEP_PS : MODE_STEP;
+}
+
 static bool set_line_twiddles(const sft_ctx* ctx, StepArgs& a) {
     if (ctx->cplx) {
         a.tw_a = ctx->tw.get(ctx->nx);
@@ -439,7 +461,7 @@ static sft_status enqueue_step(sft_ctx* ctx, int k) {
     a.k_in_chunk = k;
     if (ctx->d == 1) {
         if (!set_line_twiddles(ctx, a)) return fail(ctx, SFT_EINVAL, "twiddle table missing");
-        CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
+        CK(launch_k1_line(a, line_step_mode(ctx, a), ctx->nl, ctx->stream));
         return SFT_OK;
     }
     if (ctx->cfg.precision == 1) {
@@ -718,16 +740,22 @@ sft_status sft::validate_config(const sft_config* cfg, std::string& why) {
     int cplx = 0, nlk = 0;
     model_kind(cfg, &cplx, &nlk);
     if (cfg->noise_space != 0 && cfg->noise_space != 1) return why = "noise_space must be 0 or 1", SFT_EINVAL;
-    if (cfg->noise_space == 1 && (cfg->d != 2 || cplx))
-        return why = "real-space noise is built for 2-D real fields", SFT_EUNSUPPORTED;
+    // the 1-D variants run in the single-line kernel: power-of-two lines of up to 16384 points
+    const bool line_var_ok = cfg->d == 1 && !cplx && is_pow2(cfg->n[0]) && cfg->n[0] <= 16384 &&
+                             (nlk == NL_CUBIC || nlk == NL_GRAD2);
+    if (cfg->noise_space == 1 && !((cfg->d == 2 && !cplx) || line_var_ok))
+        return why = "real-space noise is built for 2-D real fields and 1-D real lines of up to 16384 points "
+                     "(cubic or gradient-squared term)",
+               SFT_EUNSUPPORTED;
     if (!is_pow2(cfg->n[0]) &&
         (cfg->d == 3 || cplx || cfg->dealias == 2 || cfg->noise_space != 0 || cfg->model == SFT_CUSTOM))
         return why = "lattices of p x 2^k points are built for 1-D and 2-D real fields (Model A/B, KPZ) with "
                      "Fourier-space noise and 2/3 truncation (or none)",
                SFT_EUNSUPPORTED;
-    if (cfg->dealias == 2 && (cfg->d != 2 || cplx || (nlk != NL_CUBIC && nlk != NL_GRAD2) || cfg->noise_space != 0))
-        return why = "phase-shift dealiasing is built for 2-D real fields with the cubic or gradient-squared term and "
-                     "Fourier-space noise",
+    if (cfg->dealias == 2 && (!((cfg->d == 2 && !cplx) || line_var_ok) || (nlk != NL_CUBIC && nlk != NL_GRAD2) ||
+                              cfg->noise_space != 0))
+        return why = "phase-shift dealiasing is built for 2-D real fields and 1-D real lines of up to 16384 points "
+                     "with the cubic or gradient-squared term and Fourier-space noise",
                SFT_EUNSUPPORTED;
     if (cfg->model == SFT_CUSTOM) {
         const int nl = cfg->custom_nl;
@@ -810,7 +838,7 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     if (ok && ctx->d >= 2) ok = dalloc((void**)&ctx->P, pq);
     if (ok && ctx->d >= 2 && ctx->nl == NL_GRAD2) ok = dalloc((void**)&ctx->Py, pq);
     if (ok && cfg->scheme == SFT_SETD2) ok = dalloc((void**)&ctx->fprev, ms);
-    if (ok && cfg->noise_space == 1) ok = dalloc((void**)&ctx->noise_spec, ms);
+    if (ok && cfg->noise_space == 1 && ctx->d >= 2) ok = dalloc((void**)&ctx->noise_spec, ms);
     if (ok && cfg->precision == 1) ok = dalloc((void**)&ctx->tcb1, ms) && dalloc((void**)&ctx->tcb2, ms);
     if (ok) {
         if (ctx->cplx)
@@ -855,7 +883,8 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     if (ctx->d == 1 && !ctx->cplx && k1_cluster_fft_len(ctx->nx))
         lens.push_back(k1_cluster_fft_len(ctx->nx));  // per-block FFT of the cluster kernel
     if (build_twiddles(ctx, lens) != SFT_OK) return cleanup(SFT_ECUDA);
-    if (!ctx->cplx && ctx->d >= 2 && (ctx->nx == 1024 || ctx->ny == 1024)) {
+    if (ctx->d >= 2 && (ctx->cplx ? (ctx->d == 2 && k2c_colwarp_supported(ctx->ny))
+                                  : (ctx->nx == 1024 || ctx->ny == 1024))) {
         // twiddles of the 1024-point warp transforms: entry k1 32 + t = W_1024^{t k1}
         if (!dalloc((void**)&ctx->tw32, 1024 * sizeof(float2)) || launch_twiddles32(ctx->tw32, ctx->stream) != cudaSuccess)
             return cleanup(SFT_ECUDA);
@@ -973,7 +1002,9 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
             return cleanup(SFT_ECUDA);
     }
     ctx->launches_per_step = ctx->d == 1 ? 1 : 2;
-    if (cfg->noise_space == 1) ctx->launches_per_step += 2;  // forward transform of the noise (drawn in its row pass)
+    // 2-D real-space noise: the forward transform of the noise (drawn in its row pass); 1-D lines transform it
+    // inside the step kernel
+    if (cfg->noise_space == 1 && ctx->d >= 2) ctx->launches_per_step += 2;
     if (cfg->precision == 1) ctx->launches_per_step = 9;     // prep, 4 transforms, 2 transposes, |A|^2 A, update
     {
         // column-pass variant: chosen by the plan autotuner unless SFT_COLUMN_PASS forces the
@@ -2167,7 +2198,7 @@ sft_status sft_profile(sft_ctx* ctx, int64_t nsteps, double* out_ms, int cap, in
         CK(cudaEventRecord(e[0], ctx->stream));
         if (ctx->d == 1) {
             if (!set_line_twiddles(ctx, a)) return fail(ctx, SFT_EINVAL, "twiddle table missing");
-            CK(launch_k1_line(a, MODE_STEP, ctx->nl, ctx->stream));
+            CK(launch_k1_line(a, line_step_mode(ctx, a), ctx->nl, ctx->stream));
             CK(cudaEventRecord(e[1], ctx->stream));
         } else if (ctx->cfg.precision == 1) {
             // precision study: the whole tensor-core step, reported as the first entry (the second is empty)

@@ -4,6 +4,10 @@
 
 namespace sft {
 
+// 1-D step variants (MODE_STEP_PS, MODE_STEP_RSN) on power-of-two real lines of up to 16384 points
+// (sft_k1d_var.cu)
+cudaError_t launch_k1_line_var(const StepArgs& a, int mode, int nl, cudaStream_t s);
+
 bool k1_supported(int nx, int complex_field) {
     if (!complex_field && k2_mixed_size(nx)) return true;  // p x 2^k lines (sft_k1d_mixed.cu)
     if ((nx & (nx - 1)) != 0) return false;
@@ -13,6 +17,7 @@ bool k1_supported(int nx, int complex_field) {
 cudaError_t launch_k1_line(const StepArgs& a, int mode, int nl, cudaStream_t s) {
     // complex lines read the N-point table tw_a; real lines the N/2-point table tw_a and the N-point table tw_b
     if (!a.tw_a || (nl != NL_CGL && !a.tw_b)) return cudaErrorInvalidValue;
+    if (mode == MODE_STEP_PS || mode == MODE_STEP_RSN) return launch_k1_line_var(a, mode, nl, s);
     if (nl != NL_CGL && k1_use_cluster(a.nx, a.R, mode)) return launch_k1_cluster(a, mode, nl, s);
     if (nl == NL_CGL) {
         switch (a.nx) {

@@ -120,6 +120,130 @@ __device__ __forceinline__ void line_step(const StepArgs& a, int r, bool valid, 
     }
 }
 
+// Variants of the 1-D step (the alternatives of Sec. IV steps 1 and 2), on one line per team:
+//   MODE_STEP_PS: phase-shift dealiasing -- the nonlinear term is the mean of its evaluation on the plain grid
+//     and on the grid shifted by half a cell (input phases e^{i pi k / N}, output phases e^{-i pi k / N}); the
+//     Nyquist mode is masked on input and output and every other mode is kept;
+//   MODE_STEP_RSN: real-space noise -- site s of the line takes normal s & 3 of Philox(s >> 2, step, replica,
+//     tag 3), and the update uses eta_k = DFT[eta]_k / sqrt(N) (a.noise_scale = 1 / sqrt(N)).
+// The plain evaluation of the nonlinear term waits in a.qout (M + 1 entries per line, each thread reading back
+// the entries it wrote) while the second transform pair runs, so that two spectra are never live in registers.
+template <int M, int NL, int MODE>
+__device__ __forceinline__ void line_step_var(const StepArgs& a, int r, bool valid, int t, float2* xb) {
+    using PL = FftPlan<M>;
+    constexpr int T = PL::T, E = PL::E;
+    constexpr int NX = 2 * M;
+    constexpr bool PS = MODE == MODE_STEP_PS;
+    constexpr bool G = NL == NL_GRAD2;
+    static_assert(NL == NL_CUBIC || G, "1-D variants: cubic or gradient-squared term");
+    const float2* __restrict__ twM = a.tw_a;
+    const float2* __restrict__ twN = a.tw_b;
+    const float2* __restrict__ tps = a.tw_ps;  // e^{-i pi m / N}
+    float2* ph = a.phi + (size_t)r * (M + 1);
+    const float sc = a.scale;
+    const long long step = current_step(a);
+    const uint32_t rep = (uint32_t)(a.rep0 + r);
+    // the nonlinear term evaluated on the plain grid (shift = false) or the shifted one: Xq[e] for the modes
+    // k = t + T e, XqM for the Nyquist mode
+    auto q_of = [&](bool shift, float2 (&Xq)[E], float2& XqM) {
+        float2 z[E];
+        // unrolled in groups of four: fewer input loads in flight, so the long lines do not spill
+#pragma unroll 4
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            float2 X = ph[k], Xm = ph[M - k];
+            if constexpr (PS) {
+                X = cscale(X, sc);
+                Xm = (k == 0) ? czero() : cscale(Xm, sc);  // the Nyquist mode is masked
+            } else {
+                X = (!a.dealias || 3 * k < NX) ? cscale(X, sc) : czero();
+                Xm = (!a.dealias || 3 * (M - k) < NX) ? cscale(Xm, sc) : czero();
+            }
+            if constexpr (G) {
+                X = cscale(cmuli(X), a.dk * (float)k);
+                Xm = cscale(cmuli(Xm), k == 0 ? 0.f : a.dk * (float)(M - k));
+            }
+            if (shift) {
+                X = cmul(X, cconj(__ldg(&tps[k])));
+                Xm = cmul(Xm, cconj(__ldg(&tps[M - k])));
+            }
+            z[e] = c2r_pre(X, Xm, __ldg(&twN[k]));
+        }
+        fft_line<M, true>(z, xb, t, twM);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if constexpr (G)
+                z[e] = make_float2(z[e].x * z[e].x, z[e].y * z[e].y);
+            else
+                z[e] = make_float2(z[e].x * z[e].x * z[e].x, z[e].y * z[e].y * z[e].y);
+        }
+        fft_line<M, false>(z, xb, t, twM);
+        line_post<M>(z, xb, t, twN, Xq, XqM);
+        if (shift) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) Xq[e] = cmul(Xq[e], __ldg(&tps[t + T * e]));
+        }
+    };
+    float2* qs = a.qout + (size_t)r * (M + 1);
+    {
+        float2 Xp[E], XpM;
+        q_of(false, Xp, XpM);
+        if (valid) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) qs[t + T * e] = Xp[e];
+            if (t == 0) qs[M] = XpM;
+        }
+    }
+    // PS: Xq <- the shifted evaluation, averaged with the plain one below; RSN: Xq <- the noise spectrum
+    float2 Xq[E], XqM;
+    if constexpr (PS) {
+        q_of(true, Xq, XqM);
+    } else {
+        // the packed pair m = t + T e holds sites 2m, 2m + 1: normal pair m of the tag-3 stream
+#pragma unroll
+        for (int e = 0; e < E; e += 2)
+            team_normal_pair_ks<T>(a.ks, 0, t, e, (uint32_t)step, rep, Xq[e], Xq[e + 1], 3u);
+        fft_line<M, false>(Xq, xb, t, twM);
+        line_post<M>(Xq, xb, t, twN, Xq, XqM);
+    }
+    const bool first = (a.scheme == 2) && (step == *a.first_step);
+    float2* fp = a.fprev + (size_t)r * (M + 1);
+    float2 zn0 = czero(), zn1 = czero();
+    // modes k = t + T e, then (thread 0) the Nyquist mode k = M
+#pragma unroll
+    for (int e = 0; e <= E; ++e) {
+        if constexpr (PS) {
+            if (e < E && (e & 1) == 0) team_normal_pair_ks<T>(a.ks, 0, t, e, (uint32_t)step, rep, zn0, zn1);
+        }
+        if (e == E && t != 0) break;
+        const int k = (e < E) ? t + T * e : M;
+        const float2 xv = (e < E) ? Xq[e] : XqM;
+        float2 xq = qs[k];  // the plain evaluation, written by this thread
+        if constexpr (PS) xq = cscale(cadd(xq, xv), 0.5f);
+        const bool inm = PS ? (k != M) : (!a.dealias || 3 * k < NX);
+        const float2 F = inm ? cscale(xq, nl_prefactor(a, k * k).x) : czero();
+        const Coefs co = load_coefs<false>(a.tab, k, first);
+        const float2 phv = ph[k];
+        const float2 Fp = (a.scheme == 2) ? fp[k] : czero();
+        const bool selfc = (k == 0 || k == M);
+        float2 eta;
+        if constexpr (PS) {
+            eta = (e < E) ? eta_of((e & 1) ? zn1 : zn0, selfc)
+                          : fourier_noise(a.seed, (uint64_t)k, (uint32_t)step, rep, selfc);
+        } else {
+            eta = cscale(xv, a.noise_scale);
+            if (selfc) eta.y = 0.f;
+        }
+        float2 o = setd_update<false>(co, phv, F, Fp, eta);
+        if (selfc) o.y = 0.f;
+        if (valid) {
+            ph[k] = o;
+            if (a.scheme == 2) fp[k] = F;
+            flag_nonfinite(a, o, step);
+        }
+    }
+}
+
 // Real field, N = 2M points.  Mode k of replica r sits at phi[r * (M + 1) + k].
 template <int M, int NL, int MODE>
 __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a) {
@@ -138,6 +262,10 @@ __global__ void __launch_bounds__(LineCfg<M>::THREADS) k1_real(const StepArgs a)
     float2* ph = a.phi + (size_t)rr * (M + 1);
     float2 z[E];
 
+    if constexpr (MODE == MODE_STEP_PS || MODE == MODE_STEP_RSN) {
+        line_step_var<M, NL, MODE>(a, rr, valid, t, xb);
+        return;
+    }
     if constexpr (MODE == MODE_TAN || MODE == MODE_ADJ) {
         // TAN: primal step plus dphi <- f1 dphi + A M s DFT[q'] with q' = 3 psi^2 dpsi (cubic,
         // dpsi = IDFT(M dphi)) or 2 g dg (KPZ, g = IDFT(i k M phi), dg = IDFT(i k M dphi)).

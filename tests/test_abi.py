@@ -101,27 +101,28 @@ def test_r_in_F_with_setd2_unsupported(lib):
     assert ei.value.status == lib.SFT_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("d,model,space,status", [
-    (2, 0, 2, "SFT_EINVAL"),          # no such noise space
-    (1, 0, 1, "SFT_EUNSUPPORTED"),    # real-space noise is built for 2-D real fields
-    (3, 0, 1, "SFT_EUNSUPPORTED"),
-    (2, 3, 1, "SFT_EUNSUPPORTED"),    # complex field (CGL)
+@pytest.mark.parametrize("d,n,model,space,status", [
+    (2, 16, 0, 2, "SFT_EINVAL"),          # no such noise space
+    (1, 32768, 0, 1, "SFT_EUNSUPPORTED"), # real-space noise: 2-D real fields and 1-D lines up to 16384 points
+    (1, 128, 3, 1, "SFT_EUNSUPPORTED"),   # complex line (CGL)
+    (3, 16, 0, 1, "SFT_EUNSUPPORTED"),
+    (2, 16, 3, 1, "SFT_EUNSUPPORTED"),    # complex field (CGL)
 ])
-def test_real_space_noise_limits(lib, d, model, space, status):
-    n = [16] * d
+def test_real_space_noise_limits(lib, d, n, model, space, status):
+    n = [n] * d
     cfg = lib.make_config(d, n, [1.0] * d, 1, model, [1, -0.5, 1, 0.5], 1, 0.01, 1, noise_space=space)
     with pytest.raises(lib.SftError) as ei:
         lib.sft_create(cfg)
     assert ei.value.status == getattr(lib, status)
 
 
-@pytest.mark.parametrize("d,model,space", [
-    (1, 0, 0), (3, 0, 0),  # phase-shift dealiasing is built for 2-D lattices
-    (2, 3, 0),             # complex field (CGL)
-    (2, 0, 1),             # with real-space noise
+@pytest.mark.parametrize("d,n,model,space", [
+    (1, 32768, 0, 0), (3, 16, 0, 0),  # phase shifts: 2-D real fields and 1-D lines up to 16384 points
+    (2, 16, 3, 0), (1, 128, 3, 0),    # complex fields (CGL)
+    (2, 16, 0, 1), (1, 256, 0, 1),    # with real-space noise
 ])
-def test_phase_shift_dealiasing_limits(lib, d, model, space):
-    cfg = lib.make_config(d, [16] * d, [1.0] * d, 1, model, [1, -0.5, 1, 0.5], 1, 0.01, 1, dealias=2,
+def test_phase_shift_dealiasing_limits(lib, d, n, model, space):
+    cfg = lib.make_config(d, [n] * d, [1.0] * d, 1, model, [1, -0.5, 1, 0.5], 1, 0.01, 1, dealias=2,
                           noise_space=space)
     with pytest.raises(lib.SftError) as ei:
         lib.sft_create(cfg)

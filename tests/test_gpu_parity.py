@@ -369,6 +369,12 @@ RSN_CASES = [
     ("kpz_2d_32_em", W.kpz_2d(n=[32, 32], replicas=2, scheme=0), 100),
     ("model_b_128_setd1_R3", W.model_b_1024(n=[128, 128], replicas=3, sigma0=0.3), 40),
     ("model_b_1024_setd1_R2", W.model_b_1024(replicas=2, h=0.05), 3),
+    # 1-D lines: the draw and its transform inside the line kernel
+    ("model_a_1d_256_setd1_R3", W.model_a_64(d=1, n=[256], dx=[1.0], replicas=3, sigma0=0.3), 100),
+    ("model_b_1d_2048_setd2", W.model_b_1024(d=1, n=[2048], dx=[1.0], replicas=2, h=0.025, sigma0=0.3), 100),
+    ("kpz_1d_1024_em_R2", W.kpz_1d(1024, replicas=2, scheme=0), 100),
+    ("kpz_1d_16384_setd1", W.kpz_1d(16384, replicas=2), 20),
+    ("model_a_1d_32_nodeal", W.model_a_64(d=1, n=[32], dx=[1.0], replicas=2, sigma0=0.3, dealias=0), 100),
 ]
 
 
@@ -425,6 +431,12 @@ PS_CASES = [
     ("kpz_2d_64_setd2", W.kpz_2d(n=[64, 64], scheme=2, h=0.005), 100),
     ("kpz_2d_256_em_R3", W.kpz_2d(n=[256, 256], replicas=3, scheme=0, sigma0=0.5), 20),
     ("kpz_2d_1024_setd1", W.kpz_2d(n=[1024, 1024], sigma0=0.5), 3),
+    # 1-D lines: both grids evaluated by the line kernel
+    ("model_a_1d_256_setd1_R3", W.model_a_64(d=1, n=[256], dx=[1.0], replicas=3, sigma0=0.3), 100),
+    ("model_b_1d_2048_setd2", W.model_b_1024(d=1, n=[2048], dx=[1.0], replicas=2, h=0.025, sigma0=0.3), 100),
+    ("kpz_1d_1024_em_R2", W.kpz_1d(1024, replicas=2, scheme=0, sigma0=0.5), 100),
+    ("kpz_1d_16384_setd1", W.kpz_1d(16384, replicas=2, sigma0=0.5), 20),
+    ("model_a_1d_32_setd2", W.model_a_64(d=1, n=[32], dx=[1.0], replicas=2, sigma0=0.3, scheme=2), 100),
 ]
 
 
@@ -441,6 +453,30 @@ def test_phase_shift_dealiasing_step_parity(sft, oracle_mod, name, w, nsteps):
     for r in range(w.replicas):
         assert rel_l2(got[r], o.field(r)) <= 1e-5, (name, r)
     g.close()
+
+
+@pytest.mark.parametrize("variant", ["phase_shift", "real_space_noise"])
+def test_line_variants_graph_plain_and_rejections(sft, variant):
+    """1-D variants: graph and plain launches agree bit for bit; lines longer
+    than 16384 points and complex lines are refused before any device work."""
+    kw = {"dealias": 2} if variant == "phase_shift" else {"noise_space": 1}
+    w = W.kpz_1d(512, replicas=3, sigma0=0.5)
+    mk = lambda: sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, **kw)
+    a, b = mk(), mk()
+    f = W.initial_fields(w).astype(np.float32)
+    a.set_field(f)
+    b.set_field(f)
+    a.step(37)
+    b.step_plain(37)
+    assert np.array_equal(a.spectrum().view(np.uint64), b.spectrum().view(np.uint64))
+    for s in (a, b):
+        s.close()
+    long_w = W.kpz_1d(32768, replicas=1)
+    with pytest.raises(sft.SftError):
+        sft.Stepper(long_w.d, long_w.n, long_w.dx, 1, long_w.model, long_w.p, long_w.scheme, long_w.h, 1, **kw)
+    c = W.cgl_2048(d=1, n=[128], dx=[0.5], replicas=1)
+    with pytest.raises(sft.SftError):
+        sft.Stepper(c.d, c.n, c.dx, 1, c.model, c.p, c.scheme, c.h, 1, **kw)
 
 
 def test_phase_shift_graph_plain_and_checkpoint(sft):
