@@ -44,6 +44,64 @@ __device__ __forceinline__ void pair_sync(int pc) {
         asm volatile("bar.sync 2, 64;" ::: "memory");
 }
 
+// The update of this warp's 1024 modes a_y = 1024 h + lane + 32 e, two slots (one Philox call) per trip of a loop
+// that is not unrolled; the state and the SETD2 history of the next pair of slots are loaded one trip ahead; xb
+// holds DFT[q] on entry and receives the masked, scaled new state.  HASF: the column carries F and P; S2: SETD2
+// (the history F_prev).  Returns the non-finite accumulator.
+template <int H, bool DEAL, bool HASF, bool S2>
+__device__ __forceinline__ float ccw_update(const StepArgs& a, float2* xb, size_t colbase, int c, int lane, int h,
+                                            long long step, int rep, bool first, int tabrow, float2 s) {
+    constexpr int NY = 1024 * H;
+    constexpr bool HIST = S2 && HASF;
+    const float2* __restrict__ phin = a.phi + colbase + 1024 * h;
+    const float2* fpin = HIST ? a.fprev + colbase + 1024 * h : nullptr;
+    float nf = 0.f;
+    float2 ph0 = phin[lane], ph1 = phin[lane + 32];
+    float2 fp0 = czero(), fp1 = czero();
+    if constexpr (HIST) {
+        fp0 = fpin[lane];
+        fp1 = fpin[lane + 32];
+    }
+#pragma unroll 1
+    for (int e = 0; e < 32; e += 2) {
+        float2 nx0 = czero(), nx1 = czero(), nf0 = czero(), nf1 = czero();
+        if (e + 2 < 32) {
+            nx0 = phin[lane + 32 * (e + 2)];
+            nx1 = phin[lane + 32 * (e + 3)];
+            if constexpr (HIST) {
+                nf0 = fpin[lane + 32 * (e + 2)];
+                nf1 = fpin[lane + 32 * (e + 3)];
+            }
+        }
+        float2 z0, z1;
+        team_normal_pair_ks<32>(a.ks, (uint64_t)c * NY + 1024 * h, lane, e, (uint32_t)step,
+                                (uint32_t)(a.rep0 + rep), z0, z1);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int k = lane + 32 * (e + hh);
+            const int ay = 1024 * h + k;
+            const int ays = signed_idx(ay, NY);
+            const bool inm = HASF && (!DEAL || 3 * abs(ays) < NY);
+            const float2 F = inm ? cmul(s, xb[k]) : czero();
+            const Coefs co = load_coefs<true>(a.tab, tabrow + abs(ays), S2 && first);
+            const float2 eta = eta_of(hh ? z1 : z0, false);
+            const float2 ph = hh ? ph1 : ph0;
+            float2 out = cadd(cmul(co.f1, ph), cmul(co.A, F));
+            if constexpr (HIST) out = cadd(out, cmul(co.B, hh ? fp1 : fp0));
+            out = cadd(out, cmul(co.g, eta));
+            if constexpr (HIST) a.fprev[colbase + ay] = F;
+            a.phi[colbase + ay] = out;
+            nf = nonfinite_acc(nf, out);
+            xb[k] = inm ? cscale(out, a.scale) : czero();
+        }
+        ph0 = nx0;
+        ph1 = nx1;
+        fp0 = nf0;
+        fp1 = nf1;
+    }
+    return nf;
+}
+
 // 5 blocks (20 warps) per SM: the register budget of the real warp column pass
 template <int H, bool DEAL>
 __global__ void __launch_bounds__(kCcWarps * 32, 5) k2c_cols_warp(const StepArgs a) {
@@ -67,7 +125,6 @@ __global__ void __launch_bounds__(kCcWarps * 32, 5) k2c_cols_warp(const StepArgs
     const float2* __restrict__ twN = a.tw_a;  // W_NY^k
     const float2 s = make_float2(a.s0, a.s0i);
     const int bar = pc;  // H = 2: two columns per block, barriers 1 and 2
-    const bool hist = a.scheme == 2 && has_f;
     // kCcRpb replicas per block, one after the other: the column's coefficient rows (complex, 32 bytes per mode)
     // are then read from the caches for every replica after the first
     for (int ri = 0; ri < kCcRpb; ++ri) {
@@ -102,46 +159,15 @@ __global__ void __launch_bounds__(kCcWarps * 32, 5) k2c_cols_warp(const StepArgs
     }
     __syncwarp();
 
-    // the update, two slots (one Philox call) per trip of a loop that is not unrolled; the state and the SETD2
-    // history of the next pair of slots are loaded one trip ahead; xb receives the masked, scaled new state
-    const float2* __restrict__ phin = a.phi + colbase + 1024 * h;
-    const float2* fpin = hist ? a.fprev + colbase + 1024 * h : nullptr;
-    float nf = 0.f;
-    float2 ph0 = phin[lane], ph1 = phin[lane + 32];
-    float2 fp0 = hist ? fpin[lane] : czero(), fp1 = hist ? fpin[lane + 32] : czero();
-#pragma unroll 1
-    for (int e = 0; e < 32; e += 2) {
-        float2 nx0 = czero(), nx1 = czero(), nf0 = czero(), nf1 = czero();
-        if (e + 2 < 32) {
-            nx0 = phin[lane + 32 * (e + 2)];
-            nx1 = phin[lane + 32 * (e + 3)];
-            if (hist) {
-                nf0 = fpin[lane + 32 * (e + 2)];
-                nf1 = fpin[lane + 32 * (e + 3)];
-            }
-        }
-        float2 z0, z1;
-        team_normal_pair_ks<32>(a.ks, (uint64_t)c * NY + 1024 * h, lane, e, (uint32_t)step,
-                                (uint32_t)(a.rep0 + rep), z0, z1);
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int k = lane + 32 * (e + hh);
-            const int ay = 1024 * h + k;
-            const int ays = signed_idx(ay, NY);
-            const bool inm = has_f && (!DEAL || 3 * abs(ays) < NY);
-            const float2 F = inm ? cmul(s, xb[k]) : czero();
-            const Coefs co = load_coefs<true>(a.tab, tabrow + abs(ays), first);
-            const float2 out = setd_update<true>(co, hh ? ph1 : ph0, F, hh ? fp1 : fp0, eta_of(hh ? z1 : z0, false));
-            if (hist) a.fprev[colbase + ay] = F;
-            a.phi[colbase + ay] = out;
-            nf = nonfinite_acc(nf, out);
-            xb[k] = inm ? cscale(out, a.scale) : czero();
-        }
-        ph0 = nx0;
-        ph1 = nx1;
-        fp0 = nf0;
-        fp1 = nf1;
-    }
+    // the update (ccw_update), with the column's run-time-uniform choices resolved once
+    const float nf = has_f ? (a.scheme == 2 ? ccw_update<H, DEAL, true, true>(a, xb, colbase, c, lane, h, step, rep,
+                                                                              first, tabrow, s)
+                                            : ccw_update<H, DEAL, true, false>(a, xb, colbase, c, lane, h, step, rep,
+                                                                               first, tabrow, s))
+                           : (a.scheme == 2 ? ccw_update<H, DEAL, false, true>(a, xb, colbase, c, lane, h, step, rep,
+                                                                               first, tabrow, s)
+                                            : ccw_update<H, DEAL, false, false>(a, xb, colbase, c, lane, h, step,
+                                                                                rep, first, tabrow, s));
     flag_nonfinite_acc(a, nf, step);
     __syncwarp();
 
