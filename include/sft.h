@@ -137,8 +137,8 @@ typedef struct {
      * structure of App. B; 1 draws iid N(0,1) per real-space site (Philox
      * ctr = (site >> 2, step, replica, 3), normal site & 3) and takes
      * eta_a = DFT[eta]_a / sqrt(N^d): one extra forward transform per step.
-     * 1 is built for 2-D real fields and power-of-two 1-D real lines of up to
-     * 16384 points (cubic or gradient-squared term). */
+     * 1 is built for 2-D and 3-D real fields and power-of-two 1-D real lines
+     * of up to 16384 points (cubic or gradient-squared term). */
     int noise_space;
 } sft_config;
 

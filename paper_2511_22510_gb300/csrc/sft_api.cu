@@ -743,8 +743,8 @@ sft_status sft::validate_config(const sft_config* cfg, std::string& why) {
     // the 1-D variants run in the single-line kernel: power-of-two lines of up to 16384 points
     const bool line_var_ok = cfg->d == 1 && !cplx && is_pow2(cfg->n[0]) && cfg->n[0] <= 16384 &&
                              (nlk == NL_CUBIC || nlk == NL_GRAD2);
-    if (cfg->noise_space == 1 && !((cfg->d == 2 && !cplx) || line_var_ok))
-        return why = "real-space noise is built for 2-D real fields and 1-D real lines of up to 16384 points "
+    if (cfg->noise_space == 1 && !((cfg->d >= 2 && !cplx) || line_var_ok))
+        return why = "real-space noise is built for 2-D and 3-D real fields and 1-D real lines of up to 16384 points "
                      "(cubic or gradient-squared term)",
                SFT_EUNSUPPORTED;
     if (!is_pow2(cfg->n[0]) &&

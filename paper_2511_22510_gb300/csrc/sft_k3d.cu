@@ -105,9 +105,12 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
 #pragma unroll
             for (int e = 0; e < E; e += 2) {
                 float2 zz[2] = {czero(), czero()};
-                if constexpr (MODE == MODE_STEP)
-                    team_normal_pair_ks<T>(a.ks, ((uint64_t)c * N + az) * N, t, e, (uint32_t)step,
-                                        (uint32_t)(a.rep0 + rep), zz[0], zz[1]);
+                // Fourier-space draw, unless the step reads the transformed real-space draw (noise_in)
+                if constexpr (MODE == MODE_STEP) {
+                    if (!a.noise_in)
+                        team_normal_pair_ks<T>(a.ks, ((uint64_t)c * N + az) * N, t, e, (uint32_t)step,
+                                               (uint32_t)(a.rep0 + rep), zz[0], zz[1]);
+                }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int ay = t + T * (e + h);
@@ -124,7 +127,15 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
                         const float2 F = cscale(Fh, nl_prefactor(a, q).x);
                         float2 Fp = czero();
                         if (a.scheme == 2 && has_f) Fp = a.fprev[idx];
-                        o = setd_update<false>(co, state[idx], F, Fp, eta_of(zz[h], selfc));
+                        float2 eta;
+                        if (a.noise_in) {
+                            // real-space noise (Sec. IV step 2): eta_a = DFT[eta]_a / sqrt(N^3)
+                            const float2 nv = a.noise_in[idx];
+                            eta = make_float2(nv.x * a.noise_scale, selfc ? 0.f : nv.y * a.noise_scale);
+                        } else {
+                            eta = eta_of(zz[h], selfc);
+                        }
+                        o = setd_update<false>(co, state[idx], F, Fp, eta);
                         if (line < N && a.scheme == 2 && has_f) a.fprev[idx] = F;
                     } else if constexpr (MODE == MODE_TAN) {
                         // SETD2: B dF_prev with the tangent's own history (zero at the seed)

@@ -105,7 +105,6 @@ def test_r_in_F_with_setd2_unsupported(lib):
     (2, 16, 0, 2, "SFT_EINVAL"),          # no such noise space
     (1, 32768, 0, 1, "SFT_EUNSUPPORTED"), # real-space noise: 2-D real fields and 1-D lines up to 16384 points
     (1, 128, 3, 1, "SFT_EUNSUPPORTED"),   # complex line (CGL)
-    (3, 16, 0, 1, "SFT_EUNSUPPORTED"),
     (2, 16, 3, 1, "SFT_EUNSUPPORTED"),    # complex field (CGL)
 ])
 def test_real_space_noise_limits(lib, d, n, model, space, status):

@@ -375,6 +375,11 @@ RSN_CASES = [
     ("kpz_1d_1024_em_R2", W.kpz_1d(1024, replicas=2, scheme=0), 100),
     ("kpz_1d_16384_setd1", W.kpz_1d(16384, replicas=2), 20),
     ("model_a_1d_32_nodeal", W.model_a_64(d=1, n=[32], dx=[1.0], replicas=2, sigma0=0.3, dealias=0), 100),
+    # 3-D: the row pass draws and transforms along x, the plane pass transforms along y and z, the step's plane
+    # pass reads the result
+    ("model_a_3d_16_setd1_R2", W.model_a_128_3d(n=[16, 16, 16], replicas=2, sigma0=0.3), 100),
+    ("model_b_3d_32_setd2", W.model_a_128_3d(n=[32, 32, 32], model=1, p=[1.0, -0.5, 1.0, 0.2], scheme=2, h=0.01,
+                                             sigma0=0.3), 40),
 ]
 
 
