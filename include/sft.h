@@ -174,10 +174,15 @@ typedef enum {
 sft_status sft_create(const sft_config* cfg, sft_ctx** out);
 
 /* Create one context that advances several configurations together (uneven
- * lattice sizes, same model family and scheme): each sft_step of the batch
- * context advances every member by one step inside one CUDA-graph launch.
- * Replica r of the batch is member m's replica r - offset(m).  Members must
- * share d <= 1 for the fused one-kernel path; otherwise SFT_EUNSUPPORTED. */
+ * lattice sizes, the same model and scheme; custom members the same
+ * nonlinearity and field type): each sft_step of the batch context advances
+ * every member by one step inside one CUDA-graph launch.  Plain power-of-two
+ * 1-D real lines share one persistent kernel (lines of up to 8192 points, and
+ * 16384-point lines with at least twice as many replicas as SMs); every other
+ * member (2-D, 3-D, complex, longer lines, p x 2^k points, real-space noise,
+ * phase shifts) runs its own kernels on a parallel branch of the same graph.
+ * Replica r of the batch is member m's replica r - offset(m).
+ * SFT_EUNSUPPORTED for members of different models or schemes. */
 sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out);
 
 /* Copy a host real-space field of ONE replica (bytes = n0*n1*n2*sizeof(float),

@@ -1032,11 +1032,6 @@ sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
             fprintf(stderr, "sft_create_batch: member %d: %s\n", i, why.c_str());
             return vs;
         }
-        if (cfgs[i].noise_space != 0 || cfgs[i].dealias == 2 || !is_pow2(cfgs[i].n[0])) {
-            fprintf(stderr, "sft_create_batch: member %d: real-space noise, phase-shift dealiasing and p x 2^k "
-                            "lattices are built for single contexts\n", i);
-            return SFT_EUNSUPPORTED;
-        }
         if (cfgs[i].model != cfgs[0].model || cfgs[i].scheme != cfgs[0].scheme ||
             (cfgs[0].model == SFT_CUSTOM &&
              (cfgs[i].custom_nl != cfgs[0].custom_nl || cfgs[i].complex_field != cfgs[0].complex_field))) {
@@ -1083,8 +1078,10 @@ sft_status sft_create_batch(const sft_config* cfgs, int count, sft_ctx** out) {
         roff += m->R;
         const int M = m->nx / 2;
         // lines the persistent kernel takes; longer ones that the cluster kernel runs better (few replicas) go solo
-        const int lines =
-            (m->d == 1 && !m->cplx && !k1_use_cluster(m->nx, m->R, MODE_STEP)) ? batch_lines_per_item(M) : 0;
+        // members with a step variant (real-space noise, phase shifts) or p x 2^k points run their own kernels
+        // on a graph branch of their own
+        const bool plain_line = m->d == 1 && !m->cplx && c.noise_space == 0 && c.dealias != 2 && is_pow2(m->nx);
+        const int lines = (plain_line && !k1_use_cluster(m->nx, m->R, MODE_STEP)) ? batch_lines_per_item(M) : 0;
         if (lines > 0) {
             BatchMember bm{};
             bm.a = base_args(m);

@@ -85,3 +85,52 @@ def test_batch_member_against_oracle(sft, oracle_mod):
             assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
         off += w.replicas
     batch.close()
+
+
+# members with a step variant or p x 2^k points run their own kernels on graph branches of the batch step
+VARIANT_MEMBERS = [(W.kpz_1d(1024, replicas=3), dict(noise_space=1)),
+                   (W.kpz_1d(2048, replicas=2, sigma0=0.5), dict(dealias=2)),
+                   (W.kpz_1d(768, replicas=2), {}),
+                   (W.kpz_1d(4096, replicas=5), {}),
+                   (W.kpz_2d(n=[64, 64], replicas=2), dict(noise_space=1))]
+
+
+def test_batch_with_variant_members(sft, oracle_mod):
+    cfgs = []
+    for w, kw in VARIANT_MEMBERS:
+        kw = dict(kw)
+        dealias = kw.pop("dealias", w.dealias)
+        cfgs.append(sft.make_config(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias, **kw))
+    batch = sft.Batch(cfgs)
+    fields = [start_fields(w, k) for k, (w, _) in enumerate(VARIANT_MEMBERS)]
+    off = 0
+    for (w, _), f in zip(VARIANT_MEMBERS, fields):
+        for r in range(w.replicas):
+            batch.set_field(off + r, f[r])
+        off += w.replicas
+    nst = 29
+    batch.step(nst)
+    off = 0
+    for k, ((w, kw), f) in enumerate(zip(VARIANT_MEMBERS, fields)):
+        kw = dict(kw)
+        dealias = kw.pop("dealias", w.dealias)
+        g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=dealias, **kw)
+        g.set_field(f)
+        g.step(nst)
+        ref = g.field()
+        g.close()
+        for r in range(w.replicas):
+            got = batch.field(off + r, w.shape)
+            assert np.linalg.norm(got - ref[r]) / np.linalg.norm(ref[r]) <= 1e-6, (k, r)
+        if k == 0:
+            # the real-space-noise member against the oracle
+            o = oracle_mod.Oracle(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=dealias,
+                                  **kw)
+            for r in range(w.replicas):
+                o.set_field(r, f[r].astype(np.float64))
+            o.step(nst)
+            for r in range(w.replicas):
+                got = batch.field(off + r, w.shape)
+                assert np.linalg.norm(got - o.field(r)) / np.linalg.norm(o.field(r)) <= 1e-5, (k, r)
+        off += w.replicas
+    batch.close()
