@@ -439,10 +439,10 @@ static sft_status enqueue_front(sft_ctx* ctx, StepArgs& a, int k) {
     a.tw_a = ctx->tw.get(ctx->nx / 2);
     a.tw_b = ctx->tw.get(ctx->nx);
     if (a.pshift) {
-        // phase-shift dealiasing: the row pass runs over both copies of P (plain and shifted
-        // along y), 2R rows of blocks, each averaging its two x shifts
+        // phase-shift dealiasing: the row pass runs over every copy of P (2-D: plain and shifted along y; 3-D: the
+        // four shifts of y and z), each averaging its two x shifts
         StepArgs r = a;
-        r.R = 2 * ctx->R;
+        r.R = (ctx->d == 3 ? 4 : 2) * ctx->R;  // every copy of P (2-D: y shifts; 3-D: y and z shifts)
         CK(launch_rows(ctx, r, MODE_STEP_PS));
     } else {
         CK(launch_rows(ctx, a, MODE_STEP));
@@ -752,10 +752,13 @@ sft_status sft::validate_config(const sft_config* cfg, std::string& why) {
         return why = "lattices of p x 2^k points are built for 1-D and 2-D real fields (Model A/B, KPZ) with "
                      "Fourier-space noise and 2/3 truncation (or none)",
                SFT_EUNSUPPORTED;
-    if (cfg->dealias == 2 && (!((cfg->d == 2 && !cplx) || line_var_ok) || (nlk != NL_CUBIC && nlk != NL_GRAD2) ||
-                              cfg->noise_space != 0))
-        return why = "phase-shift dealiasing is built for 2-D real fields and 1-D real lines of up to 16384 points "
-                     "with the cubic or gradient-squared term and Fourier-space noise",
+    // 3-D: the plane pass keeps two planes in shared memory (planes up to 64^2)
+    const bool ps3_ok = cfg->d == 3 && !cplx && nlk == NL_CUBIC && cfg->n[0] <= 64;
+    if (cfg->dealias == 2 && (!((cfg->d == 2 && !cplx) || line_var_ok || ps3_ok) ||
+                              (nlk != NL_CUBIC && nlk != NL_GRAD2) || cfg->noise_space != 0))
+        return why = "phase-shift dealiasing is built for 2-D real fields, 1-D real lines of up to 16384 points (cubic "
+                     "or gradient-squared term) and 3-D real fields of up to 64^3 (cubic term), with Fourier-space "
+                     "noise",
                SFT_EUNSUPPORTED;
     if (cfg->model == SFT_CUSTOM) {
         const int nl = cfg->custom_nl;
@@ -832,8 +835,9 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     const size_t ms = (size_t)ctx->R * ctx->nmodes * sizeof(float2);
     const size_t rs = (size_t)ctx->R * ctx->sites * (ctx->cplx ? sizeof(float2) : sizeof(float));
     auto dalloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
-    // phase-shift dealiasing keeps a second copy of P and Q (the grid shifted along y) behind the first
-    const size_t pq = cfg->dealias == 2 ? 2 * ms : ms;
+    // phase-shift dealiasing keeps further copies of P and Q behind the first: one per shift of the axes after x
+    // (2-D: y; 3-D: y, z and both)
+    const size_t pq = cfg->dealias == 2 ? (cfg->d == 3 ? 4 : 2) * ms : ms;
     bool ok = dalloc((void**)&ctx->phi, ms) && dalloc((void**)&ctx->Q, pq);
     if (ok && ctx->d >= 2) ok = dalloc((void**)&ctx->P, pq);
     if (ok && ctx->d >= 2 && ctx->nl == NL_GRAD2) ok = dalloc((void**)&ctx->Py, pq);

@@ -217,6 +217,154 @@ __global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes(const StepArgs
     }
 }
 
+// Phase-shift dealiasing in 3-D (the alternative of Sec. IV step 1): the nonlinear term is the mean over the 8 grids
+// shifted by half a cell along every subset of the axes.  The row pass runs over four copies of P, one per shift
+// (s_y, s_z) of the y and z axes (copy s_y + 2 s_z at ps_off (s_y + 2 s_z) behind P), each row averaged over its two
+// x shifts; this plane pass combines the four copies of Q,
+//   F = M s (1/4) sum_{s_y, s_z} e^{-i pi (s_y a_y + s_z a_z) / N} DFT_yz[Q_{s_y, s_z}],
+// updates (Fourier noise, as the plain step) and emits the four copies P_{s_y, s_z} = IDFT_yz(M phi
+// e^{+i pi (s_y a_y + s_z a_z) / N} / N^3) for the next row pass.  M keeps every mode off the Nyquist planes.  Two
+// planes of shared memory (the work plane and the accumulated force, then the new state): planes up to 64^2.
+// STEP = false (prime): the emission only, from the current state.
+__device__ __forceinline__ float2 ps_phase_conj(const float2* __restrict__ tw_ps, int s) {
+    const float2 w = __ldg(&tw_ps[abs(s)]);  // e^{-i pi |s| / N}
+    return s >= 0 ? w : cconj(w);
+}
+
+template <int N, bool STEP>
+__global__ void __launch_bounds__(PlaneCfg<N>::THREADS) k3_planes_ps(const StepArgs a) {
+    using C = PlaneCfg<N>;
+    using PL = FftPlan<N>;
+    constexpr int T = PL::T, E = PL::E, RS = C::RS;
+    static_assert(N <= 64, "two planes of shared memory");
+    extern __shared__ float2 sm[];
+    float2* S = sm;
+    float2* A = sm + (size_t)N * RS;
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    float2* xb = sm + 2 * (size_t)N * RS + (size_t)team * C::XB;
+    const int c = blockIdx.x, rep = blockIdx.y;
+    const int M = a.nx / 2;
+    const size_t base = ((size_t)rep * a.hx + c) * (size_t)N * N;
+    const float2* __restrict__ tw = a.tw_a;
+    const float2* __restrict__ tps = a.tw_ps;
+    const bool plane = (c == 0 || c == M);
+    const bool has_f = c < a.ncols;  // every x-mode but the Nyquist one
+    // the phase e^{-i pi (s_y a_y + s_z a_z) / N} of copy cp = s_y + 2 s_z at plane entry (az, ay)
+    auto phase = [&](int cp, int az, int ay) {
+        float2 ph = make_float2(1.f, 0.f);
+        if (cp & 1) ph = ps_phase_conj(tps, signed_idx(ay, N));
+        if (cp & 2) ph = cmul(ph, ps_phase_conj(tps, signed_idx(az, N)));
+        return ph;
+    };
+    if constexpr (STEP) {
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x) A[(f / N) * RS + f % N] = czero();
+        __syncthreads();
+        if (has_f) {
+            for (int cp = 0; cp < 4; ++cp) {
+                const float2* q = a.qin + (size_t)cp * a.ps_off + base;
+                block_copy<C::THREADS, N * N>(
+                    N * N, [&](int f) { return q[f]; }, [&](int f, float2 v) { S[(f / N) * RS + f % N] = v; });
+                __syncthreads();
+                plane_fft<N, true, false>(S, xb, team, t, tw);
+                __syncthreads();
+                plane_fft<N, false, false>(S, xb, team, t, tw);
+                __syncthreads();
+                for (int f = threadIdx.x; f < N * N; f += blockDim.x) {
+                    const int az = f / N, ay = f % N;
+                    A[az * RS + ay] = cadd(A[az * RS + ay], cmul(S[az * RS + ay], phase(cp, az, ay)));
+                }
+                __syncthreads();
+            }
+        }
+        const long long step = current_step(a);
+        const bool first = (a.scheme == 2) && (step == *a.first_step);
+        for (int it = 0; it < C::ITERS; ++it) {
+            const int line = team + it * C::TEAMS;
+            const int az = line < N ? line : N - 1;
+            const int azs = signed_idx(az, N);
+#pragma unroll
+            for (int e = 0; e < E; e += 2) {
+                float2 zz[2];
+                team_normal_pair_ks<T>(a.ks, ((uint64_t)c * N + az) * N, t, e, (uint32_t)step,
+                                       (uint32_t)(a.rep0 + rep), zz[0], zz[1]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ay = t + T * (e + h);
+                    const int ays = signed_idx(ay, N);
+                    const int q = c * c + ays * ays + azs * azs;
+                    const bool inm = has_f && 2 * abs(ays) != N && 2 * abs(azs) != N;
+                    const float2 F = inm ? cscale(A[az * RS + ay], 0.25f * nl_prefactor(a, q).x) : czero();
+                    const Coefs co = load_coefs<false>(a.tab, q, first);
+                    const size_t idx = base + (size_t)az * N + ay;
+                    const int mz = (N - az) % N, my = (N - ay) % N;
+                    const bool selfc = plane && az == mz && ay == my;
+                    float2 Fp = czero();
+                    if (a.scheme == 2 && has_f) Fp = a.fprev[idx];
+                    float2 o = setd_update<false>(co, a.phi[idx], F, Fp, eta_of(zz[h], selfc));
+                    if (line < N && a.scheme == 2 && has_f) a.fprev[idx] = F;
+                    if (selfc) o.y = 0.f;
+                    if (line < N) A[az * RS + ay] = o;
+                }
+            }
+        }
+        __syncthreads();
+        if (plane) {
+            for (int f = threadIdx.x; f < N * N; f += blockDim.x) {
+                const int az = f / N, ay = f % N;
+                const int mz = (N - az) % N, my = (N - ay) % N;
+                if (az > mz || (az == mz && ay > my)) A[az * RS + ay] = cconj(A[mz * RS + my]);
+            }
+            __syncthreads();
+        }
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x) {
+            const float2 o = A[(f / N) * RS + f % N];
+            a.phi[base + f] = o;
+            flag_nonfinite(a, o, step);
+        }
+    } else {
+        block_copy<C::THREADS, N * N>(
+            N * N, [&](int f) { return a.phi[base + f]; }, [&](int f, float2 v) { A[(f / N) * RS + f % N] = v; });
+    }
+    if (!has_f) return;  // whole block: P carries the x-modes off the Nyquist one
+    for (int cp = 0; cp < 4; ++cp) {
+        __syncthreads();
+        for (int f = threadIdx.x; f < N * N; f += blockDim.x) {
+            const int az = f / N, ay = f % N;
+            const bool inm = 2 * abs(signed_idx(ay, N)) != N && 2 * abs(signed_idx(az, N)) != N;
+            S[az * RS + ay] = inm ? cscale(cmul(A[az * RS + ay], cconj(phase(cp, az, ay))), a.scale) : czero();
+        }
+        __syncthreads();
+        plane_fft<N, false, true>(S, xb, team, t, tw);
+        __syncthreads();
+        plane_fft<N, true, true>(S, xb, team, t, tw);
+        __syncthreads();
+        float2* dst = a.pout + (size_t)cp * a.ps_off + base;
+        block_copy<C::THREADS, N * N>(
+            N * N, [&](int f) { return S[(f / N) * RS + f % N]; }, [&](int f, float2 v) { dst[f] = v; });
+    }
+}
+
+template <int N, bool STEP>
+static cudaError_t run_planes_ps(const StepArgs& a, cudaStream_t s) {
+    using C = PlaneCfg<N>;
+    const size_t sm = C::smem() + sizeof(float2) * (size_t)N * C::RS;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k3_planes_ps<N, STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k3_planes_ps<N, STEP><<<dim3(a.hx, a.R), C::THREADS, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t planes_ps_for(const StepArgs& a, int mode, cudaStream_t s) {
+    if (mode == MODE_STEP) return run_planes_ps<N, true>(a, s);
+    if (mode == MODE_PRIME) return run_planes_ps<N, false>(a, s);
+    return cudaErrorInvalidValue;
+}
+
 template <int N, int MODE>
 static cudaError_t run_planes(const StepArgs& a, cudaStream_t s) {
     using C = PlaneCfg<N>;
@@ -253,6 +401,15 @@ bool k3_supported(int nx, int ny, int nz, int complex_field) {
 
 cudaError_t launch_k3_planes(const StepArgs& a, int mode, int nl, cudaStream_t s) {
     if (nl != NL_CUBIC) return cudaErrorInvalidValue;
+    if (a.pshift && (mode == MODE_STEP || mode == MODE_PRIME)) {
+        if (!a.tw_ps) return cudaErrorInvalidValue;
+        switch (a.ny) {
+            case 16: return planes_ps_for<16>(a, mode, s);
+            case 32: return planes_ps_for<32>(a, mode, s);
+            case 64: return planes_ps_for<64>(a, mode, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.ny) {
         case 16: return planes_for<16>(a, mode, s);
         case 32: return planes_for<32>(a, mode, s);

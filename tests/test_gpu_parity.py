@@ -442,6 +442,11 @@ PS_CASES = [
     ("kpz_1d_1024_em_R2", W.kpz_1d(1024, replicas=2, scheme=0, sigma0=0.5), 100),
     ("kpz_1d_16384_setd1", W.kpz_1d(16384, replicas=2, sigma0=0.5), 20),
     ("model_a_1d_32_setd2", W.model_a_64(d=1, n=[32], dx=[1.0], replicas=2, sigma0=0.3, scheme=2), 100),
+    # 3-D: four copies of P (shifts of y and z), each row averaged over its two x shifts (eight grids in all)
+    ("model_a_3d_16_setd1_R2", W.model_a_128_3d(n=[16, 16, 16], replicas=2, sigma0=0.3), 100),
+    ("model_b_3d_32_setd2", W.model_a_128_3d(n=[32, 32, 32], model=1, p=[1.0, -0.5, 1.0, 0.2], scheme=2, h=0.01,
+                                             sigma0=0.3), 40),
+    ("model_a_3d_64_em", W.model_a_128_3d(n=[64, 64, 64], scheme=0, sigma0=0.3), 10),
 ]
 
 
@@ -482,6 +487,19 @@ def test_line_variants_graph_plain_and_rejections(sft, variant):
     c = W.cgl_2048(d=1, n=[128], dx=[0.5], replicas=1)
     with pytest.raises(sft.SftError):
         sft.Stepper(c.d, c.n, c.dx, 1, c.model, c.p, c.scheme, c.h, 1, **kw)
+
+
+def test_phase_shift_3d_graph_and_plain_bit_identical(sft):
+    w = W.model_a_128_3d(n=[16, 16, 16], replicas=2, sigma0=0.3, scheme=2, dealias=2)
+    a, b = gpu_stepper(sft, w), gpu_stepper(sft, w)
+    f = W.initial_fields(w).astype(np.float32)
+    a.set_field(f)
+    b.set_field(f)
+    a.step(23)
+    b.step_plain(23)
+    assert np.array_equal(a.spectrum().view(np.uint64), b.spectrum().view(np.uint64))
+    for s in (a, b):
+        s.close()
 
 
 def test_phase_shift_graph_plain_and_checkpoint(sft):
