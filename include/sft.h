@@ -111,8 +111,8 @@ typedef struct {
                         * 2^d grids shifted by half a cell along every subset of the axes, every
                         * mode but the Nyquist ones kept (alias-free for the cubic and the gradient-
                         * squared terms); built for 2-D real fields and power-of-two 1-D real lines of up
-                        * to 16384 points (Model A/B, KPZ) and 3-D real fields up to 64^3 (cubic term),
-                        * with noise_space 0, at two (2-D) or four (3-D) times the P/Q memory and two to
+                        * to 16384 points (Model A/B, KPZ), 3-D real fields up to 64^3 (cubic term) and
+                        * 2-D complex fields (CGL), with noise_space 0, at two (2-D) or four (3-D) times the P/Q memory and two to
                         * four times the transform work of a step */
     int precision;     /* 0: FP32 state and transforms; 1: the split-BF16x3 tensor-core transforms of
                         * the precision study (complex 2-D fields of 1024^2 or 2048^2 points) */

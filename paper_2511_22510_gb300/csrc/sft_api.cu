@@ -752,13 +752,15 @@ sft_status sft::validate_config(const sft_config* cfg, std::string& why) {
         return why = "lattices of p x 2^k points are built for 1-D and 2-D real fields (Model A/B, KPZ) with "
                      "Fourier-space noise and 2/3 truncation (or none)",
                SFT_EUNSUPPORTED;
-    // 3-D: the plane pass keeps two planes in shared memory (planes up to 64^2)
+    // 3-D: the plane pass keeps two planes in shared memory (planes up to 64^2); complex fields: 2-D, |A|^2 A
     const bool ps3_ok = cfg->d == 3 && !cplx && nlk == NL_CUBIC && cfg->n[0] <= 64;
-    if (cfg->dealias == 2 && (!((cfg->d == 2 && !cplx) || line_var_ok || ps3_ok) ||
-                              (nlk != NL_CUBIC && nlk != NL_GRAD2) || cfg->noise_space != 0))
+    const bool psc_ok = cfg->d == 2 && cplx && nlk == NL_CGL && cfg->precision == 0;
+    const bool ps_real = (cfg->d == 2 && !cplx) || line_var_ok || ps3_ok;
+    if (cfg->dealias == 2 && (!(ps_real || psc_ok) || (!psc_ok && nlk != NL_CUBIC && nlk != NL_GRAD2) ||
+                              cfg->noise_space != 0))
         return why = "phase-shift dealiasing is built for 2-D real fields, 1-D real lines of up to 16384 points (cubic "
-                     "or gradient-squared term) and 3-D real fields of up to 64^3 (cubic term), with Fourier-space "
-                     "noise",
+                     "or gradient-squared term), 3-D real fields of up to 64^3 (cubic term) and 2-D complex fields "
+                     "(|A|^2 A), with Fourier-space noise",
                SFT_EUNSUPPORTED;
     if (cfg->model == SFT_CUSTOM) {
         const int nl = cfg->custom_nl;

@@ -23,6 +23,12 @@ __device__ __forceinline__ int ccomp_x(int ax, int nx, int ncols) {
     return ax < m ? ax : ax - (nx - ncols);
 }
 
+// e^{-i pi s / N} for the signed index s, |s| <= N / 2, from tw_ps[m] = e^{-i pi m / N} (half-cell shift phase)
+__device__ __forceinline__ float2 cps_phase_conj(const float2* __restrict__ tw_ps, int s) {
+    const float2 w = __ldg(&tw_ps[abs(s)]);
+    return s >= 0 ? w : cconj(w);
+}
+
 template <int N>
 struct CRowCfg {
     using PL = FftPlan<N>;
@@ -106,6 +112,66 @@ __global__ void __launch_bounds__(CRowCfg<N>::THREADS) k2_rows_cplx(const StepAr
         };
         if constexpr (TAN) store(sm, a.qout);
         store(sm + ROWS * TS, a.dqout);
+        return;
+    }
+    if constexpr (MODE == MODE_STEP_PS) {
+        // phase-shift dealiasing along x (the alternative of Sec. IV step 1): |A|^2 A on the plain grid and on the
+        // grid shifted by half a cell along x (input phases e^{i pi a_x / N}, output e^{-i pi a_x / N}, signed
+        // a_x), averaged.  The block's rows are those of one copy of P (plain or shifted along y: blockIdx.y runs
+        // over 2R copies); tile 1 holds a second copy of the rows for the shifted evaluation.  The compact columns
+        // are every a_x but the Nyquist one.
+        float2* srow = sm + (ROWS + team) * TS;
+        auto load = [&](float2* dst) {
+            block_copy<C::THREADS, ROWS * N>(
+                ROWS * ncols,
+                [&](int f) {
+                    const int c = f / ROWS, yy = f % ROWS;
+                    return (y0 + yy < ny) ? a.pin[((size_t)rep * hx + c) * ny + y0 + yy] : czero();
+                },
+                [&](int f, float2 v) { dst[(f % ROWS) * TS + f / ROWS] = v; });
+        };
+        load(sm);
+        load(sm + ROWS * TS);
+        __syncthreads();
+        const float2* __restrict__ tps = a.tw_ps;
+        auto eval = [&](float2* row, bool shift) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ax = t + T * e;
+                float2 v = cmask_x(ax, nx, ncols) ? row[ccomp_x(ax, nx, ncols)] : czero();
+                if (shift) v = cmul(v, cconj(cps_phase_conj(tps, signed_idx(ax, nx))));
+                z[e] = v;
+            }
+            fft_line<N, true>(z, row, t, tw);
+#pragma unroll
+            for (int e = 0; e < E; ++e) z[e] = cscale(z[e], z[e].x * z[e].x + z[e].y * z[e].y);
+            fft_line<N, false>(z, row, t, tw);
+            team_sync<T>();
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ax = t + T * e;
+                if (cmask_x(ax, nx, ncols))
+                    row[ccomp_x(ax, nx, ncols)] = shift ? cmul(z[e], cps_phase_conj(tps, signed_idx(ax, nx))) : z[e];
+            }
+        };
+        eval(trow, false);
+        eval(srow, true);
+        // each thread reads back the entries it wrote itself
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int ax = t + T * e;
+            if (cmask_x(ax, nx, ncols)) {
+                const int cc = ccomp_x(ax, nx, ncols);
+                trow[cc] = cscale(cadd(trow[cc], srow[cc]), 0.5f);
+            }
+        }
+        __syncthreads();
+        block_copy<C::THREADS, ROWS * N>(
+            ROWS * ncols, [&](int f) { return sm[(f % ROWS) * TS + f / ROWS]; },
+            [&](int f, float2 v) {
+                const int c = f / ROWS, yy = f % ROWS;
+                if (y0 + yy < ny) a.qout[((size_t)rep * hx + c) * ny + y0 + yy] = v;
+            });
         return;
     }
     if constexpr (MODE == MODE_FWD) {
@@ -194,7 +260,8 @@ __global__ void __launch_bounds__(CColCfg<NY>::THREADS, 512 / CColCfg<NY>::THREA
     const int nx = a.nx, ncols = a.ncols;
     float2* xb = sm + team * XB;
     const float2* __restrict__ tw = a.tw_a;
-    const bool inx = !a.dealias || cmask_x(ax, nx, ncols);
+    // carried x-column: 2/3 truncation or phase shifts (every column but the Nyquist one) use the compact order
+    const bool inx = (!a.dealias && !a.pshift) || cmask_x(ax, nx, ncols);
     const int axs = signed_idx(ax, nx);
     if (!valid && T >= 32) return;
     for (int ri = 0; ri < kCRpb; ++ri) {
@@ -255,6 +322,46 @@ __global__ void __launch_bounds__(CColCfg<NY>::THREADS, 512 / CColCfg<NY>::THREA
                     float2 Fp = czero();
                     if (a.scheme == 2 && has_f) Fp = sfp[ay];
                     out[e] = setd_update<true>(co, sphi[ay], F, Fp, eta_of(out[e], false));
+                    if (a.scheme == 2 && has_f && valid) a.fprev[colbase + ay] = F;
+                }
+                if (valid) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        a.phi[colbase + t + T * e] = out[e];
+                        flag_nonfinite(a, out[e], step);
+                    }
+                }
+            } else if constexpr (MODE == MODE_STEP_PS) {
+                // phase-shift dealiasing: F = M s (Q0^ + e^{-i pi a_y / N} Q1^) / 2 from the row pass's plain (Q0)
+                // and y-shifted (Q1) copies, each already averaged over its two x shifts; M keeps every mode off
+                // the Nyquist lines; P0, P1 are emitted below
+                const long long step = current_step(a);
+                const bool first = (a.scheme == 2) && (step == *a.first_step);
+                const bool has_f = valid && inx;
+                float2 v1[E];
+                if (has_f || T < 32) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        v[e] = has_f ? a.qin[cbase + t + T * e] : czero();
+                        v1[e] = has_f ? a.qin[a.ps_off + cbase + t + T * e] : czero();
+                    }
+                    fft_line<NY, false>(v, xb, t, tw);
+                    fft_line<NY, false>(v1, xb, t, tw);
+                }
+                const float2 s = make_float2(a.s0, a.s0i);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & 1) == 0)
+                        team_normal_pair_ks<T>(a.ks, (uint64_t)ax * NY, t, e, (uint32_t)step, (uint32_t)(a.rep0 + rep),
+                                               out[e], out[e + 1]);
+                    const int ay = t + T * e;
+                    const int ays = signed_idx(ay, NY);
+                    const bool inm = has_f && 2 * abs(ays) != NY;
+                    const float2 qa = cscale(cadd(v[e], cmul(v1[e], cps_phase_conj(a.tw_ps, ays))), 0.5f);
+                    const float2 F = inm ? cmul(s, qa) : czero();
+                    const Coefs co = load_coefs<true>(a.tab, abs(axs) * (NY / 2 + 1) + abs(ays), first);
+                    const float2 Fp = (a.scheme == 2 && has_f) ? a.fprev[colbase + ay] : czero();
+                    out[e] = setd_update<true>(co, a.phi[colbase + ay], F, Fp, eta_of(out[e], false));
                     if (a.scheme == 2 && has_f && valid) a.fprev[colbase + ay] = F;
                 }
                 if (valid) {
@@ -383,7 +490,27 @@ __global__ void __launch_bounds__(CColCfg<NY>::THREADS, 512 / CColCfg<NY>::THREA
                 for (int e = 0; e < E; ++e) out[e] = a.phi[colbase + t + T * e];
             }
             const bool has_p = valid && inx;
-            if (has_p || T < 32) {
+            if (a.pshift) {
+                // phase shifts: P0 <- IFFT_y(M phi / N^2), P1 <- IFFT_y(M phi e^{i pi a_y / N} / N^2) at ps_off
+                if (has_p || T < 32) {
+#pragma unroll
+                    for (int cp = 0; cp < 2; ++cp) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            const int ays = signed_idx(t + T * e, NY);
+                            const bool inm = has_p && 2 * abs(ays) != NY;
+                            float2 x = cscale(out[e], a.scale);
+                            if (cp) x = cmul(x, cconj(cps_phase_conj(a.tw_ps, ays)));
+                            v[e] = inm ? x : czero();
+                        }
+                        fft_line<NY, true>(v, xb, t, tw);
+                        if (has_p) {
+#pragma unroll
+                            for (int e = 0; e < E; ++e) a.pout[cp * a.ps_off + cbase + t + T * e] = v[e];
+                        }
+                    }
+                }
+            } else if (has_p || T < 32) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int ay = t + T * e;
@@ -403,7 +530,7 @@ __global__ void __launch_bounds__(CColCfg<NY>::THREADS, 512 / CColCfg<NY>::THREA
 template <int N, int MODE>
 static cudaError_t run_crows(const StepArgs& a, cudaStream_t s) {
     using C = CRowCfg<N>;
-    const size_t sm = (MODE == MODE_TAN || MODE == MODE_ADJ ? 2 : 1) * C::smem();
+    const size_t sm = (MODE == MODE_TAN || MODE == MODE_ADJ || MODE == MODE_STEP_PS ? 2 : 1) * C::smem();
     static bool attr = false;
     if (!attr) {
         cudaError_t e =
@@ -437,6 +564,7 @@ static cudaError_t crows_for(const StepArgs& a, int mode, cudaStream_t s) {
         case MODE_INV: return run_crows<N, MODE_INV>(a, s);
         case MODE_TAN: return run_crows<N, MODE_TAN>(a, s);
         case MODE_ADJ: return run_crows<N, MODE_ADJ>(a, s);
+        case MODE_STEP_PS: return run_crows<N, MODE_STEP_PS>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -451,6 +579,7 @@ static cudaError_t ccols_for(const StepArgs& a, int mode, cudaStream_t s) {
         case MODE_TAN: return run_ccols<NY, MODE_TAN>(a, s);
         case MODE_ADJ: return run_ccols<NY, MODE_ADJ>(a, s);
         case MODE_ADJ_PRIME: return run_ccols<NY, MODE_ADJ_PRIME>(a, s);
+        case MODE_STEP_PS: return run_ccols<NY, MODE_STEP_PS>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -461,6 +590,7 @@ bool k2c_supported(int nx, int ny) {
 }
 
 cudaError_t launch_k2c_rows(const StepArgs& a, int mode, cudaStream_t s) {
+    if (mode == MODE_STEP_PS && !a.tw_ps) return cudaErrorInvalidValue;
     switch (a.nx) {
         case 16: return crows_for<16>(a, mode, s);
         case 32: return crows_for<32>(a, mode, s);
@@ -476,6 +606,8 @@ cudaError_t launch_k2c_rows(const StepArgs& a, int mode, cudaStream_t s) {
 }
 
 cudaError_t launch_k2c_cols(const StepArgs& a, int mode, cudaStream_t s) {
+    if (a.pshift && mode == MODE_STEP) mode = MODE_STEP_PS;
+    if (a.pshift && !a.tw_ps) return cudaErrorInvalidValue;
     switch (a.ny) {
         case 16: return ccols_for<16>(a, mode, s);
         case 32: return ccols_for<32>(a, mode, s);

@@ -117,7 +117,7 @@ def test_real_space_noise_limits(lib, d, n, model, space, status):
 
 @pytest.mark.parametrize("d,n,model,space", [
     (1, 32768, 0, 0), (3, 128, 0, 0),  # phase shifts: 2-D real fields, 1-D lines up to 16384 points, 3-D up to 64^3
-    (2, 16, 3, 0), (1, 128, 3, 0),    # complex fields (CGL)
+    (1, 128, 3, 0),                   # complex lines (CGL; 2-D complex fields are built)
     (2, 16, 0, 1), (1, 256, 0, 1),    # with real-space noise
 ])
 def test_phase_shift_dealiasing_limits(lib, d, n, model, space):

@@ -447,6 +447,11 @@ PS_CASES = [
     ("model_b_3d_32_setd2", W.model_a_128_3d(n=[32, 32, 32], model=1, p=[1.0, -0.5, 1.0, 0.2], scheme=2, h=0.01,
                                              sigma0=0.3), 40),
     ("model_a_3d_64_em", W.model_a_128_3d(n=[64, 64, 64], scheme=0, sigma0=0.3), 10),
+    # complex fields (CGL): the complex row pass averages its two x shifts, the column pass the two y copies
+    ("cgl_32_setd2_R2", W.cgl_2048(n=[32, 32], replicas=2), 100),
+    ("cgl_256_setd1", W.cgl_2048(n=[256, 256], scheme=1, p=[0.5, 0.3, 1e-2]), 40),
+    ("cgl_64_em", W.cgl_2048(n=[64, 64], scheme=0, p=[0.5, 0.3, 1e-2], sigma0=0.3), 100),
+    ("cgl_2048_setd2", W.cgl_2048(replicas=1), 3),
 ]
 
 
