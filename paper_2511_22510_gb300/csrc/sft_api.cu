@@ -21,6 +21,8 @@ namespace sft {
 // complex 2-D step on columns of 1024 or 2048 points, one warp per 1024 points (sft_k2c_colwarp.cu)
 bool k2c_colwarp_supported(int ny);
 cudaError_t launch_k2c_cols_warp(const StepArgs& a, cudaStream_t s);
+bool k2c_rowwarp_supported(int nx, int ny, int dealias);
+cudaError_t launch_k2c_rows_warp(const StepArgs& a, cudaStream_t s);
 }  // namespace sft
 
 using namespace sft;
@@ -217,6 +219,10 @@ static cudaError_t launch_rows(const sft_ctx* ctx, StepArgs a, int mode) {
     a.nz = 1;
     if (ctx->cplx) {
         a.tw_a = ctx->tw.get(ctx->nx);
+        // the step on complex rows of 1024 or 2048 points under 2/3 truncation: warp-resident transforms
+        if (mode == MODE_STEP && ctx->d == 2 && a.tw_32 && !a.pshift &&
+            k2c_rowwarp_supported(ctx->nx, ctx->ny, ctx->cfg.dealias))
+            return launch_k2c_rows_warp(a, ctx->stream);
         return launch_k2c_rows(a, mode, ctx->stream);
     }
     return launch_k2_rows(a, mode, ctx->nl, ctx->stream, mode == MODE_STEP ? ctx->row_shape : 0);
@@ -889,7 +895,8 @@ sft_status sft_create(const sft_config* cfg, sft_ctx** out) {
     if (ctx->d == 1 && !ctx->cplx && k1_cluster_fft_len(ctx->nx))
         lens.push_back(k1_cluster_fft_len(ctx->nx));  // per-block FFT of the cluster kernel
     if (build_twiddles(ctx, lens) != SFT_OK) return cleanup(SFT_ECUDA);
-    if (ctx->d >= 2 && (ctx->cplx ? (ctx->d == 2 && k2c_colwarp_supported(ctx->ny))
+    if (ctx->d >= 2 && (ctx->cplx ? (ctx->d == 2 && (k2c_colwarp_supported(ctx->ny) ||
+                                                     k2c_rowwarp_supported(ctx->nx, ctx->ny, cfg->dealias)))
                                   : (ctx->nx == 1024 || ctx->ny == 1024))) {
         // twiddles of the 1024-point warp transforms: entry k1 32 + t = W_1024^{t k1}
         if (!dalloc((void**)&ctx->tw32, 1024 * sizeof(float2)) || launch_twiddles32(ctx->tw32, ctx->stream) != cudaSuccess)

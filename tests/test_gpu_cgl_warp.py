@@ -1,10 +1,11 @@
-"""The complex 2-D step (CGL, Sec. V.C) on columns of 1024 and 2048 points,
-whose column pass holds each column in one or two warps (warp-resident
-1024-point transforms; the 2048-point columns split by parity across two
-warps), against the FP64 oracle from the same FP32 initial fields: relative L2
-<= 1e-5 per replica and every mode within 1e-4 of the RMS mode amplitude, for
-SETD-EM, SETD1 and SETD2, with and without 2/3 truncation.  The oracle runs one
-context per replica in threads (its C library releases the GIL)."""
+"""The complex 2-D step (CGL, Sec. V.C) on columns and rows of 1024 and 2048
+points, whose passes hold each line in one or two warps (warp-resident
+1024-point transforms; the 2048-point lines split across two warps), against
+the FP64 oracle from the same FP32 initial fields: relative L2 <= 1e-5 per
+replica and every mode within 1e-4 of the RMS mode amplitude, for SETD-EM,
+SETD1 and SETD2, with and without 2/3 truncation (the warp row pass runs under
+truncation, the general row pass without).  The oracle runs one context per
+replica in threads (its C library releases the GIL)."""
 import threading
 
 import numpy as np
