@@ -141,8 +141,10 @@ __global__ void __launch_bounds__(kCcWarps * 32, 5) k2c_cols_warp(const StepArgs
         fft1024_warp<false, 0u>(v, xb, lane, tw32);
         if constexpr (H == 2) {
             if (h == 1) {
+                // W_NY^k for k = lane + 32 e, e = 2 j + p: W_NY^{lane + 32 p} times the constant W_32^j
+                const float2 w0 = __ldg(&twN[lane]), w1 = __ldg(&twN[lane + 32]);
 #pragma unroll
-                for (int e = 0; e < 32; ++e) v[e] = cmul(v[e], __ldg(&twN[lane + 32 * e]));
+                for (int e = 0; e < 32; ++e) v[e] = twiddle_const<false>(cmul(v[e], (e & 1) ? w1 : w0), e >> 1, 32);
             }
 #pragma unroll
             for (int e = 0; e < 32; ++e) xb[lane + 32 * e] = v[e];
@@ -175,12 +177,14 @@ __global__ void __launch_bounds__(kCcWarps * 32, 5) k2c_cols_warp(const StepArgs
     if (has_f) {
         float2 v[32];
         if constexpr (H == 2) {
+            const float2 w0 = cconj(__ldg(&twN[lane])), w1 = cconj(__ldg(&twN[lane + 32]));
             pair_sync(bar);  // both halves of the new column are in the buffers
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
                 const int k = lane + 32 * e;
                 const float2 lo = (h == 0) ? xb[k] : xo[k], hi = (h == 0) ? xo[k] : xb[k];
-                v[e] = (h == 0) ? cadd(lo, hi) : cmul(csub(lo, hi), cconj(__ldg(&twN[k])));
+                v[e] = (h == 0) ? cadd(lo, hi)
+                                : twiddle_const<true>(cmul(csub(lo, hi), (e & 1) ? w1 : w0), e >> 1, 32);
             }
             pair_sync(bar);
         } else {

@@ -112,6 +112,12 @@ __global__ void __launch_bounds__(kCrWarps * 32, 2)
     constexpr int EH = (C::NX - C::M + 1 + 31) / 32;  // first slot whose every index is a high mode (H = 1)
     const int base_lo = (int)cr_off<H>(lane, r);
     const int base_hi = (int)(H == 1 ? cr_off<H>(lane + 32 * EH - CSH, r) : cr_off<H>(lane + 1024 - CSH, r));
+    // W_NX^k for k = lane + 32 e, e = 2 j + p, as W_NX^{lane + 32 p} times the constant W_32^j (H = 2)
+    float2 wl[2] = {czero(), czero()};
+    if constexpr (H == 2) {
+        wl[0] = __ldg(&twN[lane]);
+        wl[1] = __ldg(&twN[lane + 32]);
+    }
     float2 v[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
@@ -130,7 +136,7 @@ __global__ void __launch_bounds__(kCrWarps * 32, 2)
             const bool lo = k < C::M, hi = k + 1024 >= C::NX - C::M + 1;
             const float2 x0 = lo ? *reinterpret_cast<const float2*>(tile + base_lo + ESTEP * e) : czero();
             const float2 x1 = hi ? *reinterpret_cast<const float2*>(tile + base_hi + ESTEP * e) : czero();
-            v[e] = h == 0 ? padd(x0, x1) : cmul(psub(x0, x1), cconj(__ldg(&twN[k])));
+            v[e] = h == 0 ? padd(x0, x1) : twiddle_const<true>(cmul(psub(x0, x1), cconj(wl[e & 1])), e >> 1, 32);
         }
     }
     __syncthreads();  // every warp has read the tile: it is free for Q
@@ -144,7 +150,7 @@ __global__ void __launch_bounds__(kCrWarps * 32, 2)
         // warp 0 holds E[k] (even samples), warp 1 O[k]; X[k] = E + W^k O, X[k + 1024] = E - W^k O
         if (h == 1) {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] = cmul(v[e], __ldg(&twN[lane + 32 * e]));
+            for (int e = 0; e < 32; ++e) v[e] = twiddle_const<false>(cmul(v[e], wl[e & 1]), e >> 1, 32);
         }
 #pragma unroll
         for (int e = 0; e < 32; ++e) xb[lane + 32 * e] = v[e];
