@@ -1,7 +1,8 @@
 """Failure detection of the bounded device-side waits, without a GPU fault.
 
 Kernels that wait on an mbarrier for their own bulk/TMA copies (the
-two-rows-per-warp row pass and the pipelined column pass) bound every wait;
+two-rows-per-warp row pass, the pipelined column pass and the warp row pass
+of complex fields) bound every wait;
 a wait that runs out sets the time-out bit of the context's status word, lets
 its copies in flight land and returns, and the next synchronising call reports
 SFT_ETIMEOUT.  SFT_WAIT_LIMIT=-1 in the environment of a new context gives its
@@ -55,6 +56,34 @@ def test_wait_runs_out_and_the_device_stays_usable(sft, oracle_mod, plan, monkey
     o = oracle_mod.Oracle(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
     for r in range(w.replicas):
         o.set_field(r, f0[r].astype(np.float64))
+    o.step(3)
+    for r in range(w.replicas):
+        ref = o.field(r)
+        assert np.linalg.norm(got[r] - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+def test_complex_warp_row_pass_wait_runs_out(sft, oracle_mod, monkeypatch):
+    """The same on the complex (CGL) step at 1024^2 under 2/3 truncation, whose
+    row pass loads its tiles by TMA."""
+    w = W.cgl_2048(n=[1024, 1024], replicas=2)
+    f0 = W.initial_fields(w).astype(np.complex64)
+    monkeypatch.setenv("SFT_WAIT_LIMIT", "-1")
+    g = stepper(sft, w)
+    g.set_field(f0)
+    with pytest.raises(sft.SftError) as ei:
+        g.step(1)
+        g.sync()
+    assert ei.value.status == sft.SFT_ETIMEOUT
+    g.close()
+    monkeypatch.delenv("SFT_WAIT_LIMIT")
+    g = stepper(sft, w)
+    g.set_field(f0)
+    g.step(3)
+    got = g.field().astype(np.complex128)
+    g.close()
+    o = oracle_mod.Oracle(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
+    for r in range(w.replicas):
+        o.set_field(r, f0[r].astype(np.complex128))
     o.step(3)
     for r in range(w.replicas):
         ref = o.field(r)
