@@ -109,6 +109,28 @@ def algorithmic_bytes(w, scheme, ncols):
     return rows, cols
 
 
+def algorithmic_bytes_complex(nx, ny, scheme, dealias):
+    """The same counts per replica for the complex 2-D step (CGL): the spectrum
+    holds every a_x (nx columns); the intermediates carry the a_x with
+    3 |a_x| < nx in compact order (2 ((nx - 1) // 3) + 1 columns) under 2/3
+    truncation, all nx without it."""
+    mx = 2 * ((nx - 1) // 3) + 1 if dealias == 1 else nx
+    rows = 2 * mx * ny * 8
+    cols = (2 * mx + 2 * nx) * ny * 8
+    if scheme == 2:
+        cols += 2 * mx * ny * 8
+    return rows, cols
+
+
+def hbm_roofline(kernel, alg_bytes, launch_ms):
+    """Roofline entry of one kernel against the measured HBM copy bandwidth."""
+    peak, src = measured_peak()
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "alg_bytes_per_launch": alg_bytes, "launch_ms": launch_ms,
+            "peak_source": src}
+
+
 # sources each recorded kernel is compiled from: its translation unit and the headers it includes
 KERNEL_SOURCES = {
     "k2_cols_real": ["sft_k2d_cols.cu", "sft_k2d_cols.cuh", "sft_step_common.cuh", "sft_device.cuh", "sft_async.cuh",
@@ -716,6 +738,12 @@ def run_other(args):
                      "kernels_ms": list(map(float, prof)),
                      "plain": {"value": plain, "unit": UNIT, "replicas": 1, "graph": False,
                                "batched_speedup": value / plain}})
+        if args.workload == "cgl_2048" and not prec and w.n[0] in (1024, 2048) and w.dealias == 1:
+            # the warp row and column passes (both lines of 1024 or 2048 points under 2/3 truncation)
+            rb, cb = algorithmic_bytes_complex(w.n[0], w.n[1], w.scheme, w.dealias)
+            line["roofline"] = hbm_roofline("k2c_cols_warp", cb * w.replicas, float(prof[1]))
+            line["roofline"]["traffic"] = None
+            line["roofline_row_pass"] = hbm_roofline("k2c_rows_warp", rb * w.replicas, float(prof[0]))
     print(json.dumps(line), flush=True)
 
 
