@@ -190,6 +190,43 @@ def test_ou_stationary_variance_identity(oracle_mod):
                 assert abs(var - ref) <= 1e-12 * ref
 
 
+def test_complex_c_coefficients_closed_forms(oracle_mod):
+    """CGL, c_a = 1 - (1 + i alpha) k^2 complex (Sec. V.C): f1 = e^{c h}; the
+    exact integrals of Sec. II, A = int_0^h e^{c (h - s)} ds = (e^{ch} - 1)/c
+    (SETD-EM, SETD1) and, with the linear interpolation of F, A = ((1 + ch) e^{ch} - 1
+    - 2ch)/(c^2 h), B = (1 + ch - e^{ch})/(c^2 h) (SETD2; its first step takes
+    SETD1's); and the noise amplitude of the exact stochastic integral
+    int_0^h e^{c (h - s)} dW, whose stationary variance g^2/(1 - |f1|^2) is the
+    exact OU value (N^2/L)^d D/(-Re c) for every h (SETD-EM: (N^2/L)^d D h /
+    sinh(-Re(c) h)).  Modes with Re c > 0 (the unstable band) obey the same
+    identities with the signs carried through."""
+    N, dx, alpha, eps = 8, 0.5, 2.0, 1e-4
+    for scheme in (0, 1, 2):
+        for h in (0.05, 0.4):
+            w = W.cgl_2048(n=[N, N], dx=[dx, dx], p=[alpha, -0.5, eps], scheme=scheme, h=h)
+            o = make_oracle(oracle_mod, w)
+            KY, KX = spectral_k(w.shape, dx)
+            k2 = (KX ** 2 + KY ** 2).reshape(-1)
+            nf2 = (N * N / (N * dx)) ** 2
+            for idx in range(N * N):
+                c = 1 - (1 + 1j * alpha) * k2[idx]
+                e = np.exp(c * h)
+                for first in ((0, 1) if scheme == 2 else (0,)):
+                    f1, a, b, g = o.mode_coefs(idx, first)
+                    assert abs(f1 - e) <= 1e-14 * abs(e)
+                    if scheme == 2 and not first:
+                        a_ref = ((1 + c * h) * e - 1 - 2 * c * h) / (c * c * h)
+                        b_ref = (1 + c * h - e) / (c * c * h)
+                    else:
+                        a_ref, b_ref = (e - 1) / c, 0.0
+                    assert abs(a - a_ref) <= 1e-12 * abs(a_ref), (scheme, h, idx, a, a_ref)
+                    assert abs(b - b_ref) <= 1e-12 * max(abs(b_ref), h * h), (scheme, h, idx, b, b_ref)
+                    var = abs(g) ** 2 / (1 - abs(f1) ** 2)
+                    x = -c.real
+                    ref = nf2 * eps * h / math.sinh(x * h) if scheme == 0 else nf2 * eps / x
+                    assert abs(var - ref) <= 1e-11 * abs(ref), (scheme, h, idx, var, ref)
+
+
 def test_ou_finite_time_variance_ensemble(oracle_mod):
     """u = 0, SETD1 from phi = 0: V_n = g^2 (1 - f1^{2n}) / (1 - f1^2), and in
     the limit the linear-theory C_ET = T/(r+k^2) (Sec. V.A, sign of the
