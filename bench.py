@@ -69,6 +69,26 @@ def scheme_name(s):
     return {0: "SETD-EM", 1: "SETD1", 2: "SETD2"}[s]
 
 
+def observations(K):
+    """S(k) calls inside a timed region of K steps: one after every OBS_EVERY
+    steps, and one after all K steps when K < OBS_EVERY.  Returns (calls,
+    steps between calls)."""
+    return max(1, K // OBS_EVERY), min(OBS_EVERY, K)
+
+
+def headline_config(w, R, ws, K):
+    """The `config` of the headline line, shared by the GPU arm and the
+    reference arm (the same workload, whichever arm times it)."""
+    n_obs, obs_every = observations(K)
+    return {"workload": "model_b_1024_%s_h%g" % (scheme_name(w.scheme), w.h), "field": "Model B (conserved)",
+            "lattice": "%dx%d" % (w.n[0], w.n[1]), "replicas_per_gpu": R, "global_batch": R * ws,
+            "scheme": scheme_name(w.scheme), "h": w.h, "observe_every": obs_every,
+            "observations_timed": n_obs,
+            "setup": "schedule autotuned and step graph captured before the warm-up (sft_prepare)",
+            "parallelism": "replicas x%d" % ws,
+            "l2": "working set %.0f MB > 129 MB L2, no flush" % (R * (w.n[0] // 2 + 1) * w.n[1] * 8 * 3 / 1e6)}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -380,13 +400,16 @@ def cufft_comparison(w, R, K, stream):
 def run_reference(args):
     """The oracle as it stands, on the host cores: each timed step is one FP64
     SETD step of one replica of the workload (a bounded sample), as many as fit
-    in about a minute."""
+    in about a minute, with the S(k) observations the GPU arm takes in its
+    timed region (one per OBS_EVERY steps, at least one)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
     w = workload(args)
+    K = max(1, args.steps)
+    n_obs, obs_every = observations(K)
     f0 = W.initial_fields(w, replicas=1)[0].astype(np.float32)
     o = oracle.Oracle(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
     o.set_field(0, f0.astype(np.float64))
@@ -395,11 +418,16 @@ def run_reference(args):
     while warm < args.warmup and time.perf_counter() - t_warm < 30.0:  # warm-up steps, at most ~30 s
         o.step(1)
         warm += 1
+    o.shells()
     times = []
+    obs_done = 0
     t_start = time.perf_counter()
-    for _ in range(max(1, args.steps)):
+    for i in range(K):
         t0 = time.perf_counter()
         o.step(1)
+        if (i + 1) % obs_every == 0 and obs_done < n_obs:
+            o.shells()
+            obs_done += 1
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_start > 60.0:
             break
@@ -409,11 +437,11 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": len(times),
         "warmup": warm, "ms_per_step": 1e3 * el / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "model_b_1024_%s_h%g" % (scheme_name(args.scheme), args.h),
-                   "lattice": "%dx%d" % (args.n, args.n), "replicas": 1},
+        "config": headline_config(w, args.replicas, ws, K),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "FP64 serial oracle, %d single steps of one %dx%d replica (the GPU arm runs "
-                                   "%d replicas per step)" % (len(times), args.n, args.n, args.replicas)},
+                         "sample": "FP64 serial oracle, %d single steps of one %dx%d replica with %d S(k) "
+                                   "observations (the GPU arm runs %d replicas per step)"
+                                   % (len(times), args.n, args.n, obs_done, args.replicas)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -450,8 +478,7 @@ def run_gpu(args):
     g.sync()
     K = max(args.steps, 1)
     # S(k) every OBS_EVERY steps inside the timed region, and at least once per timed region
-    n_obs = max(1, K // OBS_EVERY)
-    obs_every = min(OBS_EVERY, K)
+    n_obs, obs_every = observations(K)
     l0 = sft.sft_kernel_launches(g.ctx)
 
     def barrier():
@@ -500,14 +527,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": warm,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded iid N(0, 0.01^2) fields, Philox noise)",
-        "config": {"workload": "model_b_1024_%s_h%g" % (scheme_name(w.scheme), w.h), "field": "Model B (conserved)",
-                   "lattice": "%dx%d" % (w.n[0], w.n[1]), "replicas_per_gpu": R, "global_batch": R * ws,
-                   "scheme": scheme_name(w.scheme), "h": w.h, "observe_every": obs_every,
-                   "observations_timed": obs_done,
-                   "setup": "schedule autotuned and step graph captured before the warm-up (sft_prepare)",
-                   "parallelism": "replicas x%d" % ws,
-                   "l2": "working set %.0f MB > 129 MB L2, no flush" % (
-                       R * (w.n[0] // 2 + 1) * w.n[1] * 8 * 3 / 1e6)},
+        "config": headline_config(w, R, ws, K),
         "roofline": roofline,
         "plan": dict(zip(("row_shape", "col_shape", "replicas_per_col_block", "pipelined_cols"), plan)),
         "step_roofline": {"bytes_per_site_step": step_bytes_site, "achieved_GBps": step_achieved,

@@ -33,3 +33,29 @@ def test_real_step_bytes_headline():
 def test_roofline_entry():
     e = bench.hbm_roofline("k", 2e9, 1.0)
     assert abs(e["achieved"] - 2000.0) < 1e-9 and abs(e["frac"] - 2000.0 / e["peak"]) < 1e-12
+
+
+def test_observation_count_matches_the_timed_loop():
+    # the GPU arm steps in chunks of obs_every and observes after each full chunk, at most n_obs times
+    for K in (1, 5, 20, 99, 100, 101, 250, 2000, 2050):
+        n_obs, obs_every = bench.observations(K)
+        done = taken = 0
+        while done < K:
+            n = min(obs_every, K - done)
+            done += n
+            if n == obs_every and taken < n_obs:
+                taken += 1
+        assert taken == n_obs >= 1, K
+        assert obs_every == min(100, K)
+
+
+def test_both_arms_name_the_same_workload():
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, bench.__file__, "--impl", "reference", "--steps", "2", "--warmup", "0",
+                          "--n", "64"], capture_output=True, text=True, timeout=300, check=True).stdout
+    line = json.loads(out.strip().splitlines()[-1])
+    w = bench.W.model_b_1024(n=[64, 64], scheme=1, h=0.05, replicas=64)
+    assert line["impl"] == "reference" and line["config"] == bench.headline_config(w, 64, 1, 2)
+    assert line["steps"] == 2 and line["warmup"] == 0 and line["e2e"]["h2d_bytes_per_step"] == 0
