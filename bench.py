@@ -532,7 +532,7 @@ def run_gpu(args):
         "plan": dict(zip(("row_shape", "col_shape", "replicas_per_col_block", "pipelined_cols"), plan)),
         "step_roofline": {"bytes_per_site_step": step_bytes_site, "achieved_GBps": step_achieved,
                           "frac": step_achieved / peak,
-                          "survey_24B_frac": 24.0 * value / peak},
+                          "frac_at_24B_per_site": 24.0 * value / peak},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
