@@ -22,7 +22,10 @@ Two noise-free steps of Model A and Model B at 1024^2 (temperature 0, so the
 noise amplitude g is zero and nothing random is involved), chained through
 P and Q exactly as the kernels chain them, equal the FP64 oracle's two steps
 (Sec. IV boxed algorithm) to rounding, with and without 2/3 truncation and
-for SETD1 and SETD2 (whose history F_prev the column pass carries)."""
+for SETD1 and SETD2 (whose history F_prev the column pass carries).  The
+column pass's noise map (which lane evaluates which Philox counter and the
+lane exchange that hands each mode its pair) reproduces the oracle's noise of
+App. B on columns on and off the self-conjugate planes."""
 import numpy as np
 import pytest
 
@@ -350,3 +353,45 @@ def test_two_noise_free_steps_match_the_oracle(oracle_mod, model, scheme, deal):
     ref = half_xmajor(o.spectrum(0))
     err = np.max(np.abs(phi - ref)) / np.sqrt(np.mean(np.abs(ref) ** 2))
     assert err < 1e-11, err
+
+
+# ------------------------------------------------------------ noise map of the column pass
+def column_noise_warp(oracle_mod, seed, cc, step, rep):
+    """eta of column cc as k2_cols_warp draws it (team_normal_pair_ks with 32
+    lanes): the trip over slots (e, e + 1), e even; lane t evaluates Philox at
+    j = cc NY + t + 32 (e + (t odd)), counter (j >> 1, step, replica, 0); even
+    lanes keep the first pair for slot e and hand the second to lane t + 1,
+    odd lanes hand the first to lane t - 1 and keep the second for slot e + 1."""
+    eta = np.zeros(NY, dtype=np.complex128)
+    plane = cc in (0, NY // 2)  # a_x = 0 or nx / 2 (nx = NY = 1024)
+    r2 = np.float32(0.70710677)  # 0x1.6a09e6p-1f
+    for e in range(0, 32, 2):
+        p = {}
+        for t in range(32):
+            j = cc * NY + t + 32 * (e + (t & 1))
+            z = oracle_mod.normals4(seed, j >> 1, step, rep, 0)
+            p[t] = (z[0:2], z[2:4])
+        for t in range(32):
+            odd = t & 1
+            recv = p[t ^ 1][1] if odd else p[t ^ 1][0]  # the partner lane's send (even lanes: p1, odd: p0)
+            z0 = recv if odd else p[t][0]
+            z1 = p[t][1] if odd else recv
+            for h, z in ((0, z0), (1, z1)):
+                ay = t + 32 * (e + h)
+                if plane and (ay == 0 or ay == NY // 2):
+                    eta[ay] = float(z[0])
+                else:
+                    eta[ay] = complex(np.float32(z[0]) * r2, np.float32(z[1]) * r2)
+    return eta
+
+
+def test_column_pass_noise_map_is_the_oracles(oracle_mod):
+    w = W.model_b_1024(replicas=1)
+    step, rep = 7, 3
+    o = oracle_mod.Oracle(w.d, w.n, w.dx, rep + 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
+    ref = half_xmajor(o.noise(rep, step))
+    ay = np.arange(NY)
+    for cc in (0, 1, 2, 341, 342, 511, 512):
+        got = column_noise_warp(oracle_mod, w.seed, cc, step, rep)
+        keep = (2 * ay <= NY) if cc in (0, NY // 2) else np.ones(NY, bool)  # plane partners: the fix-up's
+        np.testing.assert_allclose(got[keep], ref[cc][keep], rtol=2e-7, atol=0, err_msg=str(cc))
