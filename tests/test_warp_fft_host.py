@@ -25,7 +25,9 @@ P and Q exactly as the kernels chain them, equal the FP64 oracle's two steps
 for SETD1 and SETD2 (whose history F_prev the column pass carries).  The
 column pass's noise map (which lane evaluates which Philox counter and the
 lane exchange that hands each mode its pair) reproduces the oracle's noise of
-App. B on columns on and off the self-conjugate planes."""
+App. B on columns on and off the self-conjugate planes, and the complex
+column pass's map (one or two warps per column, csrc/sft_k2c_colwarp.cu)
+reproduces the oracle's complex draw."""
 import numpy as np
 import pytest
 
@@ -395,3 +397,60 @@ def test_column_pass_noise_map_is_the_oracles(oracle_mod):
         got = column_noise_warp(oracle_mod, w.seed, cc, step, rep)
         keep = (2 * ay <= NY) if cc in (0, NY // 2) else np.ones(NY, bool)  # plane partners: the fix-up's
         np.testing.assert_allclose(got[keep], ref[cc][keep], rtol=2e-7, atol=0, err_msg=str(cc))
+
+
+def complex_noise_convention(oracle_mod, seed, nyq, cols, step, rep):
+    """eta of the complex-field modes (a_x, a_y) by the counter map of App. B's
+    complex draw: mode j = a_x n_y + a_y takes the pair (j & 1) of
+    Philox(ctr = (j >> 1, step, replica, 0)), eta = (z0 + i z1) / sqrt 2."""
+    r2 = np.float32(0.70710677)
+    out = np.zeros((len(cols), nyq), dtype=np.complex128)
+    for i, c in enumerate(cols):
+        for ay in range(nyq):
+            j = c * nyq + ay
+            z = oracle_mod.normals4(seed, j >> 1, step, rep, 0)[2 * (j & 1): 2 * (j & 1) + 2]
+            out[i, ay] = complex(np.float32(z[0]) * r2, np.float32(z[1]) * r2)
+    return out
+
+
+def complex_column_noise_warp(oracle_mod, seed, c, H, step, rep):
+    """eta of column c as k2c_cols_warp draws it: warp h of the H warps holds
+    a_y = 1024 h + t + 32 e and calls team_normal_pair_ks with the base
+    j = c NY + 1024 h (the same lane exchange as the real column pass)."""
+    ny = 1024 * H
+    r2 = np.float32(0.70710677)
+    eta = np.zeros(ny, dtype=np.complex128)
+    for h in range(H):
+        jb = c * ny + 1024 * h
+        for e in range(0, 32, 2):
+            p = {}
+            for t in range(32):
+                j = jb + t + 32 * (e + (t & 1))
+                z = oracle_mod.normals4(seed, j >> 1, step, rep, 0)
+                p[t] = (z[0:2], z[2:4])
+            for t in range(32):
+                odd = t & 1
+                recv = p[t ^ 1][1] if odd else p[t ^ 1][0]
+                z0 = recv if odd else p[t][0]
+                z1 = p[t][1] if odd else recv
+                for hh, z in ((0, z0), (1, z1)):
+                    eta[1024 * h + t + 32 * (e + hh)] = complex(np.float32(z[0]) * r2, np.float32(z[1]) * r2)
+    return eta
+
+
+def test_complex_column_pass_noise_map(oracle_mod):
+    # the convention is the oracle's (a 64^2 complex field: every mode drawn, no Hermitian partner)
+    w = W.cgl_2048(n=[64, 64], replicas=2)
+    step, rep = 5, 1
+    o = oracle_mod.Oracle(w.d, w.n, w.dx, 2, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
+    ref = np.moveaxis(o.noise(rep, step), -1, 0)  # [a_x][a_y]
+    cols = [0, 1, 31, 32, 63]
+    np.testing.assert_allclose(complex_noise_convention(oracle_mod, w.seed, 64, cols, step, rep), ref[cols],
+                               rtol=2e-7, atol=0)
+    # the warp column pass on 1024- and 2048-point columns (one or two warps per column) follows it
+    for H in (1, 2):
+        ny = 1024 * H
+        for c in (0, 3, ny // 3, ny - 1):
+            got = complex_column_noise_warp(oracle_mod, w.seed, c, H, step, rep)
+            want = complex_noise_convention(oracle_mod, w.seed, ny, [c], step, rep)[0]
+            np.testing.assert_array_equal(got, want, err_msg=str((H, c)))
