@@ -9,7 +9,9 @@ operation by operation) and driven through ctypes.
 
 The C file's header lists the paper passages each part follows (Sec. II
 schemes, Sec. IV algorithm, Sec. V models, App. A-C conventions) and the
-readings taken where the paper is silent.
+readings taken where the paper is silent.  Parity unpinned: the noise counter
+map (which Philox counter each mode or site takes), a convention of this
+implementation; the structure and statistics of the noise are pinned.
 """
 from __future__ import annotations
 

@@ -53,6 +53,11 @@
  *     not spectra of real fields) and keeps every other mode.
  *   - Real-space noise: eta_a = DFT[eta]_a / sqrt(N^d), site s taking normal
  *     s & 3 of Philox(s >> 2, step, replica, tag 3).
+ *
+ * Parity unpinned: the noise counter map (which Philox counter and which word
+ * pair each mode or site takes) is a convention of this implementation; the
+ * paper fixes only the distribution of the noise, whose structure (App. B
+ * deviate counts, Hermitian symmetry, variances) is pinned.
  */
 #include <complex.h>
 #include <math.h>
