@@ -1,0 +1,74 @@
+"""Parity in the launch configuration the benchmark times.
+
+Model B, 1024^2, SETD1, h = 0.05: all 64 replicas in one context, the
+schedule chosen by the plan autotuner for 64 replicas (sft_prepare, as the
+benchmark calls it), 100 steps.  The oracle steps a sample of the replicas one
+by one (each with its replica offset in the noise counter), and every sampled
+replica meets the bounds of the headline test: relative L2 of the field
+<= 1e-5, and every stored mode within 1e-4 of the RMS mode amplitude.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+import sft_inputs as W
+
+pytestmark = pytest.mark.gpu
+
+NSTEPS = 100
+SAMPLE = (0, 37, 63)
+
+
+@pytest.fixture(scope="module")
+def sft():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_22510_gb300 as m
+    m.load_library()
+    return m
+
+
+def half_xmajor(full):
+    nx = full.shape[-1]
+    return np.moveaxis(full[..., : nx // 2 + 1], -1, 0)
+
+
+def test_bench_batch_of_64_against_the_oracle(sft, oracle_mod):
+    w = W.model_b_1024(replicas=64, h=0.05, scheme=1)
+    f32 = W.initial_fields(w).astype(np.float32)
+    ref = {}
+    errs = []
+
+    def one(r):
+        try:
+            o = oracle_mod.Oracle(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
+                                  replica0=r)
+            o.set_field(0, f32[r].astype(np.float64))
+            o.step(NSTEPS)
+            ref[r] = (o.field(0), half_xmajor(o.spectrum(0)))
+        except Exception as ex:  # reported in the main thread
+            errs.append(ex)
+
+    th = [threading.Thread(target=one, args=(r,)) for r in SAMPLE]
+    for t in th:
+        t.start()
+    g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
+    g.set_field(f32)
+    g.prepare()
+    g.step(NSTEPS)
+    field, spec = g.field(), g.spectrum()
+    used = sft.sft_get_plan(g.ctx)
+    g.close()
+    for t in th:
+        t.join()
+    if errs:
+        raise errs[0]
+    for r in SAMPLE:
+        ref_field, ref_spec = ref[r]
+        e = float(np.linalg.norm(field[r] - ref_field) / np.linalg.norm(ref_field))
+        rms = float(np.sqrt(np.mean(np.abs(ref_spec) ** 2)))
+        emax = float(np.max(np.abs(spec[r] - ref_spec))) / rms
+        assert e <= 1e-5, (r, used, "relative L2", e)
+        assert emax <= 1e-4, (r, used, "max mode error / rms", emax)
