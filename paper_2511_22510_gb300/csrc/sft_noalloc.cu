@@ -81,15 +81,31 @@ extern "C" sft_status sft_step2d_noalloc(const sft_config* cfg, void* phi_dev, v
     // the variants this entry point carries: 2-D real fields (Model A/B, KPZ), power-of-two sizes,
     // Fourier-space noise, 2/3 truncation or none
     if (cfg->d != 2 || cfg->model == SFT_CGL || cfg->model == SFT_CUSTOM || cfg->noise_space != 0 || cfg->dealias == 2 ||
-        (cfg->n[0] & (cfg->n[0] - 1)) != 0)
+        (cfg->n[0] & (cfg->n[0] - 1)) != 0) {
+        fprintf(stderr, "sft_step2d_noalloc: built for 2-D real fields (Model A, Model B, KPZ) of power-of-two sizes "
+                        "with Fourier-space noise and 2/3 truncation or none\n");
         return SFT_EUNSUPPORTED;
+    }
     const int nx = cfg->n[0], ny = cfg->n[1];
-    if (nx > kNoAllocMaxN) return SFT_EINVAL;
-    if (cfg->scheme == SFT_SETD2 && !fprev_dev) return SFT_EINVAL;
+    if (nx > kNoAllocMaxN) {
+        fprintf(stderr, "sft_step2d_noalloc: %d points per axis is above the scratch limit of %d\n", nx, kNoAllocMaxN);
+        return SFT_EINVAL;
+    }
+    if (cfg->scheme == SFT_SETD2 && !fprev_dev) {
+        fprintf(stderr, "sft_step2d_noalloc: SETD2 needs the history buffer fprev_dev\n");
+        return SFT_EINVAL;
+    }
     const int hx = nx / 2 + 1;
     const long long modes = (long long)cfg->replicas * hx * ny;
-    if (modes > kNoAllocMaxModes) return SFT_EINVAL;
-    if (step0 + nsteps > (long long)0xFFFFFFFFLL) return SFT_EINVAL;
+    if (modes > kNoAllocMaxModes) {
+        fprintf(stderr, "sft_step2d_noalloc: R (n/2 + 1) n = %lld modes is above the scratch limit of %lld\n", modes,
+                kNoAllocMaxModes);
+        return SFT_EINVAL;
+    }
+    if (step0 + nsteps > (long long)0xFFFFFFFFLL) {
+        fprintf(stderr, "sft_step2d_noalloc: step0 + nsteps must stay below 2^32 (the noise counter)\n");
+        return SFT_EINVAL;
+    }
     cudaStream_t st = (cudaStream_t)cfg->stream;
 
     // once per device, with that device current: the scratch array's device address
