@@ -138,3 +138,29 @@ def test_3x2k_lattice_limits(lib, d, model, extra):
     with pytest.raises(lib.SftError) as ei:
         lib.sft_create(cfg)
     assert ei.value.status == lib.SFT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("case,status", [
+    (dict(n=[1024, 1024]), "SFT_EINVAL"),                   # above the 512-point scratch limit
+    (dict(n=[512, 512], replicas=2), "SFT_EINVAL"),         # 2 x 257 x 512 modes > 262144
+    (dict(scheme=2, fprev=None), "SFT_EINVAL"),             # SETD2 without its history buffer
+    (dict(h=float("inf")), "SFT_EINVAL"),                   # the checks of sft_create
+    (dict(replica0=-1), "SFT_EINVAL"),
+    (dict(model=3, p=[2.0, -0.5, 1e-4]), "SFT_EUNSUPPORTED"),  # complex field
+    (dict(d=1, n=[64]), "SFT_EUNSUPPORTED"),
+    (dict(dealias=2), "SFT_EUNSUPPORTED"),
+    (dict(nsteps=-1), "SFT_EINVAL"),
+    (dict(step0=(1 << 32) - 5, nsteps=10), "SFT_EINVAL"),  # past the 32-bit noise step counter
+], ids=["n1024", "modes", "setd2_nohist", "h_inf", "replica0", "cgl", "1d", "phase_shift", "nsteps", "counter"])
+def test_noalloc_refusals_need_no_device(lib, case, status):
+    """The allocation-free entry point refuses these before it touches the device:
+    the device pointers given here are never dereferenced."""
+    kw = dict(d=2, n=[64, 64], replicas=1, model=1, p=[1.0, -1.0, 1.0, 0.1], scheme=1, h=0.05, dealias=1,
+              replica0=0, fprev=4096, step0=0, nsteps=3)
+    kw.update(case)
+    d = kw["d"]
+    cfg = lib.make_config(d, kw["n"], [1.0] * d, kw["replicas"], kw["model"], kw["p"], kw["scheme"], kw["h"], 7,
+                          kw["dealias"], replica0=kw["replica0"])
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_step2d_noalloc(cfg, 4096, kw["fprev"], 0, kw["step0"], kw["nsteps"])
+    assert ei.value.status == getattr(lib, status)
