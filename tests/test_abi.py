@@ -164,3 +164,38 @@ def test_noalloc_refusals_need_no_device(lib, case, status):
     with pytest.raises(lib.SftError) as ei:
         lib.sft_step2d_noalloc(cfg, 4096, kw["fprev"], 0, kw["step0"], kw["nsteps"])
     assert ei.value.status == getattr(lib, status)
+
+
+@pytest.mark.parametrize("case", [
+    dict(kind=7), dict(scheme=9), dict(h=0.0), dict(h=float("inf")), dict(substeps=0), dict(nsteps=-1),
+    dict(npaths=-1), dict(step0=-1), dict(kind=0, p=[0.0, 1.0, 1.0]), dict(kind=0, p=[1.0, -1.0, 1.0]),
+    dict(step0=1 << 31, nsteps=1 << 31, substeps=2), dict(u=None),
+], ids=["kind", "scheme", "h0", "hinf", "substeps", "nsteps", "npaths", "step0", "sao_a0", "sao_b", "counter",
+        "no_u"])
+def test_sde0d_refusals_need_no_device(lib, case):
+    """The 0-d SDE ensemble entry point refuses bad arguments before any launch
+    (the device pointers given here are never dereferenced)."""
+    kw = dict(kind=1, p=[2.0, 1.0, 1.0], scheme=3, h=2.0 ** -8, nsteps=4, npaths=16, substeps=1, step0=0, u=4096)
+    kw.update(case)
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_sde0d(kw["kind"], kw["p"], kw["scheme"], kw["h"], kw["nsteps"], kw["u"], kw["npaths"], seed=1,
+                      substeps=kw["substeps"], step0=kw["step0"])
+    assert ei.value.status == lib.SFT_EINVAL
+
+
+def test_sde0d_empty_work_is_a_no_op(lib):
+    # no paths or no steps: nothing to launch, nothing dereferenced
+    lib.sft_sde0d(1, [2.0, 1.0, 1.0], 3, 0.01, 5, None, 0, seed=1)
+    lib.sft_sde0d(1, [2.0, 1.0, 1.0], 3, 0.01, 0, 4096, 8, seed=1)
+
+
+def test_batch_members_must_share_model_and_scheme(lib):
+    a = lib.make_config(1, [1024], [1.0], 2, 2, [1.0, 2.0, 0.5], 1, 0.01, 3)
+    b = lib.make_config(1, [2048], [1.0], 2, 2, [1.0, 2.0, 0.5], 2, 0.01, 3)  # another scheme
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_create_batch([a, b])
+    assert ei.value.status == lib.SFT_EUNSUPPORTED
+    bad = lib.make_config(1, [1000], [1.0], 2, 2, [1.0, 2.0, 0.5], 1, 0.01, 3)  # not a built lattice size
+    with pytest.raises(lib.SftError) as ei:
+        lib.sft_create_batch([a, bad])
+    assert ei.value.status == lib.SFT_EINVAL
