@@ -1,4 +1,4 @@
-"""Parity in the launch configuration the benchmark times.
+"""Parity in the launch configurations the benchmark times.
 
 Model B, 1024^2, SETD1, h = 0.05: all 64 replicas in one context, the
 schedule chosen by the plan autotuner for 64 replicas (sft_prepare, as the
@@ -6,6 +6,11 @@ benchmark calls it), 100 steps.  The oracle steps a sample of the replicas one
 by one (each with its replica offset in the noise counter), and every sampled
 replica meets the bounds of the headline test: relative L2 of the field
 <= 1e-5, and every stored mode within 1e-4 of the RMS mode amplitude.
+
+Model A, 128^3, 32 replicas, SETD1, h = 0.01 (the linear-response workload):
+the tangent advanced with the primal over 5 steps through the C ABI with
+device buffers; the first and the last replica against the oracle's tangent
+and field (relative L2 <= 1e-5, as in the smaller tangent tests).
 """
 import threading
 
@@ -72,3 +77,47 @@ def test_bench_batch_of_64_against_the_oracle(sft, oracle_mod):
         emax = float(np.max(np.abs(spec[r] - ref_spec))) / rms
         assert e <= 1e-5, (r, used, "relative L2", e)
         assert emax <= 1e-4, (r, used, "max mode error / rms", emax)
+
+
+def test_tangent_batch_of_32_at_128_cubed_against_the_oracle(sft, oracle_mod):
+    torch = pytest.importorskip("torch")
+    w = W.model_a_128_3d(replicas=32, sigma0=0.3)
+    f32 = W.initial_fields(w).astype(np.float32)
+    d32 = W.initial_fields(w.with_(sigma0=1.0), seed_offset=9).astype(np.float32)
+    nst, sample = 5, (0, 31)
+    ref = {}
+    errs = []
+
+    def one(r):
+        try:
+            o = oracle_mod.Oracle(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
+                                  replica0=r)
+            o.set_field(0, f32[r].astype(np.float64))
+            tan = o.tangent_step(d32[r:r + 1].astype(np.float64), nst)[0]
+            ref[r] = (tan, o.field(0))
+        except Exception as ex:  # reported in the main thread
+            errs.append(ex)
+
+    th = [threading.Thread(target=one, args=(r,)) for r in sample]
+    for t in th:
+        t.start()
+    g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
+    g.set_field(f32)
+    dev_in = torch.from_numpy(d32).cuda()
+    dev_out = torch.zeros_like(dev_in)
+    torch.cuda.synchronize()
+    sft.sft_tangent_step(g.ctx, dev_in.data_ptr(), nst, dev_out.data_ptr())
+    torch.cuda.synchronize()
+    tan_g = dev_out.cpu().numpy()
+    field = g.field()
+    g.close()
+    for t in th:
+        t.join()
+    if errs:
+        raise errs[0]
+    for r in sample:
+        tan_o, field_o = ref[r]
+        e_t = float(np.linalg.norm(tan_g[r] - tan_o) / np.linalg.norm(tan_o))
+        e_f = float(np.linalg.norm(field[r] - field_o) / np.linalg.norm(field_o))
+        assert e_t <= 1e-5, (r, "tangent relative L2", e_t)
+        assert e_f <= 1e-5, (r, "field relative L2", e_f)
