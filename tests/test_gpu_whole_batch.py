@@ -11,6 +11,11 @@ Model A, 128^3, 32 replicas, SETD1, h = 0.01 (the linear-response workload):
 the tangent advanced with the primal over 5 steps through the C ABI with
 device buffers; the first and the last replica against the oracle's tangent
 and field (relative L2 <= 1e-5, as in the smaller tangent tests).
+
+CGL, 2048^2, 4 replicas, SETD2, h = 0.05 (the complex workload, whose warp
+column pass takes two replicas per block): every replica against the oracle
+after 4 steps, field relative L2 <= 1e-5 and every mode within 1e-4 of the
+RMS mode amplitude.
 """
 import threading
 
@@ -121,3 +126,40 @@ def test_tangent_batch_of_32_at_128_cubed_against_the_oracle(sft, oracle_mod):
         e_f = float(np.linalg.norm(field[r] - field_o) / np.linalg.norm(field_o))
         assert e_t <= 1e-5, (r, "tangent relative L2", e_t)
         assert e_f <= 1e-5, (r, "field relative L2", e_f)
+
+
+def test_cgl_batch_of_4_at_2048_squared_against_the_oracle(sft, oracle_mod):
+    w = W.cgl_2048(replicas=4)
+    nst = 4
+    f0 = W.initial_fields(w).astype(np.complex64)
+    want = {}
+    errs = []
+
+    def one(r):
+        try:
+            o = oracle_mod.Oracle(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
+                                  replica0=r)
+            o.set_field(0, f0[r].astype(np.complex128))
+            o.step(nst)
+            want[r] = o.field(0)
+        except Exception as ex:  # reported in the main thread
+            errs.append(ex)
+
+    th = [threading.Thread(target=one, args=(r,)) for r in range(w.replicas)]
+    for t in th:
+        t.start()
+    g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
+    g.set_field(f0)
+    g.step(nst)
+    got = g.field().astype(np.complex128)
+    g.close()
+    for t in th:
+        t.join()
+    if errs:
+        raise errs[0]
+    for r in range(w.replicas):
+        e = float(np.linalg.norm(got[r] - want[r]) / np.linalg.norm(want[r]))
+        a, b = np.fft.fft2(got[r]), np.fft.fft2(want[r])
+        worst = float(np.abs(a - b).max() / np.sqrt(np.mean(np.abs(b) ** 2)))
+        assert e <= 1e-5, (r, "relative L2", e)
+        assert worst <= 1e-4, (r, "max mode error / rms", worst)
