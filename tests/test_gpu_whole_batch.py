@@ -16,6 +16,12 @@ CGL, 2048^2, 4 replicas, SETD2, h = 0.05 (the complex workload, whose warp
 column pass takes two replicas per block): every replica against the oracle
 after 4 steps, field relative L2 <= 1e-5 and every mode within 1e-4 of the
 RMS mode amplitude.
+
+KPZ ensemble (the batched workload): 512 lines of 2^10 .. 2^16 points drawn as
+the benchmark draws them, plus 64 replicas of 256^2, in one batch context
+(the persistent launch, the cluster kernel and the graph branches the
+benchmark times), 20 steps from random fields; the first and the last replica
+of every member against the oracle (relative L2 <= 1e-5).
 """
 import threading
 
@@ -163,3 +169,30 @@ def test_cgl_batch_of_4_at_2048_squared_against_the_oracle(sft, oracle_mod):
         worst = float(np.abs(a - b).max() / np.sqrt(np.mean(np.abs(b) ** 2)))
         assert e <= 1e-5, (r, "relative L2", e)
         assert worst <= 1e-4, (r, "max mode error / rms", worst)
+
+
+def test_kpz_ensemble_batch_against_the_oracle(sft, oracle_mod):
+    lengths = W.kpz_ensemble_lengths()
+    counts = {L: lengths.count(L) for L in sorted(set(lengths))}
+    members = [W.kpz_1d(L, replicas=c) for L, c in counts.items()] + [W.kpz_2d(replicas=64)]
+    assert sum(w.replicas for w in members) == 512 + 64
+    batch = sft.Batch([sft.make_config(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, w.dealias)
+                       for w in members])
+    rng = np.random.default_rng(77)
+    f0 = [(0.3 * rng.standard_normal((w.replicas,) + w.shape)).astype(np.float32) for w in members]
+    batch.set_field(-1, np.concatenate([x.reshape(-1) for x in f0]))
+    nst = 20
+    batch.step(nst)
+    off = 0
+    for w, f in zip(members, f0):
+        for r in sorted({0, w.replicas - 1}):
+            o = oracle_mod.Oracle(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
+                                  replica0=r)
+            o.set_field(0, f[r].astype(np.float64))
+            o.step(nst)
+            ref = o.field(0)
+            got = batch.field(off + r, w.shape)
+            e = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            assert e <= 1e-5, (w.name, r, e)
+        off += w.replicas
+    batch.close()
