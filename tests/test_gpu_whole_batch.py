@@ -22,6 +22,11 @@ the benchmark draws them, plus 64 replicas of 256^2, in one batch context
 (the persistent launch, the cluster kernel and the graph branches the
 benchmark times), 20 steps from random fields; the first and the last replica
 of every member against the oracle (relative L2 <= 1e-5).
+
+Model A, 64^2, 1024 replicas, SETD1, h = 0.01 over the workload's 1000 steps
+(the dynamics do not amplify rounding here: fields one FP32 ulp apart stay
+2.6e-8 apart after 1000 steps): replicas 0, 511 and 1023 against the oracle,
+relative L2 <= 1e-5.
 """
 import threading
 
@@ -196,3 +201,22 @@ def test_kpz_ensemble_batch_against_the_oracle(sft, oracle_mod):
             assert e <= 1e-5, (w.name, r, e)
         off += w.replicas
     batch.close()
+
+
+def test_model_a_64_batch_of_1024_over_1000_steps_against_the_oracle(sft, oracle_mod):
+    w = W.model_a_64(replicas=1024)
+    nst, sample = 1000, (0, 511, 1023)
+    f32 = W.initial_fields(w).astype(np.float32)
+    g = sft.Stepper(w.d, w.n, w.dx, w.replicas, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias)
+    g.set_field(f32)
+    g.step(nst)
+    field = g.field()
+    g.close()
+    for r in sample:
+        o = oracle_mod.Oracle(w.d, w.n, w.dx, 1, w.model, w.p, w.scheme, w.h, w.seed, dealias=w.dealias,
+                              replica0=r)
+        o.set_field(0, f32[r].astype(np.float64))
+        o.step(nst)
+        ref = o.field(0)
+        e = float(np.linalg.norm(field[r] - ref) / np.linalg.norm(ref))
+        assert e <= 1e-5, (r, e)
