@@ -153,9 +153,9 @@ def hbm_roofline(kernel, alg_bytes, launch_ms):
 
 # sources each recorded kernel is compiled from: its translation unit and the headers it includes
 KERNEL_SOURCES = {
-    "k2_cols_real": ["sft_k2d_cols.cu", "sft_k2d_cols.cuh", "sft_step_common.cuh", "sft_device.cuh", "sft_async.cuh",
+    "k2_cols_real": ["sft_k2d_cols.cu", "sft_k2d_cols_large.cu", "sft_k2d_cols.cuh", "sft_step_common.cuh", "sft_device.cuh", "sft_async.cuh",
                      "sft_internal.h"],
-    "k2_rows_real": ["sft_k2d.cu", "sft_k2d.cuh", "sft_step_common.cuh", "sft_device.cuh", "sft_async.cuh",
+    "k2_rows_real": ["sft_k2d.cu", "sft_k2d_large.cu", "sft_k2d.cuh", "sft_step_common.cuh", "sft_device.cuh", "sft_async.cuh",
                      "sft_internal.h"],
     "k2_rows_pair": ["sft_k2d_pair.cu", "sft_warpfft.cuh", "sft_step_common.cuh", "sft_device.cuh", "sft_async.cuh",
                      "sft_internal.h"],

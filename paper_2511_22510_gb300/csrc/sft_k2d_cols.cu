@@ -20,6 +20,10 @@ bool k2_supported(int nx, int ny, int complex_field) {
 // per column, sft_k2d_colwarp.cu (cubic term, see k2_colwarp_supported)
 int k2_col_shapes(int ny) { return (ny & (ny - 1)) == 0 && ny >= 512 ? (ny == 1024 ? 4 : 3) : 1; }
 
+// columns of 512 to 4096 points: sft_k2d_cols_large.cu (a translation unit of its own, so that the
+// library's units compile in parallel in about the same time)
+cudaError_t launch_k2_cols_large(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape);
+
 cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s, int shape) {
     if (shape == 3 && mode == MODE_STEP && !a.rec_phi && !a.noise_in && !a.pshift) return launch_k2_cols_warp(a, nl, s);
     switch (a.ny) {
@@ -28,10 +32,10 @@ cudaError_t launch_k2_cols(const StepArgs& a, int mode, int nl, cudaStream_t s, 
         case 64: return cols_for<64>(a, mode, nl, s, shape);
         case 128: return cols_for<128>(a, mode, nl, s, shape);
         case 256: return cols_for<256>(a, mode, nl, s, shape);
-        case 512: return cols_for<512>(a, mode, nl, s, shape);
-        case 1024: return cols_for<1024>(a, mode, nl, s, shape);
-        case 2048: return cols_for<2048>(a, mode, nl, s, shape);
-        case 4096: return cols_for<4096>(a, mode, nl, s, shape);
+        case 512:
+        case 1024:
+        case 2048:
+        case 4096: return launch_k2_cols_large(a, mode, nl, s, shape);
         default: return k2_mixed_size(a.ny) ? launch_k2_cols_mixed(a, mode, nl, s) : cudaErrorInvalidValue;
     }
 }
